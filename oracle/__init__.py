@@ -1,0 +1,119 @@
+"""CPU oracle for the FE SpMV + CG path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library:
+``oracle.c`` holds the FP64 sparse product, Jacobi-PCG and the
+mixed-precision refinement; ``layout.py`` holds the numpy definitions of the
+row/column permutation and the warp-slice packing.
+
+Pins (tests that tie the oracle to something other than itself) live in
+``tests/test_oracle_pins.py``: dense brute-force products, the paper's worked
+permutation example (Sec. 5.2/5.3), zero row sums of Neumann Laplacians,
+symmetry and positive definiteness, dense direct solves, finite termination of
+CG in exact-arithmetic terms, and recovery of manufactured solutions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import layout  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib_handle = None
+
+STATUS = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_input"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc -O2 -ffp-contract=off: no fused multiply-add)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.oracle_csr_spmv.argtypes = [i64, P, P, P, P, P]
+        lib.oracle_csr_spmv.restype = None
+        lib.oracle_pcg.argtypes = [i64, P, P, P, P, P, dbl, i32, i32, i32, P, P, P]
+        lib.oracle_pcg.restype = i32
+        lib.oracle_refine.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, i32, P, P, P]
+        lib.oracle_refine.restype = i32
+        lib.oracle_round_bf16.argtypes = [ctypes.c_float]
+        lib.oracle_round_bf16.restype = ctypes.c_float
+        _lib_handle = lib
+    return _lib_handle
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(rowptr, colind, values):
+    return (np.ascontiguousarray(rowptr, dtype=np.int64),
+            np.ascontiguousarray(colind, dtype=np.int32),
+            np.ascontiguousarray(values, dtype=np.float64))
+
+
+def csr_spmv(rowptr, colind, values, x) -> np.ndarray:
+    """y = A x (FP64, sequential row sums in stored order)."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    n = len(rp) - 1
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(n, dtype=np.float64)
+    _lib().oracle_csr_spmv(n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
+    return y
+
+
+def pcg(rowptr, colind, values, b, x0=None, tol=1e-10, max_iter=100000, jacobi=True,
+        max_restarts=3):
+    """Jacobi-PCG; returns (x, info) with info = dict(status, iters, relres, true_relres)."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    tr = ctypes.c_double(0)
+    st = _lib().oracle_pcg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, max_iter,
+                           1 if jacobi else 0, max_restarts, ctypes.byref(it), ctypes.byref(rr),
+                           ctypes.byref(tr))
+    return x, dict(status=STATUS[st], iters=it.value, relres=rr.value, true_relres=tr.value)
+
+
+def round_bf16(values) -> np.ndarray:
+    """float32 -> nearest bfloat16 (ties to even), returned as float32."""
+    f = _lib().oracle_round_bf16
+    return np.array([f(float(v)) for v in np.asarray(values, dtype=np.float32)],
+                    dtype=np.float32)
+
+
+def refine(rowptr, colind, values, b, x0=None, tol=1e-10, inner_tol=1e-3, max_outer=50,
+           max_inner=20000, storage="f32"):
+    """FP64 refinement around a float/bfloat16 inner CG on S A S."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    o = ctypes.c_int(0)
+    i = ctypes.c_int(0)
+    tr = ctypes.c_double(0)
+    st = _lib().oracle_refine(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, inner_tol,
+                              max_outer, max_inner, {"f32": 0, "bf16": 1}[storage],
+                              ctypes.byref(o), ctypes.byref(i), ctypes.byref(tr))
+    return x, dict(status=STATUS[st], outer=o.value, inner=i.value, true_relres=tr.value)

@@ -1,0 +1,260 @@
+/*
+ * oracle.c -- plain, slow, obviously correct CPU reference (TEST INFRASTRUCTURE).
+ *
+ * Only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg may load this file's library.  The product path never calls it, and it
+ * shares no code with the CUDA library.
+ *
+ * Everything here is FP64 with sequential sums in index order, compiled with
+ * -ffp-contract=off (no fused multiply-add), so that each result is the plain
+ * definition evaluated left to right:
+ *
+ *   oracle_csr_spmv   y_i = sum_j A_ij x_j over the stored entries of row i, in
+ *                     stored order: the product A x = y that every format of
+ *                     Sec. 4 and Sec. 5 computes (CSR storage: Sec. 4, CSR).
+ *   oracle_pcg        textbook Jacobi-preconditioned conjugate gradients
+ *                     (Hestenes-Stiefel), the solver the paper uses for the
+ *                     Newton update K dx = R (Sec. 2.1, Sec. 4), one sparse
+ *                     product per iteration.
+ *   oracle_refine     FP64 iterative refinement around a low-precision inner
+ *                     CG on the symmetrically scaled matrix B = S A S,
+ *                     S = diag(A)^(-1/2), with B stored in FP32 or BF16 and FP64
+ *                     dot products.  The paper runs FP64 only (Sec. 2); this
+ *                     is the mixed-precision layer built on top of it.
+ *
+ * The paper gives no code for CG; these routines follow the standard
+ * algorithm step by step.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* y = A x, CSR, FP64, row by row, entries in stored order. */
+void oracle_csr_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                     const double* val, const double* x, double* y) {
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = s + val[p] * x[colind[p]];
+        y[i] = s;
+    }
+}
+
+static double dot(int64_t n, const double* a, const double* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i];
+    return s;
+}
+
+/* diag(A) entries; 0 where a row stores no diagonal */
+static void diagonal(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                     const double* val, double* d) {
+    for (int64_t i = 0; i < n; ++i) {
+        d[i] = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (colind[p] == i) d[i] = d[i] + val[p];
+    }
+}
+
+enum { OR_CONVERGED = 0, OR_NOT_CONVERGED = 1, OR_BREAKDOWN = 2, OR_BAD_INPUT = 3 };
+
+/*
+ * Jacobi-preconditioned CG (M = diag(A) when jacobi != 0, M = I otherwise).
+ *   r = b - A x0;  z = M^-1 r;  p = z;  rho = r.z
+ *   repeat: q = A p;  alpha = rho / (p.q);  x += alpha p;  r -= alpha q;
+ *           stop when ||r|| / ||b|| <= tol;
+ *           z = M^-1 r;  rho' = r.z;  beta = rho' / rho;  p = z + beta p
+ * After the loop the true residual ||b - A x|| / ||b|| is checked; if it is
+ * above tol the iteration restarts from the current x (at most max_restarts
+ * times).  iters counts every CG step over all restarts.
+ * Returns 0 converged, 1 not converged, 2 breakdown (p.q <= 0 or non-finite),
+ * 3 bad input (zero/negative diagonal with jacobi).
+ */
+int oracle_pcg(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+               const double* b, double* x, double tol, int max_iter, int jacobi,
+               int max_restarts, int* iters_out, double* relres_out, double* true_relres_out) {
+    double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* p = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* dg = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int status = OR_NOT_CONVERGED;
+    int iters = 0;
+    double relres = 0.0, true_relres = 0.0;
+    diagonal(n, rowptr, colind, val, dg);
+    if (jacobi)
+        for (int64_t i = 0; i < n; ++i)
+            if (!(dg[i] > 0.0)) { status = OR_BAD_INPUT; goto done; }
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        status = OR_CONVERGED;
+        goto done;
+    }
+    for (int restart = 0; restart <= max_restarts; ++restart) {
+        oracle_csr_spmv(n, rowptr, colind, val, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = OR_CONVERGED; true_relres = relres; goto done; }
+        for (int64_t i = 0; i < n; ++i) z[i] = jacobi ? r[i] / dg[i] : r[i];
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+        double rho = dot(n, r, z);
+        int converged = 0;
+        while (iters < max_iter) {
+            oracle_csr_spmv(n, rowptr, colind, val, p, q);
+            double pq = dot(n, p, q);
+            if (!(pq > 0.0) || !isfinite(pq)) { status = OR_BREAKDOWN; goto final; }
+            double alpha = rho / pq;
+            for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+            ++iters;
+            relres = sqrt(dot(n, r, r)) / bnorm;
+            if (!isfinite(relres)) { status = OR_BREAKDOWN; goto final; }
+            if (relres <= tol) { converged = 1; break; }
+            for (int64_t i = 0; i < n; ++i) z[i] = jacobi ? r[i] / dg[i] : r[i];
+            double rho_new = dot(n, r, z);
+            double beta = rho_new / rho;
+            rho = rho_new;
+            for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        }
+        if (!converged) { status = OR_NOT_CONVERGED; break; }
+        /* verify on the true residual */
+        oracle_csr_spmv(n, rowptr, colind, val, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        true_relres = sqrt(dot(n, r, r)) / bnorm;
+        if (true_relres <= tol) { status = OR_CONVERGED; goto done; }
+    }
+final:
+    oracle_csr_spmv(n, rowptr, colind, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    true_relres = sqrt(dot(n, r, r)) / bnorm;
+done:
+    if (iters_out) *iters_out = iters;
+    if (relres_out) *relres_out = relres;
+    if (true_relres_out) *true_relres_out = true_relres;
+    free(r); free(z); free(p); free(q); free(dg);
+    return status;
+}
+
+/* Round a float to bfloat16 (round to nearest, ties to even), returned as float. */
+static float round_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) {           /* inf / nan: truncate, keep nan */
+        if (u & 0x007fffffu) u |= 0x00400000u;
+        u &= 0xffff0000u;
+    } else {
+        uint32_t lsb = (u >> 16) & 1u;
+        u = u + 0x7fffu + lsb;
+        u &= 0xffff0000u;
+    }
+    float g;
+    memcpy(&g, &u, 4);
+    return g;
+}
+
+/* Exported for the pin test that checks the rounding against another bf16 converter. */
+float oracle_round_bf16(float f) { return round_bf16(f); }
+
+/* y = B w with B in float (values already rounded to the storage type), float sums. */
+static void spmv_f32(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                     const float* bv, const float* w, float* y) {
+    for (int64_t i = 0; i < n; ++i) {
+        float s = 0.0f;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = s + bv[p] * w[colind[p]];
+        y[i] = s;
+    }
+}
+
+static double dot_f(int64_t n, const float* a, const float* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = s + (double)a[i] * (double)b[i];
+    return s;
+}
+
+/*
+ * Mixed-precision iterative refinement.
+ *   S = diag(A)^(-1/2);  B = S A S rounded to float (storage 0) or bfloat16 (storage 1)
+ *   x = x0
+ *   repeat: r = b - A x                                  (FP64)
+ *           stop when ||r|| / ||b|| <= tol
+ *           solve B w = S r by plain CG in float vectors with FP64 dot products
+ *             until ||B w - S r|| <= inner_tol ||S r|| (recurrence) or max_inner
+ *           x = x + S w                                   (FP64)
+ * diag(B) = 1, so Jacobi on B is the identity and the inner CG is unpreconditioned.
+ * Returns 0 converged, 1 not converged (max_outer), 2 breakdown/stagnation.
+ * outer_out / inner_out: refinement steps and total inner CG steps.
+ */
+int oracle_refine(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                  const double* b, double* x, double tol, double inner_tol, int max_outer,
+                  int max_inner, int storage, int* outer_out, int* inner_out,
+                  double* true_relres_out) {
+    int64_t nnz = rowptr[n];
+    double* s = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    float* bv = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    float* rs = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* w = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* ri = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* p = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* q = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    int status = 1, outer = 0, inner_total = 0;
+    double relres = 0.0;
+    diagonal(n, rowptr, colind, val, t);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(t[i] > 0.0)) { status = 2; goto done; }
+        s[i] = 1.0 / sqrt(t[i]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            float f = (float)(s[i] * val[k] * s[colind[k]]);
+            bv[k] = storage == 1 ? round_bf16(f) : f;
+        }
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        status = 0;
+        goto done;
+    }
+    double prev = INFINITY;
+    for (outer = 0; outer <= max_outer; ++outer) {
+        oracle_csr_spmv(n, rowptr, colind, val, x, t);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = 0; break; }
+        if (outer == max_outer) { status = 1; break; }
+        if (!isfinite(relres) || relres > prev) { status = 2; break; }
+        prev = relres;
+        /* inner: B w = S r, w0 = 0 */
+        for (int64_t i = 0; i < n; ++i) {
+            rs[i] = (float)(s[i] * r[i]);
+            w[i] = 0.0f;
+            ri[i] = rs[i];
+            p[i] = rs[i];
+        }
+        double rsn = sqrt(dot_f(n, rs, rs));
+        double rho = dot_f(n, ri, ri);
+        for (int k = 0; k < max_inner; ++k) {
+            spmv_f32(n, rowptr, colind, bv, p, q);
+            double pq = dot_f(n, p, q);
+            if (!(pq > 0.0)) break;
+            float alpha = (float)(rho / pq);
+            for (int64_t i = 0; i < n; ++i) w[i] = w[i] + alpha * p[i];
+            for (int64_t i = 0; i < n; ++i) ri[i] = ri[i] - alpha * q[i];
+            ++inner_total;
+            double rho_new = dot_f(n, ri, ri);
+            if (sqrt(rho_new) <= inner_tol * rsn) break;
+            float beta = (float)(rho_new / rho);
+            rho = rho_new;
+            for (int64_t i = 0; i < n; ++i) p[i] = ri[i] + beta * p[i];
+        }
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + s[i] * (double)w[i];
+    }
+done:
+    if (outer_out) *outer_out = outer;
+    if (inner_out) *inner_out = inner_total;
+    if (true_relres_out) *true_relres_out = relres;
+    free(s); free(r); free(t); free(bv); free(rs); free(w); free(ri); free(p); free(q);
+    return status;
+}

@@ -1,0 +1,112 @@
+"""Checks of the synthetic FE inputs against the mathematics (no GPU needed)."""
+import numpy as np
+import pytest
+
+import fegen
+import oracle
+
+
+def kuhn_nnz(dims, periodic2=False, dpn=1):
+    """Closed-form nnz of a Kuhn-split grid: N + 2E node pairs, times dpn^2."""
+    a, b, c = dims
+    cz = c if periodic2 else c - 1
+    E = ((a - 1) * b * c + a * (b - 1) * c + a * b * cz          # axis edges
+         + (a - 1) * (b - 1) * c + a * (b - 1) * cz + (a - 1) * b * cz   # face diagonals
+         + (a - 1) * (b - 1) * cz)                                 # body diagonal
+    return (a * b * c + 2 * E) * dpn * dpn
+
+
+def test_nnz_closed_forms_of_the_benchmark_meshes():
+    # the three mesh sizes of the workloads, before Dirichlet elimination
+    assert kuhn_nnz((20, 20, 20)) == 110_638
+    assert kuhn_nnz((64, 64, 64), dpn=3) == 34_511_598
+    assert kuhn_nnz((24, 256, 512), periodic2=True) == 46_041_088
+
+
+@pytest.mark.parametrize("maker,dims,per,dpn", [
+    (lambda: fegen.cube_laplace(7, 1, dirichlet=False), (7, 7, 7), False, 1),
+    (lambda: fegen.cube_elasticity(5, 2, dirichlet=False), (5, 5, 5), False, 3),
+    (lambda: fegen.shell_laplace(4, 6, 10, 3, dirichlet=False), (4, 6, 10), True, 1),
+])
+def test_generated_nnz_matches_closed_form(maker, dims, per, dpn):
+    p = maker()
+    assert p.nnz == kuhn_nnz(dims, per, dpn)
+    assert p.n_rows == dims[0] * dims[1] * dims[2] * dpn
+
+
+def test_interior_rows_have_15_nodes():
+    p = fegen.cube_laplace(6, 4, dirichlet=False)
+    lens = np.diff(p.rowptr)
+    # the two corners off the split diagonal touch one cell and 4 Kuhn edges: 4 neighbours + self
+    assert lens.max() == 15 and lens.min() == 5
+
+
+def test_bitwise_symmetry():
+    for p in (fegen.cube_laplace(6, 5), fegen.cube_elasticity(4, 6),
+              fegen.shell_laplace(4, 6, 8, 7)):
+        n = p.n_rows
+        rows = np.repeat(np.arange(n), np.diff(p.rowptr))
+        fwd = dict(zip(zip(rows.tolist(), p.colind.tolist()), p.values.tolist()))
+        for (i, j), v in fwd.items():
+            assert fwd[(j, i)] == v
+
+
+def test_neumann_laplacian_rows_sum_to_zero():
+    for p in (fegen.cube_laplace(8, 8, dirichlet=False),
+              fegen.shell_laplace(4, 8, 12, 9, dirichlet=False)):
+        rs = oracle.csr_spmv(p.rowptr, p.colind, p.values, np.ones(p.n_rows))
+        absr = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.ones(p.n_rows))
+        assert np.all(np.abs(rs) <= 1e-13 * absr)
+
+
+def test_patch_test_linear_field_is_annihilated_on_interior_rows():
+    # constant D: a linear field is reproduced exactly, so interior residuals vanish
+    p = fegen.cube_laplace(7, 10, dirichlet=False)
+    u = p.node_xyz @ np.array([0.3, -1.1, 0.7]) + 0.25
+    r = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    xyz = p.node_xyz
+    interior = np.all((xyz > 1e-12) & (xyz < 1 - 1e-12), axis=1)
+    scale = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(u))
+    assert np.all(np.abs(r[interior]) <= 1e-12 * scale[interior])
+    assert np.abs(r[~interior]).max() > 1e-3      # boundary rows carry the flux
+
+
+def test_elasticity_rigid_body_modes_in_null_space():
+    p = fegen.cube_elasticity(5, 11, dirichlet=False)
+    X = p.node_xyz
+    modes = [np.tile(np.eye(3)[c], (p.n_nodes, 1)).ravel() for c in range(3)]
+    for (a, b) in ((0, 1), (1, 2), (0, 2)):             # infinitesimal rotations
+        m = np.zeros((p.n_nodes, 3))
+        m[:, a] = -X[:, b]
+        m[:, b] = X[:, a]
+        modes.append(m.ravel())
+    absA = np.abs(p.values)
+    for m in modes:
+        r = oracle.csr_spmv(p.rowptr, p.colind, p.values, m)
+        s = oracle.csr_spmv(p.rowptr, p.colind, absA, np.abs(m))
+        assert np.all(np.abs(r) <= 1e-12 * s + 1e-14)
+
+
+def test_dirichlet_systems_are_spd_and_identity_rows():
+    from test_oracle_pins import dense_of
+    for p in (fegen.cube_laplace(5, 12), fegen.cube_elasticity(4, 13),
+              fegen.shell_laplace(3, 5, 8, 14)):
+        A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+        np.linalg.cholesky(A)          # raises if not SPD
+        d = p.dirichlet.astype(bool)
+        assert d.any()
+        assert np.array_equal(A[d][:, d], np.eye(d.sum()))
+        assert not A[d][:, ~d].any() and not A[~d][:, d].any()
+
+
+def test_generation_is_deterministic():
+    a = fegen.cube_elasticity(4, 99)
+    b = fegen.cube_elasticity(4, 99)
+    assert np.array_equal(a.values, b.values) and np.array_equal(a.colind, b.colind)
+    c = fegen.cube_elasticity(4, 100)
+    assert not np.array_equal(a.values, c.values)
+
+
+def test_inverted_tet_is_rejected():
+    with pytest.raises(ValueError):
+        fegen.cube_laplace(5, 1, jitter=0.9)

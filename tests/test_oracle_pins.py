@@ -1,0 +1,288 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU needed).
+
+Each test ties one oracle routine to something it does not compute itself:
+a dense brute-force product, the paper's worked example, a closed form, a
+dense direct solve, or a property exact arithmetic guarantees.  A dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails at
+least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import fegen
+import oracle
+from oracle import layout
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_of(rowptr, colind, values, n):
+    """Dense matrix built entry by entry (duplicates summed)."""
+    A = np.zeros((n, n))
+    for i in range(n):
+        for p in range(rowptr[i], rowptr[i + 1]):
+            A[i, colind[p]] += values[p]
+    return A
+
+
+def small_problems():
+    return [fegen.cube_laplace(4, 7, dirichlet=False), fegen.cube_laplace(5, 8),
+            fegen.cube_elasticity(3, 9, dirichlet=False), fegen.cube_elasticity(4, 10),
+            fegen.shell_laplace(3, 5, 8, 11, dirichlet=False), fegen.shell_laplace(4, 6, 8, 12)]
+
+
+# ---------------------------------------------------------------- sparse product
+
+def test_spmv_integer_matrix_exact():
+    # 3x3 matrix with integer entries: every product and sum is exact in FP64
+    rowptr = np.array([0, 2, 2, 5])
+    colind = np.array([2, 0, 0, 1, 2])
+    values = np.array([3.0, -1.0, 2.0, 5.0, -4.0])
+    x = np.array([7.0, -2.0, 0.5])
+    y = oracle.csr_spmv(rowptr, colind, values, x)
+    assert y.tolist() == [3 * 0.5 - 7.0, 0.0, 2 * 7.0 - 10.0 - 2.0]
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_spmv_matches_dense_brute_force(k):
+    p = small_problems()[k]
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    x = fegen.random_vector(p.n_rows, 100 + k)
+    y = oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    yd = A @ x
+    bound = np.abs(A) @ np.abs(x)
+    assert np.all(np.abs(y - yd) <= 1e-14 * bound + 1e-300)
+
+
+def test_spmv_empty_rows_and_empty_matrix():
+    rowptr = np.array([0, 0, 1, 1])
+    y = oracle.csr_spmv(rowptr, np.array([2]), np.array([4.0]), np.array([1.0, 2.0, 3.0]))
+    assert y.tolist() == [0.0, 12.0, 0.0]
+    y0 = oracle.csr_spmv(np.array([0]), np.array([], dtype=np.int32), np.array([]), np.array([]))
+    assert y0.shape == (0,)
+
+
+def test_worked_example_k1r_k1rs():
+    g = json.load(open(os.path.join(GOLDEN, "worked_example_k1r.json")))
+    x, P, A, c = (np.array(g[k]) for k in ("x", "P", "A", "c"))
+    # x'(.) = x(P(.))
+    assert x[P - 1].tolist() == g["x_prime"]
+    # c' = P^-1 applied to c
+    cp = layout.worked_example_renumber(c, P)
+    assert cp.tolist() == g["c_prime"]
+    order = np.argsort(cp, kind="stable")
+    assert cp[order].tolist() == g["c_dprime"]
+    assert A[order].tolist() == g["A_dprime"]
+    # the row's product is unchanged by the renumbering, through the oracle
+    n = len(x)
+    rowptr = np.array([0, len(A)] + [len(A)] * (n - 1))
+    y = oracle.csr_spmv(rowptr, c - 1, A.astype(float), x.astype(float))
+    assert y[0] == g["row_dot"]
+    xp = x[P - 1].astype(float)
+    y2 = oracle.csr_spmv(rowptr, np.array(g["c_dprime"]) - 1,
+                         np.array(g["A_dprime"], dtype=float), xp)
+    assert y2[0] == g["row_dot"]
+
+
+# ------------------------------------------------------------- permutation + packing
+
+@pytest.mark.parametrize("k", range(6))
+def test_permute_csr_is_PAPt(k):
+    p = small_problems()[k]
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    P = layout.row_permutation(p.rowptr, p.dofs_per_node, p.node_xyz, "morton", sigma=16)
+    assert sorted(P.tolist()) == list(range(p.n_rows))
+    rp2, ci2, v2, vmap = layout.permute_csr(p.rowptr, p.colind, p.values, P)
+    A2 = dense_of(rp2, ci2, v2, p.n_rows)
+    assert np.array_equal(A2, A[np.ix_(P, P)])
+    for i in range(p.n_rows):
+        assert np.all(np.diff(ci2[rp2[i]:rp2[i + 1]]) > 0)
+    assert np.array_equal(v2[vmap], p.values)
+    # y' = A' x' with x' = x[P] gives y[P]
+    x = fegen.random_vector(p.n_rows, 5)
+    y = oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    y2 = oracle.csr_spmv(rp2, ci2, v2, x[P])
+    assert np.all(np.abs(y2 - y[P]) <= 1e-14 * (np.abs(A) @ np.abs(x))[P] + 1e-300)
+
+
+def test_morton_codes_of_cube_corners():
+    corners = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], float)
+    code = layout.morton_codes(corners)
+    full = (1 << layout.MORTON_BITS) - 1
+    expect = []
+    for i, j, k in corners.astype(int):
+        c = 0
+        for b in range(layout.MORTON_BITS):
+            c |= ((i * full >> b) & 1) << (3 * b + 2)
+            c |= ((j * full >> b) & 1) << (3 * b + 1)
+            c |= ((k * full >> b) & 1) << (3 * b)
+        expect.append(c)
+    assert code.tolist() == expect
+    assert code[-1] == (1 << 63) - 1
+    # z-order of the corners: x most significant, then y, then z
+    assert np.argsort(code).tolist() == list(range(8))
+
+
+def test_length_sort_is_stable_and_windowed():
+    lens = np.array([3, 5, 5, 1, 7, 2, 2, 9])
+    rowptr = np.concatenate([[0], np.cumsum(lens)])
+    P = layout.row_permutation(rowptr, 1, None, "none", sigma=4)
+    assert P.tolist() == [1, 2, 0, 3, 7, 4, 5, 6]
+    Pg = layout.row_permutation(rowptr, 1, None, "none", sigma=100)
+    assert Pg.tolist() == [7, 4, 1, 2, 0, 5, 6, 3]
+
+
+def test_slice_plan_k1_and_k2_threshold_rule():
+    # one group of 32 rows: row 0 has 100 entries, the rest 5
+    lens = np.array([100] + [5] * 31)
+    rowptr = np.concatenate([[0], np.cumsum(lens)])
+    k1 = layout.slice_plan(rowptr, threshold=0, V=1)
+    assert k1 == [(0, 32, 1, 100)]
+    # tau = 7: T = 16 (ceil(100/16) = 7 <= 7, ceil(100/8) = 13 > 7); 16 warps of 2 rows
+    k2 = layout.slice_plan(rowptr, threshold=7, V=1)
+    assert len(k2) == 16
+    assert k2[0] == (0, 2, 16, 7)
+    assert k2[1] == (2, 2, 16, 1)
+    # V = 2 rounds each width up to even
+    assert layout.slice_plan(rowptr, threshold=7, V=2)[1] == (2, 2, 16, 2)
+    # tau larger than any row keeps T = 1; row > 32*tau uses a whole warp per row
+    assert layout.slice_plan(rowptr, threshold=200, V=1) == k1
+    big = np.concatenate([[0], np.cumsum(np.array([2000] + [1] * 3))])
+    plan = layout.slice_plan(big, threshold=10, V=1)
+    assert plan[0] == (0, 1, 32, 63) and len(plan) == 4
+
+
+@pytest.mark.parametrize("threshold,V", [(0, 1), (0, 2), (4, 2), (3, 4)])
+def test_pack_roundtrip_reproduces_rows(threshold, V):
+    p = fegen.cube_elasticity(3, 13)
+    P = layout.row_permutation(p.rowptr, 3, p.node_xyz, "morton", sigma=64)
+    rp2, ci2, v2, _ = layout.permute_csr(p.rowptr, p.colind, p.values, P)
+    meta, col, val, pmap = layout.pack(rp2, ci2, v2, threshold, V)
+    assert np.array_equal(col[pmap], ci2) and np.array_equal(val[pmap], v2)
+    pad = np.ones(len(col), bool)
+    pad[pmap] = False
+    assert np.all(col[pad] == -1) and np.all(val[pad] == 0)
+    # walk the slices the way a warp does and rebuild every row's entries
+    seen = {}
+    for off32, w, r0, lt in meta:
+        T = 1 << int(lt)
+        for lane in range(32):
+            r = r0 + lane // T
+            for step in range(w):
+                pos = off32 * 32 + (step // V) * 32 * V + lane * V + step % V
+                if col[pos] >= 0:
+                    seen.setdefault(r, []).append((step * T + lane % T, col[pos], val[pos]))
+    for i in range(p.n_rows):
+        ents = sorted(seen.get(i, []))
+        assert [e[1] for e in ents] == ci2[rp2[i]:rp2[i + 1]].tolist()
+        assert [e[2] for e in ents] == v2[rp2[i]:rp2[i + 1]].tolist()
+
+
+# ------------------------------------------------------------------ conjugate gradient
+
+def test_pcg_matches_dense_solve():
+    p = fegen.cube_laplace(6, 21)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    b = fegen.random_vector(p.n_rows, 22)
+    x, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12)
+    assert info["status"] == "converged" and info["true_relres"] <= 1e-12
+    xd = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 10 * cond * 1e-12
+
+
+def test_pcg_recovers_manufactured_solution():
+    p = fegen.cube_elasticity(5, 23)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    x, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12)
+    assert info["status"] == "converged"
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-8
+
+
+def test_cg_finite_termination_distinct_eigenvalues():
+    # block-diagonal SPD matrix with exactly 3 distinct eigenvalues {1, 3, 4}:
+    # blocks [[2,1],[1,2]] (eigenvalues 1, 3) and diagonal 4s; plain CG ends in 3 steps
+    n_blocks, n4 = 5, 4
+    rows, cols, vals = [], [], []
+    for b in range(n_blocks):
+        i = 2 * b
+        for (r, c, v) in ((i, i, 2.0), (i, i + 1, 1.0), (i + 1, i, 1.0), (i + 1, i + 1, 2.0)):
+            rows.append(r), cols.append(c), vals.append(v)
+    for k in range(n4):
+        i = 2 * n_blocks + k
+        rows.append(i), cols.append(i), vals.append(4.0)
+    n = 2 * n_blocks + n4
+    order = np.lexsort((cols, rows))
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))])
+    b = fegen.random_vector(n, 3)
+    x, info = oracle.pcg(rowptr, np.array(cols)[order], np.array(vals)[order], b,
+                         tol=1e-13, jacobi=False, max_restarts=0)
+    assert info["status"] == "converged" and info["iters"] == 3
+
+
+def test_jacobi_pcg_on_diagonal_matrix_is_one_step():
+    n = 9
+    d = np.arange(1, n + 1, dtype=float)
+    b = fegen.random_vector(n, 4)
+    x, info = oracle.pcg(np.arange(n + 1), np.arange(n), d, b, tol=1e-14, max_restarts=0)
+    assert info["iters"] == 1
+    assert np.allclose(x, b / d, rtol=1e-15, atol=0)
+
+
+def test_cg_error_decreases_in_A_norm():
+    p = fegen.cube_laplace(6, 24)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    b = fegen.random_vector(p.n_rows, 25)
+    xs = np.linalg.solve(A, b)
+    errs = []
+    for k in range(1, 25):
+        x, _ = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=0.0, max_iter=k, max_restarts=0)
+        e = x - xs
+        errs.append(e @ A @ e)
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+
+
+def test_pcg_status_codes():
+    # indefinite diagonal: Jacobi rejects it, plain CG breaks down (p.q <= 0)
+    rowptr, colind = np.arange(3), np.arange(2)
+    vals = np.array([1.0, -1.0])
+    b = np.array([1.0, 1.0])
+    _, info = oracle.pcg(rowptr, colind, vals, b)
+    assert info["status"] == "bad_input"
+    _, info = oracle.pcg(rowptr, colind, vals, b, jacobi=False)
+    assert info["status"] == "breakdown"
+    p = fegen.cube_laplace(6, 26)
+    _, info = oracle.pcg(p.rowptr, p.colind, p.values, fegen.random_vector(p.n_rows, 1),
+                         tol=1e-12, max_iter=3, max_restarts=0)
+    assert info["status"] == "not_converged" and info["iters"] == 3
+    x, info = oracle.pcg(p.rowptr, p.colind, p.values, np.zeros(p.n_rows))
+    assert info["status"] == "converged" and not x.any()
+
+
+# ------------------------------------------------------------- mixed-precision refinement
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    v = np.concatenate([rng.standard_normal(2000).astype(np.float32),
+                        np.array([1.0, -0.0, 1e-40, 3.0e38, 1.00390625, 1.01171875], np.float32)])
+    ours = oracle.round_bf16(v)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(ours.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_refinement_reaches_fp64_solution(storage):
+    p = fegen.cube_laplace(8, 27)
+    b = fegen.random_vector(p.n_rows, 28)
+    xr, info = oracle.refine(p.rowptr, p.colind, p.values, b, tol=1e-10, inner_tol=1e-3,
+                             storage=storage)
+    assert info["status"] == "converged" and info["true_relres"] <= 1e-10
+    x64, _ = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(xr - x64) / np.linalg.norm(x64) <= cond * 1e-10
