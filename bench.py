@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark: FE SpMV effective HBM bandwidth (and CG solves) on one GB300.
+
+Workload: P1 linear elasticity on a jittered 64^3-node Kuhn tet grid
+(786,432 rows, ~34M nnz after clamping z=0), randomly numbered, seeded
+(fegen.cube_elasticity(64, 1502)); x ~ U[-1, 1] (seed 1504).
+
+One step = one FP64 product y' = A' x' by the FE warp-slice kernel in the
+handle's permuted numbering (the operator CG applies every iteration).  Steps
+are timed one by one with CUDA events on the launching stream, with a 256 MB
+write between steps so that every step streams the matrix from HBM (the matrix
+alone, 414 MB, is also larger than the 126 MB L2).  Effective bandwidth uses
+the minimum bytes of one product: nnz*(8 B value + 4 B index) + n*(8 B x + 8 B y).
+
+Also reported: the CSR baselines, the product in the input numbering, the end-to-end
+call with host buffers (copies inside the timed region), CG solves when
+available, the CPU oracle timed on the host cores, and SM clocks sampled during
+the run.
+
+--impl reference times the CPU oracle (plain FP64 CSR product) on the same
+matrix and prints the same JSON line with "impl": "reference".
+N > 1 (torchrun): every rank runs an independent replica (the product does not
+shard); value is the sum over ranks of bytes / the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SpMV effective HBM GB/s (% of ~8 TB/s); CG solves/s and p50/p99 latency at 1e-10"
+WORKLOAD = "cube_elasticity_64"
+NOMINAL_HBM_GBS = 8000.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sliced_f64_cube_elasticity_64.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1501_00324_gb300", "csrc", "spmv_kernels.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sigma", type=int, default=1024)
+    ap.add_argument("--vec", type=int, default=2)
+    ap.add_argument("--threshold", type=int, default=0)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--only-spmv", action="store_true",
+                    help="time the FE product only (for profiling runs)")
+    ap.add_argument("--cg-solves", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def min_bytes(n, nnz, val_bytes=8, vec_bytes=8):
+    return nnz * (val_bytes + 4) + n * 2 * vec_bytes
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None, "no ncu summary committed"
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not h or not b:
+        return None, "summary lacks traffic figures"
+    if h.group(1) != kernel_hash():
+        return None, "kernel changed since the ncu capture"
+    return float(b.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        mhz, mx, reasons, loaded = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm, smax, pw = float(r[1]), float(r[2]), float(r[3])
+            except (ValueError, IndexError):
+                continue
+            mx = smax
+            mhz.append(sm)
+            if pw > 250:
+                loaded.append(sm)
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        use = loaded or mhz
+        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz), "samples_under_load": len(loaded)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_spmv(p, x, seconds):
+    """Time the oracle's FP64 CSR product (one host core) for about `seconds`."""
+    import oracle
+    oracle.csr_spmv(p.rowptr, p.colind, p.values, x)          # warm
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return k, el
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: the same matrix and metric, FP64 CSR product on one host core."""
+    if rank != 0:
+        return
+    import fegen
+    import oracle
+    p = fegen.cube_elasticity(64, 1502)
+    x = fegen.random_vector(p.n_rows, 1504)
+    for _ in range(max(0, args.warmup)):
+        oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    el = time.perf_counter() - t0
+    mb = min_bytes(p.n_rows, p.nnz)
+    gbs = mb * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": p.n_rows, "nnz": p.nnz,
+                   "kernel": "oracle_csr_spmv (plain C, FP64, sequential rows)"},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full products of the {WORKLOAD} matrix"},
+        "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import fegen
+    import paper_1501_00324_gb300 as fs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    p = fegen.cube_elasticity(64, 1502)
+    n, nnz = p.n_rows, p.nnz
+    x = fegen.random_vector(n, 1504)
+    t0 = time.perf_counter()
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.vec,
+                       threshold=args.threshold, block=args.block)
+    create_s = time.perf_counter() - t0
+    info = fs.spmv_get_info(A)
+
+    xd = torch.from_numpy(x).to(dev)
+    xp = torch.empty_like(xd)
+    fs.spmv_permute(A, xd, xp, 0)
+    yp = torch.empty_like(xd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    mb = min_bytes(n, nnz)
+
+    def timed_steps(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for (a, b) in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for (a, b) in evs]
+
+    fe = lambda: fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    for _ in range(args.warmup):
+        fe()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    with clocks:
+        barrier(world)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        times = timed_steps(fe, args.steps)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - wall0
+        extra = {}
+        if not args.only_spmv:
+            # product in the input numbering (permute x in, y out)
+            y_user = torch.empty_like(xd)
+            t_user = timed_steps(lambda: fs.spmv_apply(A, xd, y_user), max(10, args.steps // 4))
+            extra["fe_input_numbering_gbs"] = round(mb / (statistics.mean(t_user) * 1e-3) / 1e9, 1)
+            # CSR baselines on the input CSR
+            for lanes in (1, 4, 8):
+                B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
+                                   csr_lanes=lanes)
+                fs.spmv_apply(B, xd, y_user)
+                tb = timed_steps(lambda: fs.spmv_apply(B, xd, y_user), max(10, args.steps // 4))
+                extra[f"csr_{'scalar' if lanes == 1 else f'vector{lanes}'}_gbs"] = round(
+                    mb / (statistics.mean(tb) * 1e-3) / 1e9, 1)
+                fs.spmv_destroy(B)
+            # end to end with host buffers (pinned), copies inside the timed region
+            xh = torch.from_numpy(x).pin_memory().numpy()
+            yh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+            k_e2e = max(10, args.steps // 4)
+            fs.spmv_apply(A, xh, yh)
+            torch.cuda.synchronize()
+            te0 = time.perf_counter()
+            for _ in range(k_e2e):
+                fs.spmv_apply(A, xh, yh)      # synchronous: H2D, permute, kernel, permute, D2H
+            te = (time.perf_counter() - te0) / k_e2e
+            extra["e2e"] = {"value": round(mb / te / 1e9, 1), "unit": "GB/s",
+                            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+            if hasattr(fs, "cg_solve"):
+                extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves)
+    clk = clocks.summary()
+
+    t_mean = statistics.mean(times) * 1e-3
+    t_max = reduce_max(t_mean, world)
+    value = mb * world / t_max / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = mb / t_mean / 1e9
+    traffic, traffic_src = profile_traffic()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0 and not args.only_spmv:
+            k, el = cpu_oracle_spmv(p, x, args.cpu_seconds)
+            cpu = {"value": round(mb * k / el / 1e9, 3), "unit": "GB/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"{k} full FP64 CSR products of the {WORKLOAD} matrix in {el:.1f} s"}
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": n, "nnz": nnz,
+                       "kernel": f"sliced_f64 V={info['vec']} threshold={args.threshold} "
+                                 f"sigma={args.sigma} block={args.block}",
+                       "order": "Morton nodes, windowed length sort, sorted columns",
+                       "l2": "256 MB write between steps; matrix 414 MB > L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "create_s": round(create_s, 2),
+                       "packed_len": info["packed_len"],
+                       "padding_pct": round(100.0 * (info["packed_len"] - nnz) / max(nnz, 1), 2)},
+            "pct_of_8tbs": round(100 * value / world / NOMINAL_HBM_GBS, 1),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "traffic_source": traffic_src,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks
+                         else "fallback 6.8 TB/s",
+                         "bytes_per_launch": mb},
+            "gpu_launches": args.steps,
+            "wall_s_timed": round(wall, 4),
+            "clocks": clk,
+        }
+        line["e2e"] = extra.pop("e2e", None)
+        line.update(extra)
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    fs.spmv_destroy(A)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_cg(fs, torch, A, p, n_solves):
+    """FP64 Jacobi-PCG solves to 1e-10 on the same matrix (b = A u*, u* manufactured)."""
+    import fegen
+    u = fegen.manufactured_solution(p)
+    ud = torch.from_numpy(u).cuda()
+    bd = torch.empty_like(ud)
+    fs.spmv_apply(A, ud, bd)
+    lat, iters = [], []
+    for _ in range(n_solves):
+        xs = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fs.cg_solve(A, bd, xs, tol=1e-10)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+        iters.append(res["iters"])
+    lat_ms = sorted(1e3 * t for t in lat)
+    return {"precision": "f64", "tol": 1e-10, "solves": n_solves,
+            "solves_per_s": round(n_solves / sum(lat), 3),
+            "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat_ms, 99)), 2),
+            "iters": iters}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * fespmv.h -- C ABI of the GB300 finite-element SpMV + CG library.
+ *
+ * Paper: J. Wong, E. Kuhl, E. Darve, "A New Sparse Matrix Vector Multiplication
+ * GPU Algorithm Designed for Finite Element Problems" (arXiv:1501.00324).
+ *
+ * The library computes y = A x for sparse stiffness matrices of unstructured
+ * finite-element meshes (Sec. 4 states the problem: given A and x, compute y)
+ * and runs the Jacobi-preconditioned conjugate-gradient solve of K dx = R that
+ * the paper's Newton loop performs (Sec. 2.1, Sec. 4), on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (FESPMV_OK) on success or a negative FESPMV_ERR_* code; nothing
+ *     aborts or traps.  fespmv_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ *   - Host arrays passed to spmv_create are read during the call and not
+ *     retained.  Device arrays passed to spmv_apply / cg_solve stay owned by the
+ *     caller and must hold the stated number of elements.
+ *   - All device work is ordered on the caller's stream (a cudaStream_t passed
+ *     as fespmv_stream_t; NULL = legacy default stream).
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ *   - Indices are 0-based; CSR row offsets are int64, column indices int32.
+ */
+#ifndef FESPMV_H
+#define FESPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fespmv_stream_t; /* identical to cudaStream_t */
+typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory it allocates */
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define FESPMV_OK                  0
+#define FESPMV_ERR_INVALID_ARG    -1  /* null pointer, bad size or bad option */
+#define FESPMV_ERR_BAD_CSR        -2  /* rowptr not monotone, column out of range, duplicate */
+#define FESPMV_ERR_OOM            -3  /* device or host allocation failed */
+#define FESPMV_ERR_CUDA           -4  /* a CUDA runtime call failed (message has the name) */
+#define FESPMV_ERR_BREAKDOWN      -5  /* CG: p.Ap <= 0 or a non-finite scalar */
+#define FESPMV_ERR_NOT_CONVERGED  -6  /* CG: iteration limit reached above tolerance */
+#define FESPMV_ERR_UNSUPPORTED    -7  /* option combination not built for this handle */
+
+/* ---- matrix formats and kernels ---------------------------------------------------- */
+/* Storage built by spmv_create. */
+#define FESPMV_FMT_CSR     0  /* the input CSR as given: baseline kernels (Sec. 4, CSR) */
+#define FESPMV_FMT_SLICED  1  /* FE warp slices: locality order, length sort, packed
+                                 column-major slices (Sec. 5.1-5.5, ELL-WARP K1/K2) */
+
+/* Node locality orders for FESPMV_FMT_SLICED. */
+#define FESPMV_REORDER_NONE    0  /* keep the input numbering */
+#define FESPMV_REORDER_MORTON  1  /* Z-order curve of node_xyz (requires mesh->node_xyz) */
+
+/* Kernel selection for FESPMV_FMT_CSR (csr_lanes) is by lanes per row:
+ * 1 = one thread per row (CSR scalar, Sec. 4), 2..32 (power of two) = that many
+ * lanes of a warp per row with a shuffle reduction (CSR vector, Sec. 4). */
+
+/* Value copies kept by a handle (bitmask in fespmv_options.precisions). */
+#define FESPMV_PREC_F64      1  /* FP64 values (always kept) */
+#define FESPMV_PREC_F32      2  /* FP32 values of S A S, S = diag(A)^-1/2, for refined CG */
+
+typedef struct {
+    int32_t format;      /* FESPMV_FMT_*; 0 = CSR baseline */
+    int32_t reorder;     /* FESPMV_REORDER_*; SLICED only; MORTON needs node_xyz */
+    int32_t sigma;       /* SLICED: rows per length-sort window (stable, longest first);
+                            0 = no sort; >= n_rows = the paper's global sort (Sec. 5.1) */
+    int32_t threshold;   /* SLICED: K2 threshold, max entries per lane (Sec. 5.4); 0 = K1 */
+    int32_t vec;         /* SLICED: entries per lane per load, 1, 2 or 4; 0 = 2 */
+    int32_t csr_lanes;   /* CSR: lanes per row, 1..32 power of two; 0 = 1 (scalar) */
+    int32_t precisions;  /* FESPMV_PREC_* bitmask; 0 = FP64 only */
+    int32_t block;       /* threads per block for the SpMV kernel, multiple of 32, <= 1024
+                            (<= 256 for SLICED); 0 = 256 */
+} fespmv_options;
+
+typedef struct {
+    int32_t dofs_per_node;   /* rows = dofs_per_node * n_nodes, row = d*node + c; 0 = 1 */
+    const double* node_xyz;  /* host, n_nodes x 3 coordinates, or NULL */
+} fespmv_mesh_info;
+
+/* Sizes of a built handle. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    int64_t n_slices;        /* SLICED: warps per product; CSR: 0 */
+    int64_t packed_len;      /* SLICED: stored entries including padding; CSR: nnz */
+    int64_t device_bytes;    /* device memory owned by the handle */
+    int32_t format;
+    int32_t vec;
+} fespmv_info;
+
+/*
+ * spmv_create -- build a handle for y = A x from a host CSR matrix.
+ *   n_rows          square matrix order (>= 0)
+ *   rowptr          host int64[n_rows+1], rowptr[0] = 0, non-decreasing
+ *   colind          host int32[nnz], each in [0, n_rows), no duplicates within a row
+ *   values          host double[nnz]
+ *   mesh            optional mesh metadata (NULL: one dof per node, no coordinates)
+ *   opts            optional options (NULL or zero-initialised: defaults)
+ * SLICED handles reorder on the host (Sec. 5.1 row sort, Sec. 5.2 symmetric
+ * renumbering x' = x(P), c' = P^-1(c), Sec. 5.3 per-row column sort), pack
+ * the warp slices and copy them to the device once.  Errors: INVALID_ARG,
+ * BAD_CSR, OOM, CUDA.  On error *out is set to NULL.
+ */
+int spmv_create(fespmv_mat_t* out, int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
+                const double* values, const fespmv_mesh_info* mesh, const fespmv_options* opts,
+                fespmv_stream_t stream);
+
+/* Free every device and host resource of the handle (NULL is ignored).  The
+ * caller must make sure no work using the handle is still running. */
+void spmv_destroy(fespmv_mat_t A);
+
+/* I/O flags for spmv_apply and cg_solve. */
+#define FESPMV_IO_PERMUTED  1  /* vectors are in the handle's permuted numbering */
+#define FESPMV_IO_HOST      2  /* vectors are host memory: copied in and out on the stream,
+                                  and the call waits for the stream before returning */
+
+/*
+ * spmv_apply -- y = A x in FP64.
+ *   x, y  n_rows doubles each, device memory unless FESPMV_IO_HOST; x and y must
+ *         not overlap.  Without FESPMV_IO_PERMUTED they are in the numbering of
+ *         the CSR given to spmv_create; a SLICED handle then permutes x on the way
+ *         in and y on the way out (two gathers of n_rows entries).
+ * Result per entry: the exact sum over the stored entries of the row, rounded
+ * with a different association than a left-to-right sum (componentwise error
+ * well under 1e-12 * sum_j |A_ij x_j|).  Errors: INVALID_ARG, CUDA.
+ */
+int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv_stream_t stream);
+
+/* Vector permutation between the input numbering and a SLICED handle's numbering
+ * (device arrays of n_rows doubles, no overlap):
+ *   direction 0: out[i'] = in[P[i']]   (input -> permuted, x' = x(P), Sec. 5.2)
+ *   direction 1: out[i]  = in[Pinv[i]] (permuted -> input)
+ * CSR handles copy.  Errors: INVALID_ARG, CUDA. */
+int spmv_permute(fespmv_mat_t A, const double* in, double* out, int32_t direction,
+                 fespmv_stream_t stream);
+
+/*
+ * spmv_update_values -- replace the matrix values, keeping the pattern (the
+ * per-Newton-step refresh of Sec. 6, "Cost of Reordering Matrix Values": one
+ * gather through the map computed at create time, on the device).
+ *   values  double[nnz] in the CSR order given to spmv_create; device memory
+ *           unless FESPMV_IO_HOST is set in flags.
+ * FP32 scaled copies kept by the handle are rebuilt too.  Errors: INVALID_ARG, CUDA.
+ */
+int spmv_update_values(fespmv_mat_t A, const double* values, int32_t flags,
+                       fespmv_stream_t stream);
+
+int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
+
+/* Arrays spmv_export can copy to the host (for tests and inspection). */
+#define FESPMV_EXPORT_PERM     0  /* int32[n_rows]: P, P[new] = old (SLICED) */
+#define FESPMV_EXPORT_META     1  /* uint32[n_slices*4]: (offset/32, width, first row, log2 T) */
+#define FESPMV_EXPORT_COLS     2  /* int32[packed_len]: packed column indices, -1 = padding */
+#define FESPMV_EXPORT_VALUES   3  /* double[packed_len]: packed values, 0 = padding */
+#define FESPMV_EXPORT_SRCMAP   4  /* int64[packed_len]: CSR position of each packed entry, -1 pad */
+#define FESPMV_EXPORT_DIAG     5  /* double[n_rows]: diag(A) in the handle's numbering */
+/* Copy internal array `what` into host buffer `out` of `bytes` bytes (must be at
+ * least the array's size).  Synchronises the stream.  Errors: INVALID_ARG,
+ * UNSUPPORTED (array not held by this handle), CUDA. */
+int spmv_export(fespmv_mat_t A, int32_t what, void* out, size_t bytes, fespmv_stream_t stream);
+
+/*
+ * spmv_plan -- the host part of spmv_create for FESPMV_FMT_SLICED, with no
+ * device work (usable without a GPU).  Computes the same permutation, slice
+ * metadata, packed columns and value map that spmv_create uploads.
+ *   info     out: n_rows, nnz, n_slices, packed_len (always written)
+ *   perm     out: int32[n_rows] or NULL
+ *   meta     out: uint32[n_slices*4] or NULL
+ *   cols     out: int32[packed_len] or NULL
+ *   srcmap   out: int64[packed_len] or NULL
+ * Call once with NULL arrays to learn the sizes, then again with buffers.
+ * Errors: INVALID_ARG, BAD_CSR, OOM (host), UNSUPPORTED.
+ */
+int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
+              const fespmv_mesh_info* mesh, const fespmv_options* opts, fespmv_info* info,
+              int32_t* perm, uint32_t* meta, int32_t* cols, int64_t* srcmap);
+
+/* Human-readable name of a status code, and the last failure message of the
+ * calling thread (empty if none).  Both strings are static or thread-local. */
+const char* fespmv_status_string(int status);
+const char* fespmv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FESPMV_H */

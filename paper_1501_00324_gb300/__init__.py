@@ -1,0 +1,241 @@
+"""Python binding of libfespmv (include/fespmv.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: device vectors are torch CUDA tensors (their
+``data_ptr()`` is passed), host arrays are numpy arrays, and the stream
+defaults to torch's current CUDA stream.  The compiled library must be present
+(it is built in-tree by ``__graft_entry__.build()`` or on first import); if it
+cannot be loaded, importing this package raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+# ---- constants mirrored from include/fespmv.h -------------------------------------
+FESPMV_OK = 0
+FESPMV_ERR_INVALID_ARG = -1
+FESPMV_ERR_BAD_CSR = -2
+FESPMV_ERR_OOM = -3
+FESPMV_ERR_CUDA = -4
+FESPMV_ERR_BREAKDOWN = -5
+FESPMV_ERR_NOT_CONVERGED = -6
+FESPMV_ERR_UNSUPPORTED = -7
+
+FESPMV_FMT_CSR = 0
+FESPMV_FMT_SLICED = 1
+FESPMV_REORDER_NONE = 0
+FESPMV_REORDER_MORTON = 1
+FESPMV_PREC_F64 = 1
+FESPMV_PREC_F32 = 2
+FESPMV_IO_PERMUTED = 1
+FESPMV_IO_HOST = 2
+FESPMV_EXPORT_PERM = 0
+FESPMV_EXPORT_META = 1
+FESPMV_EXPORT_COLS = 2
+FESPMV_EXPORT_VALUES = 3
+FESPMV_EXPORT_SRCMAP = 4
+FESPMV_EXPORT_DIAG = 5
+
+
+class FespmvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class fespmv_options(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in
+                ("format", "reorder", "sigma", "threshold", "vec", "csr_lanes", "precisions",
+                 "block")]
+
+
+class fespmv_mesh_info(ctypes.Structure):
+    _fields_ = [("dofs_per_node", ctypes.c_int32), ("node_xyz", ctypes.c_void_p)]
+
+
+class fespmv_info(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_slices", ctypes.c_int64),
+                ("packed_len", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("format", ctypes.c_int32), ("vec", ctypes.c_int32)]
+
+
+def _load():
+    path = _build.build()
+    try:
+        return ctypes.CDLL(path)
+    except OSError as e:  # pragma: no cover - a broken build is an error, not a fallback
+        raise ImportError(f"libfespmv could not be loaded from {path}: {e}") from e
+
+
+LIB_PATH = _build.SO
+_lib = _load()
+_P = ctypes.c_void_p
+_i32, _i64 = ctypes.c_int32, ctypes.c_int64
+_lib.spmv_create.argtypes = [ctypes.POINTER(_P), _i64, _P, _P, _P, ctypes.POINTER(fespmv_mesh_info),
+                             ctypes.POINTER(fespmv_options), _P]
+_lib.spmv_create.restype = ctypes.c_int
+_lib.spmv_destroy.argtypes = [_P]
+_lib.spmv_destroy.restype = None
+_lib.spmv_apply.argtypes = [_P, _P, _P, _i32, _P]
+_lib.spmv_apply.restype = ctypes.c_int
+_lib.spmv_permute.argtypes = [_P, _P, _P, _i32, _P]
+_lib.spmv_permute.restype = ctypes.c_int
+_lib.spmv_update_values.argtypes = [_P, _P, _i32, _P]
+_lib.spmv_update_values.restype = ctypes.c_int
+_lib.spmv_get_info.argtypes = [_P, ctypes.POINTER(fespmv_info)]
+_lib.spmv_get_info.restype = ctypes.c_int
+_lib.spmv_export.argtypes = [_P, _i32, _P, ctypes.c_size_t, _P]
+_lib.spmv_export.restype = ctypes.c_int
+_lib.spmv_plan.argtypes = [_i64, _P, _P, ctypes.POINTER(fespmv_mesh_info),
+                           ctypes.POINTER(fespmv_options), ctypes.POINTER(fespmv_info), _P, _P, _P, _P]
+_lib.spmv_plan.restype = ctypes.c_int
+_lib.fespmv_status_string.argtypes = [ctypes.c_int]
+_lib.fespmv_status_string.restype = ctypes.c_char_p
+_lib.fespmv_last_error.argtypes = []
+_lib.fespmv_last_error.restype = ctypes.c_char_p
+
+
+def lib():
+    """The loaded ctypes library (for callers that marshal arguments themselves)."""
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FESPMV_OK:
+        msg = _lib.fespmv_last_error().decode() or _lib.fespmv_status_string(rc).decode()
+        raise FespmvError(rc, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """Address of a torch tensor or numpy array (contiguity is the caller's job)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+class Matrix:
+    """A handle returned by spmv_create (owns device memory until spmv_destroy)."""
+
+    def __init__(self, handle: ctypes.c_void_p, n_rows: int, nnz: int):
+        self.handle = handle
+        self.n_rows = n_rows
+        self.nnz = nnz
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.spmv_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=FESPMV_FMT_SLICED,
+                reorder=None, sigma=0, threshold=0, vec=0, csr_lanes=0, precisions=0, block=0,
+                stream=None) -> Matrix:
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
+    if reorder is None:
+        reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
+    opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block)
+    mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
+    h = _P()
+    n = len(rowptr) - 1
+    _check(_lib.spmv_create(ctypes.byref(h), n, _ptr(rowptr), _ptr(colind), _ptr(values),
+                            ctypes.byref(mesh), ctypes.byref(opts), _stream(stream)))
+    return Matrix(h, n, int(rowptr[-1]))
+
+
+def spmv_destroy(A: Matrix):
+    if A.handle:
+        _lib.spmv_destroy(A.handle)
+        A.handle = None
+
+
+def spmv_apply(A: Matrix, x, y, flags=0, stream=None):
+    if isinstance(x, np.ndarray):
+        flags |= FESPMV_IO_HOST
+    _check(_lib.spmv_apply(A.handle, _ptr(x), _ptr(y), flags, _stream(stream)))
+    return y
+
+
+def spmv_permute(A: Matrix, x, out, direction=0, stream=None):
+    _check(_lib.spmv_permute(A.handle, _ptr(x), _ptr(out), direction, _stream(stream)))
+    return out
+
+
+def spmv_update_values(A: Matrix, values, flags=0, stream=None):
+    if isinstance(values, np.ndarray):
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        flags |= FESPMV_IO_HOST
+    _check(_lib.spmv_update_values(A.handle, _ptr(values), flags, _stream(stream)))
+
+
+def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
+              threshold=0, vec=0) -> dict:
+    """Host-only planning: returns perm, meta (S x 4), cols and srcmap as numpy arrays."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
+    if reorder is None:
+        reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0)
+    mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
+    info = fespmv_info()
+    n = len(rowptr) - 1
+    args = (n, _ptr(rowptr), _ptr(colind), ctypes.byref(mesh), ctypes.byref(opts), ctypes.byref(info))
+    _check(_lib.spmv_plan(*args, None, None, None, None))
+    perm = np.zeros(max(n, 1), np.int32)
+    meta = np.zeros(max(info.n_slices * 4, 1), np.uint32)
+    cols = np.zeros(max(info.packed_len, 1), np.int32)
+    src = np.zeros(max(info.packed_len, 1), np.int64)
+    _check(_lib.spmv_plan(*args, _ptr(perm), _ptr(meta), _ptr(cols), _ptr(src)))
+    return dict(perm=perm[:n], meta=meta[:info.n_slices * 4].reshape(-1, 4),
+                cols=cols[:info.packed_len], srcmap=src[:info.packed_len])
+
+
+def spmv_get_info(A: Matrix) -> dict:
+    info = fespmv_info()
+    _check(_lib.spmv_get_info(A.handle, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in fespmv_info._fields_}
+
+
+_EXPORT_DTYPES = {FESPMV_EXPORT_PERM: (np.int32, "n_rows"), FESPMV_EXPORT_META: (np.uint32, "meta"),
+                  FESPMV_EXPORT_COLS: (np.int32, "packed_len"),
+                  FESPMV_EXPORT_VALUES: (np.float64, "packed_len"),
+                  FESPMV_EXPORT_SRCMAP: (np.int64, "packed_len"),
+                  FESPMV_EXPORT_DIAG: (np.float64, "n_rows")}
+
+
+def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
+    info = spmv_get_info(A)
+    dt, key = _EXPORT_DTYPES[what]
+    count = info["n_slices"] * 4 if key == "meta" else info[key]
+    out = np.zeros(max(count, 1), dtype=dt)
+    _check(_lib.spmv_export(A.handle, what, _ptr(out), out.nbytes, _stream(stream)))
+    out = out[:count]
+    return out.reshape(-1, 4) if key == "meta" else out

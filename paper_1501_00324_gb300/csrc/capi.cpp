@@ -1,0 +1,399 @@
+// C ABI entry points (include/fespmv.h): handle lifetime, SpMV, permutation,
+// value refresh and inspection.  Every entry point catches C++ exceptions and
+// turns them into status codes.
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace fespmv {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s failed: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FESPMV_ERR_OOM : FESPMV_ERR_CUDA;
+}
+
+int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;  // keep every pointer valid for empty matrices
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu bytes) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FESPMV_ERR_OOM : FESPMV_ERR_CUDA;
+    }
+    A->device_bytes += (int64_t)bytes;
+    return FESPMV_OK;
+}
+
+static void free_handle(fespmv_mat* A) {
+    if (!A) return;
+    void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
+                    A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
+                    A->d_vals_in};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete A;
+}
+
+static int ck(cudaError_t e, const char* what) {
+    return e == cudaSuccess ? FESPMV_OK : cuda_fail(e, what);
+}
+
+#define TRY(expr)                 \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != FESPMV_OK) {   \
+            free_handle(A);       \
+            return rc_;           \
+        }                         \
+    } while (0)
+
+static bool pow2_upto32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
+
+static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                       const double* values, const fespmv_mesh_info* mesh,
+                       const fespmv_options* opts_in, cudaStream_t s) {
+    if (!out) { set_error("out is NULL"); return FESPMV_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (n < 0 || n > (int64_t)INT32_MAX - 1) {
+        set_error("n_rows %lld outside [0, 2^31-1)", (long long)n);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (!rowptr || (n > 0 && rowptr[n] > 0 && (!colind || !values))) {
+        set_error("rowptr, colind or values is NULL");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    fespmv_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts_in) o = *opts_in;
+    if (o.format != FESPMV_FMT_CSR && o.format != FESPMV_FMT_SLICED) {
+        set_error("unknown format %d", o.format); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.vec == 0) o.vec = 2;
+    if (o.vec != 1 && o.vec != 2 && o.vec != 4) {
+        set_error("vec must be 1, 2 or 4 (got %d)", o.vec); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.csr_lanes == 0) o.csr_lanes = 1;
+    if (!pow2_upto32(o.csr_lanes)) {
+        set_error("csr_lanes must be a power of two <= 32 (got %d)", o.csr_lanes);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.block == 0) o.block = 256;
+    if (o.block < 32 || o.block > 1024 || o.block % 32) {
+        set_error("block must be a multiple of 32 in [32, 1024] (got %d)", o.block);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.format == FESPMV_FMT_SLICED && o.block > 256) {
+        set_error("SLICED kernels take at most 256 threads per block (got %d)", o.block);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.sigma < 0 || o.threshold < 0) {
+        set_error("sigma and threshold must be >= 0"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.reorder == FESPMV_REORDER_MORTON && (!mesh || !mesh->node_xyz) && o.format == FESPMV_FMT_SLICED) {
+        set_error("REORDER_MORTON needs mesh->node_xyz"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32)) {
+        set_error("unknown precision bits 0x%x", o.precisions); return FESPMV_ERR_INVALID_ARG;
+    }
+    int rc = validate_csr(n, rowptr, colind);
+    if (rc) return rc;
+    const int64_t nnz = rowptr[n];
+    int dpn = (mesh && mesh->dofs_per_node > 0) ? mesh->dofs_per_node : 1;
+
+    fespmv_mat* A = new fespmv_mat();
+    A->n = n;
+    A->nnz = nnz;
+    A->format = o.format;
+    A->block = o.block;
+    A->csr_lanes = o.csr_lanes;
+    A->vec = o.vec;
+    A->precisions = o.precisions | FESPMV_PREC_F64;
+
+    // values reach the device once; the packed array is filled by a gather kernel
+    TRY(device_alloc(A, (void**)&A->d_vals_in, sizeof(double) * nnz, "input values"));
+    TRY(ck(cudaMemcpyAsync(A->d_vals_in, values, sizeof(double) * nnz, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+    TRY(device_alloc(A, (void**)&A->d_diagpos, sizeof(int64_t) * n, "diagonal map"));
+    TRY(device_alloc(A, (void**)&A->d_diag, sizeof(double) * n, "diagonal"));
+
+    if (o.format == FESPMV_FMT_CSR) {
+        // check duplicates and locate diagonals
+        std::vector<int64_t> diagpos((size_t)n, -1);
+        std::vector<int32_t> cols;
+        for (int64_t i = 0; i < n; ++i) {
+            cols.assign(colind + rowptr[i], colind + rowptr[i + 1]);
+            std::sort(cols.begin(), cols.end());
+            for (size_t k = 1; k < cols.size(); ++k)
+                if (cols[k] == cols[k - 1]) {
+                    set_error("duplicate column %d in row %lld", cols[k], (long long)i);
+                    free_handle(A);
+                    return FESPMV_ERR_BAD_CSR;
+                }
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+                if (colind[p] == i) diagpos[(size_t)i] = p;
+        }
+        TRY(device_alloc(A, (void**)&A->d_rowptr, sizeof(int64_t) * (n + 1), "rowptr"));
+        TRY(device_alloc(A, (void**)&A->d_colind, sizeof(int32_t) * nnz, "colind"));
+        TRY(device_alloc(A, (void**)&A->d_val, sizeof(double) * nnz, "values"));
+        TRY(ck(cudaMemcpyAsync(A->d_rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_colind, colind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_diagpos, diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(launch_fill_values(A, A->d_vals_in, s));
+        TRY(ck(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    } else {
+        Plan plan;
+        TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
+                       o.threshold, o.vec, plan));
+        A->n_slices = plan.n_slices;
+        A->packed_len = plan.packed_len;
+        TRY(device_alloc(A, (void**)&A->d_meta, sizeof(uint4) * plan.n_slices, "slice metadata"));
+        TRY(device_alloc(A, (void**)&A->d_col, sizeof(int32_t) * plan.packed_len, "packed columns"));
+        TRY(device_alloc(A, (void**)&A->d_val, sizeof(double) * plan.packed_len, "packed values"));
+        TRY(device_alloc(A, (void**)&A->d_src, sizeof(int64_t) * plan.packed_len, "value map"));
+        TRY(device_alloc(A, (void**)&A->d_perm, sizeof(int32_t) * n, "permutation"));
+        TRY(device_alloc(A, (void**)&A->d_pinv, sizeof(int32_t) * n, "inverse permutation"));
+        TRY(device_alloc(A, (void**)&A->d_xp, sizeof(double) * n, "permuted x"));
+        TRY(device_alloc(A, (void**)&A->d_yp, sizeof(double) * n, "permuted y"));
+        TRY(ck(cudaMemcpyAsync(A->d_meta, plan.meta.data(), sizeof(uint4) * plan.n_slices, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_col, plan.col.data(), sizeof(int32_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_src, plan.src.data(), sizeof(int64_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_perm, plan.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_pinv, plan.pinv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(ck(cudaMemcpyAsync(A->d_diagpos, plan.diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(launch_fill_values(A, A->d_vals_in, s));
+        // host vectors must stay alive until the copies finish
+        TRY(ck(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    }
+    cudaFree(A->d_vals_in);     // staging is re-allocated by spmv_update_values when needed
+    A->device_bytes -= (int64_t)(nnz > 0 ? sizeof(double) * nnz : 16);
+    A->d_vals_in = nullptr;
+    *out = A;
+    return FESPMV_OK;
+}
+
+}  // namespace fespmv
+
+using namespace fespmv;
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                    \
+    }                                                                \
+    catch (const std::bad_alloc&) {                                  \
+        set_error("host allocation failed");                         \
+        return FESPMV_ERR_OOM;                                       \
+    }                                                                \
+    catch (...) {                                                    \
+        set_error("unexpected C++ exception");                       \
+        return FESPMV_ERR_INVALID_ARG;                               \
+    }
+
+extern "C" {
+
+int spmv_create(fespmv_mat_t* out, int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
+                const double* values, const fespmv_mesh_info* mesh, const fespmv_options* opts,
+                fespmv_stream_t stream) {
+    GUARD_BEGIN
+    return create_impl(out, n_rows, rowptr, colind, values, mesh, opts, (cudaStream_t)stream);
+    GUARD_END
+}
+
+void spmv_destroy(fespmv_mat_t A) {
+    try {
+        free_handle(A);
+    } catch (...) {
+    }
+}
+
+static int ensure_host_staging(fespmv_mat* A) {
+    if (!A->d_xh) {
+        int rc = device_alloc(A, (void**)&A->d_xh, sizeof(double) * A->n, "host-I/O x");
+        if (rc) return rc;
+    }
+    if (!A->d_yh) {
+        int rc = device_alloc(A, (void**)&A->d_yh, sizeof(double) * A->n, "host-I/O y");
+        if (rc) return rc;
+    }
+    return FESPMV_OK;
+}
+
+int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!A || (A->n > 0 && (!x || !y))) { set_error("null argument"); return FESPMV_ERR_INVALID_ARG; }
+    if (flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST)) {
+        set_error("unknown flags 0x%x", flags); return FESPMV_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->n == 0) return FESPMV_OK;
+    const double* xd = x;
+    double* yd = y;
+    if (flags & FESPMV_IO_HOST) {
+        int rc = ensure_host_staging(A);
+        if (rc) return rc;
+        FESPMV_CUDA(cudaMemcpyAsync(A->d_xh, x, sizeof(double) * A->n, cudaMemcpyHostToDevice, s));
+        xd = A->d_xh;
+        yd = A->d_yh;
+    }
+    int rc;
+    if (A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED)) {
+        if ((rc = launch_gather(xd, A->d_perm, A->d_xp, A->n, s))) return rc;
+        if ((rc = launch_spmv(A, A->d_xp, A->d_yp, s))) return rc;
+        if ((rc = launch_gather(A->d_yp, A->d_pinv, yd, A->n, s))) return rc;
+    } else {
+        if ((rc = launch_spmv(A, xd, yd, s))) return rc;
+    }
+    if (flags & FESPMV_IO_HOST) {
+        FESPMV_CUDA(cudaMemcpyAsync(y, yd, sizeof(double) * A->n, cudaMemcpyDeviceToHost, s));
+        FESPMV_CUDA(cudaStreamSynchronize(s));
+    }
+    return FESPMV_OK;
+    GUARD_END
+}
+
+int spmv_permute(fespmv_mat_t A, const double* in, double* out, int32_t direction,
+                 fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!A || (A->n > 0 && (!in || !out)) || (direction != 0 && direction != 1)) {
+        set_error("bad argument"); return FESPMV_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->n == 0) return FESPMV_OK;
+    if (A->format != FESPMV_FMT_SLICED) {
+        FESPMV_CUDA(cudaMemcpyAsync(out, in, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
+        return FESPMV_OK;
+    }
+    return launch_gather(in, direction == 0 ? A->d_perm : A->d_pinv, out, A->n, s);
+    GUARD_END
+}
+
+int spmv_update_values(fespmv_mat_t A, const double* values, int32_t flags, fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!A || (A->nnz > 0 && !values) || (flags & ~FESPMV_IO_HOST)) {
+        set_error("bad argument"); return FESPMV_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* src = values;
+    if (flags & FESPMV_IO_HOST) {
+        if (!A->d_vals_in) {
+            int rc = device_alloc(A, (void**)&A->d_vals_in, sizeof(double) * A->nnz, "value staging");
+            if (rc) return rc;
+        }
+        FESPMV_CUDA(cudaMemcpyAsync(A->d_vals_in, values, sizeof(double) * A->nnz, cudaMemcpyHostToDevice, s));
+        src = A->d_vals_in;
+    }
+    int rc = launch_fill_values(A, src, s);
+    if (rc) return rc;
+    if (flags & FESPMV_IO_HOST) FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+    GUARD_END
+}
+
+int spmv_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, const fespmv_mesh_info* mesh,
+              const fespmv_options* opts_in, fespmv_info* info, int32_t* perm, uint32_t* meta,
+              int32_t* cols, int64_t* srcmap) {
+    GUARD_BEGIN
+    if (!rowptr || !info || n < 0 || n > (int64_t)INT32_MAX - 1) {
+        set_error("bad argument"); return FESPMV_ERR_INVALID_ARG;
+    }
+    fespmv_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts_in) o = *opts_in;
+    if (o.vec == 0) o.vec = 2;
+    if ((o.vec != 1 && o.vec != 2 && o.vec != 4) || o.sigma < 0 || o.threshold < 0) {
+        set_error("bad options"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.reorder == FESPMV_REORDER_MORTON && (!mesh || !mesh->node_xyz)) {
+        set_error("REORDER_MORTON needs mesh->node_xyz"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (n > 0 && rowptr[n] > 0 && !colind) { set_error("colind is NULL"); return FESPMV_ERR_INVALID_ARG; }
+    int rc = validate_csr(n, rowptr, colind);
+    if (rc) return rc;
+    Plan plan;
+    rc = build_plan(n, rowptr, colind, (mesh && mesh->dofs_per_node > 0) ? mesh->dofs_per_node : 1,
+                    mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma, o.threshold, o.vec, plan);
+    if (rc) return rc;
+    info->n_rows = n;
+    info->nnz = rowptr[n];
+    info->n_slices = plan.n_slices;
+    info->packed_len = plan.packed_len;
+    info->device_bytes = 0;
+    info->format = FESPMV_FMT_SLICED;
+    info->vec = o.vec;
+    if (perm) std::memcpy(perm, plan.perm.data(), sizeof(int32_t) * (size_t)n);
+    if (meta) std::memcpy(meta, plan.meta.data(), sizeof(uint32_t) * 4 * (size_t)plan.n_slices);
+    if (cols) std::memcpy(cols, plan.col.data(), sizeof(int32_t) * (size_t)plan.packed_len);
+    if (srcmap) std::memcpy(srcmap, plan.src.data(), sizeof(int64_t) * (size_t)plan.packed_len);
+    return FESPMV_OK;
+    GUARD_END
+}
+
+int spmv_get_info(fespmv_mat_t A, fespmv_info* info) {
+    if (!A || !info) { set_error("null argument"); return FESPMV_ERR_INVALID_ARG; }
+    info->n_rows = A->n;
+    info->nnz = A->nnz;
+    info->n_slices = A->n_slices;
+    info->packed_len = A->format == FESPMV_FMT_SLICED ? A->packed_len : A->nnz;
+    info->device_bytes = A->device_bytes;
+    info->format = A->format;
+    info->vec = A->vec;
+    return FESPMV_OK;
+}
+
+int spmv_export(fespmv_mat_t A, int32_t what, void* out, size_t bytes, fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!A || !out) { set_error("null argument"); return FESPMV_ERR_INVALID_ARG; }
+    const void* src = nullptr;
+    size_t need = 0;
+    bool sliced = A->format == FESPMV_FMT_SLICED;
+    switch (what) {
+        case FESPMV_EXPORT_PERM: src = A->d_perm; need = 4 * (size_t)A->n; break;
+        case FESPMV_EXPORT_META: src = A->d_meta; need = 16 * (size_t)A->n_slices; break;
+        case FESPMV_EXPORT_COLS: src = A->d_col; need = 4 * (size_t)A->packed_len; break;
+        case FESPMV_EXPORT_VALUES:
+            src = A->d_val; need = 8 * (size_t)(sliced ? A->packed_len : A->nnz); break;
+        case FESPMV_EXPORT_SRCMAP: src = A->d_src; need = 8 * (size_t)A->packed_len; break;
+        case FESPMV_EXPORT_DIAG: src = A->d_diag; need = 8 * (size_t)A->n; break;
+        default: set_error("unknown export %d", what); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (!sliced && what != FESPMV_EXPORT_VALUES && what != FESPMV_EXPORT_DIAG) {
+        set_error("array %d exists only for SLICED handles", what); return FESPMV_ERR_UNSUPPORTED;
+    }
+    if (bytes < need) { set_error("buffer of %zu bytes, need %zu", bytes, need); return FESPMV_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (need) FESPMV_CUDA(cudaMemcpyAsync(out, src, need, cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+    GUARD_END
+}
+
+const char* fespmv_status_string(int status) {
+    switch (status) {
+        case FESPMV_OK: return "ok";
+        case FESPMV_ERR_INVALID_ARG: return "invalid argument";
+        case FESPMV_ERR_BAD_CSR: return "malformed CSR";
+        case FESPMV_ERR_OOM: return "out of memory";
+        case FESPMV_ERR_CUDA: return "CUDA error";
+        case FESPMV_ERR_BREAKDOWN: return "CG breakdown";
+        case FESPMV_ERR_NOT_CONVERGED: return "CG not converged";
+        case FESPMV_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* fespmv_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

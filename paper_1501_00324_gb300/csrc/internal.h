@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fespmv.h"
+
+namespace fespmv {
+
+// Per-thread last error message (fespmv_last_error).
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FESPMV_CUDA(call)                                         \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::fespmv::cuda_fail(e_, #call); \
+    } while (0)
+
+// Host-side result of reordering and packing (see plan.cpp).
+struct Plan {
+    std::vector<int32_t> perm;      // P[new] = old
+    std::vector<int32_t> pinv;      // Pinv[old] = new
+    std::vector<uint32_t> meta;     // 4 per slice: offset/32, width, first row, log2 T
+    std::vector<int32_t> col;       // packed columns (new numbering), -1 = padding
+    std::vector<int64_t> src;       // packed entry -> input CSR position, -1 = padding
+    std::vector<int64_t> diagpos;   // new row -> input CSR position of its diagonal, -1 none
+    int64_t n_slices = 0;
+    int64_t packed_len = 0;
+};
+
+// Builds the locality order, windowed length sort, symmetric renumbering with
+// sorted columns and the warp-slice packing.  Returns FESPMV_OK or an error code
+// (message set).
+int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
+               const double* node_xyz, int reorder, int sigma, int threshold, int vec,
+               Plan& out);
+
+// Validates a host CSR (monotone offsets, columns in range); duplicates are
+// detected by build_plan for SLICED and by validate_csr_rows for CSR.
+int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind);
+
+}  // namespace fespmv
+
+// The opaque handle.
+struct fespmv_mat {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int format = FESPMV_FMT_CSR;
+    int block = 256;
+    int precisions = FESPMV_PREC_F64;
+    int64_t device_bytes = 0;
+
+    // FESPMV_FMT_CSR
+    int csr_lanes = 1;
+    int64_t* d_rowptr = nullptr;
+    int32_t* d_colind = nullptr;
+    double* d_val = nullptr;          // CSR values, or packed values for SLICED
+
+    // FESPMV_FMT_SLICED
+    int vec = 2;
+    int64_t n_slices = 0;
+    int64_t packed_len = 0;
+    uint4* d_meta = nullptr;
+    int32_t* d_col = nullptr;
+    int32_t* d_perm = nullptr;
+    int32_t* d_pinv = nullptr;
+    int64_t* d_src = nullptr;
+
+    // both formats
+    int64_t* d_diagpos = nullptr;     // row (handle numbering) -> input CSR position of diagonal
+    double* d_diag = nullptr;         // diag(A) in handle numbering
+    double* d_xp = nullptr;           // permuted-I/O scratch (n each)
+    double* d_yp = nullptr;
+    double* d_xh = nullptr;           // host-I/O staging (n each), allocated on first use
+    double* d_yh = nullptr;
+    double* d_vals_in = nullptr;      // update_values staging (nnz), allocated on first use
+};
+
+namespace fespmv {
+
+int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what);
+
+// Kernel launchers (spmv_kernels.cu); all enqueue on `s` and return FESPMV_OK or
+// FESPMV_ERR_CUDA.
+int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
+int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
+int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
+
+}  // namespace fespmv

@@ -1,0 +1,208 @@
+// Host planner: locality order, windowed row-length sort, symmetric renumbering
+// with sorted columns, and warp-slice packing.
+//
+// Paper mapping (arXiv:1501.00324):
+//   Sec. 5.1 (ELL-WARP, K1): sort rows by length, group 32 rows per warp, pad
+//            each warp to its own longest row, store column-major.
+//   Sec. 5.2 (K1r): renumber x and the columns with the same permutation,
+//            x'(.) = x(P(.)), c' = P^-1(c), so results need no remap on store.
+//   Sec. 5.3 (K1rs): sort the renumbered columns inside each row, moving the
+//            values with them.
+//   Sec. 5.4 (K2): with a threshold tau, a 32-row group whose longest row
+//            needs more than tau steps per lane gets T = 2, 4, ... 32 lanes per
+//            row (T the smallest power of two with ceil(maxlen/T) <= tau) and
+//            splits into T warps of 32/T rows.
+// Design choices of this library (not in the paper): the length sort is stable
+// and confined to windows of `sigma` rows of a locality order (the Morton curve
+// of the node coordinates, dofs of a node kept adjacent), so that rows handled
+// by one warp stay close in the mesh and their x gathers share cache lines; and
+// each lane reads V consecutive entries per load (V = 1 is the paper's layout).
+//
+// Compiled with -ffp-contract=off: the Morton quantisation is a floating-point
+// decision that must round the same way as the reference definition.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace fespmv {
+
+static const int kMortonBits = 21;
+
+int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind) {
+    if (rowptr[0] != 0) {
+        set_error("rowptr[0] = %lld, expected 0", (long long)rowptr[0]);
+        return FESPMV_ERR_BAD_CSR;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) {
+            set_error("rowptr decreases at row %lld", (long long)i);
+            return FESPMV_ERR_BAD_CSR;
+        }
+    const int64_t nnz = rowptr[n];
+    for (int64_t p = 0; p < nnz; ++p)
+        if (colind[p] < 0 || (int64_t)colind[p] >= n) {
+            set_error("column index %d at position %lld outside [0, %lld)", colind[p],
+                      (long long)p, (long long)n);
+            return FESPMV_ERR_BAD_CSR;
+        }
+    return FESPMV_OK;
+}
+
+// Nodes in Morton order of their coordinates (ties by node number).
+static void morton_node_order(int64_t n_nodes, const double* xyz, std::vector<int64_t>& order) {
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = hi[d] = n_nodes ? xyz[d] : 0.0;
+    }
+    for (int64_t i = 0; i < n_nodes; ++i)
+        for (int d = 0; d < 3; ++d) {
+            double v = xyz[i * 3 + d];
+            if (v < lo[d]) lo[d] = v;
+            if (v > hi[d]) hi[d] = v;
+        }
+    const double scale = (double)((1u << kMortonBits) - 1u);
+    std::vector<uint64_t> code((size_t)n_nodes);
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        uint64_t q[3];
+        for (int d = 0; d < 3; ++d) {
+            if (hi[d] > lo[d]) {
+                double t = (xyz[i * 3 + d] - lo[d]) / (hi[d] - lo[d]);
+                t = t * scale;
+                q[d] = (uint64_t)std::floor(t);
+            } else {
+                q[d] = 0;
+            }
+        }
+        uint64_t c = 0;
+        for (int b = 0; b < kMortonBits; ++b)
+            for (int d = 0; d < 3; ++d) c |= ((q[d] >> b) & 1ull) << (3 * b + (2 - d));
+        code[(size_t)i] = c;
+    }
+    order.resize((size_t)n_nodes);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return code[(size_t)a] < code[(size_t)b]; });
+}
+
+int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
+               const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out) {
+    if (dpn <= 0) dpn = 1;
+    if (n % dpn != 0) {
+        set_error("n_rows %lld is not a multiple of dofs_per_node %d", (long long)n, dpn);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    const int64_t n_nodes = n / dpn;
+
+    // 1. locality order of nodes, expanded to rows (dofs of a node adjacent)
+    std::vector<int64_t> nodes;
+    if (reorder == FESPMV_REORDER_MORTON && node_xyz) {
+        morton_node_order(n_nodes, node_xyz, nodes);
+    } else {
+        nodes.resize((size_t)n_nodes);
+        std::iota(nodes.begin(), nodes.end(), (int64_t)0);
+    }
+    out.perm.resize((size_t)n);
+    for (int64_t k = 0; k < n_nodes; ++k)
+        for (int c = 0; c < dpn; ++c) out.perm[(size_t)(k * dpn + c)] = (int32_t)(nodes[(size_t)k] * dpn + c);
+
+    // 2. stable longest-first sort inside windows of sigma rows
+    if (sigma > 0) {
+        for (int64_t s = 0; s < n; s += sigma) {
+            int64_t e = std::min<int64_t>(n, s + sigma);
+            std::stable_sort(out.perm.begin() + s, out.perm.begin() + e, [&](int32_t a, int32_t b) {
+                return (rowptr[a + 1] - rowptr[a]) > (rowptr[b + 1] - rowptr[b]);
+            });
+        }
+    }
+    out.pinv.assign((size_t)n, 0);
+    for (int64_t i = 0; i < n; ++i) out.pinv[(size_t)out.perm[(size_t)i]] = (int32_t)i;
+
+    // 3. permuted rows with renumbered, sorted columns: (new col, input position)
+    std::vector<int64_t> rp2((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = out.perm[(size_t)i];
+        rp2[(size_t)i + 1] = rp2[(size_t)i] + (rowptr[o + 1] - rowptr[o]);
+    }
+    const int64_t nnz = rp2[(size_t)n];
+    std::vector<int32_t> c2((size_t)nnz);
+    std::vector<int64_t> s2((size_t)nnz);
+    out.diagpos.assign((size_t)n, -1);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = out.perm[(size_t)i];
+        row.clear();
+        for (int64_t p = rowptr[o]; p < rowptr[o + 1]; ++p)
+            row.emplace_back(out.pinv[(size_t)colind[p]], p);
+        std::sort(row.begin(), row.end());
+        for (size_t k = 0; k < row.size(); ++k) {
+            if (k > 0 && row[k].first == row[k - 1].first) {
+                set_error("duplicate column %d in row %lld", colind[row[k].second], (long long)o);
+                return FESPMV_ERR_BAD_CSR;
+            }
+            c2[(size_t)rp2[(size_t)i] + k] = row[k].first;
+            s2[(size_t)rp2[(size_t)i] + k] = row[k].second;
+            if (row[k].first == (int32_t)i) out.diagpos[(size_t)i] = row[k].second;
+        }
+    }
+
+    // 4. slice plan: per 32-row group choose T, split into T warps of 32/T rows
+    struct Slice { int64_t r0; int nr; int T; int64_t w; };
+    std::vector<Slice> slices;
+    for (int64_t g0 = 0; g0 < n; g0 += 32) {
+        int m = (int)std::min<int64_t>(32, n - g0);
+        int64_t maxlen = 0;
+        for (int r = 0; r < m; ++r) maxlen = std::max(maxlen, rp2[(size_t)(g0 + r + 1)] - rp2[(size_t)(g0 + r)]);
+        int T = 1;
+        if (threshold > 0)
+            while (T < 32 && (maxlen + T - 1) / T > threshold) T *= 2;
+        int rpw = 32 / T;
+        for (int j = 0; j < T; ++j) {
+            int64_t r0 = g0 + (int64_t)j * rpw;
+            if (r0 >= g0 + m) break;
+            int nr = (int)std::min<int64_t>(rpw, g0 + m - r0);
+            int64_t ml = 0;
+            for (int r = 0; r < nr; ++r) ml = std::max(ml, rp2[(size_t)(r0 + r + 1)] - rp2[(size_t)(r0 + r)]);
+            int64_t w = (ml + T - 1) / T;
+            w = (w + V - 1) / V * V;
+            slices.push_back({r0, nr, T, w});
+        }
+    }
+    out.n_slices = (int64_t)slices.size();
+    int64_t total = 0;
+    for (const Slice& s : slices) total += 32 * s.w;
+    if (total / 32 > (int64_t)UINT32_MAX) {
+        set_error("packed matrix too large for 32-bit slice offsets");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    out.packed_len = total;
+    out.col.assign((size_t)total, -1);
+    out.src.assign((size_t)total, -1);
+    out.meta.assign((size_t)out.n_slices * 4, 0);
+    int64_t off = 0;
+    for (size_t si = 0; si < slices.size(); ++si) {
+        const Slice& s = slices[si];
+        int lt = 0;
+        while ((1 << lt) < s.T) ++lt;
+        out.meta[si * 4 + 0] = (uint32_t)(off / 32);
+        out.meta[si * 4 + 1] = (uint32_t)s.w;
+        out.meta[si * 4 + 2] = (uint32_t)s.r0;
+        out.meta[si * 4 + 3] = (uint32_t)lt;
+        for (int r = 0; r < s.nr; ++r) {
+            int64_t a = rp2[(size_t)(s.r0 + r)], b = rp2[(size_t)(s.r0 + r + 1)];
+            for (int64_t k = 0; k < b - a; ++k) {
+                int64_t lane = (int64_t)r * s.T + k % s.T;
+                int64_t step = k / s.T;
+                int64_t pos = off + (step / V) * 32 * V + lane * V + step % V;
+                out.col[(size_t)pos] = c2[(size_t)(a + k)];
+                out.src[(size_t)pos] = s2[(size_t)(a + k)];
+            }
+        }
+        off += 32 * s.w;
+    }
+    return FESPMV_OK;
+}
+
+}  // namespace fespmv
