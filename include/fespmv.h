@@ -178,6 +178,56 @@ int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
               const fespmv_mesh_info* mesh, const fespmv_options* opts, fespmv_info* info,
               int32_t* perm, uint32_t* meta, int32_t* cols, int64_t* srcmap);
 
+/* ---- conjugate gradients ----------------------------------------------------------- */
+#define FESPMV_CG_F64          0  /* FP64 Jacobi-PCG on the handle's FP64 values */
+#define FESPMV_CG_X0           4  /* flag: x holds the initial guess (otherwise x0 = 0) */
+#define FESPMV_CG_NO_PRECOND   8  /* flag: plain CG instead of Jacobi-PCG */
+
+typedef struct {
+    double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2; 0 = 1e-10 */
+    int32_t max_iter;      /* iteration limit over all restarts; 0 = 100000 */
+    int32_t precision;     /* FESPMV_CG_F64 */
+    int32_t flags;         /* FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 |
+                              FESPMV_CG_NO_PRECOND */
+    int32_t max_restarts;  /* restarts from the true residual; 0 = 3, < 0 = none */
+    int32_t check_every;   /* iterations per graph launch between host polls; 0 = 16 */
+    int32_t reserved;
+} cg_options;
+
+typedef struct {
+    int32_t status;        /* FESPMV_OK, FESPMV_ERR_NOT_CONVERGED or FESPMV_ERR_BREAKDOWN */
+    int32_t iters;         /* CG iterations over all restarts */
+    int32_t restarts;      /* restarts taken */
+    int32_t reserved;
+    double relres;         /* recurrence residual ||r_k|| / ||b|| at exit */
+    double true_relres;    /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+} cg_result;
+
+/*
+ * cg_solve -- solve A x = b by Jacobi-preconditioned conjugate gradients, the
+ * linear solver of the paper's Newton step K dx = R (Sec. 2.1; Jacobi
+ * preconditioning as in Sec. 2.1), textbook Hestenes-Stiefel recurrences:
+ *   r = b - A x0, z = D^-1 r, p = z, rho = r.z;
+ *   repeat q = A p; alpha = rho / p.q; x += alpha p; r -= alpha q;
+ *          stop when ||r|| <= tol ||b||; z = D^-1 r; beta = r.z / rho; p = z + beta p.
+ * After the recurrence stops, ||b - A x|| is recomputed in FP64; above tol the
+ * iteration restarts from x (max_restarts times).
+ *   b, x   n_rows doubles (device unless FESPMV_IO_HOST; permuted numbering with
+ *          FESPMV_IO_PERMUTED); x is overwritten with the solution.
+ *   opts   NULL = defaults;  res  optional result record.
+ * The matrix must be symmetric positive definite with a positive diagonal.
+ * Work runs on `stream` as CUDA graphs of check_every iterations with the
+ * scalars kept on the device; the call blocks the host until the solve ends
+ * (it polls a status word after each graph).  Dot products are reduced in a
+ * fixed order, so repeated solves of the same system give bitwise-equal x.
+ * Workspace (6 vectors of n_rows doubles) is allocated on the first call and
+ * kept by the handle.  Returns FESPMV_OK, FESPMV_ERR_NOT_CONVERGED,
+ * FESPMV_ERR_BREAKDOWN (p.Ap <= 0, non-finite scalars or a non-positive
+ * diagonal with Jacobi), INVALID_ARG, OOM or CUDA.
+ */
+int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts, cg_result* res,
+             fespmv_stream_t stream);
+
 /* Human-readable name of a status code, and the last failure message of the
  * calling thread (empty if none).  Both strings are static or thread-local. */
 const char* fespmv_status_string(int status);

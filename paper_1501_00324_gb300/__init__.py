@@ -40,6 +40,9 @@ FESPMV_EXPORT_COLS = 2
 FESPMV_EXPORT_VALUES = 3
 FESPMV_EXPORT_SRCMAP = 4
 FESPMV_EXPORT_DIAG = 5
+FESPMV_CG_F64 = 0
+FESPMV_CG_X0 = 4
+FESPMV_CG_NO_PRECOND = 8
 
 
 class FespmvError(RuntimeError):
@@ -62,6 +65,18 @@ class fespmv_info(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_slices", ctypes.c_int64),
                 ("packed_len", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("format", ctypes.c_int32), ("vec", ctypes.c_int32)]
+
+
+class cg_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class cg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("true_relres", ctypes.c_double)]
 
 
 def _load():
@@ -94,6 +109,8 @@ _lib.spmv_export.restype = ctypes.c_int
 _lib.spmv_plan.argtypes = [_i64, _P, _P, ctypes.POINTER(fespmv_mesh_info),
                            ctypes.POINTER(fespmv_options), ctypes.POINTER(fespmv_info), _P, _P, _P, _P]
 _lib.spmv_plan.restype = ctypes.c_int
+_lib.cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), ctypes.POINTER(cg_result), _P]
+_lib.cg_solve.restype = ctypes.c_int
 _lib.fespmv_status_string.argtypes = [ctypes.c_int]
 _lib.fespmv_status_string.restype = ctypes.c_char_p
 _lib.fespmv_last_error.argtypes = []
@@ -239,3 +256,19 @@ def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
     _check(_lib.spmv_export(A.handle, what, _ptr(out), out.nbytes, _stream(stream)))
     out = out[:count]
     return out.reshape(-1, 4) if key == "meta" else out
+
+
+def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
+             max_restarts=0, check_every=0, stream=None) -> dict:
+    """Solve A x = b; returns the cg_result fields as a dict.
+
+    CG outcomes (converged, not converged, breakdown) are reported in
+    result["status"]; argument and CUDA errors raise FespmvError."""
+    if isinstance(b, np.ndarray):
+        flags |= FESPMV_IO_HOST
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, 0)
+    r = cg_result()
+    rc = _lib.cg_solve(A.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r), _stream(stream))
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return {k: getattr(r, k) for k, _ in cg_result._fields_ if k != "reserved"}

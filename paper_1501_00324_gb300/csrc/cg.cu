@@ -1,0 +1,543 @@
+// Jacobi-preconditioned conjugate gradients on the device (cg_solve).
+//
+// The paper solves K dx = R with Jacobi-preconditioned CG inside each Newton
+// step (Sec. 2.1, Sec. 4); the recurrences are the textbook Hestenes-Stiefel
+// ones.  GB300 layout of one iteration, three kernels, all scalars on the device:
+//   1. cg_spmv_dot   q = A p (the SpMV kernel of the handle) fused with p.q;
+//                    the last block to finish reduces the per-block partial sums
+//                    in a fixed order and forms alpha = rho / p.q
+//   2. cg_update     x += alpha p, r -= alpha q, z = D^-1 r on the fly, r.z and
+//                    r.r; the last block forms beta, counts the iteration and
+//                    sets the status word (converged / breakdown / limit)
+//   3. cg_pupdate    p = D^-1 r + beta p (z is never stored)
+// Every kernel returns at once when the status word is no longer RUNNING, so a
+// CUDA graph of `check_every` iterations can be launched repeatedly and the
+// host only polls the status between graphs.  All reductions have a fixed
+// order, so a solve is bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "spmv_device.cuh"
+
+namespace fespmv {
+
+enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_BREAKDOWN = 2, CG_MAXITER = 3, CG_BADDIAG = 4 };
+
+struct CgScalars {
+    double rho, pq, alpha, beta, rr, bb, thresh2, true_rr;
+    int iters, max_iter, status, pad;
+    unsigned int counter, pad2;
+};
+
+struct CgWork {
+    int64_t n = 0;
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *dinv = nullptr;
+    double* partials = nullptr;
+    CgScalars* sc = nullptr;
+    CgScalars* h_sc = nullptr;  // pinned host mirror, 2 slots
+    unsigned upd_grid = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+// ------------------------------------------------------------------ reductions
+
+// Sum over the block of K values (fixed order); the result is valid in thread 0.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+    __shared__ double sh[K][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Block sums go to partials[k*gridDim.x + block]; the last block to arrive sums
+// them in block order and returns true (result in thread 0's v).
+template <int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counter) {
+    __shared__ bool last;
+    block_sum<K>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    double t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] += __ldcg(partials + k * gridDim.x + i);
+    block_sum<K>(t);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = t[k];
+    if (threadIdx.x == 0) *counter = 0;
+    return true;
+}
+
+__device__ __forceinline__ void finish_pq(double pq, CgScalars* sc) {
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) sc->status = CG_BREAKDOWN;
+    else sc->alpha = sc->rho / pq;
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <int V, int U>
+__global__ void __launch_bounds__(256) cg_spmv_dot_sliced(const uint4* __restrict__ meta,
+                                                          const int32_t* __restrict__ col,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ p,
+                                                          double* __restrict__ q, int64_t n_slices,
+                                                          int64_t n, double* partials,
+                                                          CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    if (warp < n_slices) {
+        const uint4 m = meta[warp];
+        const double sum = sliced_row_sum_f64<V, U>(m, col, val, p, lane);
+        const int lt = (int)m.w;
+        const int64_t row = (int64_t)m.z + (lane >> lt);
+        if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+            q[row] = sum;
+            v[0] = p[row] * sum;
+        }
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+}
+
+template <int L>
+__global__ void cg_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ p,
+                                double* __restrict__ q, int64_t n, double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    double v[1] = {0.0};
+    const double sum = csr_row_sum_f64<L>(row, sub, n, rowptr, col, val, p);
+    if (row < n && sub == 0) {
+        q[row] = sum;
+        v[0] = p[row] * sum;
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+}
+
+__global__ void __launch_bounds__(256) cg_update(int64_t n, double* __restrict__ x,
+                                                 double* __restrict__ r,
+                                                 const double* __restrict__ p,
+                                                 const double* __restrict__ q,
+                                                 const double* __restrict__ dinv, double* partials,
+                                                 CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const double a = sc->alpha;
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(a, p[i], x[i]);
+        const double ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        v[0] = fma(ri, dinv[i] * ri, v[0]);
+        v[1] = fma(ri, ri, v[1]);
+    }
+    if (grid_sum<2>(v, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->rr = v[1];
+        if (!isfinite(v[0]) || !isfinite(v[1])) sc->status = CG_BREAKDOWN;
+        else if (v[1] <= sc->thresh2) sc->status = CG_CONVERGED;
+        else if (sc->iters >= sc->max_iter) sc->status = CG_MAXITER;
+        else {
+            sc->beta = v[0] / sc->rho;
+            sc->rho = v[0];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) cg_pupdate(int64_t n, double* __restrict__ p,
+                                                  const double* __restrict__ r,
+                                                  const double* __restrict__ dinv,
+                                                  const CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const double beta = sc->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+
+// dinv = 1/diag (Jacobi) or 1; a non-positive or non-finite diagonal marks BADDIAG.
+__global__ void cg_dinv(int64_t n, const double* __restrict__ diag, double* __restrict__ dinv,
+                        int jacobi, CgScalars* sc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = diag[i];
+        if (!jacobi) {
+            dinv[i] = 1.0;
+        } else if (d > 0.0 && isfinite(d)) {
+            dinv[i] = 1.0 / d;
+        } else {
+            dinv[i] = 0.0;
+            sc->status = CG_BADDIAG;
+        }
+    }
+}
+
+// r = b - Ax (Ax = q, or 0 when q is null), p = D^-1 r; rho = r.z, rr = r.r, bb = b.b.
+__global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restrict__ b,
+                                               const double* __restrict__ q, double* __restrict__ r,
+                                               double* __restrict__ p,
+                                               const double* __restrict__ dinv, double tol2,
+                                               double* partials, CgScalars* sc) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        const double ri = q ? bi - q[i] : bi;
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        p[i] = zi;
+        v[0] = fma(ri, zi, v[0]);
+        v[1] = fma(ri, ri, v[1]);
+        v[2] = fma(bi, bi, v[2]);
+    }
+    if (grid_sum<3>(v, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->rho = v[0];
+        sc->rr = v[1];
+        sc->bb = v[2];
+        sc->thresh2 = tol2 * v[2];
+        if (sc->status == CG_BADDIAG) return;
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) sc->status = CG_BREAKDOWN;
+        else if (v[1] <= sc->thresh2) sc->status = CG_CONVERGED;
+        else if (sc->iters >= sc->max_iter) sc->status = CG_MAXITER;
+        else sc->status = CG_RUNNING;
+    }
+}
+
+// true_rr = ||b - q||^2 with q = A x.
+__global__ void __launch_bounds__(256) cg_true_residual(int64_t n, const double* __restrict__ b,
+                                                        const double* __restrict__ q,
+                                                        double* partials, CgScalars* sc) {
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = b[i] - q[i];
+        v[0] = fma(d, d, v[0]);
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) sc->true_rr = v[0];
+}
+
+// ------------------------------------------------------------------ host side
+
+void free_cg(fespmv_mat* A) {
+    CgWork* w = A->cg;
+    if (!w) return;
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    for (cudaEvent_t e : w->ev)
+        if (e) cudaEventDestroy(e);
+    if (w->cap) cudaStreamDestroy(w->cap);
+    void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (w->h_sc) cudaFreeHost(w->h_sc);
+    delete w;
+    A->cg = nullptr;
+}
+
+static unsigned spmv_grid(const fespmv_mat* A) {
+    if (A->format == FESPMV_FMT_SLICED) return grid_for(A->n_slices * 32, A->block);
+    return grid_for(A->n * A->csr_lanes, A->block);
+}
+
+static int ensure_workspace(fespmv_mat* A) {
+    if (A->cg) return FESPMV_OK;
+    CgWork* w = new CgWork();
+    A->cg = w;
+    w->n = A->n;
+    int dev = 0, sms = 0;
+    FESPMV_CUDA(cudaGetDevice(&dev));
+    FESPMV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    w->upd_grid = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
+    const size_t nb = sizeof(double) * (size_t)A->n;
+    double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv};
+    for (double** v : vecs) {
+        int rc = device_alloc(A, (void**)v, nb, "CG vector");
+        if (rc) return rc;
+    }
+    const size_t np = 3 * (size_t)std::max(spmv_grid(A), w->upd_grid) + 1;
+    int rc = device_alloc(A, (void**)&w->partials, sizeof(double) * np, "CG partial sums");
+    if (rc) return rc;
+    rc = device_alloc(A, (void**)&w->sc, sizeof(CgScalars), "CG scalars");
+    if (rc) return rc;
+    FESPMV_CUDA(cudaMallocHost((void**)&w->h_sc, 2 * sizeof(CgScalars)));
+    FESPMV_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : w->ev) FESPMV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return FESPMV_OK;
+}
+
+template <int V>
+static void launch_spmv_dot_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
+    cg_spmv_dot_sliced<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->p,
+                                                               w->q, A->n_slices, A->n, w->partials,
+                                                               w->sc);
+}
+
+template <int L>
+static void launch_spmv_dot_csr(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    cg_spmv_dot_csr<L><<<spmv_grid(A), A->block, 0, s>>>(A->d_rowptr, A->d_colind, A->d_val, w->p,
+                                                         w->q, A->n, w->partials, w->sc);
+}
+
+static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    if (A->format == FESPMV_FMT_SLICED) {
+        switch (A->vec) {
+            case 1: launch_spmv_dot_sliced<1>(A, w, s); break;
+            case 4: launch_spmv_dot_sliced<4>(A, w, s); break;
+            default: launch_spmv_dot_sliced<2>(A, w, s); break;
+        }
+    } else {
+        switch (A->csr_lanes) {
+            case 1: launch_spmv_dot_csr<1>(A, w, s); break;
+            case 2: launch_spmv_dot_csr<2>(A, w, s); break;
+            case 4: launch_spmv_dot_csr<4>(A, w, s); break;
+            case 8: launch_spmv_dot_csr<8>(A, w, s); break;
+            case 16: launch_spmv_dot_csr<16>(A, w, s); break;
+            default: launch_spmv_dot_csr<32>(A, w, s); break;
+        }
+    }
+    cg_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->p, w->q, w->dinv, w->partials, w->sc);
+    cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->sc);
+}
+
+static int ensure_graph(fespmv_mat* A, int chunk) {
+    CgWork* w = A->cg;
+    if (w->graph && w->graph_chunk == chunk) return FESPMV_OK;
+    if (w->graph) {
+        cudaGraphExecDestroy(w->graph);
+        w->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    FESPMV_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) launch_iteration(A, w, w->cap);
+    cudaError_t e = cudaStreamEndCapture(w->cap, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&w->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    w->graph_chunk = chunk;
+    return FESPMV_OK;
+}
+
+static int read_scalars(CgWork* w, cudaStream_t s, int slot) {
+    FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[slot], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+}
+
+// Run graphs of `chunk` iterations until the status word leaves RUNNING.  The
+// next graph is queued before the previous one's status is read, so the GPU
+// never waits for the host; graphs queued after convergence are no-ops.
+static int iterate(fespmv_mat* A, cudaStream_t s, int chunk, int max_iter) {
+    CgWork* w = A->cg;
+    int rc = ensure_graph(A, chunk);
+    if (rc) return rc;
+    const int64_t max_graphs = (int64_t)max_iter / chunk + 3;
+    int64_t launched = 0;
+    int slot = 0;
+    FESPMV_CUDA(cudaGraphLaunch(w->graph, s));
+    FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[0], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaEventRecord(w->ev[0], s));
+    ++launched;
+    for (;;) {
+        const int next = slot ^ 1;
+        if (launched < max_graphs) {
+            FESPMV_CUDA(cudaGraphLaunch(w->graph, s));
+            FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[next], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+            FESPMV_CUDA(cudaEventRecord(w->ev[next], s));
+            ++launched;
+        }
+        FESPMV_CUDA(cudaEventSynchronize(w->ev[slot]));
+        if (w->h_sc[slot].status != CG_RUNNING || launched >= max_graphs) break;
+        slot = next;
+    }
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+}
+
+static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_options* opts,
+                         cg_result* res, cudaStream_t s) {
+    cg_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.tol == 0.0) o.tol = 1e-10;
+    if (o.max_iter == 0) o.max_iter = 100000;
+    if (o.max_restarts == 0) o.max_restarts = 3;
+    if (o.max_restarts < 0) o.max_restarts = 0;
+    if (o.check_every == 0) o.check_every = 16;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.check_every > 4096 ||
+        o.precision != FESPMV_CG_F64 ||
+        (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND))) {
+        set_error("bad cg_options");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (A->n == 0) return FESPMV_OK;
+    int rc = ensure_workspace(A);
+    if (rc) return rc;
+    CgWork* w = A->cg;
+    const size_t nb = sizeof(double) * (size_t)A->n;
+    const bool host = o.flags & FESPMV_IO_HOST;
+    const bool permute = A->format == FESPMV_FMT_SLICED && !(o.flags & FESPMV_IO_PERMUTED);
+
+    // b (and x0) into the handle's numbering
+    const double* bsrc = b;
+    if (host) {
+        FESPMV_CUDA(cudaMemcpyAsync(w->q, b, nb, cudaMemcpyHostToDevice, s));
+        bsrc = w->q;
+    }
+    if (permute) {
+        if ((rc = launch_gather(bsrc, A->d_perm, w->b, A->n, s))) return rc;
+    } else {
+        FESPMV_CUDA(cudaMemcpyAsync(w->b, bsrc, nb, cudaMemcpyDeviceToDevice, s));
+    }
+    const bool has_x0 = o.flags & FESPMV_CG_X0;
+    if (has_x0) {
+        const double* xsrc = x;
+        if (host) {
+            FESPMV_CUDA(cudaMemcpyAsync(w->q, x, nb, cudaMemcpyHostToDevice, s));
+            xsrc = w->q;
+        }
+        if (permute) {
+            if ((rc = launch_gather(xsrc, A->d_perm, w->x, A->n, s))) return rc;
+        } else {
+            FESPMV_CUDA(cudaMemcpyAsync(w->x, xsrc, nb, cudaMemcpyDeviceToDevice, s));
+        }
+    } else {
+        FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, s));
+    }
+
+    CgScalars init;
+    std::memset(&init, 0, sizeof(init));
+    init.max_iter = o.max_iter;
+    init.status = CG_RUNNING;
+    FESPMV_CUDA(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    cg_dinv<<<w->upd_grid, 256, 0, s>>>(A->n, A->d_diag, w->dinv, (o.flags & FESPMV_CG_NO_PRECOND) ? 0 : 1,
+                                        w->sc);
+    FESPMV_CUDA(cudaGetLastError());
+
+    const double tol2 = o.tol * o.tol;
+    int restarts = 0;
+    bool need_ax = has_x0;
+    int status = CG_RUNNING;
+    for (;;) {
+        if (need_ax) {
+            if ((rc = launch_spmv(A, w->x, w->q, s))) return rc;
+        }
+        cg_init<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, need_ax ? w->q : nullptr, w->r, w->p, w->dinv,
+                                            tol2, w->partials, w->sc);
+        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = read_scalars(w, s, 0))) return rc;
+        if (w->h_sc[0].status == CG_BADDIAG) {
+            set_error("Jacobi preconditioning needs a positive, finite diagonal");
+            if (res) res->status = FESPMV_ERR_BREAKDOWN;
+            return FESPMV_ERR_BREAKDOWN;
+        }
+        if (w->h_sc[0].bb == 0.0) {  // b = 0: the solution is x = 0
+            FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, s));
+            status = CG_CONVERGED;
+            FESPMV_CUDA(cudaMemsetAsync(&w->sc->true_rr, 0, sizeof(double), s));
+            if ((rc = read_scalars(w, s, 0))) return rc;
+            break;
+        }
+        if (w->h_sc[0].status == CG_RUNNING) {
+            if ((rc = iterate(A, s, o.check_every, o.max_iter))) return rc;
+        }
+        // true residual in FP64
+        if ((rc = launch_spmv(A, w->x, w->q, s))) return rc;
+        cg_true_residual<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, w->q, w->partials, w->sc);
+        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = read_scalars(w, s, 0))) return rc;
+        status = w->h_sc[0].status;
+        if (status == CG_RUNNING) status = CG_MAXITER;  // polling limit reached
+        const bool true_ok = w->h_sc[0].true_rr <= w->h_sc[0].thresh2;
+        if (status == CG_CONVERGED && !true_ok) {
+            if (restarts < o.max_restarts && w->h_sc[0].iters < o.max_iter) {
+                ++restarts;
+                need_ax = true;
+                continue;
+            }
+            status = CG_MAXITER;
+        }
+        break;
+    }
+
+    // x back to the caller's numbering
+    double* xdst = host ? w->q : x;
+    if (permute) {
+        if ((rc = launch_gather(w->x, A->d_pinv, xdst, A->n, s))) return rc;
+    } else {
+        FESPMV_CUDA(cudaMemcpyAsync(xdst, w->x, nb, cudaMemcpyDeviceToDevice, s));
+    }
+    if (host) {
+        FESPMV_CUDA(cudaMemcpyAsync(x, w->q, nb, cudaMemcpyDeviceToHost, s));
+        FESPMV_CUDA(cudaStreamSynchronize(s));
+    }
+    const CgScalars& h = w->h_sc[0];
+    const int out = status == CG_CONVERGED ? FESPMV_OK
+                  : status == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
+    if (res) {
+        res->status = out;
+        res->iters = h.iters;
+        res->restarts = restarts;
+        res->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        res->true_relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+    }
+    if (out == FESPMV_ERR_BREAKDOWN) set_error("CG breakdown (p.Ap <= 0 or a non-finite scalar)");
+    if (out == FESPMV_ERR_NOT_CONVERGED) set_error("CG stopped above the tolerance");
+    return out;
+}
+
+}  // namespace fespmv
+
+extern "C" int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts,
+                        cg_result* res, fespmv_stream_t stream) {
+    try {
+        if (!A || (A->n > 0 && (!b || !x))) {
+            fespmv::set_error("null argument");
+            return FESPMV_ERR_INVALID_ARG;
+        }
+        return fespmv::cg_solve_impl(A, b, x, opts, res, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        fespmv::set_error("host allocation failed");
+        return FESPMV_ERR_OOM;
+    } catch (...) {
+        fespmv::set_error("unexpected C++ exception");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+}

@@ -46,6 +46,10 @@ int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind);
 
 }  // namespace fespmv
 
+namespace fespmv {
+struct CgWork;  // cg.cu
+}
+
 // The opaque handle.
 struct fespmv_mat {
     int64_t n = 0;
@@ -79,6 +83,8 @@ struct fespmv_mat {
     double* d_xh = nullptr;           // host-I/O staging (n each), allocated on first use
     double* d_yh = nullptr;
     double* d_vals_in = nullptr;      // update_values staging (nnz), allocated on first use
+
+    fespmv::CgWork* cg = nullptr;     // CG workspace, allocated by the first cg_solve
 };
 
 namespace fespmv {
@@ -90,5 +96,9 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what);
 int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
+unsigned grid_for(int64_t work, int block);
+
+// CG (cg.cu)
+void free_cg(fespmv_mat* A);
 
 }  // namespace fespmv

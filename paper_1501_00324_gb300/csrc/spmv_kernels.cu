@@ -17,77 +17,25 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "spmv_device.cuh"
 
 namespace fespmv {
 
 // ---------------------------------------------------------------- CSR baselines
 
-__global__ void csr_scalar_f64(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, const double* __restrict__ x,
-                               double* __restrict__ y, int64_t n) {
-    int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (row >= n) return;
-    double sum = 0.0;
-    for (int64_t p = rowptr[row]; p < rowptr[row + 1]; ++p) sum = fma(val[p], __ldg(x + col[p]), sum);
-    y[row] = sum;
-}
-
 template <int L>
-__global__ void csr_vector_f64(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, const double* __restrict__ x,
-                               double* __restrict__ y, int64_t n) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t row = t / L;
-    int sub = (int)(t % L);
-    double sum = 0.0;
-    if (row < n) {
-        int64_t e = rowptr[row + 1];
-        for (int64_t p = rowptr[row] + sub; p < e; p += L) sum = fma(val[p], __ldg(x + col[p]), sum);
-    }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, L);
+__global__ void csr_f64(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        const double* __restrict__ val, const double* __restrict__ x,
+                        double* __restrict__ y, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    double sum = csr_row_sum_f64<L>(row, sub, n, rowptr, col, val, x);
     if (row < n && sub == 0) y[row] = sum;
 }
 
 // ---------------------------------------------------------------- warp slices
 
-template <int V> struct Vec;
-template <> struct Vec<1> {
-    double v[1]; int32_t c[1];
-    __device__ __forceinline__ void load(const double* vp, const int32_t* cp) {
-        v[0] = __ldcs(vp); c[0] = __ldcs(cp);
-    }
-};
-template <> struct Vec<2> {
-    double v[2]; int32_t c[2];
-    __device__ __forceinline__ void load(const double* vp, const int32_t* cp) {
-        double2 a = __ldcs(reinterpret_cast<const double2*>(vp));
-        int2 b = __ldcs(reinterpret_cast<const int2*>(cp));
-        v[0] = a.x; v[1] = a.y; c[0] = b.x; c[1] = b.y;
-    }
-};
-template <> struct Vec<4> {
-    double v[4]; int32_t c[4];
-    __device__ __forceinline__ void load(const double* vp, const int32_t* cp) {
-        double2 a = __ldcs(reinterpret_cast<const double2*>(vp));
-        double2 a2 = __ldcs(reinterpret_cast<const double2*>(vp) + 1);
-        int4 b = __ldcs(reinterpret_cast<const int4*>(cp));
-        v[0] = a.x; v[1] = a.y; v[2] = a2.x; v[3] = a2.y;
-        c[0] = b.x; c[1] = b.y; c[2] = b.z; c[3] = b.w;
-    }
-};
-
-template <int V>
-__device__ __forceinline__ void fma_chunk(const Vec<V>& e, const double* __restrict__ x, double& sum) {
-    double xv[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) xv[k] = e.c[k] >= 0 ? __ldg(x + e.c[k]) : 0.0;
-#pragma unroll
-    for (int k = 0; k < V; ++k) sum = fma(e.v[k], xv[k], sum);
-}
-
-// U chunks of V steps are loaded before any is consumed, so each lane keeps
-// U*(8V + 4V) bytes of matrix stream in flight.
 template <int V, int U>
 __global__ void __launch_bounds__(256) sliced_f64(const uint4* __restrict__ meta,
                                                   const int32_t* __restrict__ col,
@@ -99,33 +47,10 @@ __global__ void __launch_bounds__(256) sliced_f64(const uint4* __restrict__ meta
     const int lane = threadIdx.x & 31;
     if (warp >= n_slices) return;          // whole warps leave together
     const uint4 m = meta[warp];
-    const int64_t off = (int64_t)m.x * 32;
-    const int w = (int)m.y;
+    const double sum = sliced_row_sum_f64<V, U>(m, col, val, x, lane);
     const int lt = (int)m.w;
-    const double* vp = val + off + lane * V;
-    const int32_t* cp = col + off + lane * V;
-    double sum = 0.0;
-    int s = 0;
-    for (; s + U * V <= w; s += U * V) {
-        Vec<V> e[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) e[u].load(vp + u * 32 * V, cp + u * 32 * V);
-#pragma unroll
-        for (int u = 0; u < U; ++u) fma_chunk<V>(e[u], x, sum);
-        vp += U * 32 * V;
-        cp += U * 32 * V;
-    }
-    for (; s < w; s += V) {
-        Vec<V> e;
-        e.load(vp, cp);
-        fma_chunk<V>(e, x, sum);
-        vp += 32 * V;
-        cp += 32 * V;
-    }
-    const int T = 1 << lt;
-    for (int o = T >> 1; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
     const int64_t row = (int64_t)m.z + (lane >> lt);
-    if ((lane & (T - 1)) == 0 && row < n) y[row] = sum;
+    if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
 }
 
 // ---------------------------------------------------------------- gathers
@@ -155,7 +80,7 @@ __global__ void fill_diag_f64(const double* __restrict__ vals_in, const int64_t*
     }
 }
 
-static unsigned grid_for(int64_t work, int block) {
+unsigned grid_for(int64_t work, int block) {
     return (unsigned)((work + block - 1) / block);
 }
 
@@ -182,10 +107,10 @@ int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s) {
 }
 
 template <int L>
-static void launch_csr_vector(const fespmv_mat* A, const double* x, double* y, cudaStream_t s) {
+static void launch_csr(const fespmv_mat* A, const double* x, double* y, cudaStream_t s) {
     int64_t threads = A->n * L;
-    csr_vector_f64<L><<<grid_for(threads, A->block), A->block, 0, s>>>(A->d_rowptr, A->d_colind,
-                                                                     A->d_val, x, y, A->n);
+    csr_f64<L><<<grid_for(threads, A->block), A->block, 0, s>>>(A->d_rowptr, A->d_colind,
+                                                              A->d_val, x, y, A->n);
 }
 
 template <int V>
@@ -200,15 +125,12 @@ int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s)
     if (A->n == 0) return FESPMV_OK;
     if (A->format == FESPMV_FMT_CSR) {
         switch (A->csr_lanes) {
-            case 1:
-                csr_scalar_f64<<<grid_for(A->n, A->block), A->block, 0, s>>>(A->d_rowptr, A->d_colind,
-                                                                           A->d_val, x, y, A->n);
-                break;
-            case 2: launch_csr_vector<2>(A, x, y, s); break;
-            case 4: launch_csr_vector<4>(A, x, y, s); break;
-            case 8: launch_csr_vector<8>(A, x, y, s); break;
-            case 16: launch_csr_vector<16>(A, x, y, s); break;
-            default: launch_csr_vector<32>(A, x, y, s); break;
+            case 1: launch_csr<1>(A, x, y, s); break;
+            case 2: launch_csr<2>(A, x, y, s); break;
+            case 4: launch_csr<4>(A, x, y, s); break;
+            case 8: launch_csr<8>(A, x, y, s); break;
+            case 16: launch_csr<16>(A, x, y, s); break;
+            default: launch_csr<32>(A, x, y, s); break;
         }
     } else {
         switch (A->vec) {

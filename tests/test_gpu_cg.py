@@ -1,0 +1,129 @@
+"""GPU conjugate gradients through the C ABI, checked against the FP64 oracle.
+
+Pass criteria: the true residual ||b - A x|| / ||b||, recomputed by the oracle
+from the GPU's x, is at most the requested tolerance (plus 1 % for the
+oracle's own rounding); x agrees with the oracle's PCG solution within
+cond(A) * tol (both are tol-accurate solutions of the same system); the
+iteration count is within 2 % (+2) of the oracle's, since the two differ only
+in rounding order.
+"""
+import numpy as np
+import pytest
+
+import fegen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1501_00324_gb300 as fs  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def true_relres(p, x, b):
+    r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def solve(A, b, **kw):
+    bd = dev(b)
+    xd = torch.zeros_like(bd)
+    res = fs.cg_solve(A, bd, xd, **kw)
+    torch.cuda.synchronize()
+    return xd.cpu().numpy(), res
+
+
+def make(p, **kw):
+    return fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, **kw)
+
+
+FORMATS = [dict(format=fs.FESPMV_FMT_SLICED, sigma=512), dict(format=fs.FESPMV_FMT_CSR, csr_lanes=4),
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=4, vec=1)]
+
+
+@pytest.mark.parametrize("fmt", range(len(FORMATS)))
+@pytest.mark.parametrize("name", ["cube_laplace_20", "elasticity_8", "shell_5x16x24"])
+def test_cg_matches_oracle(name, fmt):
+    p = {"cube_laplace_20": lambda: fegen.cube_laplace(20, 1501),
+         "elasticity_8": lambda: fegen.cube_elasticity(8, 51),
+         "shell_5x16x24": lambda: fegen.shell_laplace(5, 16, 24, 52)}[name]()
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, **FORMATS[fmt])
+    x, res = solve(A, b, tol=1e-10)
+    assert res["status"] == 0, res
+    assert true_relres(p, x, b) <= 1.01e-10
+    assert res["true_relres"] <= 1e-10
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    assert info["status"] == "converged"
+    assert abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+    # both are 1e-10-residual solutions: their gap is bounded by cond(A) * 2e-10
+    from test_oracle_pins import dense_of
+    if p.n_rows <= 3000:
+        cond = np.linalg.cond(dense_of(p.rowptr, p.colind, p.values, p.n_rows))
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= cond * 2e-10
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-6
+
+
+def test_cg_is_bitwise_reproducible_and_host_io():
+    p = fegen.cube_elasticity(9, 53)
+    b = fegen.random_vector(p.n_rows, 54)
+    A = make(p, sigma=256)
+    x1, r1 = solve(A, b)
+    x2, r2 = solve(A, b)
+    assert r1["iters"] == r2["iters"] and np.array_equal(x1.view(np.uint64), x2.view(np.uint64))
+    xh = np.zeros(p.n_rows)
+    r3 = fs.cg_solve(A, b, xh)          # numpy arrays: host I/O through the same entry point
+    assert r3["status"] == 0 and np.array_equal(xh.view(np.uint64), x1.view(np.uint64))
+
+
+def test_cg_options_and_status_codes():
+    p = fegen.cube_laplace(10, 55)
+    b = fegen.random_vector(p.n_rows, 56)
+    A = make(p, sigma=128)
+    # iteration limit
+    x, res = solve(A, b, tol=1e-12, max_iter=5, max_restarts=-1)
+    assert res["status"] == fs.FESPMV_ERR_NOT_CONVERGED and res["iters"] == 5
+    # plain CG agrees with the oracle's plain CG
+    x, res = solve(A, b, tol=1e-10, flags=fs.FESPMV_CG_NO_PRECOND)
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10, jacobi=False)
+    assert res["status"] == 0 and abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+    # warm start from the solution: converged before the first iteration
+    bd = dev(b)
+    xd = dev(x)
+    res = fs.cg_solve(A, bd, xd, flags=fs.FESPMV_CG_X0)
+    assert res["status"] == 0 and res["iters"] == 0
+    # b = 0 gives x = 0
+    z = torch.zeros(p.n_rows, dtype=torch.float64, device="cuda")
+    xd = torch.ones_like(z)
+    res = fs.cg_solve(A, z, xd)
+    assert res["status"] == 0 and not xd.any().item()
+    # every graph size reaches the same iterate
+    xs = [solve(A, b, check_every=c)[0] for c in (1, 7, 64)]
+    assert all(np.array_equal(xs[0], xi) for xi in xs[1:])
+
+
+def test_cg_breakdown_on_indefinite_and_bad_diagonal():
+    # diag(1, -1): Jacobi rejects the diagonal; plain CG meets p.Ap <= 0
+    A = fs.spmv_create(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0, -1.0]),
+                       format=fs.FESPMV_FMT_CSR)
+    b = np.array([1.0, 1.0])
+    x, res = solve(A, b)
+    assert res["status"] == fs.FESPMV_ERR_BREAKDOWN
+    x, res = solve(A, b, flags=fs.FESPMV_CG_NO_PRECOND)
+    assert res["status"] == fs.FESPMV_ERR_BREAKDOWN
+
+
+def test_cg_full_size_elasticity_64():
+    """The benchmark system (786,432 rows): residual checked by the oracle's product."""
+    p = fegen.cube_elasticity(64, 1502)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, sigma=1024)
+    x, res = solve(A, b, tol=1e-10)
+    assert res["status"] == 0, res
+    assert true_relres(p, x, b) <= 1.01e-10
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-5
