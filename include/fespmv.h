@@ -228,6 +228,36 @@ typedef struct {
 int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts, cg_result* res,
              fespmv_stream_t stream);
 
+/*
+ * cg_solve_csr_static -- cg_solve for a CSR matrix that allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory -- code that runs inside another framework's
+ * memory pool, plugins that must not grow the process's device footprint, and
+ * latency-critical loops that cannot block on the allocator -- and therefore
+ * cannot create a handle with spmv_create.
+ *   n_rows                 at most 262,144 (larger sizes return INVALID_ARG)
+ *   rowptr, colind, values device CSR arrays (int64[n+1], int32[nnz], double[nnz]),
+ *                          same rules as spmv_create; not validated on the device
+ *   b                      device double[n_rows]
+ *   x                      device double[n_rows]; initial guess with FESPMV_CG_X0,
+ *                          overwritten with the solution
+ *   csr_lanes              lanes per row of the CSR kernel (1..32, power of two; 0 = 4)
+ *   opts, res              as for cg_solve (IO flags other than FESPMV_CG_X0 and
+ *                          FESPMV_CG_NO_PRECOND are rejected)
+ * Same Jacobi-PCG recurrences and kernels as cg_solve on a FESPMV_FMT_CSR handle.
+ * The workspace (about 8.3 MB) is one fixed device array inside this library;
+ * every GPU that loads the library holds it until the process exits.  The
+ * first call on a device resolves that array's address for the device, so make
+ * that first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind; each call clears the state it needs, but calls
+ * whose work overlaps on the GPU (from several threads or streams) race on
+ * the array and must be serialised by the caller.  The call calls no device or
+ * host allocator and blocks the host until the solve ends.
+ */
+int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
+                        const double* values, const double* b, double* x, int32_t csr_lanes,
+                        const cg_options* opts, cg_result* res, fespmv_stream_t stream);
+
 /* Human-readable name of a status code, and the last failure message of the
  * calling thread (empty if none).  Both strings are static or thread-local. */
 const char* fespmv_status_string(int status);

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "spmv_device.cuh"
@@ -523,6 +524,230 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
     return out;
 }
 
+// ------------------------------------------------------------------ allocation-free CSR solve
+//
+// cg_solve_csr_static serves callers that cannot allocate device memory: code
+// running where cudaMalloc is forbidden or unavailable (inside a framework's
+// own memory pool, a plugin that must not grow the process's device
+// footprint, or a real-time loop that may not block on the allocator).  The
+// caller passes the CSR matrix, b and x in device memory; the CG workspace
+// (r, p, q, D^-1, partial sums, scalars) lives in the fixed array below, which
+// every GPU that loads this library holds until the process exits.
+constexpr int64_t kStaticMaxRows = int64_t(1) << 18;     // 262,144 rows
+constexpr int64_t kStaticPartials = 32768;                // >= every grid used below (x3 for K=3)
+constexpr size_t kStaticVecBytes = sizeof(double) * kStaticMaxRows;
+constexpr size_t kStaticBytes = 4 * kStaticVecBytes + sizeof(double) * kStaticPartials + 256;
+
+static __device__ __align__(256) unsigned char g_cg_static_scratch[kStaticBytes];
+
+static std::mutex g_static_mutex;
+static void* g_static_ptr[64];  // device address of the array, per device ordinal
+
+// Resolves the array's device address for the current device (first call on
+// that device only).
+static int static_scratch(void** out) {
+    int dev = 0;
+    FESPMV_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d not supported by cg_solve_csr_static", dev);
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_cg_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_cg_static_scratch)");
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return FESPMV_OK;
+}
+
+__global__ void cg_static_reset(CgScalars* sc, int max_iter) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CgScalars z = {};
+        z.max_iter = max_iter;
+        z.status = CG_RUNNING;
+        *sc = z;
+    }
+}
+
+__global__ void csr_diag(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         const double* __restrict__ val, double* __restrict__ diag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (col[p] == i) d += val[p];
+        diag[i] = d;
+    }
+}
+
+template <int L>
+__global__ void csr_spmv_static(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ x,
+                                double* __restrict__ y, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    const double sum = csr_row_sum_f64<L>(row, sub, n, rowptr, col, val, x);
+    if (row < n && sub == 0) y[row] = sum;
+}
+
+struct StaticCsr {
+    int64_t n;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    int lanes;
+    unsigned spmv_grid;
+};
+
+template <int L>
+static void static_launch(const StaticCsr& m, bool dot, const double* x, double* y, double* partials,
+                          CgScalars* sc, cudaStream_t s) {
+    if (dot)
+        cg_spmv_dot_csr<L><<<m.spmv_grid, 256, 0, s>>>(m.rowptr, m.col, m.val, x, y, m.n, partials, sc);
+    else
+        csr_spmv_static<L><<<m.spmv_grid, 256, 0, s>>>(m.rowptr, m.col, m.val, x, y, m.n);
+}
+
+static void static_spmv(const StaticCsr& m, bool dot, const double* x, double* y, double* partials,
+                        CgScalars* sc, cudaStream_t s) {
+    switch (m.lanes) {
+        case 1: static_launch<1>(m, dot, x, y, partials, sc, s); break;
+        case 2: static_launch<2>(m, dot, x, y, partials, sc, s); break;
+        case 4: static_launch<4>(m, dot, x, y, partials, sc, s); break;
+        case 8: static_launch<8>(m, dot, x, y, partials, sc, s); break;
+        case 16: static_launch<16>(m, dot, x, y, partials, sc, s); break;
+        default: static_launch<32>(m, dot, x, y, partials, sc, s); break;
+    }
+}
+
+static int static_read(CgScalars* h, const CgScalars* sc, cudaStream_t s) {
+    FESPMV_CUDA(cudaMemcpyAsync(h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+}
+
+static int cg_static_impl(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* values,
+                          const double* b, double* x, int lanes, const cg_options* opts,
+                          cg_result* res, cudaStream_t s) {
+    cg_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.tol == 0.0) o.tol = 1e-10;
+    if (o.max_iter == 0) o.max_iter = 100000;
+    if (o.max_restarts == 0) o.max_restarts = 3;
+    if (o.max_restarts < 0) o.max_restarts = 0;
+    if (o.check_every == 0) o.check_every = 16;
+    if (lanes == 0) lanes = 4;
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (n < 0 || n > kStaticMaxRows) {
+        set_error("cg_solve_csr_static handles at most %lld rows (got %lld)",
+                  (long long)kStaticMaxRows, (long long)n);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.precision != FESPMV_CG_F64 ||
+        (o.flags & ~(FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND)) ||
+        !(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)) {
+        set_error("bad options for cg_solve_csr_static");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    if (n == 0) return FESPMV_OK;
+    if (!rowptr || !colind || !values || !b || !x) {
+        set_error("null argument");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc) return rc;
+    unsigned char* sp = static_cast<unsigned char*>(base);
+    double* r = reinterpret_cast<double*>(sp);
+    double* p = reinterpret_cast<double*>(sp + kStaticVecBytes);
+    double* q = reinterpret_cast<double*>(sp + 2 * kStaticVecBytes);
+    double* dinv = reinterpret_cast<double*>(sp + 3 * kStaticVecBytes);
+    double* partials = reinterpret_cast<double*>(sp + 4 * kStaticVecBytes);
+    CgScalars* sc = reinterpret_cast<CgScalars*>(sp + 4 * kStaticVecBytes + sizeof(double) * kStaticPartials);
+
+    int dev = 0, sms = 0;
+    FESPMV_CUDA(cudaGetDevice(&dev));
+    FESPMV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned upd = std::max(1u, std::min(grid_for(n, 256), (unsigned)(sms * 8)));
+    StaticCsr m{n, rowptr, colind, values, lanes, grid_for(n * lanes, 256)};
+    if ((int64_t)m.spmv_grid > kStaticPartials || 3 * (int64_t)upd > kStaticPartials) {
+        set_error("grid too large for the static partial-sum buffer");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+
+    // every call starts from cleared scalars; vectors are fully written before use
+    cg_static_reset<<<1, 32, 0, s>>>(sc, o.max_iter);
+    csr_diag<<<upd, 256, 0, s>>>(n, rowptr, colind, values, q);
+    cg_dinv<<<upd, 256, 0, s>>>(n, q, dinv, (o.flags & FESPMV_CG_NO_PRECOND) ? 0 : 1, sc);
+    const bool has_x0 = o.flags & FESPMV_CG_X0;
+    if (!has_x0) FESPMV_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+    FESPMV_CUDA(cudaGetLastError());
+
+    const double tol2 = o.tol * o.tol;
+    CgScalars h;
+    int restarts = 0;
+    bool need_ax = has_x0;
+    int status = CG_RUNNING;
+    for (;;) {
+        if (need_ax) static_spmv(m, false, x, q, partials, sc, s);
+        cg_init<<<upd, 256, 0, s>>>(n, b, need_ax ? q : nullptr, r, p, dinv, tol2, partials, sc);
+        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = static_read(&h, sc, s))) return rc;
+        if (h.status == CG_BADDIAG) {
+            set_error("Jacobi preconditioning needs a positive, finite diagonal");
+            if (res) res->status = FESPMV_ERR_BREAKDOWN;
+            return FESPMV_ERR_BREAKDOWN;
+        }
+        if (h.bb == 0.0) {
+            FESPMV_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+            FESPMV_CUDA(cudaStreamSynchronize(s));
+            h.true_rr = 0.0;
+            status = CG_CONVERGED;
+            break;
+        }
+        while (h.status == CG_RUNNING) {
+            for (int k = 0; k < o.check_every; ++k) {
+                static_spmv(m, true, p, q, partials, sc, s);
+                cg_update<<<upd, 256, 0, s>>>(n, x, r, p, q, dinv, partials, sc);
+                cg_pupdate<<<upd, 256, 0, s>>>(n, p, r, dinv, sc);
+            }
+            FESPMV_CUDA(cudaGetLastError());
+            if ((rc = static_read(&h, sc, s))) return rc;
+        }
+        static_spmv(m, false, x, q, partials, sc, s);
+        cg_true_residual<<<upd, 256, 0, s>>>(n, b, q, partials, sc);
+        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = static_read(&h, sc, s))) return rc;
+        status = h.status;
+        if (status == CG_CONVERGED && !(h.true_rr <= h.thresh2)) {
+            if (restarts < o.max_restarts && h.iters < o.max_iter) {
+                ++restarts;
+                need_ax = true;
+                continue;
+            }
+            status = CG_MAXITER;
+        }
+        break;
+    }
+    const int out = status == CG_CONVERGED ? FESPMV_OK
+                  : status == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
+    if (res) {
+        res->status = out;
+        res->iters = h.iters;
+        res->restarts = restarts;
+        res->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        res->true_relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+    }
+    if (out == FESPMV_ERR_BREAKDOWN) set_error("CG breakdown (p.Ap <= 0 or a non-finite scalar)");
+    if (out == FESPMV_ERR_NOT_CONVERGED) set_error("CG stopped above the tolerance");
+    return out;
+}
+
 }  // namespace fespmv
 
 extern "C" int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts,
@@ -536,6 +761,19 @@ extern "C" int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_opt
     } catch (const std::bad_alloc&) {
         fespmv::set_error("host allocation failed");
         return FESPMV_ERR_OOM;
+    } catch (...) {
+        fespmv::set_error("unexpected C++ exception");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
+                                   const double* values, const double* b, double* x,
+                                   int32_t csr_lanes, const cg_options* opts, cg_result* res,
+                                   fespmv_stream_t stream) {
+    try {
+        return fespmv::cg_static_impl(n_rows, rowptr, colind, values, b, x, csr_lanes, opts, res,
+                                      (cudaStream_t)stream);
     } catch (...) {
         fespmv::set_error("unexpected C++ exception");
         return FESPMV_ERR_INVALID_ARG;
