@@ -243,7 +243,8 @@ def main():
     x = fegen.random_vector(n, 1504)
     t0 = time.perf_counter()
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.vec,
-                       threshold=args.threshold, block=args.block)
+                       threshold=args.threshold, block=args.block,
+                       precisions=0 if args.only_spmv else fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
     create_s = time.perf_counter() - t0
     info = fs.spmv_get_info(A)
 
@@ -285,6 +286,15 @@ def main():
             y_user = torch.empty_like(xd)
             t_user = timed_steps(lambda: fs.spmv_apply(A, xd, y_user), max(10, args.steps // 4))
             extra["fe_input_numbering_gbs"] = round(mb / (statistics.mean(t_user) * 1e-3) / 1e9, 1)
+            # low-precision products of B = S A S (the refined CG's inner operator)
+            xs = xp.float()
+            ys = torch.empty_like(xs)
+            for name, prec, vb in (("fp32", fs.FESPMV_PREC_F32, 4), ("bf16", fs.FESPMV_PREC_BF16, 2)):
+                f = lambda: fs.spmv_apply_scaled(A, xs, ys, prec, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+                f()
+                tl = timed_steps(f, max(10, args.steps // 4))
+                extra[f"{name}_spmv_gbs"] = round(nnz * (vb + 4) + n * 8) / (statistics.mean(tl) * 1e-3) / 1e9
+                extra[f"{name}_spmv_gbs"] = round(extra[f"{name}_spmv_gbs"], 1)
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
@@ -307,7 +317,9 @@ def main():
             extra["e2e"] = {"value": round(mb / te / 1e9, 1), "unit": "GB/s",
                             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
             if hasattr(fs, "cg_solve"):
-                extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves)
+                extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves, fs.FESPMV_CG_F64)
+                extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
+                                                  fs.FESPMV_CG_F32_REFINE)
     clk = clocks.summary()
 
     t_mean = statistics.mean(times) * 1e-3
@@ -361,24 +373,29 @@ def main():
         dist.destroy_process_group()
 
 
-def bench_cg(fs, torch, A, p, n_solves):
-    """FP64 Jacobi-PCG solves to 1e-10 on the same matrix (b = A u*, u* manufactured)."""
+def bench_cg(fs, torch, A, p, n_solves, precision):
+    """CG solves to 1e-10 on the same matrix (b = A u*, u* manufactured)."""
     import fegen
     u = fegen.manufactured_solution(p)
     ud = torch.from_numpy(u).cuda()
     bd = torch.empty_like(ud)
     fs.spmv_apply(A, ud, bd)
-    lat, iters = [], []
+    lat, iters, outer, rel = [], [], [], []
+    fs.cg_solve(A, bd, torch.zeros_like(bd), tol=1e-10, precision=precision)   # warm: graphs
     for _ in range(n_solves):
         xs = torch.zeros_like(bd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = fs.cg_solve(A, bd, xs, tol=1e-10)
+        res = fs.cg_solve(A, bd, xs, tol=1e-10, precision=precision)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0)
         iters.append(res["iters"])
+        outer.append(res["outer"])
+        rel.append(res["true_relres"])
+        assert res["status"] == 0, res
     lat_ms = sorted(1e3 * t for t in lat)
-    return {"precision": "f64", "tol": 1e-10, "solves": n_solves,
+    return {"precision": {0: "f64", 1: "f32_refine", 2: "bf16_refine"}[precision], "tol": 1e-10,
+            "solves": n_solves, "outer": outer[0], "true_relres_max": max(rel),
             "solves_per_s": round(n_solves / sum(lat), 3),
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 2),

@@ -60,7 +60,8 @@ typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory 
 
 /* Value copies kept by a handle (bitmask in fespmv_options.precisions). */
 #define FESPMV_PREC_F64      1  /* FP64 values (always kept) */
-#define FESPMV_PREC_F32      2  /* FP32 values of S A S, S = diag(A)^-1/2, for refined CG */
+#define FESPMV_PREC_F32      2  /* FP32 values of B = S A S, S = diag(A)^-1/2 (refined CG) */
+#define FESPMV_PREC_BF16     4  /* bfloat16 values of B = S A S (refined CG) */
 
 typedef struct {
     int32_t format;      /* FESPMV_FMT_*; 0 = CSR baseline */
@@ -150,6 +151,19 @@ int spmv_update_values(fespmv_mat_t A, const double* values, int32_t flags,
 
 int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
 
+/*
+ * spmv_apply_scaled -- y = B x for the low-precision copy B = S A S (S =
+ * diag(A)^-1/2) kept with FESPMV_PREC_F32 or FESPMV_PREC_BF16: B's stored
+ * values, float x and y, float products and sums.  This is the operator of
+ * the refined CG's inner iterations.
+ *   precision  FESPMV_PREC_F32 or FESPMV_PREC_BF16
+ *   x, y       device float[n_rows] (permuted numbering with FESPMV_IO_PERMUTED;
+ *              without it a SLICED handle gathers x in and y out)
+ * Errors: INVALID_ARG, UNSUPPORTED (copy not held), CUDA.
+ */
+int spmv_apply_scaled(fespmv_mat_t A, const float* x, float* y, int32_t precision, int32_t flags,
+                      fespmv_stream_t stream);
+
 /* Arrays spmv_export can copy to the host (for tests and inspection). */
 #define FESPMV_EXPORT_PERM     0  /* int32[n_rows]: P, P[new] = old (SLICED) */
 #define FESPMV_EXPORT_META     1  /* uint32[n_slices*4]: (offset/32, width, first row, log2 T) */
@@ -157,6 +171,9 @@ int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
 #define FESPMV_EXPORT_VALUES   3  /* double[packed_len]: packed values, 0 = padding */
 #define FESPMV_EXPORT_SRCMAP   4  /* int64[packed_len]: CSR position of each packed entry, -1 pad */
 #define FESPMV_EXPORT_DIAG     5  /* double[n_rows]: diag(A) in the handle's numbering */
+#define FESPMV_EXPORT_VALUES_F32  6  /* float[packed_len or nnz]: values of B = S A S */
+#define FESPMV_EXPORT_VALUES_BF16 7  /* uint16[packed_len or nnz]: bfloat16 bits of B */
+#define FESPMV_EXPORT_SCALE    8  /* double[n_rows]: S = diag(A)^-1/2, handle numbering */
 /* Copy internal array `what` into host buffer `out` of `bytes` bytes (must be at
  * least the array's size).  Synchronises the stream.  Errors: INVALID_ARG,
  * UNSUPPORTED (array not held by this handle), CUDA. */
@@ -180,6 +197,8 @@ int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
 
 /* ---- conjugate gradients ----------------------------------------------------------- */
 #define FESPMV_CG_F64          0  /* FP64 Jacobi-PCG on the handle's FP64 values */
+#define FESPMV_CG_F32_REFINE   1  /* FP64 refinement around FP32 CG on B = S A S (FP32 values) */
+#define FESPMV_CG_BF16_REFINE  2  /* FP64 refinement around FP32 CG on B = S A S (BF16 values) */
 #define FESPMV_CG_X0           4  /* flag: x holds the initial guess (otherwise x0 = 0) */
 #define FESPMV_CG_NO_PRECOND   8  /* flag: plain CG instead of Jacobi-PCG */
 
@@ -191,14 +210,15 @@ typedef struct {
                               FESPMV_CG_NO_PRECOND */
     int32_t max_restarts;  /* restarts from the true residual; 0 = 3, < 0 = none */
     int32_t check_every;   /* iterations per graph launch between host polls; 0 = 16 */
-    int32_t reserved;
+    int32_t max_outer;     /* refinement: FP64 residual steps; 0 = 60 */
+    double inner_tol;      /* refinement: inner CG stops at ||r_in|| <= inner_tol ||S r||; 0 = 1e-2 */
 } cg_options;
 
 typedef struct {
     int32_t status;        /* FESPMV_OK, FESPMV_ERR_NOT_CONVERGED or FESPMV_ERR_BREAKDOWN */
     int32_t iters;         /* CG iterations over all restarts */
-    int32_t restarts;      /* restarts taken */
-    int32_t reserved;
+    int32_t restarts;      /* restarts taken (FP64) */
+    int32_t outer;         /* refinement steps taken (refined precisions) */
     double relres;         /* recurrence residual ||r_k|| / ||b|| at exit */
     double true_relres;    /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
 } cg_result;
@@ -221,7 +241,19 @@ typedef struct {
  * (it polls a status word after each graph).  Dot products are reduced in a
  * fixed order, so repeated solves of the same system give bitwise-equal x.
  * Workspace (6 vectors of n_rows doubles) is allocated on the first call and
- * kept by the handle.  Returns FESPMV_OK, FESPMV_ERR_NOT_CONVERGED,
+ * kept by the handle.
+ *
+ * precision FESPMV_CG_F32_REFINE / FESPMV_CG_BF16_REFINE (the handle must hold the
+ * FP32 / BF16 copy, FESPMV_PREC_F32 / FESPMV_PREC_BF16 at create): mixed-precision
+ * iterative refinement, x0 = 0 (or x with FESPMV_CG_X0),
+ *   repeat: r = b - A x in FP64;  stop when ||r|| <= tol ||b||;
+ *           solve B w = S r by plain CG with FP32 vectors and FP32 arithmetic in
+ *           the product, FP64 dot products, until ||B w - S r|| <= inner_tol ||S r||
+ *           or max_iter inner steps;  x += S w in FP64.
+ * diag(B) = 1, so Jacobi on B is the identity.  iters counts inner steps, outer
+ * the FP64 residual steps.  A refinement step that does not reduce ||r|| ends
+ * the solve with FESPMV_ERR_NOT_CONVERGED (the low-precision operator is too
+ * far from A for this system: contraction needs cond(B) * u_storage < 1).  Returns FESPMV_OK, FESPMV_ERR_NOT_CONVERGED,
  * FESPMV_ERR_BREAKDOWN (p.Ap <= 0, non-finite scalars or a non-positive
  * diagonal with Jacobi), INVALID_ARG, OOM or CUDA.
  */

@@ -54,6 +54,10 @@ def _lib():
         lib.oracle_pcg.restype = i32
         lib.oracle_refine.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, i32, P, P, P]
         lib.oracle_refine.restype = i32
+        lib.oracle_scaled_values.argtypes = [i64, P, P, P, i32, P]
+        lib.oracle_scaled_values.restype = i32
+        lib.oracle_csr_spmv_f32.argtypes = [i64, P, P, P, P, P]
+        lib.oracle_csr_spmv_f32.restype = None
         lib.oracle_round_bf16.argtypes = [ctypes.c_float]
         lib.oracle_round_bf16.restype = ctypes.c_float
         _lib_handle = lib
@@ -101,6 +105,28 @@ def round_bf16(values) -> np.ndarray:
     f = _lib().oracle_round_bf16
     return np.array([f(float(v)) for v in np.asarray(values, dtype=np.float32)],
                     dtype=np.float32)
+
+
+def scaled_values(rowptr, colind, values, storage="f32") -> np.ndarray:
+    """Values of B = S A S (S = diag(A)^-1/2) rounded to float or bfloat16 (as float32)."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    out = np.empty(len(va), dtype=np.float32)
+    st = _lib().oracle_scaled_values(len(rp) - 1, _p(rp), _p(ci), _p(va),
+                                     {"f32": 0, "bf16": 1}[storage], _p(out))
+    if st != 0:
+        raise ValueError("non-positive diagonal")
+    return out
+
+
+def csr_spmv_f32(rowptr, colind, bvalues, x) -> np.ndarray:
+    """y = B x with float values, float vector and float left-to-right row sums."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    bv = np.ascontiguousarray(bvalues, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty(len(rp) - 1, dtype=np.float32)
+    _lib().oracle_csr_spmv_f32(len(rp) - 1, _p(rp), _p(ci), _p(bv), _p(x), _p(y))
+    return y
 
 
 def refine(rowptr, colind, values, b, x0=None, tol=1e-10, inner_tol=1e-3, max_outer=50,

@@ -172,6 +172,32 @@ static double dot_f(int64_t n, const float* a, const float* b) {
     return s;
 }
 
+/* B = S A S in the refinement's storage: bv[k] = round((s_i * a_ik) * s_k), with
+ * s_i = 1/sqrt(a_ii) in FP64, rounded to float (storage 0) or bfloat16 (1).
+ * Returns 0, or 2 if a diagonal entry is not positive. */
+int oracle_scaled_values(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                         const double* val, int storage, float* bv) {
+    double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    diagonal(n, rowptr, colind, val, d);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(d[i] > 0.0)) { free(d); return 2; }
+        d[i] = 1.0 / sqrt(d[i]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            float f = (float)(d[i] * val[k] * d[colind[k]]);
+            bv[k] = storage == 1 ? round_bf16(f) : f;
+        }
+    free(d);
+    return 0;
+}
+
+/* y = B x in float, rows summed left to right (the refinement's inner product). */
+void oracle_csr_spmv_f32(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                         const float* bv, const float* x, float* y) {
+    spmv_f32(n, rowptr, colind, bv, x, y);
+}
+
 /*
  * Mixed-precision iterative refinement.
  *   S = diag(A)^(-1/2);  B = S A S rounded to float (storage 0) or bfloat16 (storage 1)

@@ -32,6 +32,7 @@ FESPMV_REORDER_NONE = 0
 FESPMV_REORDER_MORTON = 1
 FESPMV_PREC_F64 = 1
 FESPMV_PREC_F32 = 2
+FESPMV_PREC_BF16 = 4
 FESPMV_IO_PERMUTED = 1
 FESPMV_IO_HOST = 2
 FESPMV_EXPORT_PERM = 0
@@ -40,7 +41,12 @@ FESPMV_EXPORT_COLS = 2
 FESPMV_EXPORT_VALUES = 3
 FESPMV_EXPORT_SRCMAP = 4
 FESPMV_EXPORT_DIAG = 5
+FESPMV_EXPORT_VALUES_F32 = 6
+FESPMV_EXPORT_VALUES_BF16 = 7
+FESPMV_EXPORT_SCALE = 8
 FESPMV_CG_F64 = 0
+FESPMV_CG_F32_REFINE = 1
+FESPMV_CG_BF16_REFINE = 2
 FESPMV_CG_X0 = 4
 FESPMV_CG_NO_PRECOND = 8
 
@@ -70,12 +76,13 @@ class fespmv_info(ctypes.Structure):
 class cg_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double)]
 
 
 class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("outer", ctypes.c_int32), ("relres", ctypes.c_double),
                 ("true_relres", ctypes.c_double)]
 
 
@@ -98,6 +105,8 @@ _lib.spmv_destroy.argtypes = [_P]
 _lib.spmv_destroy.restype = None
 _lib.spmv_apply.argtypes = [_P, _P, _P, _i32, _P]
 _lib.spmv_apply.restype = ctypes.c_int
+_lib.spmv_apply_scaled.argtypes = [_P, _P, _P, _i32, _i32, _P]
+_lib.spmv_apply_scaled.restype = ctypes.c_int
 _lib.spmv_permute.argtypes = [_P, _P, _P, _i32, _P]
 _lib.spmv_permute.restype = ctypes.c_int
 _lib.spmv_update_values.argtypes = [_P, _P, _i32, _P]
@@ -200,6 +209,11 @@ def spmv_apply(A: Matrix, x, y, flags=0, stream=None):
     return y
 
 
+def spmv_apply_scaled(A: Matrix, x, y, precision=FESPMV_PREC_F32, flags=0, stream=None):
+    _check(_lib.spmv_apply_scaled(A.handle, _ptr(x), _ptr(y), precision, flags, _stream(stream)))
+    return y
+
+
 def spmv_permute(A: Matrix, x, out, direction=0, stream=None):
     _check(_lib.spmv_permute(A.handle, _ptr(x), _ptr(out), direction, _stream(stream)))
     return out
@@ -245,7 +259,10 @@ _EXPORT_DTYPES = {FESPMV_EXPORT_PERM: (np.int32, "n_rows"), FESPMV_EXPORT_META: 
                   FESPMV_EXPORT_COLS: (np.int32, "packed_len"),
                   FESPMV_EXPORT_VALUES: (np.float64, "packed_len"),
                   FESPMV_EXPORT_SRCMAP: (np.int64, "packed_len"),
-                  FESPMV_EXPORT_DIAG: (np.float64, "n_rows")}
+                  FESPMV_EXPORT_DIAG: (np.float64, "n_rows"),
+                  FESPMV_EXPORT_VALUES_F32: (np.float32, "packed_len"),
+                  FESPMV_EXPORT_VALUES_BF16: (np.uint16, "packed_len"),
+                  FESPMV_EXPORT_SCALE: (np.float64, "n_rows")}
 
 
 def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
@@ -259,16 +276,16 @@ def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
 
 
 def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
-             max_restarts=0, check_every=0, stream=None) -> dict:
+             max_restarts=0, check_every=0, max_outer=0, inner_tol=0.0, stream=None) -> dict:
     """Solve A x = b; returns the cg_result fields as a dict.
 
     CG outcomes (converged, not converged, breakdown) are reported in
     result["status"]; argument and CUDA errors raise FespmvError."""
     if isinstance(b, np.ndarray):
         flags |= FESPMV_IO_HOST
-    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, 0)
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
     r = cg_result()
     rc = _lib.cg_solve(A.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r), _stream(stream))
     if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
         _check(rc)
-    return {k: getattr(r, k) for k, _ in cg_result._fields_ if k != "reserved"}
+    return {k: getattr(r, k) for k, _ in cg_result._fields_}

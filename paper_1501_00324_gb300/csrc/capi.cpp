@@ -45,7 +45,8 @@ static void free_handle(fespmv_mat* A) {
     free_cg(A);
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
-                    A->d_vals_in};
+                    A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
+                    A->d_ys};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;
@@ -63,6 +64,20 @@ static int ck(cudaError_t e, const char* what) {
             return rc_;           \
         }                         \
     } while (0)
+
+// Storage for S and the low-precision copies of S A S requested at create.
+static int alloc_scaled(fespmv_mat* A, int64_t len) {
+    if (!(A->precisions & (FESPMV_PREC_F32 | FESPMV_PREC_BF16))) return FESPMV_OK;
+    int rc = device_alloc(A, (void**)&A->d_scale, sizeof(double) * A->n, "scale S");
+    if (!rc) rc = device_alloc(A, (void**)&A->d_flag, sizeof(int), "diagonal flag");
+    if (!rc && (A->precisions & FESPMV_PREC_F32))
+        rc = device_alloc(A, (void**)&A->d_val32, sizeof(float) * len, "FP32 values");
+    if (!rc && (A->precisions & FESPMV_PREC_BF16))
+        rc = device_alloc(A, (void**)&A->d_val16, sizeof(uint16_t) * len, "BF16 values");
+    if (!rc) rc = device_alloc(A, (void**)&A->d_xs, sizeof(float) * A->n, "float x scratch");
+    if (!rc) rc = device_alloc(A, (void**)&A->d_ys, sizeof(float) * A->n, "float y scratch");
+    return rc;
+}
 
 static bool pow2_upto32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
 
@@ -109,7 +124,7 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     if (o.reorder == FESPMV_REORDER_MORTON && (!mesh || !mesh->node_xyz) && o.format == FESPMV_FMT_SLICED) {
         set_error("REORDER_MORTON needs mesh->node_xyz"); return FESPMV_ERR_INVALID_ARG;
     }
-    if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32)) {
+    if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32 | FESPMV_PREC_BF16)) {
         set_error("unknown precision bits 0x%x", o.precisions); return FESPMV_ERR_INVALID_ARG;
     }
     int rc = validate_csr(n, rowptr, colind);
@@ -154,6 +169,7 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         TRY(ck(cudaMemcpyAsync(A->d_rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
         TRY(ck(cudaMemcpyAsync(A->d_colind, colind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
         TRY(ck(cudaMemcpyAsync(A->d_diagpos, diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(alloc_scaled(A, nnz));
         TRY(launch_fill_values(A, A->d_vals_in, s));
         TRY(ck(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
     } else {
@@ -176,9 +192,19 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         TRY(ck(cudaMemcpyAsync(A->d_perm, plan.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
         TRY(ck(cudaMemcpyAsync(A->d_pinv, plan.pinv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
         TRY(ck(cudaMemcpyAsync(A->d_diagpos, plan.diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(alloc_scaled(A, plan.packed_len));
         TRY(launch_fill_values(A, A->d_vals_in, s));
         // host vectors must stay alive until the copies finish
         TRY(ck(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    }
+    if (A->d_flag) {
+        int bad = 0;
+        TRY(ck(cudaMemcpy(&bad, A->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy"));
+        if (bad) {
+            set_error("FP32/BF16 copies of S A S need a positive, finite diagonal");
+            free_handle(A);
+            return FESPMV_ERR_INVALID_ARG;
+        }
     }
     cudaFree(A->d_vals_in);     // staging is re-allocated by spmv_update_values when needed
     A->device_bytes -= (int64_t)(nnz > 0 ? sizeof(double) * nnz : 16);
@@ -262,6 +288,30 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
         FESPMV_CUDA(cudaStreamSynchronize(s));
     }
     return FESPMV_OK;
+    GUARD_END
+}
+
+int spmv_apply_scaled(fespmv_mat_t A, const float* x, float* y, int32_t precision, int32_t flags,
+                      fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!A || (A->n > 0 && (!x || !y)) || (flags & ~FESPMV_IO_PERMUTED) ||
+        (precision != FESPMV_PREC_F32 && precision != FESPMV_PREC_BF16)) {
+        set_error("bad argument"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if ((precision == FESPMV_PREC_F32 && !A->d_val32) || (precision == FESPMV_PREC_BF16 && !A->d_val16)) {
+        set_error("the handle holds no %s copy (FESPMV_PREC_* at create)",
+                  precision == FESPMV_PREC_F32 ? "FP32" : "BF16");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->n == 0) return FESPMV_OK;
+    int rc;
+    if (A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED)) {
+        if ((rc = launch_gather_f32(x, A->d_perm, A->d_xs, A->n, s))) return rc;
+        if ((rc = launch_spmv_low(A, precision, A->d_xs, A->d_ys, s))) return rc;
+        return launch_gather_f32(A->d_ys, A->d_pinv, y, A->n, s);
+    }
+    return launch_spmv_low(A, precision, x, y, s);
     GUARD_END
 }
 
@@ -368,9 +418,16 @@ int spmv_export(fespmv_mat_t A, int32_t what, void* out, size_t bytes, fespmv_st
             src = A->d_val; need = 8 * (size_t)(sliced ? A->packed_len : A->nnz); break;
         case FESPMV_EXPORT_SRCMAP: src = A->d_src; need = 8 * (size_t)A->packed_len; break;
         case FESPMV_EXPORT_DIAG: src = A->d_diag; need = 8 * (size_t)A->n; break;
+        case FESPMV_EXPORT_VALUES_F32:
+            src = A->d_val32; need = 4 * (size_t)(sliced ? A->packed_len : A->nnz); break;
+        case FESPMV_EXPORT_VALUES_BF16:
+            src = A->d_val16; need = 2 * (size_t)(sliced ? A->packed_len : A->nnz); break;
+        case FESPMV_EXPORT_SCALE: src = A->d_scale; need = 8 * (size_t)A->n; break;
         default: set_error("unknown export %d", what); return FESPMV_ERR_INVALID_ARG;
     }
-    if (!sliced && what != FESPMV_EXPORT_VALUES && what != FESPMV_EXPORT_DIAG) {
+    if (!src) { set_error("array %d is not held by this handle", what); return FESPMV_ERR_UNSUPPORTED; }
+    if (!sliced && (what == FESPMV_EXPORT_PERM || what == FESPMV_EXPORT_META ||
+                    what == FESPMV_EXPORT_COLS || what == FESPMV_EXPORT_SRCMAP)) {
         set_error("array %d exists only for SLICED handles", what); return FESPMV_ERR_UNSUPPORTED;
     }
     if (bytes < need) { set_error("buffer of %zu bytes, need %zu", bytes, need); return FESPMV_ERR_INVALID_ARG; }

@@ -32,6 +32,8 @@ struct CgScalars {
     double rho, pq, alpha, beta, rr, bb, thresh2, true_rr;
     int iters, max_iter, status, pad;
     unsigned int counter, pad2;
+    double thresh_in;   // refinement: inner stop threshold on r_in.r_in
+    int iters_in, pad3; // refinement: inner steps of the current outer step
 };
 
 struct CgWork {
@@ -45,6 +47,10 @@ struct CgWork {
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // refinement (float inner CG): w, r_in, p, q
+    float *w32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
+    int chunk_low[2] = {0, 0};
 };
 
 // ------------------------------------------------------------------ reductions
@@ -253,12 +259,150 @@ __global__ void __launch_bounds__(256) cg_true_residual(int64_t n, const double*
     if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) sc->true_rr = v[0];
 }
 
+// ------------------------------------------------------------------ refinement kernels
+// Inner CG on B = S A S with float vectors and float products; dot products and
+// all scalars in FP64 (the oracle's refinement, step by step).
+
+__device__ __forceinline__ void finish_pq_inner(double pq, CgScalars* sc) {
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) sc->status = CG_BREAKDOWN;
+    else sc->alpha = sc->rho / pq;
+}
+
+template <typename VT, int V, int U>
+__global__ void __launch_bounds__(256) cg32_spmv_dot_sliced(const uint4* __restrict__ meta,
+                                                            const int32_t* __restrict__ col,
+                                                            const VT* __restrict__ val,
+                                                            const float* __restrict__ p,
+                                                            float* __restrict__ q, int64_t n_slices,
+                                                            int64_t n, double* partials,
+                                                            CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    if (warp < n_slices) {
+        const uint4 m = meta[warp];
+        const float sum = sliced_row_sum_low<VT, V, U>(m, col, val, p, lane);
+        const int lt = (int)m.w;
+        const int64_t row = (int64_t)m.z + (lane >> lt);
+        if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+            q[row] = sum;
+            v[0] = (double)p[row] * (double)sum;
+        }
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+}
+
+template <typename VT, int L>
+__global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const VT* __restrict__ val, const float* __restrict__ p,
+                                  float* __restrict__ q, int64_t n, double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    double v[1] = {0.0};
+    const float sum = csr_row_sum_low<VT, L>(row, sub, n, rowptr, col, val, p);
+    if (row < n && sub == 0) {
+        q[row] = sum;
+        v[0] = (double)p[row] * (double)sum;
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+}
+
+__global__ void __launch_bounds__(256) cg32_update(int64_t n, float* __restrict__ w,
+                                                   float* __restrict__ r,
+                                                   const float* __restrict__ p,
+                                                   const float* __restrict__ q, double* partials,
+                                                   CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const float a = (float)sc->alpha;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        w[i] = fmaf(a, p[i], w[i]);
+        const float ri = fmaf(-a, q[i], r[i]);
+        r[i] = ri;
+        v[0] = fma((double)ri, (double)ri, v[0]);
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->iters_in += 1;
+        sc->rr = v[0];
+        if (!isfinite(v[0])) sc->status = CG_BREAKDOWN;
+        else if (v[0] <= sc->thresh_in) sc->status = CG_CONVERGED;
+        else if (sc->iters_in >= sc->max_iter) sc->status = CG_MAXITER;
+        else {
+            sc->beta = v[0] / sc->rho;
+            sc->rho = v[0];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) cg32_pupdate(int64_t n, float* __restrict__ p,
+                                                    const float* __restrict__ r, const CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const float beta = (float)sc->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+
+// Outer step: r = b - Ax (FP64; Ax = q or 0), rhs = float(S r); inner state
+// w = 0, r_in = p = rhs.  Sums: r.r (outer), rhs.rhs (inner rho), b.b.
+__global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* __restrict__ b,
+                                                       const double* __restrict__ q,
+                                                       const double* __restrict__ scale,
+                                                       float* __restrict__ w, float* __restrict__ r_in,
+                                                       float* __restrict__ p, double tol2,
+                                                       double inner_tol2, double* partials,
+                                                       CgScalars* sc) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        const double ri = q ? bi - q[i] : bi;
+        const float rs = (float)(scale[i] * ri);
+        w[i] = 0.0f;
+        r_in[i] = rs;
+        p[i] = rs;
+        v[0] = fma(ri, ri, v[0]);
+        v[1] = fma((double)rs, (double)rs, v[1]);
+        v[2] = fma(bi, bi, v[2]);
+    }
+    if (grid_sum<3>(v, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->true_rr = v[0];
+        sc->rho = v[1];
+        sc->bb = v[2];
+        sc->thresh2 = tol2 * v[2];
+        sc->thresh_in = inner_tol2 * v[1];
+        sc->iters_in = 0;
+        if (!isfinite(v[0]) || !isfinite(v[1])) sc->status = CG_BREAKDOWN;
+        else if (v[0] <= sc->thresh2) sc->status = CG_CONVERGED;
+        else sc->status = CG_RUNNING;
+    }
+}
+
+// x += S w in FP64.
+__global__ void __launch_bounds__(256) refine_update(int64_t n, double* __restrict__ x,
+                                                     const double* __restrict__ scale,
+                                                     const float* __restrict__ w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fma(scale[i], (double)w[i], x[i]);
+}
+
 // ------------------------------------------------------------------ host side
 
 void free_cg(fespmv_mat* A) {
     CgWork* w = A->cg;
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
+    for (cudaGraphExec_t g : w->graph_low)
+        if (g) cudaGraphExecDestroy(g);
+    for (float* f : {w->w32, w->r32, w->p32, w->q32})
+        if (f) cudaFree(f);
     for (cudaEvent_t e : w->ev)
         if (e) cudaEventDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
@@ -361,24 +505,20 @@ static int read_scalars(CgWork* w, cudaStream_t s, int slot) {
     return FESPMV_OK;
 }
 
-// Run graphs of `chunk` iterations until the status word leaves RUNNING.  The
-// next graph is queued before the previous one's status is read, so the GPU
-// never waits for the host; graphs queued after convergence are no-ops.
-static int iterate(fespmv_mat* A, cudaStream_t s, int chunk, int max_iter) {
-    CgWork* w = A->cg;
-    int rc = ensure_graph(A, chunk);
-    if (rc) return rc;
-    const int64_t max_graphs = (int64_t)max_iter / chunk + 3;
+// Launch graph `g` repeatedly until the status word leaves RUNNING.  The next
+// graph is queued before the previous one's status is read, so the GPU never
+// waits for the host; graphs queued after the stop are no-ops.
+static int run_graphs(CgWork* w, cudaGraphExec_t g, cudaStream_t s, int64_t max_graphs) {
     int64_t launched = 0;
     int slot = 0;
-    FESPMV_CUDA(cudaGraphLaunch(w->graph, s));
+    FESPMV_CUDA(cudaGraphLaunch(g, s));
     FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[0], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     FESPMV_CUDA(cudaEventRecord(w->ev[0], s));
     ++launched;
     for (;;) {
         const int next = slot ^ 1;
         if (launched < max_graphs) {
-            FESPMV_CUDA(cudaGraphLaunch(w->graph, s));
+            FESPMV_CUDA(cudaGraphLaunch(g, s));
             FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[next], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
             FESPMV_CUDA(cudaEventRecord(w->ev[next], s));
             ++launched;
@@ -388,6 +528,149 @@ static int iterate(fespmv_mat* A, cudaStream_t s, int chunk, int max_iter) {
         slot = next;
     }
     FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+}
+
+static int iterate(fespmv_mat* A, cudaStream_t s, int chunk, int max_iter) {
+    int rc = ensure_graph(A, chunk);
+    if (rc) return rc;
+    return run_graphs(A->cg, A->cg->graph, s, (int64_t)max_iter / chunk + 3);
+}
+
+// ---- refinement
+
+template <typename VT, int V>
+static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
+    constexpr int U = (V == 4) ? 4 : 8;
+    cg32_spmv_dot_sliced<VT, V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, val, w->p32,
+                                                                     w->q32, A->n_slices, A->n,
+                                                                     w->partials, w->sc);
+}
+
+template <typename VT, int L>
+static void launch_inner_dot_csr(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
+    cg32_spmv_dot_csr<VT, L><<<spmv_grid(A), A->block, 0, s>>>(A->d_rowptr, A->d_colind, val, w->p32,
+                                                               w->q32, A->n, w->partials, w->sc);
+}
+
+template <typename VT>
+static void launch_inner_dot(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
+    if (A->format == FESPMV_FMT_SLICED) {
+        switch (A->vec) {
+            case 1: launch_inner_dot_sliced<VT, 1>(A, w, val, s); break;
+            case 4: launch_inner_dot_sliced<VT, 4>(A, w, val, s); break;
+            default: launch_inner_dot_sliced<VT, 2>(A, w, val, s); break;
+        }
+    } else {
+        switch (A->csr_lanes) {
+            case 1: launch_inner_dot_csr<VT, 1>(A, w, val, s); break;
+            case 2: launch_inner_dot_csr<VT, 2>(A, w, val, s); break;
+            case 4: launch_inner_dot_csr<VT, 4>(A, w, val, s); break;
+            case 8: launch_inner_dot_csr<VT, 8>(A, w, val, s); break;
+            case 16: launch_inner_dot_csr<VT, 16>(A, w, val, s); break;
+            default: launch_inner_dot_csr<VT, 32>(A, w, val, s); break;
+        }
+    }
+}
+
+static void launch_inner_iteration(const fespmv_mat* A, CgWork* w, int bf16, cudaStream_t s) {
+    if (bf16)
+        launch_inner_dot<__nv_bfloat16>(A, w, reinterpret_cast<const __nv_bfloat16*>(A->d_val16), s);
+    else
+        launch_inner_dot<float>(A, w, A->d_val32, s);
+    cg32_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->w32, w->r32, w->p32, w->q32, w->partials, w->sc);
+    cg32_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p32, w->r32, w->sc);
+}
+
+static int ensure_graph_low(fespmv_mat* A, int bf16, int chunk) {
+    CgWork* w = A->cg;
+    if (w->graph_low[bf16] && w->chunk_low[bf16] == chunk) return FESPMV_OK;
+    if (w->graph_low[bf16]) {
+        cudaGraphExecDestroy(w->graph_low[bf16]);
+        w->graph_low[bf16] = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    FESPMV_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) launch_inner_iteration(A, w, bf16, w->cap);
+    cudaError_t e = cudaStreamEndCapture(w->cap, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&w->graph_low[bf16], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    w->chunk_low[bf16] = chunk;
+    return FESPMV_OK;
+}
+
+static int ensure_low_workspace(fespmv_mat* A) {
+    CgWork* w = A->cg;
+    if (w->w32) return FESPMV_OK;
+    const size_t nb = sizeof(float) * (size_t)A->n;
+    float** vecs[] = {&w->w32, &w->r32, &w->p32, &w->q32};
+    for (float** v : vecs) {
+        int rc = device_alloc(A, (void**)v, nb, "refinement vector");
+        if (rc) return rc;
+    }
+    return FESPMV_OK;
+}
+
+// Mixed-precision iterative refinement (see cg_solve in fespmv.h).  b and x0 are
+// already in the handle's numbering in w->b / w->x.
+static int refine_impl(fespmv_mat* A, const cg_options& o, bool has_x0, cg_result* res, cudaStream_t s,
+                       int* status_out) {
+    CgWork* w = A->cg;
+    const int bf16 = o.precision == FESPMV_CG_BF16_REFINE ? 1 : 0;
+    int rc = ensure_low_workspace(A);
+    if (rc) return rc;
+    if ((rc = ensure_graph_low(A, bf16, o.check_every))) return rc;
+    int bad = 0;
+    FESPMV_CUDA(cudaMemcpyAsync(&bad, A->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("refinement needs a positive, finite diagonal (S = diag(A)^-1/2)");
+        return FESPMV_ERR_BREAKDOWN;
+    }
+    CgScalars init;
+    std::memset(&init, 0, sizeof(init));
+    init.max_iter = o.max_iter;
+    FESPMV_CUDA(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    const double tol2 = o.tol * o.tol, in2 = o.inner_tol * o.inner_tol;
+    double prev = INFINITY;
+    int outer = 0;
+    int status = CG_MAXITER;
+    for (;; ++outer) {
+        const bool ax = has_x0 || outer > 0;
+        if (ax && (rc = launch_spmv(A, w->x, w->q, s))) return rc;
+        refine_residual<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, ax ? w->q : nullptr, A->d_scale, w->w32,
+                                                    w->r32, w->p32, tol2, in2, w->partials, w->sc);
+        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = read_scalars(w, s, 0))) return rc;
+        const CgScalars& h = w->h_sc[0];
+        if (h.bb == 0.0) {
+            FESPMV_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * (size_t)A->n, s));
+            status = CG_CONVERGED;
+            break;
+        }
+        if (h.status == CG_CONVERGED) { status = CG_CONVERGED; break; }
+        if (h.status == CG_BREAKDOWN) { status = CG_BREAKDOWN; break; }
+        if (outer >= o.max_outer) { status = CG_MAXITER; break; }
+        if (!(h.true_rr < prev)) {  // no progress: the low-precision operator is too far from A
+            set_error("refinement stagnated: ||b - A x|| did not decrease");
+            status = CG_MAXITER;
+            break;
+        }
+        prev = h.true_rr;
+        if ((rc = run_graphs(w, w->graph_low[bf16], s, (int64_t)o.max_iter / o.check_every + 3))) return rc;
+        refine_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, A->d_scale, w->w32);
+        FESPMV_CUDA(cudaGetLastError());
+    }
+    const CgScalars& h = w->h_sc[0];
+    if (res) {
+        res->iters = h.iters;
+        res->outer = outer;
+        res->relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+        res->true_relres = res->relres;
+    }
+    *status_out = status;
     return FESPMV_OK;
 }
 
@@ -401,11 +684,22 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
     if (o.max_restarts == 0) o.max_restarts = 3;
     if (o.max_restarts < 0) o.max_restarts = 0;
     if (o.check_every == 0) o.check_every = 16;
+    if (o.max_outer == 0) o.max_outer = 60;
+    if (o.inner_tol == 0.0) o.inner_tol = 1e-2;
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.check_every > 4096 ||
-        o.precision != FESPMV_CG_F64 ||
+        o.precision < FESPMV_CG_F64 || o.precision > FESPMV_CG_BF16_REFINE || o.max_outer < 0 ||
+        !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
         (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND))) {
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.precision == FESPMV_CG_F32_REFINE && !A->d_val32) {
+        set_error("FESPMV_CG_F32_REFINE needs a handle created with FESPMV_PREC_F32");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    if (o.precision == FESPMV_CG_BF16_REFINE && !A->d_val16) {
+        set_error("FESPMV_CG_BF16_REFINE needs a handle created with FESPMV_PREC_BF16");
+        return FESPMV_ERR_UNSUPPORTED;
     }
     if (res) std::memset(res, 0, sizeof(*res));
     if (A->n == 0) return FESPMV_OK;
@@ -443,6 +737,11 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
         FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, s));
     }
 
+    int status = CG_RUNNING;
+    int restarts = 0;
+    if (o.precision != FESPMV_CG_F64) {
+        if ((rc = refine_impl(A, o, has_x0, res, s, &status))) return rc;
+    } else {
     CgScalars init;
     std::memset(&init, 0, sizeof(init));
     init.max_iter = o.max_iter;
@@ -453,9 +752,7 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
     FESPMV_CUDA(cudaGetLastError());
 
     const double tol2 = o.tol * o.tol;
-    int restarts = 0;
     bool need_ax = has_x0;
-    int status = CG_RUNNING;
     for (;;) {
         if (need_ax) {
             if ((rc = launch_spmv(A, w->x, w->q, s))) return rc;
@@ -496,6 +793,7 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
             status = CG_MAXITER;
         }
         break;
+    }
     }
 
     // x back to the caller's numbering

@@ -83,6 +83,12 @@ struct fespmv_mat {
     double* d_xh = nullptr;           // host-I/O staging (n each), allocated on first use
     double* d_yh = nullptr;
     double* d_vals_in = nullptr;      // update_values staging (nnz), allocated on first use
+    float* d_val32 = nullptr;         // B = S A S in FP32 (same positions as d_val)
+    uint16_t* d_val16 = nullptr;      // B in bfloat16 bits
+    double* d_scale = nullptr;        // S = diag(A)^-1/2 (handle numbering)
+    int* d_flag = nullptr;            // set to 1 when diag(A) has a non-positive entry
+    float* d_xs = nullptr;            // float permuted-I/O scratch (n each)
+    float* d_ys = nullptr;
 
     fespmv::CgWork* cg = nullptr;     // CG workspace, allocated by the first cg_solve
 };
@@ -97,6 +103,11 @@ int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s)
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
 unsigned grid_for(int64_t work, int block);
+// Rebuilds S and the FP32/BF16 copies of S A S from the FP64 values (if held).
+int launch_build_scaled(fespmv_mat* A, cudaStream_t s);
+// y = B x with the FP32 (precision FESPMV_PREC_F32) or BF16 copy, handle numbering.
+int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
+int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s);
 
 // CG (cg.cu)
 void free_cg(fespmv_mat* A);

@@ -103,3 +103,111 @@ __device__ __forceinline__ double csr_row_sum_f64(int64_t row, int sub, int64_t 
 }
 
 }  // namespace fespmv
+
+// ---------------------------------------------------------------- low-precision cores
+// Values of B = S A S stored as float or bfloat16, x and the sums in float.
+#include <cuda_bf16.h>
+
+namespace fespmv {
+
+template <typename VT, int V> struct LowChunk;
+template <int V> struct LowChunk<float, V> {
+    float v[V]; int32_t c[V];
+    __device__ __forceinline__ void load(const float* vp, const int32_t* cp) {
+        if constexpr (V == 1) {
+            v[0] = ld_stream(vp); c[0] = ld_stream(cp);
+        } else if constexpr (V == 2) {
+            float2 a = ld_stream(reinterpret_cast<const float2*>(vp));
+            int2 b = ld_stream(reinterpret_cast<const int2*>(cp));
+            v[0] = a.x; v[1] = a.y; c[0] = b.x; c[1] = b.y;
+        } else {
+            float4 a = ld_stream(reinterpret_cast<const float4*>(vp));
+            int4 b = ld_stream(reinterpret_cast<const int4*>(cp));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            c[0] = b.x; c[1] = b.y; c[2] = b.z; c[3] = b.w;
+        }
+    }
+};
+template <int V> struct LowChunk<__nv_bfloat16, V> {
+    float v[V]; int32_t c[V];
+    __device__ __forceinline__ void load(const __nv_bfloat16* vp, const int32_t* cp) {
+        if constexpr (V == 1) {
+            unsigned short u = ld_stream(reinterpret_cast<const unsigned short*>(vp));
+            v[0] = __uint_as_float((unsigned)u << 16);
+            c[0] = ld_stream(cp);
+        } else if constexpr (V == 2) {
+            unsigned u = ld_stream(reinterpret_cast<const unsigned*>(vp));
+            v[0] = __uint_as_float(u << 16); v[1] = __uint_as_float(u & 0xffff0000u);
+            int2 b = ld_stream(reinterpret_cast<const int2*>(cp));
+            c[0] = b.x; c[1] = b.y;
+        } else {
+            uint2 u = ld_stream(reinterpret_cast<const uint2*>(vp));
+            v[0] = __uint_as_float(u.x << 16); v[1] = __uint_as_float(u.x & 0xffff0000u);
+            v[2] = __uint_as_float(u.y << 16); v[3] = __uint_as_float(u.y & 0xffff0000u);
+            int4 b = ld_stream(reinterpret_cast<const int4*>(cp));
+            c[0] = b.x; c[1] = b.y; c[2] = b.z; c[3] = b.w;
+        }
+    }
+};
+
+template <typename VT, int V, int U>
+__device__ __forceinline__ float sliced_row_sum_low(const uint4 m, const int32_t* __restrict__ col,
+                                                    const VT* __restrict__ val,
+                                                    const float* __restrict__ x, int lane) {
+    const int64_t off = (int64_t)m.x * 32;
+    const int w = (int)m.y;
+    const int lt = (int)m.w;
+    const VT* vp = val + off + lane * V;
+    const int32_t* cp = col + off + lane * V;
+    float sum = 0.0f;
+    int s = 0;
+    for (; s + U * V <= w; s += U * V) {
+        LowChunk<VT, V> e[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) e[u].load(vp + u * 32 * V, cp + u * 32 * V);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                sum = fmaf(e[u].v[k], e[u].c[k] >= 0 ? __ldg(x + e[u].c[k]) : 0.0f, sum);
+        vp += U * 32 * V;
+        cp += U * 32 * V;
+    }
+    for (; s < w; s += V) {
+        LowChunk<VT, V> e;
+        e.load(vp, cp);
+#pragma unroll
+        for (int k = 0; k < V; ++k) sum = fmaf(e.v[k], e.c[k] >= 0 ? __ldg(x + e.c[k]) : 0.0f, sum);
+        vp += 32 * V;
+        cp += 32 * V;
+    }
+    const int T = 1 << lt;
+    for (int o = T >> 1; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    return sum;
+}
+
+template <typename VT>
+__device__ __forceinline__ float low_to_float(VT v);
+template <> __device__ __forceinline__ float low_to_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ float low_to_float<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+template <typename VT, int L>
+__device__ __forceinline__ float csr_row_sum_low(int64_t row, int sub, int64_t n,
+                                                 const int64_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const VT* __restrict__ val,
+                                                 const float* __restrict__ x) {
+    float sum = 0.0f;
+    if (row < n) {
+        const int64_t e = rowptr[row + 1];
+        for (int64_t p = rowptr[row] + sub; p < e; p += L)
+            sum = fmaf(low_to_float<VT>(val[p]), __ldg(x + col[p]), sum);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, L);
+    return sum;
+}
+
+}  // namespace fespmv

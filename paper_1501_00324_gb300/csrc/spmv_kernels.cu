@@ -53,10 +53,93 @@ __global__ void __launch_bounds__(256) sliced_f64(const uint4* __restrict__ meta
     if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
 }
 
+// ---------------------------------------------------------------- low precision (B = S A S)
+
+template <typename VT, int V, int U>
+__global__ void __launch_bounds__(256) sliced_low(const uint4* __restrict__ meta,
+                                                  const int32_t* __restrict__ col,
+                                                  const VT* __restrict__ val,
+                                                  const float* __restrict__ x,
+                                                  float* __restrict__ y, int64_t n_slices, int64_t n) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_slices) return;
+    const uint4 m = meta[warp];
+    const float sum = sliced_row_sum_low<VT, V, U>(m, col, val, x, lane);
+    const int lt = (int)m.w;
+    const int64_t row = (int64_t)m.z + (lane >> lt);
+    if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
+}
+
+template <typename VT, int L>
+__global__ void csr_low(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        const VT* __restrict__ val, const float* __restrict__ x,
+                        float* __restrict__ y, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    const float sum = csr_row_sum_low<VT, L>(row, sub, n, rowptr, col, val, x);
+    if (row < n && sub == 0) y[row] = sum;
+}
+
+// S = diag(A)^-1/2; a non-positive or non-finite diagonal sets *bad.
+__global__ void scale_from_diag(const double* __restrict__ diag, double* __restrict__ scale,
+                                int64_t n, int* bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double d = diag[i];
+        if (d > 0.0 && isfinite(d)) {
+            scale[i] = 1.0 / sqrt(d);
+        } else {
+            scale[i] = 0.0;
+            *bad = 1;
+        }
+    }
+}
+
+__device__ __forceinline__ void store_low(float b, float* f32, uint16_t* b16, int64_t pos) {
+    if (f32) f32[pos] = b;
+    if (b16) b16[pos] = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+}
+
+// B = S A S entry by entry: b = (float)((s_row * a) * s_col), padding stays 0.
+template <int V>
+__global__ void build_scaled_sliced(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
+                                   const double* __restrict__ val, const double* __restrict__ scale,
+                                   float* f32, uint16_t* b16, int64_t n_slices) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_slices) return;
+    const uint4 m = meta[warp];
+    const int64_t off = (int64_t)m.x * 32;
+    const int64_t row = (int64_t)m.z + (lane >> m.w);
+    for (int st = 0; st < (int)m.y; ++st) {
+        const int64_t pos = off + (int64_t)(st / V) * 32 * V + lane * V + st % V;
+        const int32_t c = col[pos];
+        const float b = c >= 0 ? (float)((scale[row] * val[pos]) * scale[c]) : 0.0f;
+        store_low(b, f32, b16, pos);
+    }
+}
+
+__global__ void build_scaled_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const double* __restrict__ scale,
+                                 float* f32, uint16_t* b16, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            store_low((float)((scale[i] * val[p]) * scale[col[p]]), f32, b16, p);
+}
+
 // ---------------------------------------------------------------- gathers
 
 __global__ void gather_f64(const double* __restrict__ in, const int32_t* __restrict__ idx,
                            double* __restrict__ out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __ldg(in + idx[i]);
+}
+
+__global__ void gather_f32(const float* __restrict__ in, const int32_t* __restrict__ idx,
+                           float* __restrict__ out, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = __ldg(in + idx[i]);
 }
@@ -91,6 +174,33 @@ int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, 
     return FESPMV_OK;
 }
 
+int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s) {
+    if (n == 0) return FESPMV_OK;
+    gather_f32<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+int launch_build_scaled(fespmv_mat* A, cudaStream_t s) {
+    if (!A->d_scale || A->n == 0) return FESPMV_OK;
+    FESPMV_CUDA(cudaMemsetAsync(A->d_flag, 0, sizeof(int), s));
+    scale_from_diag<<<grid_for(A->n, 256), 256, 0, s>>>(A->d_diag, A->d_scale, A->n, A->d_flag);
+    if (!A->d_val32 && !A->d_val16) return FESPMV_OK;
+    if (A->format == FESPMV_FMT_SLICED) {
+        const unsigned g = grid_for(A->n_slices * 32, 256);
+        switch (A->vec) {
+            case 1: build_scaled_sliced<1><<<g, 256, 0, s>>>(A->d_meta, A->d_col, A->d_val, A->d_scale, A->d_val32, A->d_val16, A->n_slices); break;
+            case 4: build_scaled_sliced<4><<<g, 256, 0, s>>>(A->d_meta, A->d_col, A->d_val, A->d_scale, A->d_val32, A->d_val16, A->n_slices); break;
+            default: build_scaled_sliced<2><<<g, 256, 0, s>>>(A->d_meta, A->d_col, A->d_val, A->d_scale, A->d_val32, A->d_val16, A->n_slices); break;
+        }
+    } else {
+        build_scaled_csr<<<grid_for(A->n, 256), 256, 0, s>>>(A->d_rowptr, A->d_colind, A->d_val, A->d_scale,
+                                                           A->d_val32, A->d_val16, A->n);
+    }
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s) {
     if (A->format == FESPMV_FMT_SLICED) {
         if (A->packed_len > 0)
@@ -103,7 +213,7 @@ int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s) {
     if (A->n > 0)
         fill_diag_f64<<<grid_for(A->n, 256), 256, 0, s>>>(vals_in, A->d_diagpos, A->d_diag, A->n);
     FESPMV_CUDA(cudaGetLastError());
-    return FESPMV_OK;
+    return launch_build_scaled(A, s);
 }
 
 template <int L>
@@ -119,6 +229,48 @@ static void launch_sliced(const fespmv_mat* A, const double* x, double* y, cudaS
     int64_t threads = A->n_slices * 32;
     sliced_f64<V, U><<<grid_for(threads, A->block), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val,
                                                                      x, y, A->n_slices, A->n);
+}
+
+template <typename VT, int V>
+static void launch_sliced_low(const fespmv_mat* A, const VT* val, const float* x, float* y, cudaStream_t s) {
+    constexpr int U = (V == 4) ? 4 : 8;
+    sliced_low<VT, V, U><<<grid_for(A->n_slices * 32, A->block), A->block, 0, s>>>(A->d_meta, A->d_col, val, x,
+                                                                               y, A->n_slices, A->n);
+}
+
+template <typename VT, int L>
+static void launch_csr_low(const fespmv_mat* A, const VT* val, const float* x, float* y, cudaStream_t s) {
+    csr_low<VT, L><<<grid_for(A->n * L, A->block), A->block, 0, s>>>(A->d_rowptr, A->d_colind, val, x, y, A->n);
+}
+
+template <typename VT>
+static void dispatch_low(const fespmv_mat* A, const VT* val, const float* x, float* y, cudaStream_t s) {
+    if (A->format == FESPMV_FMT_SLICED) {
+        switch (A->vec) {
+            case 1: launch_sliced_low<VT, 1>(A, val, x, y, s); break;
+            case 4: launch_sliced_low<VT, 4>(A, val, x, y, s); break;
+            default: launch_sliced_low<VT, 2>(A, val, x, y, s); break;
+        }
+    } else {
+        switch (A->csr_lanes) {
+            case 1: launch_csr_low<VT, 1>(A, val, x, y, s); break;
+            case 2: launch_csr_low<VT, 2>(A, val, x, y, s); break;
+            case 4: launch_csr_low<VT, 4>(A, val, x, y, s); break;
+            case 8: launch_csr_low<VT, 8>(A, val, x, y, s); break;
+            case 16: launch_csr_low<VT, 16>(A, val, x, y, s); break;
+            default: launch_csr_low<VT, 32>(A, val, x, y, s); break;
+        }
+    }
+}
+
+int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s) {
+    if (A->n == 0) return FESPMV_OK;
+    if (precision == FESPMV_PREC_F32)
+        dispatch_low<float>(A, A->d_val32, x, y, s);
+    else
+        dispatch_low<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->d_val16), x, y, s);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
 }
 
 int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s) {

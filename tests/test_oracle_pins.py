@@ -286,3 +286,23 @@ def test_refinement_reaches_fp64_solution(storage):
     A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
     cond = np.linalg.cond(A)
     assert np.linalg.norm(xr - x64) / np.linalg.norm(x64) <= cond * 1e-10
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_scaled_values_match_dense_scaling(storage):
+    p = fegen.cube_elasticity(3, 29)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    s = 1.0 / np.sqrt(np.diag(A))
+    Bd = (s[:, None] * A) * s[None, :]
+    bv = oracle.scaled_values(p.rowptr, p.colind, p.values, storage)
+    B = dense_of(p.rowptr, p.colind, bv.astype(np.float64), p.n_rows)
+    u = 2.0 ** -24 if storage == "f32" else 2.0 ** -8   # unit roundoff, 24- or 8-bit significand
+    assert np.all(np.abs(B - Bd) <= u * np.abs(Bd) * 1.0001)
+    assert np.array_equal(B, B.T)                        # symmetric scaling keeps symmetry
+    assert np.all(np.abs(np.diag(B) - 1.0) <= u)
+    # float products: within the float rounding bound of the dense FP64 product
+    x = fegen.random_vector(p.n_rows, 30).astype(np.float32)
+    y = oracle.csr_spmv_f32(p.rowptr, p.colind, bv, x)
+    yd = B @ x.astype(np.float64)
+    L = np.diff(p.rowptr).max()
+    assert np.all(np.abs(y - yd) <= (L + 1) * 2.0 ** -24 * (np.abs(B) @ np.abs(x)))
