@@ -51,6 +51,26 @@ struct CgWork {
     float *w32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
     int chunk_low[2] = {0, 0};
+    double* h_io = nullptr;     // pinned host staging of n doubles (solve server)
+    int64_t bytes = 0;          // device bytes held
+};
+
+// One solve in flight (see the host side below).
+struct CgRun {
+    fespmv_mat* A = nullptr;
+    CgWork* w = nullptr;
+    cudaStream_t s = nullptr;
+    cg_options o{};
+    bool permute = false, has_x0 = false, out_host = false;
+    double* x_out = nullptr;
+    int phase = 5;             // PH_DONE
+    int restarts = 0, outer = 0;
+    double prev = 0.0;
+    int64_t graphs_left = 0;
+    int queued = 0, head = 0;
+    int status = 0, error = 0;
+    cudaGraphExec_t graph = nullptr;
+    CgScalars last{};
 };
 
 // ------------------------------------------------------------------ reductions
@@ -394,55 +414,105 @@ __global__ void __launch_bounds__(256) refine_update(int64_t n, double* __restri
 }
 
 // ------------------------------------------------------------------ host side
-
-void free_cg(fespmv_mat* A) {
-    CgWork* w = A->cg;
-    if (!w) return;
-    if (w->graph) cudaGraphExecDestroy(w->graph);
-    for (cudaGraphExec_t g : w->graph_low)
-        if (g) cudaGraphExecDestroy(g);
-    for (float* f : {w->w32, w->r32, w->p32, w->q32})
-        if (f) cudaFree(f);
-    for (cudaEvent_t e : w->ev)
-        if (e) cudaEventDestroy(e);
-    if (w->cap) cudaStreamDestroy(w->cap);
-    void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    if (w->h_sc) cudaFreeHost(w->h_sc);
-    delete w;
-    A->cg = nullptr;
-}
+//
+// A solve in flight is a CgRun: a small state machine that enqueues work on
+// its stream and advances when the event of its last status copy has fired.
+// cg_solve drives one run to the end (blocking); the solve server advances
+// many runs round-robin, each on its own stream and workspace, so their
+// iterations overlap on the device.
 
 static unsigned spmv_grid(const fespmv_mat* A) {
     if (A->format == FESPMV_FMT_SLICED) return grid_for(A->n_slices * 32, A->block);
     return grid_for(A->n * A->csr_lanes, A->block);
 }
 
-static int ensure_workspace(fespmv_mat* A) {
-    if (A->cg) return FESPMV_OK;
+void destroy_work(CgWork* w) {
+    if (!w) return;
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    for (cudaGraphExec_t g : w->graph_low)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t e : w->ev)
+        if (e) cudaEventDestroy(e);
+    if (w->cap) cudaStreamDestroy(w->cap);
+    void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc,
+                    w->w32, w->r32, w->p32, w->q32};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (w->h_sc) cudaFreeHost(w->h_sc);
+    if (w->h_io) cudaFreeHost(w->h_io);
+    delete w;
+}
+
+void free_cg(fespmv_mat* A) {
+    destroy_work(A->cg);
+    A->cg = nullptr;
+}
+
+static int work_alloc(CgWork* w, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu bytes) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FESPMV_ERR_OOM : FESPMV_ERR_CUDA;
+    }
+    w->bytes += (int64_t)bytes;
+    return FESPMV_OK;
+}
+
+// Workspace bytes one solve of A needs (FP64 vectors, partial sums, scalars and,
+// for refined precisions, the float vectors).
+int64_t work_bytes(const fespmv_mat* A, bool refine) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
+    const int64_t np = 3 * std::max<int64_t>(spmv_grid(A), upd) + 1;
+    int64_t b = 6 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
+    if (refine) b += 4 * 4 * A->n;
+    return b;
+}
+
+int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
+    *out = nullptr;
     CgWork* w = new CgWork();
-    A->cg = w;
     w->n = A->n;
-    int dev = 0, sms = 0;
-    FESPMV_CUDA(cudaGetDevice(&dev));
-    FESPMV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int dev = 0, sms = 0, rc;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+        destroy_work(w);
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
     w->upd_grid = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
     const size_t nb = sizeof(double) * (size_t)A->n;
     double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv};
-    for (double** v : vecs) {
-        int rc = device_alloc(A, (void**)v, nb, "CG vector");
-        if (rc) return rc;
-    }
+    for (double** v : vecs)
+        if ((rc = work_alloc(w, (void**)v, nb, "CG vector"))) { destroy_work(w); return rc; }
     const size_t np = 3 * (size_t)std::max(spmv_grid(A), w->upd_grid) + 1;
-    int rc = device_alloc(A, (void**)&w->partials, sizeof(double) * np, "CG partial sums");
-    if (rc) return rc;
-    rc = device_alloc(A, (void**)&w->sc, sizeof(CgScalars), "CG scalars");
-    if (rc) return rc;
-    FESPMV_CUDA(cudaMallocHost((void**)&w->h_sc, 2 * sizeof(CgScalars)));
-    FESPMV_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
-    for (cudaEvent_t& e : w->ev) FESPMV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
+        (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
+        destroy_work(w);
+        return rc;
+    }
+    if ((e = cudaMallocHost((void**)&w->h_sc, 2 * sizeof(CgScalars))) != cudaSuccess ||
+        (host_staging && (e = cudaMallocHost((void**)&w->h_io, nb ? nb : 16)) != cudaSuccess) ||
+        (e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&w->ev[1], cudaEventDisableTiming)) != cudaSuccess) {
+        destroy_work(w);
+        return cuda_fail(e, "CG workspace setup");
+    }
+    *out = w;
     return FESPMV_OK;
+}
+
+static int ensure_workspace(fespmv_mat* A) {
+    if (A->cg) return FESPMV_OK;
+    int rc = create_work(A, false, &A->cg);
+    if (rc == FESPMV_OK) A->device_bytes += A->cg->bytes;
+    return rc;
 }
 
 template <int V>
@@ -479,65 +549,6 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     cg_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->p, w->q, w->dinv, w->partials, w->sc);
     cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->sc);
 }
-
-static int ensure_graph(fespmv_mat* A, int chunk) {
-    CgWork* w = A->cg;
-    if (w->graph && w->graph_chunk == chunk) return FESPMV_OK;
-    if (w->graph) {
-        cudaGraphExecDestroy(w->graph);
-        w->graph = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    FESPMV_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) launch_iteration(A, w, w->cap);
-    cudaError_t e = cudaStreamEndCapture(w->cap, &g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&w->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    w->graph_chunk = chunk;
-    return FESPMV_OK;
-}
-
-static int read_scalars(CgWork* w, cudaStream_t s, int slot) {
-    FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[slot], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-    FESPMV_CUDA(cudaStreamSynchronize(s));
-    return FESPMV_OK;
-}
-
-// Launch graph `g` repeatedly until the status word leaves RUNNING.  The next
-// graph is queued before the previous one's status is read, so the GPU never
-// waits for the host; graphs queued after the stop are no-ops.
-static int run_graphs(CgWork* w, cudaGraphExec_t g, cudaStream_t s, int64_t max_graphs) {
-    int64_t launched = 0;
-    int slot = 0;
-    FESPMV_CUDA(cudaGraphLaunch(g, s));
-    FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[0], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-    FESPMV_CUDA(cudaEventRecord(w->ev[0], s));
-    ++launched;
-    for (;;) {
-        const int next = slot ^ 1;
-        if (launched < max_graphs) {
-            FESPMV_CUDA(cudaGraphLaunch(g, s));
-            FESPMV_CUDA(cudaMemcpyAsync(&w->h_sc[next], w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-            FESPMV_CUDA(cudaEventRecord(w->ev[next], s));
-            ++launched;
-        }
-        FESPMV_CUDA(cudaEventSynchronize(w->ev[slot]));
-        if (w->h_sc[slot].status != CG_RUNNING || launched >= max_graphs) break;
-        slot = next;
-    }
-    FESPMV_CUDA(cudaStreamSynchronize(s));
-    return FESPMV_OK;
-}
-
-static int iterate(fespmv_mat* A, cudaStream_t s, int chunk, int max_iter) {
-    int rc = ensure_graph(A, chunk);
-    if (rc) return rc;
-    return run_graphs(A->cg, A->cg->graph, s, (int64_t)max_iter / chunk + 3);
-}
-
-// ---- refinement
 
 template <typename VT, int V>
 static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
@@ -582,103 +593,49 @@ static void launch_inner_iteration(const fespmv_mat* A, CgWork* w, int bf16, cud
     cg32_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p32, w->r32, w->sc);
 }
 
-static int ensure_graph_low(fespmv_mat* A, int bf16, int chunk) {
-    CgWork* w = A->cg;
-    if (w->graph_low[bf16] && w->chunk_low[bf16] == chunk) return FESPMV_OK;
-    if (w->graph_low[bf16]) {
-        cudaGraphExecDestroy(w->graph_low[bf16]);
-        w->graph_low[bf16] = nullptr;
+// Graph of `chunk` iterations (kind 0: FP64; 1: FP32 inner; 2: BF16 inner) for
+// this workspace; kernel arguments are the workspace's fixed pointers.
+static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
+    cudaGraphExec_t& slot = kind == 0 ? w->graph : w->graph_low[kind - 1];
+    int& slot_chunk = kind == 0 ? w->graph_chunk : w->chunk_low[kind - 1];
+    if (slot && slot_chunk == chunk) return FESPMV_OK;
+    if (slot) {
+        cudaGraphExecDestroy(slot);
+        slot = nullptr;
     }
     cudaGraph_t g = nullptr;
     FESPMV_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) launch_inner_iteration(A, w, bf16, w->cap);
+    for (int i = 0; i < chunk; ++i) {
+        if (kind == 0) launch_iteration(A, w, w->cap);
+        else launch_inner_iteration(A, w, kind - 1, w->cap);
+    }
     cudaError_t e = cudaStreamEndCapture(w->cap, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&w->graph_low[bf16], g, 0);
+    e = cudaGraphInstantiate(&slot, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    w->chunk_low[bf16] = chunk;
+    slot_chunk = chunk;
     return FESPMV_OK;
 }
 
-static int ensure_low_workspace(fespmv_mat* A) {
-    CgWork* w = A->cg;
+static int ensure_low_workspace(CgWork* w) {
     if (w->w32) return FESPMV_OK;
-    const size_t nb = sizeof(float) * (size_t)A->n;
+    const size_t nb = sizeof(float) * (size_t)w->n;
     float** vecs[] = {&w->w32, &w->r32, &w->p32, &w->q32};
     for (float** v : vecs) {
-        int rc = device_alloc(A, (void**)v, nb, "refinement vector");
+        int rc = work_alloc(w, (void**)v, nb, "refinement vector");
         if (rc) return rc;
     }
     return FESPMV_OK;
 }
 
-// Mixed-precision iterative refinement (see cg_solve in fespmv.h).  b and x0 are
-// already in the handle's numbering in w->b / w->x.
-static int refine_impl(fespmv_mat* A, const cg_options& o, bool has_x0, cg_result* res, cudaStream_t s,
-                       int* status_out) {
-    CgWork* w = A->cg;
-    const int bf16 = o.precision == FESPMV_CG_BF16_REFINE ? 1 : 0;
-    int rc = ensure_low_workspace(A);
-    if (rc) return rc;
-    if ((rc = ensure_graph_low(A, bf16, o.check_every))) return rc;
-    int bad = 0;
-    FESPMV_CUDA(cudaMemcpyAsync(&bad, A->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FESPMV_CUDA(cudaStreamSynchronize(s));
-    if (bad) {
-        set_error("refinement needs a positive, finite diagonal (S = diag(A)^-1/2)");
-        return FESPMV_ERR_BREAKDOWN;
-    }
-    CgScalars init;
-    std::memset(&init, 0, sizeof(init));
-    init.max_iter = o.max_iter;
-    FESPMV_CUDA(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-    const double tol2 = o.tol * o.tol, in2 = o.inner_tol * o.inner_tol;
-    double prev = INFINITY;
-    int outer = 0;
-    int status = CG_MAXITER;
-    for (;; ++outer) {
-        const bool ax = has_x0 || outer > 0;
-        if (ax && (rc = launch_spmv(A, w->x, w->q, s))) return rc;
-        refine_residual<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, ax ? w->q : nullptr, A->d_scale, w->w32,
-                                                    w->r32, w->p32, tol2, in2, w->partials, w->sc);
-        FESPMV_CUDA(cudaGetLastError());
-        if ((rc = read_scalars(w, s, 0))) return rc;
-        const CgScalars& h = w->h_sc[0];
-        if (h.bb == 0.0) {
-            FESPMV_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * (size_t)A->n, s));
-            status = CG_CONVERGED;
-            break;
-        }
-        if (h.status == CG_CONVERGED) { status = CG_CONVERGED; break; }
-        if (h.status == CG_BREAKDOWN) { status = CG_BREAKDOWN; break; }
-        if (outer >= o.max_outer) { status = CG_MAXITER; break; }
-        if (!(h.true_rr < prev)) {  // no progress: the low-precision operator is too far from A
-            set_error("refinement stagnated: ||b - A x|| did not decrease");
-            status = CG_MAXITER;
-            break;
-        }
-        prev = h.true_rr;
-        if ((rc = run_graphs(w, w->graph_low[bf16], s, (int64_t)o.max_iter / o.check_every + 3))) return rc;
-        refine_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, A->d_scale, w->w32);
-        FESPMV_CUDA(cudaGetLastError());
-    }
-    const CgScalars& h = w->h_sc[0];
-    if (res) {
-        res->iters = h.iters;
-        res->outer = outer;
-        res->relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
-        res->true_relres = res->relres;
-    }
-    *status_out = status;
-    return FESPMV_OK;
+__global__ void cg_copy_flag(CgScalars* sc, const int* flag) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->pad = flag ? *flag : 0;
 }
 
-static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_options* opts,
-                         cg_result* res, cudaStream_t s) {
-    cg_options o;
-    std::memset(&o, 0, sizeof(o));
-    if (opts) o = *opts;
+enum Phase { PH_INIT_WAIT, PH_ITER, PH_TRUE_WAIT, PH_RES_WAIT, PH_OUT_WAIT, PH_DONE };
+
+static int normalize_options(cg_options& o) {
     if (o.tol == 0.0) o.tol = 1e-10;
     if (o.max_iter == 0) o.max_iter = 100000;
     if (o.max_restarts == 0) o.max_restarts = 3;
@@ -693,133 +650,304 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
     }
-    if (o.precision == FESPMV_CG_F32_REFINE && !A->d_val32) {
+    return FESPMV_OK;
+}
+
+int check_precision(const fespmv_mat* A, int precision) {
+    if (precision == FESPMV_CG_F32_REFINE && !A->d_val32) {
         set_error("FESPMV_CG_F32_REFINE needs a handle created with FESPMV_PREC_F32");
         return FESPMV_ERR_UNSUPPORTED;
     }
-    if (o.precision == FESPMV_CG_BF16_REFINE && !A->d_val16) {
+    if (precision == FESPMV_CG_BF16_REFINE && !A->d_val16) {
         set_error("FESPMV_CG_BF16_REFINE needs a handle created with FESPMV_PREC_BF16");
         return FESPMV_ERR_UNSUPPORTED;
     }
-    if (res) std::memset(res, 0, sizeof(*res));
-    if (A->n == 0) return FESPMV_OK;
-    int rc = ensure_workspace(A);
+    return FESPMV_OK;
+}
+
+// Copies the status word to the host and records the event of slot `k`.
+static int enqueue_status(CgRun& r, int k) {
+    FESPMV_CUDA(cudaMemcpyAsync(&r.w->h_sc[k], r.w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, r.s));
+    FESPMV_CUDA(cudaEventRecord(r.w->ev[k], r.s));
+    return FESPMV_OK;
+}
+
+static int enqueue_graph(CgRun& r) {
+    const int k = (r.head + r.queued) & 1;
+    FESPMV_CUDA(cudaGraphLaunch(r.graph, r.s));
+    int rc = enqueue_status(r, k);
     if (rc) return rc;
-    CgWork* w = A->cg;
-    const size_t nb = sizeof(double) * (size_t)A->n;
-    const bool host = o.flags & FESPMV_IO_HOST;
-    const bool permute = A->format == FESPMV_FMT_SLICED && !(o.flags & FESPMV_IO_PERMUTED);
+    ++r.queued;
+    --r.graphs_left;
+    return FESPMV_OK;
+}
 
-    // b (and x0) into the handle's numbering
-    const double* bsrc = b;
-    if (host) {
-        FESPMV_CUDA(cudaMemcpyAsync(w->q, b, nb, cudaMemcpyHostToDevice, s));
-        bsrc = w->q;
-    }
-    if (permute) {
-        if ((rc = launch_gather(bsrc, A->d_perm, w->b, A->n, s))) return rc;
-    } else {
-        FESPMV_CUDA(cudaMemcpyAsync(w->b, bsrc, nb, cudaMemcpyDeviceToDevice, s));
-    }
-    const bool has_x0 = o.flags & FESPMV_CG_X0;
-    if (has_x0) {
-        const double* xsrc = x;
-        if (host) {
-            FESPMV_CUDA(cudaMemcpyAsync(w->q, x, nb, cudaMemcpyHostToDevice, s));
-            xsrc = w->q;
-        }
-        if (permute) {
-            if ((rc = launch_gather(xsrc, A->d_perm, w->x, A->n, s))) return rc;
-        } else {
-            FESPMV_CUDA(cudaMemcpyAsync(w->x, xsrc, nb, cudaMemcpyDeviceToDevice, s));
-        }
-    } else {
-        FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, s));
-    }
+static int start_graphs(CgRun& r, int kind, int max_iter) {
+    int rc = ensure_graph(r.A, r.w, kind, r.o.check_every);
+    if (rc) return rc;
+    r.graph = kind == 0 ? r.w->graph : r.w->graph_low[kind - 1];
+    r.graphs_left = (int64_t)max_iter / r.o.check_every + 3;
+    r.head = 0;
+    r.queued = 0;
+    if ((rc = enqueue_graph(r))) return rc;
+    if (r.graphs_left > 0 && (rc = enqueue_graph(r))) return rc;
+    r.phase = PH_ITER;
+    return FESPMV_OK;
+}
 
-    int status = CG_RUNNING;
-    int restarts = 0;
-    if (o.precision != FESPMV_CG_F64) {
-        if ((rc = refine_impl(A, o, has_x0, res, s, &status))) return rc;
-    } else {
+static int enqueue_init(CgRun& r, bool ax) {
+    CgWork* w = r.w;
+    int rc;
+    if (ax && (rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
+    cg_init<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, w->r, w->p, w->dinv,
+                                          r.o.tol * r.o.tol, w->partials, w->sc);
+    FESPMV_CUDA(cudaGetLastError());
+    r.phase = PH_INIT_WAIT;
+    return enqueue_status(r, 0);
+}
+
+static int enqueue_residual(CgRun& r, bool ax) {
+    CgWork* w = r.w;
+    int rc;
+    if (ax && (rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
+    refine_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, r.A->d_scale, w->w32,
+                                                  w->r32, w->p32, r.o.tol * r.o.tol,
+                                                  r.o.inner_tol * r.o.inner_tol, w->partials, w->sc);
+    FESPMV_CUDA(cudaGetLastError());
+    r.phase = PH_RES_WAIT;
+    return enqueue_status(r, 0);
+}
+
+int run_begin(CgRun& r) {
+    CgWork* w = r.w;
+    int rc;
+    r.restarts = 0;
+    r.outer = 0;
+    r.prev = INFINITY;
+    r.status = CG_RUNNING;
+    r.error = FESPMV_OK;
+    r.queued = 0;
+    r.head = 0;
     CgScalars init;
     std::memset(&init, 0, sizeof(init));
-    init.max_iter = o.max_iter;
+    init.max_iter = r.o.max_iter;
     init.status = CG_RUNNING;
-    FESPMV_CUDA(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-    cg_dinv<<<w->upd_grid, 256, 0, s>>>(A->n, A->d_diag, w->dinv, (o.flags & FESPMV_CG_NO_PRECOND) ? 0 : 1,
-                                        w->sc);
+    // the pinned slot doubles as the upload buffer: it is not read until the first status copy
+    w->h_sc[1] = init;
+    FESPMV_CUDA(cudaMemcpyAsync(w->sc, &w->h_sc[1], sizeof(CgScalars), cudaMemcpyHostToDevice, r.s));
+    if (r.o.precision == FESPMV_CG_F64) {
+        cg_dinv<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, r.A->d_diag, w->dinv,
+                                              (r.o.flags & FESPMV_CG_NO_PRECOND) ? 0 : 1, w->sc);
+        FESPMV_CUDA(cudaGetLastError());
+        return enqueue_init(r, r.has_x0);
+    }
+    if ((rc = ensure_low_workspace(w))) return rc;
+    cg_copy_flag<<<1, 32, 0, r.s>>>(w->sc, r.A->d_flag);
     FESPMV_CUDA(cudaGetLastError());
+    return enqueue_residual(r, r.has_x0);
+}
 
-    const double tol2 = o.tol * o.tol;
-    bool need_ax = has_x0;
-    for (;;) {
-        if (need_ax) {
-            if ((rc = launch_spmv(A, w->x, w->q, s))) return rc;
-        }
-        cg_init<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, need_ax ? w->q : nullptr, w->r, w->p, w->dinv,
-                                            tol2, w->partials, w->sc);
-        FESPMV_CUDA(cudaGetLastError());
-        if ((rc = read_scalars(w, s, 0))) return rc;
-        if (w->h_sc[0].status == CG_BADDIAG) {
-            set_error("Jacobi preconditioning needs a positive, finite diagonal");
-            if (res) res->status = FESPMV_ERR_BREAKDOWN;
-            return FESPMV_ERR_BREAKDOWN;
-        }
-        if (w->h_sc[0].bb == 0.0) {  // b = 0: the solution is x = 0
-            FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, s));
-            status = CG_CONVERGED;
-            FESPMV_CUDA(cudaMemsetAsync(&w->sc->true_rr, 0, sizeof(double), s));
-            if ((rc = read_scalars(w, s, 0))) return rc;
-            break;
-        }
-        if (w->h_sc[0].status == CG_RUNNING) {
-            if ((rc = iterate(A, s, o.check_every, o.max_iter))) return rc;
-        }
-        // true residual in FP64
-        if ((rc = launch_spmv(A, w->x, w->q, s))) return rc;
-        cg_true_residual<<<w->upd_grid, 256, 0, s>>>(A->n, w->b, w->q, w->partials, w->sc);
-        FESPMV_CUDA(cudaGetLastError());
-        if ((rc = read_scalars(w, s, 0))) return rc;
-        status = w->h_sc[0].status;
-        if (status == CG_RUNNING) status = CG_MAXITER;  // polling limit reached
-        const bool true_ok = w->h_sc[0].true_rr <= w->h_sc[0].thresh2;
-        if (status == CG_CONVERGED && !true_ok) {
-            if (restarts < o.max_restarts && w->h_sc[0].iters < o.max_iter) {
-                ++restarts;
-                need_ax = true;
-                continue;
-            }
-            status = CG_MAXITER;
-        }
-        break;
-    }
-    }
-
-    // x back to the caller's numbering
-    double* xdst = host ? w->q : x;
-    if (permute) {
-        if ((rc = launch_gather(w->x, A->d_pinv, xdst, A->n, s))) return rc;
+static int finish(CgRun& r, int status) {
+    r.status = status;
+    CgWork* w = r.w;
+    const size_t nb = sizeof(double) * (size_t)r.A->n;
+    double* dst = r.out_host ? w->q : r.x_out;
+    int rc;
+    if (r.permute) {
+        if ((rc = launch_gather(w->x, r.A->d_pinv, dst, r.A->n, r.s))) return rc;
     } else {
-        FESPMV_CUDA(cudaMemcpyAsync(xdst, w->x, nb, cudaMemcpyDeviceToDevice, s));
+        FESPMV_CUDA(cudaMemcpyAsync(dst, w->x, nb, cudaMemcpyDeviceToDevice, r.s));
     }
-    if (host) {
-        FESPMV_CUDA(cudaMemcpyAsync(x, w->q, nb, cudaMemcpyDeviceToHost, s));
-        FESPMV_CUDA(cudaStreamSynchronize(s));
+    if (r.out_host) FESPMV_CUDA(cudaMemcpyAsync(r.x_out, w->q, nb, cudaMemcpyDeviceToHost, r.s));
+    FESPMV_CUDA(cudaEventRecord(w->ev[0], r.s));
+    r.phase = PH_OUT_WAIT;
+    return FESPMV_OK;
+}
+
+// Advance the run by at most one phase.  Returns FESPMV_OK with *progress set
+// when something happened, or an error.  block: wait for the pending event.
+int run_step(CgRun& r, bool block, bool* progress) {
+    *progress = false;
+    if (r.phase == PH_DONE) return FESPMV_OK;
+    CgWork* w = r.w;
+    const int k = r.phase == PH_ITER ? r.head : 0;
+    cudaEvent_t ev = w->ev[k];
+    if (block) {
+        FESPMV_CUDA(cudaEventSynchronize(ev));
+    } else {
+        cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaErrorNotReady) return FESPMV_OK;
+        if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery");
     }
-    const CgScalars& h = w->h_sc[0];
-    const int out = status == CG_CONVERGED ? FESPMV_OK
-                  : status == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
+    *progress = true;
+    const CgScalars h = w->h_sc[k];
+    int rc = FESPMV_OK;
+    switch (r.phase) {
+        case PH_INIT_WAIT:
+            r.last = h;
+            if (h.status == CG_BADDIAG) {
+                set_error("Jacobi preconditioning needs a positive, finite diagonal");
+                r.error = FESPMV_ERR_BREAKDOWN;
+                r.phase = PH_DONE;
+                return FESPMV_OK;
+            }
+            if (h.bb == 0.0) {  // b = 0: x = 0
+                FESPMV_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * (size_t)r.A->n, r.s));
+                r.last.true_rr = 0.0;
+                return finish(r, CG_CONVERGED);
+            }
+            if (h.status == CG_RUNNING) return start_graphs(r, 0, r.o.max_iter);
+            // converged (or failed) before iterating: confirm on the true residual
+            if ((rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
+            cg_true_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, w->q, w->partials, w->sc);
+            FESPMV_CUDA(cudaGetLastError());
+            r.phase = PH_TRUE_WAIT;
+            return enqueue_status(r, 0);
+        case PH_ITER: {
+            r.last = h;
+            --r.queued;
+            r.head ^= 1;
+            if (h.status == CG_RUNNING && r.graphs_left > 0) return enqueue_graph(r);
+            if (r.queued > 0) return FESPMV_OK;  // let the no-op graphs drain
+            if (r.o.precision == FESPMV_CG_F64) {
+                if ((rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
+                cg_true_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, w->q, w->partials, w->sc);
+                FESPMV_CUDA(cudaGetLastError());
+                r.phase = PH_TRUE_WAIT;
+                return enqueue_status(r, 0);
+            }
+            refine_update<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->x, r.A->d_scale, w->w32);
+            FESPMV_CUDA(cudaGetLastError());
+            ++r.outer;
+            return enqueue_residual(r, true);
+        }
+        case PH_TRUE_WAIT: {
+            r.last = h;
+            int st = h.status == CG_RUNNING ? CG_MAXITER : h.status;
+            if (st == CG_CONVERGED && !(h.true_rr <= h.thresh2)) {
+                if (r.restarts < r.o.max_restarts && h.iters < r.o.max_iter) {
+                    ++r.restarts;
+                    return enqueue_init(r, true);
+                }
+                st = CG_MAXITER;
+            }
+            return finish(r, st);
+        }
+        case PH_RES_WAIT:
+            r.last = h;
+            if (h.pad) {
+                set_error("refinement needs a positive, finite diagonal (S = diag(A)^-1/2)");
+                r.error = FESPMV_ERR_BREAKDOWN;
+                r.phase = PH_DONE;
+                return FESPMV_OK;
+            }
+            if (h.bb == 0.0) {
+                FESPMV_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * (size_t)r.A->n, r.s));
+                return finish(r, CG_CONVERGED);
+            }
+            if (h.status == CG_CONVERGED || h.status == CG_BREAKDOWN) return finish(r, h.status);
+            if (r.outer >= r.o.max_outer) return finish(r, CG_MAXITER);
+            if (!(h.true_rr < r.prev)) {  // no progress: the low-precision operator is too far from A
+                set_error("refinement stagnated: ||b - A x|| did not decrease");
+                return finish(r, CG_MAXITER);
+            }
+            r.prev = h.true_rr;
+            return start_graphs(r, r.o.precision == FESPMV_CG_BF16_REFINE ? 2 : 1, r.o.max_iter);
+        case PH_OUT_WAIT:
+            r.phase = PH_DONE;
+            return FESPMV_OK;
+        default:
+            return FESPMV_OK;
+    }
+}
+
+int run_result(const CgRun& r, cg_result* res) {
+    if (r.error) {
+        if (res) res->status = r.error;
+        return r.error;
+    }
+    const int out = r.status == CG_CONVERGED ? FESPMV_OK
+                  : r.status == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
     if (res) {
+        const CgScalars& h = r.last;
         res->status = out;
         res->iters = h.iters;
-        res->restarts = restarts;
-        res->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-        res->true_relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+        res->restarts = r.restarts;
+        res->outer = r.outer;
+        if (r.o.precision == FESPMV_CG_F64) {
+            res->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+            res->true_relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+        } else {
+            res->relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+            res->true_relres = res->relres;
+        }
     }
     if (out == FESPMV_ERR_BREAKDOWN) set_error("CG breakdown (p.Ap <= 0 or a non-finite scalar)");
-    if (out == FESPMV_ERR_NOT_CONVERGED) set_error("CG stopped above the tolerance");
+    if (out == FESPMV_ERR_NOT_CONVERGED && r.o.precision == FESPMV_CG_F64)
+        set_error("CG stopped above the tolerance");
     return out;
+}
+
+// Stage b (and x0) into the workspace's permuted vectors on stream s.
+int stage_inputs(CgRun& r, const double* b, const double* x0, bool host) {
+    CgWork* w = r.w;
+    const size_t nb = sizeof(double) * (size_t)r.A->n;
+    int rc;
+    const double* bsrc = b;
+    if (host) {
+        FESPMV_CUDA(cudaMemcpyAsync(w->q, b, nb, cudaMemcpyHostToDevice, r.s));
+        bsrc = w->q;
+    }
+    if (r.permute) {
+        if ((rc = launch_gather(bsrc, r.A->d_perm, w->b, r.A->n, r.s))) return rc;
+    } else {
+        FESPMV_CUDA(cudaMemcpyAsync(w->b, bsrc, nb, cudaMemcpyDeviceToDevice, r.s));
+    }
+    if (x0) {
+        const double* xsrc = x0;
+        if (host) {
+            FESPMV_CUDA(cudaMemcpyAsync(w->q, x0, nb, cudaMemcpyHostToDevice, r.s));
+            xsrc = w->q;
+        }
+        if (r.permute) {
+            if ((rc = launch_gather(xsrc, r.A->d_perm, w->x, r.A->n, r.s))) return rc;
+        } else {
+            FESPMV_CUDA(cudaMemcpyAsync(w->x, xsrc, nb, cudaMemcpyDeviceToDevice, r.s));
+        }
+    } else {
+        FESPMV_CUDA(cudaMemsetAsync(w->x, 0, nb, r.s));
+    }
+    return FESPMV_OK;
+}
+
+static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_options* opts,
+                         cg_result* res, cudaStream_t s) {
+    cg_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    int rc = normalize_options(o);
+    if (rc) return rc;
+    if ((rc = check_precision(A, o.precision))) return rc;
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (A->n == 0) return FESPMV_OK;
+    if ((rc = ensure_workspace(A))) return rc;
+    CgRun r;
+    r.A = A;
+    r.w = A->cg;
+    r.s = s;
+    r.o = o;
+    r.permute = A->format == FESPMV_FMT_SLICED && !(o.flags & FESPMV_IO_PERMUTED);
+    r.has_x0 = o.flags & FESPMV_CG_X0;
+    r.out_host = o.flags & FESPMV_IO_HOST;
+    r.x_out = x;
+    if ((rc = stage_inputs(r, b, r.has_x0 ? x : nullptr, r.out_host))) return rc;
+    if ((rc = run_begin(r))) return rc;
+    while (r.phase != PH_DONE) {
+        bool progress;
+        if ((rc = run_step(r, true, &progress))) return rc;
+    }
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return run_result(r, res);
 }
 
 // ------------------------------------------------------------------ allocation-free CSR solve
