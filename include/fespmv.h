@@ -43,6 +43,7 @@ typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory 
 #define FESPMV_ERR_BREAKDOWN      -5  /* CG: p.Ap <= 0 or a non-finite scalar */
 #define FESPMV_ERR_NOT_CONVERGED  -6  /* CG: iteration limit reached above tolerance */
 #define FESPMV_ERR_UNSUPPORTED    -7  /* option combination not built for this handle */
+#define FESPMV_PENDING             1  /* srv_poll: the solve has not finished yet */
 
 /* ---- matrix formats and kernels ---------------------------------------------------- */
 /* Storage built by spmv_create. */
@@ -289,6 +290,66 @@ int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts,
 int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
                         const double* values, const double* b, double* x, int32_t csr_lanes,
                         const cg_options* opts, cg_result* res, fespmv_stream_t stream);
+
+/* ---- solve server: continuous batching of CG solves ------------------------------- */
+typedef struct fespmv_server* fespmv_server_t;
+
+typedef struct {
+    double t_queue_s;    /* submit -> admitted to a slot */
+    double t_solve_s;    /* admitted -> finished (result on the host) */
+    double t_total_s;    /* submit -> finished */
+} srv_timing;
+
+typedef struct {
+    int64_t submitted, completed, queued, active, peak_active;
+    int64_t workspace_bytes, peak_workspace_bytes;
+} srv_stats;
+
+/*
+ * srv_create -- start a solve server on the current device.  The paper solves
+ * one system at a time; this layer serves many CG solves at once, as the
+ * Newton steps of several simulations would submit them.
+ *   workspace_budget_bytes  device bytes the server may hold for solve
+ *                           workspaces (vectors, partial sums); matrices are
+ *                           the caller's and not counted
+ *   max_active              most solves in flight at once
+ * A scheduler thread admits queued requests in arrival order as soon as a slot
+ * is free and the request's workspace fits in the budget (idle workspaces are
+ * reused for the same matrix and released for others when needed), runs each
+ * admitted solve on its own stream, and advances all of them round-robin, one
+ * graph of check_every iterations at a time, so their iterations overlap on
+ * the device.  A solve in the mix runs the kernels, grids and reduction order
+ * of cg_solve, so its x is bitwise equal to cg_solve's on the same handle.
+ * Errors: INVALID_ARG, OOM.
+ */
+int srv_create(fespmv_server_t* out, int64_t workspace_budget_bytes, int32_t max_active);
+
+/* Make handle A solvable by the server; *matrix_id names it in srv_submit.  The
+ * handle stays the caller's: it must outlive the server and must not be used
+ * by other calls while solves on it are in flight.  Errors: INVALID_ARG, OOM
+ * (one workspace of A is larger than the whole budget). */
+int srv_register(fespmv_server_t S, fespmv_mat_t A, int32_t* matrix_id);
+
+/* Queue the solve A x = b (b: host double[n_rows] in the input numbering,
+ * copied before the call returns; x0 = 0).  opts as for cg_solve except that
+ * FESPMV_IO_PERMUTED and FESPMV_CG_X0 are refused.  *ticket identifies the
+ * request.  Thread-safe.  Errors: INVALID_ARG, UNSUPPORTED, OOM. */
+int srv_submit(fespmv_server_t S, int32_t matrix_id, const double* b, const cg_options* opts,
+               int64_t* ticket);
+
+/* Collect a request: with wait = 0 returns FESPMV_PENDING while it runs; once it
+ * has finished, writes x (host double[n_rows], may be NULL), res and timing (may
+ * be NULL), releases the ticket and returns the solve's status (FESPMV_OK,
+ * NOT_CONVERGED, BREAKDOWN, or the error that stopped it).  wait = 1 blocks until
+ * the request finishes.  Thread-safe. */
+int srv_poll(fespmv_server_t S, int64_t ticket, int32_t wait, double* x, cg_result* res,
+             srv_timing* timing);
+
+int srv_get_stats(fespmv_server_t S, srv_stats* stats);
+
+/* Finish every queued and running solve, stop the scheduler and free the
+ * workspaces (not the registered handles).  Uncollected results are dropped. */
+void srv_destroy(fespmv_server_t S);
 
 /* Human-readable name of a status code, and the last failure message of the
  * calling thread (empty if none).  Both strings are static or thread-local. */

@@ -25,6 +25,7 @@ FESPMV_ERR_CUDA = -4
 FESPMV_ERR_BREAKDOWN = -5
 FESPMV_ERR_NOT_CONVERGED = -6
 FESPMV_ERR_UNSUPPORTED = -7
+FESPMV_PENDING = 1
 
 FESPMV_FMT_CSR = 0
 FESPMV_FMT_SLICED = 1
@@ -86,6 +87,17 @@ class cg_result(ctypes.Structure):
                 ("true_relres", ctypes.c_double)]
 
 
+class srv_timing(ctypes.Structure):
+    _fields_ = [("t_queue_s", ctypes.c_double), ("t_solve_s", ctypes.c_double),
+                ("t_total_s", ctypes.c_double)]
+
+
+class srv_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "queued", "active",
+                                              "peak_active", "workspace_bytes",
+                                              "peak_workspace_bytes")]
+
+
 def _load():
     path = _build.build()
     try:
@@ -120,6 +132,18 @@ _lib.spmv_plan.argtypes = [_i64, _P, _P, ctypes.POINTER(fespmv_mesh_info),
 _lib.spmv_plan.restype = ctypes.c_int
 _lib.cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), ctypes.POINTER(cg_result), _P]
 _lib.cg_solve.restype = ctypes.c_int
+_lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
+_lib.srv_create.restype = ctypes.c_int
+_lib.srv_register.argtypes = [_P, _P, ctypes.POINTER(_i32)]
+_lib.srv_register.restype = ctypes.c_int
+_lib.srv_submit.argtypes = [_P, _i32, _P, ctypes.POINTER(cg_options), ctypes.POINTER(_i64)]
+_lib.srv_submit.restype = ctypes.c_int
+_lib.srv_poll.argtypes = [_P, _i64, _i32, _P, ctypes.POINTER(cg_result), ctypes.POINTER(srv_timing)]
+_lib.srv_poll.restype = ctypes.c_int
+_lib.srv_get_stats.argtypes = [_P, ctypes.POINTER(srv_stats)]
+_lib.srv_get_stats.restype = ctypes.c_int
+_lib.srv_destroy.argtypes = [_P]
+_lib.srv_destroy.restype = None
 _lib.fespmv_status_string.argtypes = [ctypes.c_int]
 _lib.fespmv_status_string.restype = ctypes.c_char_p
 _lib.fespmv_last_error.argtypes = []
@@ -289,3 +313,64 @@ def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, fl
     if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
         _check(rc)
     return {k: getattr(r, k) for k, _ in cg_result._fields_}
+
+
+class Server:
+    """A solve server (srv_create); destroy it with srv_destroy."""
+
+    def __init__(self, handle, sizes):
+        self.handle = handle
+        self.sizes = sizes          # matrix id -> n_rows
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.srv_destroy(self.handle)
+            self.handle = None
+
+
+def srv_create(workspace_budget_bytes: int, max_active: int) -> Server:
+    h = _P()
+    _check(_lib.srv_create(ctypes.byref(h), workspace_budget_bytes, max_active))
+    return Server(h, {})
+
+
+def srv_register(S: Server, A: Matrix) -> int:
+    mid = _i32()
+    _check(_lib.srv_register(S.handle, A.handle, ctypes.byref(mid)))
+    S.sizes[mid.value] = A.n_rows
+    return mid.value
+
+
+def srv_submit(S: Server, matrix_id: int, b, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64,
+               flags=0, max_restarts=0, check_every=0, max_outer=0, inner_tol=0.0) -> int:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
+    t = _i64()
+    _check(_lib.srv_submit(S.handle, matrix_id, _ptr(b), ctypes.byref(o), ctypes.byref(t)))
+    return t.value
+
+
+def srv_poll(S: Server, ticket: int, n_rows: int, wait=True):
+    """Returns None while pending (wait=False), else (status, x, result dict, timing dict)."""
+    x = np.zeros(max(n_rows, 1))
+    r = cg_result()
+    tm = srv_timing()
+    rc = _lib.srv_poll(S.handle, ticket, 1 if wait else 0, _ptr(x), ctypes.byref(r), ctypes.byref(tm))
+    if rc == FESPMV_PENDING:
+        return None
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return (rc, x[:n_rows], {k: getattr(r, k) for k, _ in cg_result._fields_},
+            {k: getattr(tm, k) for k, _ in srv_timing._fields_})
+
+
+def srv_get_stats(S: Server) -> dict:
+    st = srv_stats()
+    _check(_lib.srv_get_stats(S.handle, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in srv_stats._fields_}
+
+
+def srv_destroy(S: Server):
+    if S.handle:
+        _lib.srv_destroy(S.handle)
+        S.handle = None

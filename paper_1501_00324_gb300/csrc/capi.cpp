@@ -448,6 +448,7 @@ const char* fespmv_status_string(int status) {
         case FESPMV_ERR_BREAKDOWN: return "CG breakdown";
         case FESPMV_ERR_NOT_CONVERGED: return "CG not converged";
         case FESPMV_ERR_UNSUPPORTED: return "unsupported";
+        case FESPMV_PENDING: return "pending";
         default: return "unknown status";
     }
 }

@@ -23,55 +23,9 @@
 
 #include "internal.h"
 #include "spmv_device.cuh"
+#include "cg_run.h"
 
 namespace fespmv {
-
-enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_BREAKDOWN = 2, CG_MAXITER = 3, CG_BADDIAG = 4 };
-
-struct CgScalars {
-    double rho, pq, alpha, beta, rr, bb, thresh2, true_rr;
-    int iters, max_iter, status, pad;
-    unsigned int counter, pad2;
-    double thresh_in;   // refinement: inner stop threshold on r_in.r_in
-    int iters_in, pad3; // refinement: inner steps of the current outer step
-};
-
-struct CgWork {
-    int64_t n = 0;
-    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *dinv = nullptr;
-    double* partials = nullptr;
-    CgScalars* sc = nullptr;
-    CgScalars* h_sc = nullptr;  // pinned host mirror, 2 slots
-    unsigned upd_grid = 0;
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int graph_chunk = 0;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    // refinement (float inner CG): w, r_in, p, q
-    float *w32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-    cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
-    int chunk_low[2] = {0, 0};
-    double* h_io = nullptr;     // pinned host staging of n doubles (solve server)
-    int64_t bytes = 0;          // device bytes held
-};
-
-// One solve in flight (see the host side below).
-struct CgRun {
-    fespmv_mat* A = nullptr;
-    CgWork* w = nullptr;
-    cudaStream_t s = nullptr;
-    cg_options o{};
-    bool permute = false, has_x0 = false, out_host = false;
-    double* x_out = nullptr;
-    int phase = 5;             // PH_DONE
-    int restarts = 0, outer = 0;
-    double prev = 0.0;
-    int64_t graphs_left = 0;
-    int queued = 0, head = 0;
-    int status = 0, error = 0;
-    cudaGraphExec_t graph = nullptr;
-    CgScalars last{};
-};
 
 // ------------------------------------------------------------------ reductions
 
@@ -618,7 +572,7 @@ static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
     return FESPMV_OK;
 }
 
-static int ensure_low_workspace(CgWork* w) {
+int ensure_low_work(CgWork* w) {
     if (w->w32) return FESPMV_OK;
     const size_t nb = sizeof(float) * (size_t)w->n;
     float** vecs[] = {&w->w32, &w->r32, &w->p32, &w->q32};
@@ -633,9 +587,8 @@ __global__ void cg_copy_flag(CgScalars* sc, const int* flag) {
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->pad = flag ? *flag : 0;
 }
 
-enum Phase { PH_INIT_WAIT, PH_ITER, PH_TRUE_WAIT, PH_RES_WAIT, PH_OUT_WAIT, PH_DONE };
 
-static int normalize_options(cg_options& o) {
+int normalize_options(cg_options& o) {
     if (o.tol == 0.0) o.tol = 1e-10;
     if (o.max_iter == 0) o.max_iter = 100000;
     if (o.max_restarts == 0) o.max_restarts = 3;
@@ -741,7 +694,7 @@ int run_begin(CgRun& r) {
         FESPMV_CUDA(cudaGetLastError());
         return enqueue_init(r, r.has_x0);
     }
-    if ((rc = ensure_low_workspace(w))) return rc;
+    if ((rc = ensure_low_work(w))) return rc;
     cg_copy_flag<<<1, 32, 0, r.s>>>(w->sc, r.A->d_flag);
     FESPMV_CUDA(cudaGetLastError());
     return enqueue_residual(r, r.has_x0);

@@ -1,0 +1,113 @@
+"""The solve server (continuous batching) through the C ABI.
+
+Each result in the mix must equal, bit for bit, the result of cg_solve on the
+same handle alone (the server runs the same kernels, grids and fixed-order
+reductions on its own workspace), and must meet its tolerance on the true
+residual recomputed by the oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import fegen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1501_00324_gb300 as fs  # noqa: E402
+
+
+def problems():
+    return [fegen.cube_laplace(12, 81), fegen.cube_elasticity(8, 82), fegen.shell_laplace(5, 16, 24, 83),
+            fegen.cube_laplace(16, 84)]
+
+
+def alone(A, b, **kw):
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    res = fs.cg_solve(A, bd, xd, **kw)
+    torch.cuda.synchronize()
+    return xd.cpu().numpy(), res
+
+
+def test_results_in_the_mix_equal_results_alone():
+    ps = problems()
+    mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=256,
+                           precisions=fs.FESPMV_PREC_F32) for p in ps]
+    S = fs.srv_create(1 << 30, 6)
+    ids = [fs.srv_register(S, A) for A in mats]
+    rng = np.random.default_rng(85)
+    reqs = []
+    for k in range(24):
+        m = int(rng.integers(len(ps)))
+        b = fegen.random_vector(ps[m].n_rows, 1000 + k)
+        tol = [1e-8, 1e-10][k % 2]
+        prec = [fs.FESPMV_CG_F64, fs.FESPMV_CG_F32_REFINE][(k // 2) % 2]
+        reqs.append((m, b, tol, prec))
+    tickets = [fs.srv_submit(S, ids[m], b, tol=tol, precision=prec) for (m, b, tol, prec) in reqs]
+    results = [fs.srv_poll(S, t, ps[m].n_rows) for t, (m, _, _, _) in zip(tickets, reqs)]
+    st = fs.srv_get_stats(S)
+    assert st["completed"] == 24 and st["peak_active"] > 1
+    for (m, b, tol, prec), (rc, x, res, tm) in zip(reqs, results):
+        assert rc == 0, res
+        p = ps[m]
+        r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        assert np.linalg.norm(r) <= tol * 1.01 * np.linalg.norm(b)
+        xa, ra = alone(mats[m], b, tol=tol, precision=prec)
+        assert np.array_equal(x.view(np.uint64), xa.view(np.uint64))
+        assert res["iters"] == ra["iters"] and res["outer"] == ra["outer"]
+        assert tm["t_total_s"] >= tm["t_solve_s"] > 0
+    fs.srv_destroy(S)
+
+
+def test_budget_admission_and_late_arrivals():
+    ps = problems()[:2]
+    mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=256)
+            for p in ps]
+    # a budget that holds one workspace of the larger matrix, and a few small ones
+    n_big = max(p.n_rows for p in ps)
+    budget = 80 * n_big + (1 << 20)
+    S = fs.srv_create(budget, 8)
+    ids = [fs.srv_register(S, A) for A in mats]
+    tickets = []
+    for k in range(6):
+        m = k % 2
+        tickets.append((m, fs.srv_submit(S, ids[m], fegen.random_vector(ps[m].n_rows, 2000 + k))))
+    time.sleep(0.01)
+    for k in range(6, 12):                 # arrive while the first wave runs
+        m = k % 2
+        tickets.append((m, fs.srv_submit(S, ids[m], fegen.random_vector(ps[m].n_rows, 2000 + k))))
+    for m, t in tickets:
+        rc, x, res, tm = fs.srv_poll(S, t, ps[m].n_rows)
+        assert rc == 0
+    st = fs.srv_get_stats(S)
+    assert st["completed"] == 12 and st["peak_workspace_bytes"] <= budget
+    fs.srv_destroy(S)
+
+
+def test_errors_are_per_request():
+    p = fegen.cube_laplace(10, 86)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=128)
+    bad = fs.spmv_create(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0, -1.0]),
+                         format=fs.FESPMV_FMT_CSR)
+    S = fs.srv_create(1 << 28, 4)
+    ia, ib = fs.srv_register(S, A), fs.srv_register(S, bad)
+    with pytest.raises(fs.FespmvError):
+        fs.srv_submit(S, 99, np.zeros(3))
+    with pytest.raises(fs.FespmvError):
+        fs.srv_submit(S, ia, np.zeros(p.n_rows), flags=fs.FESPMV_CG_X0)
+    with pytest.raises(fs.FespmvError):       # the handle holds no FP32 copy
+        fs.srv_submit(S, ia, np.zeros(p.n_rows), precision=fs.FESPMV_CG_F32_REFINE)
+    t1 = fs.srv_submit(S, ib, np.array([1.0, 1.0]))
+    t2 = fs.srv_submit(S, ia, fegen.random_vector(p.n_rows, 3))
+    assert fs.srv_poll(S, t1, 2)[0] == fs.FESPMV_ERR_BREAKDOWN
+    rc, x, res, tm = fs.srv_poll(S, t2, p.n_rows)
+    assert rc == 0
+    t3 = fs.srv_submit(S, ia, fegen.random_vector(p.n_rows, 4), tol=1e-12, max_iter=3,
+                       max_restarts=-1)
+    assert fs.srv_poll(S, t3, p.n_rows)[0] == fs.FESPMV_ERR_NOT_CONVERGED
+    with pytest.raises(fs.FespmvError):       # a collected ticket is gone
+        fs.srv_poll(S, t3, p.n_rows)
+    fs.srv_destroy(S)
