@@ -59,6 +59,11 @@ def parse_args():
                     help="time the FE product only (for profiling runs)")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of each serving run (server and one-at-a-time); 0 skips")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the full serving pool: 48 meshes of 5k..3M rows (else 12 of 5k..300k)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -320,6 +325,8 @@ def main():
                 extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves, fs.FESPMV_CG_F64)
                 extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                   fs.FESPMV_CG_F32_REFINE)
+            if args.serve_seconds > 0 and hasattr(fs, "srv_create"):
+                extra["serving"] = bench_serving(fs, torch, args)
     clk = clocks.summary()
 
     t_mean = statistics.mean(times) * 1e-3
@@ -371,6 +378,124 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_pool(n_meshes, lo, hi, seed):
+    """Meshes with row counts log-uniform in [lo, hi], kinds cycling cube / elasticity / shell."""
+    import fegen
+    rng = np.random.default_rng(seed)
+    rows = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_meshes))
+    pool = []
+    for i, N in enumerate(rows):
+        kind = i % 3
+        if kind == 0:
+            p = fegen.cube_laplace(max(3, round(N ** (1 / 3))), seed + 1 + i)
+        elif kind == 1:
+            p = fegen.cube_elasticity(max(3, round((N / 3) ** (1 / 3))), seed + 1 + i)
+        else:
+            s = (N / (24 * 256 * 512)) ** (1 / 3)
+            p = fegen.shell_laplace(max(3, round(24 * s)), max(4, round(256 * s)),
+                                    max(8, round(512 * s)), seed + 1 + i)
+        pool.append(p)
+    return pool
+
+
+def bench_serving(fs, torch, args):
+    """Poisson arrivals of CG solves over a resident mesh pool: the solve server
+    (continuous batching, FP32-refined CG) against one-at-a-time FP64 cg_solve on
+    the same arrival trace.  Each run lasts args.serve_seconds; requests still
+    queued at the end are cancelled and counted as not served."""
+    import threading
+    import fegen
+    if args.serve_full:
+        n_mesh, lo, hi = 48, 5_000, 3_000_000
+    else:
+        n_mesh, lo, hi = 12, 5_000, 300_000
+    t0 = time.perf_counter()
+    pool = serving_pool(n_mesh, lo, hi, 1505)
+    mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=1024,
+                           precisions=fs.FESPMV_PREC_F32) for p in pool]
+    rhs = [[fegen.random_vector(p.n_rows, 7000 + 10 * i + k) for k in range(2)]
+           for i, p in enumerate(pool)]
+    setup_s = time.perf_counter() - t0
+    T = args.serve_seconds
+
+    def make_trace(rate, seed):
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * T * 1.5) + 10))
+        arrivals = arrivals[arrivals < T]
+        return [(float(a), int(rng.integers(n_mesh)), [1e-8, 1e-10][int(rng.integers(2))],
+                 int(rng.integers(2))) for a in arrivals]
+
+    trace = make_trace(args.serve_rate, 1506)
+
+    def summarize(trace, lat, served, elapsed):
+        lat = np.array(sorted(lat)) * 1e3
+        return {"offered": len(trace), "served": served,
+                "offered_per_s": round(len(trace) / T, 1),
+                "solves_per_s": round(served / elapsed, 2) if elapsed > 0 else 0.0,
+                "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
+                "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None}
+
+    def run_server(trace):
+        S = fs.srv_create(48 << 30, 64)
+        ids = [fs.srv_register(S, A) for A in mats]
+        tickets = []
+        start = time.perf_counter()
+        for (a, m, tol, k) in trace:
+            now = time.perf_counter() - start
+            if now < a:
+                time.sleep(a - now)
+            tickets.append(fs.srv_submit(S, ids[m], rhs[m][k], tol=tol,
+                                         precision=fs.FESPMV_CG_F32_REFINE))
+        fs.srv_cancel_queued(S)
+        lat, served = [], 0
+        for t in tickets:
+            rc, _, res, tm = fs.srv_poll(S, t, 0)
+            if rc == 0:
+                served += 1
+                lat.append(tm["t_total_s"])
+        elapsed = time.perf_counter() - start
+        st = fs.srv_get_stats(S)
+        fs.srv_destroy(S)
+        out = summarize(trace, lat, served, elapsed)
+        out.update({"precision": "f32_refine", "peak_active": st["peak_active"],
+                    "peak_workspace_gb": round(st["peak_workspace_bytes"] / 2 ** 30, 2)})
+        return out
+
+    def run_single(trace):
+        """One-at-a-time FP64 cg_solve, FIFO, on the same arrivals (host vectors)."""
+        lat, served = [], 0
+        start = time.perf_counter()
+        for (a, m, tol, k) in trace:
+            now = time.perf_counter() - start
+            if now >= T:
+                break
+            if now < a:
+                time.sleep(a - now)
+            x = np.zeros(pool[m].n_rows)
+            res = fs.cg_solve(mats[m], rhs[m][k], x, tol=tol)
+            if res["status"] == 0:
+                served += 1
+                lat.append(time.perf_counter() - start - a)
+        elapsed = time.perf_counter() - start
+        out = summarize(trace, lat, served, elapsed)
+        out["precision"] = "f64"
+        return out
+
+    over = {"server": run_server(trace), "one_at_a_time": run_single(trace)}
+    # a second arrival stream at 80 % of the one-at-a-time capacity, where queues stay short
+    rate2 = 0.8 * max(1.0, over["one_at_a_time"]["solves_per_s"])
+    trace2 = make_trace(rate2, 1507)
+    steady = {"rate_per_s": round(rate2, 1), "server": run_server(trace2),
+              "one_at_a_time": run_single(trace2)}
+    for A in mats:
+        fs.spmv_destroy(A)
+    return {"pool": {"meshes": n_mesh, "rows_min": min(p.n_rows for p in pool),
+                     "rows_max": max(p.n_rows for p in pool),
+                     "rows_total": sum(p.n_rows for p in pool),
+                     "nnz_total": sum(p.nnz for p in pool), "setup_s": round(setup_s, 1)},
+            "seconds": T, "overload": dict(rate_per_s=args.serve_rate, **over), "steady": steady}
 
 
 def bench_cg(fs, torch, A, p, n_solves, precision):

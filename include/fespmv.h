@@ -43,6 +43,7 @@ typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory 
 #define FESPMV_ERR_BREAKDOWN      -5  /* CG: p.Ap <= 0 or a non-finite scalar */
 #define FESPMV_ERR_NOT_CONVERGED  -6  /* CG: iteration limit reached above tolerance */
 #define FESPMV_ERR_UNSUPPORTED    -7  /* option combination not built for this handle */
+#define FESPMV_ERR_CANCELLED      -8  /* srv_poll: the request was cancelled before it started */
 #define FESPMV_PENDING             1  /* srv_poll: the solve has not finished yet */
 
 /* ---- matrix formats and kernels ---------------------------------------------------- */
@@ -346,6 +347,11 @@ int srv_poll(fespmv_server_t S, int64_t ticket, int32_t wait, double* x, cg_resu
              srv_timing* timing);
 
 int srv_get_stats(fespmv_server_t S, srv_stats* stats);
+
+/* Drop every request still waiting for a slot: each finishes with
+ * FESPMV_ERR_CANCELLED (collect it with srv_poll as usual); solves already
+ * running are not touched.  *n_cancelled (may be NULL) receives the count. */
+int srv_cancel_queued(fespmv_server_t S, int64_t* n_cancelled);
 
 /* Finish every queued and running solve, stop the scheduler and free the
  * workspaces (not the registered handles).  Uncollected results are dropped. */

@@ -25,6 +25,7 @@ FESPMV_ERR_CUDA = -4
 FESPMV_ERR_BREAKDOWN = -5
 FESPMV_ERR_NOT_CONVERGED = -6
 FESPMV_ERR_UNSUPPORTED = -7
+FESPMV_ERR_CANCELLED = -8
 FESPMV_PENDING = 1
 
 FESPMV_FMT_CSR = 0
@@ -142,6 +143,8 @@ _lib.srv_poll.argtypes = [_P, _i64, _i32, _P, ctypes.POINTER(cg_result), ctypes.
 _lib.srv_poll.restype = ctypes.c_int
 _lib.srv_get_stats.argtypes = [_P, ctypes.POINTER(srv_stats)]
 _lib.srv_get_stats.restype = ctypes.c_int
+_lib.srv_cancel_queued.argtypes = [_P, ctypes.POINTER(_i64)]
+_lib.srv_cancel_queued.restype = ctypes.c_int
 _lib.srv_destroy.argtypes = [_P]
 _lib.srv_destroy.restype = None
 _lib.fespmv_status_string.argtypes = [ctypes.c_int]
@@ -351,16 +354,18 @@ def srv_submit(S: Server, matrix_id: int, b, tol=1e-10, max_iter=0, precision=FE
 
 
 def srv_poll(S: Server, ticket: int, n_rows: int, wait=True):
-    """Returns None while pending (wait=False), else (status, x, result dict, timing dict)."""
-    x = np.zeros(max(n_rows, 1))
+    """Returns None while pending (wait=False), else (status, x, result dict, timing dict).
+    n_rows = 0 skips copying x."""
+    x = np.zeros(max(n_rows, 1)) if n_rows > 0 else None
     r = cg_result()
     tm = srv_timing()
-    rc = _lib.srv_poll(S.handle, ticket, 1 if wait else 0, _ptr(x), ctypes.byref(r), ctypes.byref(tm))
+    rc = _lib.srv_poll(S.handle, ticket, 1 if wait else 0, _ptr(x) if x is not None else None,
+                       ctypes.byref(r), ctypes.byref(tm))
     if rc == FESPMV_PENDING:
         return None
-    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN, FESPMV_ERR_CANCELLED):
         _check(rc)
-    return (rc, x[:n_rows], {k: getattr(r, k) for k, _ in cg_result._fields_},
+    return (rc, x[:n_rows] if x is not None else None, {k: getattr(r, k) for k, _ in cg_result._fields_},
             {k: getattr(tm, k) for k, _ in srv_timing._fields_})
 
 
@@ -368,6 +373,12 @@ def srv_get_stats(S: Server) -> dict:
     st = srv_stats()
     _check(_lib.srv_get_stats(S.handle, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in srv_stats._fields_}
+
+
+def srv_cancel_queued(S: Server) -> int:
+    n = _i64()
+    _check(_lib.srv_cancel_queued(S.handle, ctypes.byref(n)))
+    return n.value
 
 
 def srv_destroy(S: Server):

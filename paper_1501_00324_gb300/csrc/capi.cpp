@@ -449,6 +449,7 @@ const char* fespmv_status_string(int status) {
         case FESPMV_ERR_NOT_CONVERGED: return "CG not converged";
         case FESPMV_ERR_UNSUPPORTED: return "unsupported";
         case FESPMV_PENDING: return "pending";
+        case FESPMV_ERR_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }

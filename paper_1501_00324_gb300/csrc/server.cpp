@@ -344,6 +344,7 @@ int srv_poll(fespmv_server_t S, int64_t ticket, int32_t wait, double* x, cg_resu
     const int rc = q->rc;
     if (rc != FESPMV_OK && rc != FESPMV_ERR_NOT_CONVERGED && rc != FESPMV_ERR_BREAKDOWN)
         set_error("%s", q->error.c_str());
+    if (rc == FESPMV_ERR_CANCELLED && timing) timing->t_solve_s = 0.0;
     S->tickets.erase(it);
     delete q;
     return rc;
@@ -362,6 +363,27 @@ int srv_get_stats(fespmv_server_t S, srv_stats* st) {
     st->peak_active = S->peak_active;
     st->workspace_bytes = S->used;
     st->peak_workspace_bytes = S->peak_bytes;
+    return FESPMV_OK;
+}
+
+int srv_cancel_queued(fespmv_server_t S, int64_t* n_cancelled) {
+    if (!S) {
+        set_error("null argument");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    int64_t n = 0;
+    const double t = now_s();
+    for (Request* q : S->queue) {
+        q->rc = FESPMV_ERR_CANCELLED;
+        q->error = "cancelled before it started";
+        q->state = RQ_DONE;
+        q->t_done = t;
+        ++n;
+    }
+    S->queue.clear();
+    if (n_cancelled) *n_cancelled = n;
+    S->cv_done.notify_all();
     return FESPMV_OK;
 }
 

@@ -111,3 +111,16 @@ def test_errors_are_per_request():
     with pytest.raises(fs.FespmvError):       # a collected ticket is gone
         fs.srv_poll(S, t3, p.n_rows)
     fs.srv_destroy(S)
+
+
+def test_cancel_queued():
+    p = fegen.cube_laplace(16, 87)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256)
+    S = fs.srv_create(1 << 28, 1)                   # one slot: the rest wait in the queue
+    mid = fs.srv_register(S, A)
+    tickets = [fs.srv_submit(S, mid, fegen.random_vector(p.n_rows, 50 + k)) for k in range(20)]
+    n = fs.srv_cancel_queued(S)
+    assert 1 <= n <= 19
+    codes = [fs.srv_poll(S, t, p.n_rows)[0] for t in tickets]
+    assert codes.count(fs.FESPMV_ERR_CANCELLED) == n and codes.count(0) == 20 - n
+    fs.srv_destroy(S)
