@@ -292,6 +292,57 @@ int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* co
                         const double* values, const double* b, double* x, int32_t csr_lanes,
                         const cg_options* opts, cg_result* res, fespmv_stream_t stream);
 
+/* ---- batches of independent FE problems ------------------------------------------- */
+typedef struct fespmv_batch* fespmv_batch_t;
+
+/*
+ * batch_create -- many independent matrices (meshes of uneven sizes) held as one
+ * block-diagonal SLICED matrix.  Each problem j is ordered, renumbered and
+ * column-sorted on its own (as spmv_create does: Sec. 5.1-5.3) and padded with
+ * identity rows to a multiple of 32 rows, so that no warp slice (Sec. 5.1, 5.4)
+ * spans two problems; one product then computes every problem's product in a
+ * single launch.  The paper treats one matrix at a time; batching is this
+ * library's layer on top.
+ *   count            number of problems (>= 1)
+ *   n_rows[j]        rows of problem j
+ *   rowptr[j], colind[j], values[j]   host CSR of problem j (rules of spmv_create)
+ *   mesh             NULL or count entries (dofs_per_node, node_xyz per problem)
+ *   opts             as spmv_create (format is SLICED; FP32 values of S A S are
+ *                    always kept for the refined solver; block <= 256)
+ * Host planning runs one thread per core over the problems.
+ * Errors: INVALID_ARG, BAD_CSR (message names the problem), OOM, CUDA, UNSUPPORTED.
+ */
+int batch_create(fespmv_batch_t* out, int32_t count, const int64_t* n_rows,
+                 const int64_t* const* rowptr, const int32_t* const* colind,
+                 const double* const* values, const fespmv_mesh_info* mesh,
+                 const fespmv_options* opts, fespmv_stream_t stream);
+void batch_destroy(fespmv_batch_t B);
+
+/* y = A x for every problem at once, FP64.  x, y: device doubles, the problems'
+ * vectors concatenated in input numbering (sum of n_rows entries). */
+int batch_spmv(fespmv_batch_t B, const double* x, double* y, fespmv_stream_t stream);
+
+/*
+ * batch_cg_solve -- solve every problem A_j x_j = b_j by the refined CG of
+ * cg_solve (FESPMV_CG_F32_REFINE, the default here, or FESPMV_CG_BF16_REFINE;
+ * FESPMV_CG_F64 is taken as F32_REFINE), all problems in lockstep: each
+ * refinement step runs one batched FP64 residual, then inner FP32 iterations
+ * of all problems still refining, as CUDA graphs of check_every iterations
+ * (five launches per iteration for the whole batch), then x_j += S w_j.
+ * Scalars are per problem; finished problems are skipped by every kernel.
+ *   b, x     concatenated vectors (device, or host with FESPMV_IO_HOST);
+ *            x: initial guess with FESPMV_CG_X0, else zero; overwritten
+ *   results  NULL or count entries
+ * Returns FESPMV_OK when every problem converged, else the first failing
+ * problem's status (results has each one).
+ */
+int batch_cg_solve(fespmv_batch_t B, const double* b, double* x, const cg_options* opts,
+                   cg_result* results, fespmv_stream_t stream);
+
+/* Sizes: info->n_rows is the total input rows; *padded_rows (may be NULL) the
+ * rows of the padded block-diagonal matrix. */
+int batch_get_info(fespmv_batch_t B, fespmv_info* info, int64_t* padded_rows);
+
 /* ---- solve server: continuous batching of CG solves ------------------------------- */
 typedef struct fespmv_server* fespmv_server_t;
 

@@ -147,6 +147,17 @@ _lib.srv_cancel_queued.argtypes = [_P, ctypes.POINTER(_i64)]
 _lib.srv_cancel_queued.restype = ctypes.c_int
 _lib.srv_destroy.argtypes = [_P]
 _lib.srv_destroy.restype = None
+_PP = ctypes.POINTER(_P)
+_lib.batch_create.argtypes = [ctypes.POINTER(_P), _i32, _P, _P, _P, _P, _P, ctypes.POINTER(fespmv_options), _P]
+_lib.batch_create.restype = ctypes.c_int
+_lib.batch_destroy.argtypes = [_P]
+_lib.batch_destroy.restype = None
+_lib.batch_spmv.argtypes = [_P, _P, _P, _P]
+_lib.batch_spmv.restype = ctypes.c_int
+_lib.batch_cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), _P, _P]
+_lib.batch_cg_solve.restype = ctypes.c_int
+_lib.batch_get_info.argtypes = [_P, ctypes.POINTER(fespmv_info), ctypes.POINTER(_i64)]
+_lib.batch_get_info.restype = ctypes.c_int
 _lib.fespmv_status_string.argtypes = [ctypes.c_int]
 _lib.fespmv_status_string.restype = ctypes.c_char_p
 _lib.fespmv_last_error.argtypes = []
@@ -385,3 +396,83 @@ def srv_destroy(S: Server):
     if S.handle:
         _lib.srv_destroy(S.handle)
         S.handle = None
+
+
+class Batch:
+    """A batch handle (batch_create); destroy with batch_destroy."""
+
+    def __init__(self, handle, n_rows):
+        self.handle = handle
+        self.n_rows = list(n_rows)
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_rows)]).astype(np.int64)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.batch_destroy(self.handle)
+            self.handle = None
+
+
+def batch_create(problems, sigma=0, threshold=0, vec=0, precisions=0, block=0, reorder=None,
+                 stream=None) -> Batch:
+    """problems: sequence of (rowptr, colind, values, node_xyz or None, dofs_per_node)."""
+    keep = []
+    n = len(problems)
+    n_rows = np.array([len(p[0]) - 1 for p in problems], dtype=np.int64)
+    rp = (_P * n)()
+    ci = (_P * n)()
+    va = (_P * n)()
+    mesh = (fespmv_mesh_info * n)()
+    any_xyz = False
+    for j, (r, c, v, xyz, dpn) in enumerate(problems):
+        r = np.ascontiguousarray(r, dtype=np.int64)
+        c = np.ascontiguousarray(c, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        keep += [r, c, v]
+        rp[j], ci[j], va[j] = r.ctypes.data, c.ctypes.data, v.ctypes.data
+        if xyz is not None:
+            xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+            keep.append(xyz)
+            any_xyz = True
+        mesh[j] = fespmv_mesh_info(dpn, None if xyz is None else xyz.ctypes.data)
+    if reorder is None:
+        reorder = FESPMV_REORDER_MORTON if any_xyz else FESPMV_REORDER_NONE
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, precisions, block)
+    h = _P()
+    _check(_lib.batch_create(ctypes.byref(h), n, _ptr(n_rows), ctypes.cast(rp, _P),
+                             ctypes.cast(ci, _P), ctypes.cast(va, _P), ctypes.cast(mesh, _P),
+                             ctypes.byref(opts), _stream(stream)))
+    return Batch(h, n_rows)
+
+
+def batch_destroy(B: Batch):
+    if B.handle:
+        _lib.batch_destroy(B.handle)
+        B.handle = None
+
+
+def batch_spmv(B: Batch, x, y, stream=None):
+    _check(_lib.batch_spmv(B.handle, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def batch_cg_solve(B: Batch, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F32_REFINE, flags=0,
+                   check_every=0, max_outer=0, inner_tol=0.0, stream=None):
+    """Returns (status, list of per-problem result dicts)."""
+    if isinstance(b, np.ndarray):
+        flags |= FESPMV_IO_HOST
+    o = cg_options(tol, max_iter, precision, flags, 0, check_every, max_outer, inner_tol)
+    res = (cg_result * len(B.n_rows))()
+    rc = _lib.batch_cg_solve(B.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.cast(res, _P),
+                             _stream(stream))
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return rc, [{k: getattr(r, k) for k, _ in cg_result._fields_} for r in res]
+
+
+def batch_get_info(B: Batch) -> dict:
+    info = fespmv_info()
+    pad = _i64()
+    _check(_lib.batch_get_info(B.handle, ctypes.byref(info), ctypes.byref(pad)))
+    d = {k: getattr(info, k) for k, _ in fespmv_info._fields_}
+    d["padded_rows"] = pad.value
+    return d

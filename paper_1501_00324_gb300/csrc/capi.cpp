@@ -40,7 +40,7 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what) {
     return FESPMV_OK;
 }
 
-static void free_handle(fespmv_mat* A) {
+void free_handle(fespmv_mat* A) {
     if (!A) return;
     free_cg(A);
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
@@ -66,7 +66,7 @@ static int ck(cudaError_t e, const char* what) {
     } while (0)
 
 // Storage for S and the low-precision copies of S A S requested at create.
-static int alloc_scaled(fespmv_mat* A, int64_t len) {
+int alloc_scaled(fespmv_mat* A, int64_t len) {
     if (!(A->precisions & (FESPMV_PREC_F32 | FESPMV_PREC_BF16))) return FESPMV_OK;
     int rc = device_alloc(A, (void**)&A->d_scale, sizeof(double) * A->n, "scale S");
     if (!rc) rc = device_alloc(A, (void**)&A->d_flag, sizeof(int), "diagonal flag");
@@ -77,6 +77,30 @@ static int alloc_scaled(fespmv_mat* A, int64_t len) {
     if (!rc) rc = device_alloc(A, (void**)&A->d_xs, sizeof(float) * A->n, "float x scratch");
     if (!rc) rc = device_alloc(A, (void**)&A->d_ys, sizeof(float) * A->n, "float y scratch");
     return rc;
+}
+
+// Device arrays of a SLICED handle from a host plan (perm/pinv/diagpos of n rows).
+int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s) {
+    const int64_t n = A->n;
+    A->n_slices = plan.n_slices;
+    A->packed_len = plan.packed_len;
+    int rc;
+    if ((rc = device_alloc(A, (void**)&A->d_meta, sizeof(uint4) * plan.n_slices, "slice metadata")) ||
+        (rc = device_alloc(A, (void**)&A->d_col, sizeof(int32_t) * plan.packed_len, "packed columns")) ||
+        (rc = device_alloc(A, (void**)&A->d_val, sizeof(double) * plan.packed_len, "packed values")) ||
+        (rc = device_alloc(A, (void**)&A->d_src, sizeof(int64_t) * plan.packed_len, "value map")) ||
+        (rc = device_alloc(A, (void**)&A->d_perm, sizeof(int32_t) * n, "permutation")) ||
+        (rc = device_alloc(A, (void**)&A->d_pinv, sizeof(int32_t) * n, "inverse permutation")) ||
+        (rc = device_alloc(A, (void**)&A->d_xp, sizeof(double) * n, "permuted x")) ||
+        (rc = device_alloc(A, (void**)&A->d_yp, sizeof(double) * n, "permuted y")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_meta, plan.meta.data(), sizeof(uint4) * plan.n_slices, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_col, plan.col.data(), sizeof(int32_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_src, plan.src.data(), sizeof(int64_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_perm, plan.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_pinv, plan.pinv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_diagpos, plan.diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")))
+        return rc;
+    return FESPMV_OK;
 }
 
 static bool pow2_upto32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
@@ -176,22 +200,7 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         Plan plan;
         TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
                        o.threshold, o.vec, plan));
-        A->n_slices = plan.n_slices;
-        A->packed_len = plan.packed_len;
-        TRY(device_alloc(A, (void**)&A->d_meta, sizeof(uint4) * plan.n_slices, "slice metadata"));
-        TRY(device_alloc(A, (void**)&A->d_col, sizeof(int32_t) * plan.packed_len, "packed columns"));
-        TRY(device_alloc(A, (void**)&A->d_val, sizeof(double) * plan.packed_len, "packed values"));
-        TRY(device_alloc(A, (void**)&A->d_src, sizeof(int64_t) * plan.packed_len, "value map"));
-        TRY(device_alloc(A, (void**)&A->d_perm, sizeof(int32_t) * n, "permutation"));
-        TRY(device_alloc(A, (void**)&A->d_pinv, sizeof(int32_t) * n, "inverse permutation"));
-        TRY(device_alloc(A, (void**)&A->d_xp, sizeof(double) * n, "permuted x"));
-        TRY(device_alloc(A, (void**)&A->d_yp, sizeof(double) * n, "permuted y"));
-        TRY(ck(cudaMemcpyAsync(A->d_meta, plan.meta.data(), sizeof(uint4) * plan.n_slices, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
-        TRY(ck(cudaMemcpyAsync(A->d_col, plan.col.data(), sizeof(int32_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
-        TRY(ck(cudaMemcpyAsync(A->d_src, plan.src.data(), sizeof(int64_t) * plan.packed_len, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
-        TRY(ck(cudaMemcpyAsync(A->d_perm, plan.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
-        TRY(ck(cudaMemcpyAsync(A->d_pinv, plan.pinv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
-        TRY(ck(cudaMemcpyAsync(A->d_diagpos, plan.diagpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"));
+        TRY(upload_sliced(A, plan, s));
         TRY(alloc_scaled(A, plan.packed_len));
         TRY(launch_fill_values(A, A->d_vals_in, s));
         // host vectors must stay alive until the copies finish

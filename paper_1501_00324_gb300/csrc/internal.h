@@ -33,6 +33,21 @@ struct Plan {
     int64_t packed_len = 0;
 };
 
+// Permuted CSR (stage 1 of planning): P, Pinv, rows in new order with columns
+// renumbered and sorted, each entry's input position, each row's diagonal position.
+struct Permuted {
+    std::vector<int32_t> perm, pinv;
+    std::vector<int64_t> rp2;
+    std::vector<int32_t> c2;
+    std::vector<int64_t> s2;      // input CSR position; -2 = constant 1.0 (batch padding)
+    std::vector<int64_t> diagpos;
+};
+int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
+                      const double* node_xyz, int reorder, int sigma, Permuted& out);
+// Stage 2: the K1/K2 warp slices of a permuted CSR (meta, col, src, sizes of `out`).
+int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
+                const std::vector<int64_t>& s2, int threshold, int vec, Plan& out);
+
 // Builds the locality order, windowed length sort, symmetric renumbering with
 // sorted columns and the warp-slice packing.  Returns FESPMV_OK or an error code
 // (message set).
@@ -108,6 +123,11 @@ int launch_build_scaled(fespmv_mat* A, cudaStream_t s);
 // y = B x with the FP32 (precision FESPMV_PREC_F32) or BF16 copy, handle numbering.
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s);
+
+// Handle plumbing (capi.cpp)
+void free_handle(fespmv_mat* A);
+int alloc_scaled(fespmv_mat* A, int64_t len);
+int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s);
 
 // CG (cg.cu)
 void free_cg(fespmv_mat* A);

@@ -87,8 +87,8 @@ static void morton_node_order(int64_t n_nodes, const double* xyz, std::vector<in
                      [&](int64_t a, int64_t b) { return code[(size_t)a] < code[(size_t)b]; });
 }
 
-int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
-               const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out) {
+int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
+                      const double* node_xyz, int reorder, int sigma, Permuted& out) {
     if (dpn <= 0) dpn = 1;
     if (n % dpn != 0) {
         set_error("n_rows %lld is not a multiple of dofs_per_node %d", (long long)n, dpn);
@@ -121,14 +121,14 @@ int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
     for (int64_t i = 0; i < n; ++i) out.pinv[(size_t)out.perm[(size_t)i]] = (int32_t)i;
 
     // 3. permuted rows with renumbered, sorted columns: (new col, input position)
-    std::vector<int64_t> rp2((size_t)n + 1, 0);
+    out.rp2.assign((size_t)n + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t o = out.perm[(size_t)i];
-        rp2[(size_t)i + 1] = rp2[(size_t)i] + (rowptr[o + 1] - rowptr[o]);
+        out.rp2[(size_t)i + 1] = out.rp2[(size_t)i] + (rowptr[o + 1] - rowptr[o]);
     }
-    const int64_t nnz = rp2[(size_t)n];
-    std::vector<int32_t> c2((size_t)nnz);
-    std::vector<int64_t> s2((size_t)nnz);
+    const int64_t nnz = out.rp2[(size_t)n];
+    out.c2.resize((size_t)nnz);
+    out.s2.resize((size_t)nnz);
     out.diagpos.assign((size_t)n, -1);
     std::vector<std::pair<int32_t, int64_t>> row;
     for (int64_t i = 0; i < n; ++i) {
@@ -142,13 +142,18 @@ int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
                 set_error("duplicate column %d in row %lld", colind[row[k].second], (long long)o);
                 return FESPMV_ERR_BAD_CSR;
             }
-            c2[(size_t)rp2[(size_t)i] + k] = row[k].first;
-            s2[(size_t)rp2[(size_t)i] + k] = row[k].second;
+            out.c2[(size_t)out.rp2[(size_t)i] + k] = row[k].first;
+            out.s2[(size_t)out.rp2[(size_t)i] + k] = row[k].second;
             if (row[k].first == (int32_t)i) out.diagpos[(size_t)i] = row[k].second;
         }
     }
+    return FESPMV_OK;
+}
 
-    // 4. slice plan: per 32-row group choose T, split into T warps of 32/T rows
+int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
+                const std::vector<int64_t>& s2, int threshold, int V, Plan& out) {
+    const int64_t n = (int64_t)rp2.size() - 1;
+    // slice plan: per 32-row group choose T, split into T warps of 32/T rows
     struct Slice { int64_t r0; int nr; int T; int64_t w; };
     std::vector<Slice> slices;
     for (int64_t g0 = 0; g0 < n; g0 += 32) {
@@ -173,7 +178,7 @@ int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
     out.n_slices = (int64_t)slices.size();
     int64_t total = 0;
     for (const Slice& s : slices) total += 32 * s.w;
-    if (total / 32 > (int64_t)UINT32_MAX) {
+    if (total / 32 > (int64_t)UINT32_MAX || n > (int64_t)UINT32_MAX) {
         set_error("packed matrix too large for 32-bit slice offsets");
         return FESPMV_ERR_UNSUPPORTED;
     }
@@ -202,6 +207,19 @@ int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
         }
         off += 32 * s.w;
     }
+    return FESPMV_OK;
+}
+
+int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
+               const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out) {
+    Permuted pm;
+    int rc = order_and_permute(n, rowptr, colind, dpn, node_xyz, reorder, sigma, pm);
+    if (rc) return rc;
+    rc = pack_slices(pm.rp2, pm.c2, pm.s2, threshold, V, out);
+    if (rc) return rc;
+    out.perm.swap(pm.perm);
+    out.pinv.swap(pm.pinv);
+    out.diagpos.swap(pm.diagpos);
     return FESPMV_OK;
 }
 

@@ -144,13 +144,14 @@ __global__ void gather_f32(const float* __restrict__ in, const int32_t* __restri
     if (i < n) out[i] = __ldg(in + idx[i]);
 }
 
-// packed[q] = values[src[q]] (0 for padding); diag[i] = values[diagpos[i]].
+// packed[q] = values[src[q]]; src = -1 is padding (0), -2 a batch padding row's
+// unit diagonal (1).  diag[i] = values[diagpos[i]] with the same conventions.
 __global__ void fill_values_f64(const double* __restrict__ vals_in, const int64_t* __restrict__ src,
                                 double* __restrict__ packed, int64_t len) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q < len) {
         int64_t s = src[q];
-        packed[q] = s >= 0 ? vals_in[s] : 0.0;
+        packed[q] = s >= 0 ? vals_in[s] : (s == -2 ? 1.0 : 0.0);
     }
 }
 
@@ -159,7 +160,7 @@ __global__ void fill_diag_f64(const double* __restrict__ vals_in, const int64_t*
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) {
         int64_t s = diagpos[i];
-        diag[i] = s >= 0 ? vals_in[s] : 0.0;
+        diag[i] = s >= 0 ? vals_in[s] : (s == -2 ? 1.0 : 0.0);
     }
 }
 
