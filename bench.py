@@ -300,6 +300,16 @@ def main():
                 tl = timed_steps(f, max(10, args.steps // 4))
                 extra[f"{name}_spmv_gbs"] = round(nnz * (vb + 4) + n * 8) / (statistics.mean(tl) * 1e-3) / 1e9
                 extra[f"{name}_spmv_gbs"] = round(extra[f"{name}_spmv_gbs"], 1)
+            # 32 right-hand sides in one pass over the FP32 matrix (row-major n x 32)
+            X32 = torch.rand((n, 32), dtype=torch.float32, device=dev)
+            Y32 = torch.empty_like(X32)
+            fm = lambda: fs.spmv_apply_multi(A, X32, Y32, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm()
+            tm32 = timed_steps(fm, max(10, args.steps // 8))
+            tmean = statistics.mean(tm32) * 1e-3
+            extra["multi32_fp32"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
+                                     "us_per_apply": round(tmean * 1e6, 1),
+                                     "us_per_rhs": round(tmean * 1e6 / 32, 2)}
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,

@@ -132,6 +132,22 @@ void spmv_destroy(fespmv_mat_t A);
  */
 int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv_stream_t stream);
 
+/*
+ * spmv_apply_multi -- Y = A X for k right-hand sides at once (1 <= k <= 32), the
+ * matrix streamed from memory once for all columns (the paper applies one
+ * vector at a time; this is the batched layer's product).
+ *   X, Y       device, row-major n_rows x k (k values per row), double with
+ *              precision FESPMV_PREC_F64 (FP64 values and arithmetic) or float
+ *              with FESPMV_PREC_F32 (the FP32 copy of B = S A S, float
+ *              arithmetic); input numbering unless FESPMV_IO_PERMUTED
+ * Needs a SLICED handle built with threshold 0 (one lane per row).  Each entry
+ * of Y is the sum of its row's products in the order of the row's stored
+ * entries (one FMA chain per row and column).
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM (scratch for the input numbering), CUDA.
+ */
+int spmv_apply_multi(fespmv_mat_t A, const void* X, void* Y, int32_t k, int32_t precision,
+                     int32_t flags, fespmv_stream_t stream);
+
 /* Vector permutation between the input numbering and a SLICED handle's numbering
  * (device arrays of n_rows doubles, no overlap):
  *   direction 0: out[i'] = in[P[i']]   (input -> permuted, x' = x(P), Sec. 5.2)

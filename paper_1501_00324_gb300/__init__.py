@@ -120,6 +120,8 @@ _lib.spmv_apply.argtypes = [_P, _P, _P, _i32, _P]
 _lib.spmv_apply.restype = ctypes.c_int
 _lib.spmv_apply_scaled.argtypes = [_P, _P, _P, _i32, _i32, _P]
 _lib.spmv_apply_scaled.restype = ctypes.c_int
+_lib.spmv_apply_multi.argtypes = [_P, _P, _P, _i32, _i32, _i32, _P]
+_lib.spmv_apply_multi.restype = ctypes.c_int
 _lib.spmv_permute.argtypes = [_P, _P, _P, _i32, _P]
 _lib.spmv_permute.restype = ctypes.c_int
 _lib.spmv_update_values.argtypes = [_P, _P, _i32, _P]
@@ -250,6 +252,13 @@ def spmv_apply(A: Matrix, x, y, flags=0, stream=None):
 def spmv_apply_scaled(A: Matrix, x, y, precision=FESPMV_PREC_F32, flags=0, stream=None):
     _check(_lib.spmv_apply_scaled(A.handle, _ptr(x), _ptr(y), precision, flags, _stream(stream)))
     return y
+
+
+def spmv_apply_multi(A: Matrix, X, Y, precision=FESPMV_PREC_F64, flags=0, stream=None):
+    """Y = A X for X of shape (n_rows, k), k <= 32 (torch CUDA tensors)."""
+    k = X.shape[1] if X.dim() == 2 else 1
+    _check(_lib.spmv_apply_multi(A.handle, _ptr(X), _ptr(Y), k, precision, flags, _stream(stream)))
+    return Y
 
 
 def spmv_permute(A: Matrix, x, out, direction=0, stream=None):

@@ -46,7 +46,7 @@ void free_handle(fespmv_mat* A) {
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
-                    A->d_ys};
+                    A->d_ys, A->d_xk, A->d_yk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;
@@ -84,6 +84,9 @@ int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s) {
     const int64_t n = A->n;
     A->n_slices = plan.n_slices;
     A->packed_len = plan.packed_len;
+    A->max_lanes_log2 = 0;
+    for (int64_t i = 0; i < plan.n_slices; ++i)
+        A->max_lanes_log2 = std::max<int>(A->max_lanes_log2, (int)plan.meta[(size_t)i * 4 + 3]);
     int rc;
     if ((rc = device_alloc(A, (void**)&A->d_meta, sizeof(uint4) * plan.n_slices, "slice metadata")) ||
         (rc = device_alloc(A, (void**)&A->d_col, sizeof(int32_t) * plan.packed_len, "packed columns")) ||

@@ -102,6 +102,9 @@ struct fespmv_mat {
     uint16_t* d_val16 = nullptr;      // B in bfloat16 bits
     double* d_scale = nullptr;        // S = diag(A)^-1/2 (handle numbering)
     int* d_flag = nullptr;            // set to 1 when diag(A) has a non-positive entry
+    double* d_xk = nullptr;           // multi-RHS permuted-I/O scratch (32 n doubles each)
+    double* d_yk = nullptr;
+    int max_lanes_log2 = 0;           // largest log2(lanes per row) over the slices
     float* d_xs = nullptr;            // float permuted-I/O scratch (n each)
     float* d_ys = nullptr;
 
