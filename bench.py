@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--serve-full", action="store_true",
                     help="the full serving pool: 48 meshes of 5k..3M rows (else 12 of 5k..300k)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--batch-meshes", type=int, default=256,
+                    help="cubes in the batched solve (node counts log-uniform in [1k, 200k]); 0 skips")
     return ap.parse_args()
 
 
@@ -335,6 +337,8 @@ def main():
                 extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves, fs.FESPMV_CG_F64)
                 extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                   fs.FESPMV_CG_F32_REFINE)
+            if args.batch_meshes > 0:
+                extra["batched"] = bench_batched(fs, torch, args)
             if args.serve_seconds > 0 and hasattr(fs, "srv_create"):
                 extra["serving"] = bench_serving(fs, torch, args)
     clk = clocks.summary()
@@ -506,6 +510,62 @@ def bench_serving(fs, torch, args):
                      "rows_total": sum(p.n_rows for p in pool),
                      "nnz_total": sum(p.nnz for p in pool), "setup_s": round(setup_s, 1)},
             "seconds": T, "overload": dict(rate_per_s=args.serve_rate, **over), "steady": steady}
+
+
+def bench_batched(fs, torch, args):
+    """Many independent cube Laplacians (node counts log-uniform in [1k, 200k]) solved
+    together by batch_cg_solve (FP32 inner CG, FP64 refinement, tol 1e-10), against
+    the same problems solved one after another with cg_solve (FP32-refined, and FP64)."""
+    import fegen
+    rng = np.random.default_rng(2000)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=args.batch_meshes))
+    t0 = time.perf_counter()
+    ps = [fegen.cube_laplace(max(3, round(N ** (1 / 3))), 2000 + i) for i, N in enumerate(sizes)]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    B = fs.batch_create([(p.rowptr, p.colind, p.values, p.node_xyz, 1) for p in ps], sigma=1024)
+    create_s = time.perf_counter() - t0
+    bs = [fegen.random_vector(p.n_rows, 5000 + j) for j, p in enumerate(ps)]
+    bd = torch.from_numpy(np.concatenate(bs)).cuda()
+    xd = torch.zeros_like(bd)
+    fs.batch_cg_solve(B, bd, xd, tol=1e-10)            # warm: graph capture
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, res = fs.batch_cg_solve(B, bd, xd, tol=1e-10)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    assert rc == 0
+    batch_s = min(times)
+    info = fs.batch_get_info(B)
+    fs.batch_destroy(B)
+    seq = {}
+    for name, prec in (("f32_refine", fs.FESPMV_CG_F32_REFINE), ("f64", fs.FESPMV_CG_F64)):
+        mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=1024,
+                               precisions=fs.FESPMV_PREC_F32) for p in ps]
+        bds = [torch.from_numpy(b).cuda() for b in bs]
+        xs = [torch.zeros_like(b) for b in bds]
+        for A, b, x in zip(mats, bds, xs):              # warm: graphs per handle
+            fs.cg_solve(A, b, x, tol=1e-10, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for A, b, x in zip(mats, bds, xs):
+            x.zero_()
+            fs.cg_solve(A, b, x, tol=1e-10, precision=prec)
+        torch.cuda.synchronize()
+        seq[name] = round(time.perf_counter() - t0, 4)
+        for A in mats:
+            fs.spmv_destroy(A)
+    return {"meshes": len(ps), "rows_total": info["n_rows"], "padded_rows": info["padded_rows"],
+            "nnz_total": info["nnz"], "gen_s": round(gen_s, 1), "create_s": round(create_s, 1),
+            "batched_s": round(batch_s, 4), "solves_per_s": round(len(ps) / batch_s, 1),
+            "max_outer": max(r["outer"] for r in res), "max_inner_iters": max(r["iters"] for r in res),
+            "one_after_another_s": seq,
+            "speedup_vs_sequential_f32": round(seq["f32_refine"] / batch_s, 2),
+            "speedup_vs_sequential_f64": round(seq["f64"] / batch_s, 2)}
 
 
 def bench_cg(fs, torch, A, p, n_solves, precision):
