@@ -41,8 +41,9 @@ import numpy as np  # noqa: E402
 METRIC = "SpMV effective HBM GB/s (% of ~8 TB/s); CG solves/s and p50/p99 latency at 1e-10"
 WORKLOAD = "cube_elasticity_64"
 NOMINAL_HBM_GBS = 8000.0
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sliced_f64_cube_elasticity_64.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1501_00324_gb300", "csrc", "spmv_kernels.cu")
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1501_00324_gb300", "csrc", f)
+               for f in ("spmv_kernels.cu", "spmv_device.cuh")]
 
 
 def parse_args():
@@ -55,8 +56,12 @@ def parse_args():
     ap.add_argument("--vec", type=int, default=2)
     ap.add_argument("--threshold", type=int, default=0)
     ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--kernel", choices=["f64", "df64"], default="f64",
+                    help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
+    ap.add_argument("--profile-target", choices=["multi", "fp32", "cg", "cg_f32"], default=None,
+                    help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-seconds", type=float, default=8.0,
@@ -81,13 +86,16 @@ def measured_peaks():
 
 
 def kernel_hash():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
-def profile_traffic():
+def profile_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(os.path.join(PROFILES, f"sliced_{kernel}_cube_elasticity_64.md")).read()
     except OSError:
         return None, "no ncu summary committed"
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
@@ -251,7 +259,8 @@ def main():
     t0 = time.perf_counter()
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.vec,
                        threshold=args.threshold, block=args.block,
-                       precisions=0 if args.only_spmv else fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+                       precisions=(0 if args.only_spmv else fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+                       | (fs.FESPMV_PREC_DF64 if args.kernel == "df64" else 0))
     create_s = time.perf_counter() - t0
     info = fs.spmv_get_info(A)
 
@@ -274,6 +283,9 @@ def main():
         return [a.elapsed_time(b) for (a, b) in evs]
 
     fe = lambda: fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    if args.profile_target:
+        profile_piece(fs, torch, A, p, xp, args)
+        return
     for _ in range(args.warmup):
         fe()
     torch.cuda.synchronize()
@@ -349,7 +361,7 @@ def main():
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = mb / t_mean / 1e9
-    traffic, traffic_src = profile_traffic()
+    traffic, traffic_src = profile_traffic(args.kernel)
 
     if rank == 0:
         cpu = None
@@ -361,10 +373,11 @@ def main():
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.kernel == "f64" else "df64 (float pairs, fp32 FMA)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": n, "nnz": nnz,
-                       "kernel": f"sliced_f64 V={info['vec']} threshold={args.threshold} "
+                       "kernel": f"sliced_{args.kernel} V={info['vec']} threshold={args.threshold} "
                                  f"sigma={args.sigma} block={args.block}",
                        "order": "Morton nodes, windowed length sort, sorted columns",
                        "l2": "256 MB write between steps; matrix 414 MB > L2",
@@ -403,13 +416,15 @@ def serving_pool(n_meshes, lo, hi, seed):
     for i, N in enumerate(rows):
         kind = i % 3
         if kind == 0:
-            p = fegen.cube_laplace(max(3, round(N ** (1 / 3))), seed + 1 + i)
+            p = fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd),
+                                 seed + 1 + i)
         elif kind == 1:
-            p = fegen.cube_elasticity(max(3, round((N / 3) ** (1 / 3))), seed + 1 + i)
+            p = fegen.valid_seed(lambda sd: fegen.cube_elasticity(max(3, round((N / 3) ** (1 / 3))), sd),
+                                 seed + 1 + i)
         else:
             s = (N / (24 * 256 * 512)) ** (1 / 3)
-            p = fegen.shell_laplace(max(3, round(24 * s)), max(4, round(256 * s)),
-                                    max(8, round(512 * s)), seed + 1 + i)
+            p = fegen.valid_seed(lambda sd: fegen.shell_laplace(max(3, round(24 * s)), max(4, round(256 * s)),
+                                                                max(8, round(512 * s)), sd), seed + 1 + i)
         pool.append(p)
     return pool
 
@@ -520,7 +535,8 @@ def bench_batched(fs, torch, args):
     rng = np.random.default_rng(2000)
     sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=args.batch_meshes))
     t0 = time.perf_counter()
-    ps = [fegen.cube_laplace(max(3, round(N ** (1 / 3))), 2000 + i) for i, N in enumerate(sizes)]
+    ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 2000 + i)
+          for i, N in enumerate(sizes)]
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     B = fs.batch_create([(p.rowptr, p.colind, p.values, p.node_xyz, 1) for p in ps], sigma=1024)
@@ -566,6 +582,33 @@ def bench_batched(fs, torch, args):
             "one_after_another_s": seq,
             "speedup_vs_sequential_f32": round(seq["f32_refine"] / batch_s, 2),
             "speedup_vs_sequential_f64": round(seq["f64"] / batch_s, 2)}
+
+
+def profile_piece(fs, torch, A, p, xp, args):
+    """Warm-up then `steps` launches of one piece, for ncu launch lists and captures."""
+    n = p.n_rows
+    t = args.profile_target
+    if t == "multi":
+        X = torch.rand((n, 32), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "fp32":
+        xs = xp.float()
+        ys = torch.empty_like(xs)
+        f = lambda: fs.spmv_apply_scaled(A, xs, ys, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    else:
+        b = torch.rand(n, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        prec = fs.FESPMV_CG_F64 if t == "cg" else fs.FESPMV_CG_F32_REFINE
+        f = lambda: fs.cg_solve(A, b, x, tol=1e-30, max_iter=32, max_restarts=-1, max_outer=1,  # noqa: E731
+                                precision=prec)
+    for _ in range(args.warmup):
+        f()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        f()
+    torch.cuda.synchronize()
+    print(f"profile target {t}: {args.steps} runs done", flush=True)
 
 
 def bench_cg(fs, torch, A, p, n_solves, precision):

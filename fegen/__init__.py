@@ -11,9 +11,10 @@ Workloads (all sizes are node grids, hex cells split into 6 Kuhn tetrahedra):
 
 * ``cube_laplace``      unit cube, D = I, interior nodes jittered +-0.2h,
                         random node numbering, Dirichlet on the z=0 face.
-                        (Jitter +-0.2h keeps every Kuhn tetrahedron valid: its
-                        smallest height is h/sqrt(2) = 0.707h, the largest
-                        relative vertex displacement 2*0.2*sqrt(3)h = 0.69h.)
+                        (+-0.2h almost never inverts a Kuhn tetrahedron -- its
+                        smallest height is h/sqrt(2) = 0.707h -- but a tilted
+                        face can; the generator then raises, and the pools
+                        below redraw with the next seed, see valid_seed.)
 * ``cube_elasticity``   unit cube, 3 dof/node (dof = 3*node + c), per-tet
                         Young's modulus log-uniform in [0.5, 2], nu = 0.3,
                         clamped (all 3 dof) on the z=0 face.
@@ -225,6 +226,18 @@ def shell_laplace(nr: int = 24, nt: int = 256, nph: int = 512, seed: int = 1503,
     base = np.round(idx[:, 1]) == 0
     return _assemble(f"shell_laplace_{nr}x{nt}x{nph}", 1, (nr, nt, nph), 1, xyz, perm,
                      fib.ravel(), d_iso, d_ani, 0.0, base, seed, dirichlet)
+
+
+def valid_seed(maker, seed: int, tries: int = 16):
+    """maker(seed) for seed, seed + 100003, seed + 2*100003, ... until no tetrahedron
+    is inverted by the jitter; returns the problem (its .seed says which draw)."""
+    last = None
+    for k in range(tries):
+        try:
+            return maker(seed + 100003 * k)
+        except ValueError as e:
+            last = e
+    raise last
 
 
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

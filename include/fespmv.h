@@ -64,6 +64,13 @@ typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory 
 #define FESPMV_PREC_F64      1  /* FP64 values (always kept) */
 #define FESPMV_PREC_F32      2  /* FP32 values of B = S A S, S = diag(A)^-1/2 (refined CG) */
 #define FESPMV_PREC_BF16     4  /* bfloat16 values of B = S A S (refined CG) */
+#define FESPMV_PREC_DF64     8  /* SLICED: also keep the FP64 values as float pairs
+                                   (hi, lo) and compute every FP64 product of the handle
+                                   (spmv_apply, cg_solve) on the FP32 pipe with
+                                   error-free transformations; values or x entries
+                                   outside |v| in [2^-50, 2^50] (and Inf/NaN) take an
+                                   exact FP64 path.  Componentwise error below
+                                   (L+2) 2^-47 sum_j |A_ij x_j| for rows of L entries. */
 
 typedef struct {
     int32_t format;      /* FESPMV_FMT_*; 0 = CSR baseline */

@@ -35,6 +35,7 @@ FESPMV_REORDER_MORTON = 1
 FESPMV_PREC_F64 = 1
 FESPMV_PREC_F32 = 2
 FESPMV_PREC_BF16 = 4
+FESPMV_PREC_DF64 = 8
 FESPMV_IO_PERMUTED = 1
 FESPMV_IO_HOST = 2
 FESPMV_EXPORT_PERM = 0

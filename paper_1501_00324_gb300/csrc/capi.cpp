@@ -46,7 +46,7 @@ void free_handle(fespmv_mat* A) {
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
-                    A->d_ys, A->d_xk, A->d_yk};
+                    A->d_ys, A->d_xk, A->d_yk, A->d_vdf, A->d_xdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;
@@ -151,7 +151,10 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     if (o.reorder == FESPMV_REORDER_MORTON && (!mesh || !mesh->node_xyz) && o.format == FESPMV_FMT_SLICED) {
         set_error("REORDER_MORTON needs mesh->node_xyz"); return FESPMV_ERR_INVALID_ARG;
     }
-    if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32 | FESPMV_PREC_BF16)) {
+    if (o.precisions & FESPMV_PREC_DF64 && o.format != FESPMV_FMT_SLICED) {
+        set_error("FESPMV_PREC_DF64 needs a SLICED handle"); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32 | FESPMV_PREC_BF16 | FESPMV_PREC_DF64)) {
         set_error("unknown precision bits 0x%x", o.precisions); return FESPMV_ERR_INVALID_ARG;
     }
     int rc = validate_csr(n, rowptr, colind);
@@ -204,6 +207,10 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
                        o.threshold, o.vec, plan));
         TRY(upload_sliced(A, plan, s));
+        if (A->precisions & FESPMV_PREC_DF64) {
+            TRY(device_alloc(A, (void**)&A->d_vdf, sizeof(float2) * plan.packed_len, "float-pair values"));
+            TRY(device_alloc(A, (void**)&A->d_xdf, sizeof(float2) * n, "float-pair x"));
+        }
         TRY(alloc_scaled(A, plan.packed_len));
         TRY(launch_fill_values(A, A->d_vals_in, s));
         // host vectors must stay alive until the copies finish
@@ -288,7 +295,18 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
         yd = A->d_yh;
     }
     int rc;
-    if (A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED)) {
+    if (A->d_vdf) {   // float-pair FP64 product
+        const double* xp = xd;
+        if (!(flags & FESPMV_IO_PERMUTED)) {
+            if ((rc = launch_gather_split(xd, A->d_perm, A->d_xp, A->d_xdf, A->n, s))) return rc;
+            xp = A->d_xp;
+        } else if ((rc = launch_split(xd, A->d_xdf, A->n, s))) {
+            return rc;
+        }
+        double* yp = (flags & FESPMV_IO_PERMUTED) ? yd : A->d_yp;
+        if ((rc = launch_spmv_df(A, A->d_xdf, xp, yp, s))) return rc;
+        if (!(flags & FESPMV_IO_PERMUTED) && (rc = launch_gather(A->d_yp, A->d_pinv, yd, A->n, s))) return rc;
+    } else if (A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED)) {
         if ((rc = launch_gather(xd, A->d_perm, A->d_xp, A->n, s))) return rc;
         if ((rc = launch_spmv(A, A->d_xp, A->d_yp, s))) return rc;
         if ((rc = launch_gather(A->d_yp, A->d_pinv, yd, A->n, s))) return rc;

@@ -114,6 +114,32 @@ __global__ void __launch_bounds__(256) cg_spmv_dot_sliced(const uint4* __restric
     if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
+template <int V, int U>
+__global__ void __launch_bounds__(256) cg_spmv_dot_df(const uint4* __restrict__ meta,
+                                                      const int32_t* __restrict__ col,
+                                                      const float2* __restrict__ vdf,
+                                                      const double* __restrict__ val,
+                                                      const double* __restrict__ p,
+                                                      const float2* __restrict__ pdf,
+                                                      double* __restrict__ q, int64_t n_slices,
+                                                      int64_t n, double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    if (warp < n_slices) {
+        const uint4 m = meta[warp];
+        const double sum = sliced_row_sum_df<V, U>(m, col, vdf, val, pdf, p, lane);
+        const int lt = (int)m.w;
+        const int64_t row = (int64_t)m.z + (lane >> lt);
+        if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+            q[row] = sum;
+            v[0] = p[row] * sum;
+        }
+    }
+    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+}
+
 template <int L>
 __global__ void cg_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ p,
@@ -164,12 +190,15 @@ __global__ void __launch_bounds__(256) cg_update(int64_t n, double* __restrict__
 __global__ void __launch_bounds__(256) cg_pupdate(int64_t n, double* __restrict__ p,
                                                   const double* __restrict__ r,
                                                   const double* __restrict__ dinv,
-                                                  const CgScalars* sc) {
+                                                  float2* __restrict__ pdf, const CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     const double beta = sc->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], dinv[i] * r[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double pi = fma(beta, p[i], dinv[i] * r[i]);
+        p[i] = pi;
+        if (pdf) pdf[i] = df_split(pi);
+    }
 }
 
 // dinv = 1/diag (Jacobi) or 1; a non-positive or non-finite diagonal marks BADDIAG.
@@ -194,7 +223,8 @@ __global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restri
                                                const double* __restrict__ q, double* __restrict__ r,
                                                double* __restrict__ p,
                                                const double* __restrict__ dinv, double tol2,
-                                               double* partials, CgScalars* sc) {
+                                               double* partials, CgScalars* sc,
+                                               float2* __restrict__ pdf) {
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -203,6 +233,7 @@ __global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restri
         const double zi = dinv[i] * ri;
         r[i] = ri;
         p[i] = zi;
+        if (pdf) pdf[i] = df_split(zi);
         v[0] = fma(ri, zi, v[0]);
         v[1] = fma(ri, ri, v[1]);
         v[2] = fma(bi, bi, v[2]);
@@ -389,7 +420,7 @@ void destroy_work(CgWork* w) {
         if (e) cudaEventDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
     void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc,
-                    w->w32, w->r32, w->p32, w->q32};
+                    w->w32, w->r32, w->p32, w->q32, w->pdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -424,6 +455,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
     const int64_t np = 3 * std::max<int64_t>(spmv_grid(A), upd) + 1;
     int64_t b = 6 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
+    if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
     return b;
 }
@@ -444,6 +476,10 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
     double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv};
     for (double** v : vecs)
         if ((rc = work_alloc(w, (void**)v, nb, "CG vector"))) { destroy_work(w); return rc; }
+    if (A->d_vdf && (rc = work_alloc(w, (void**)&w->pdf, sizeof(float2) * (size_t)A->n, "CG float-pair p"))) {
+        destroy_work(w);
+        return rc;
+    }
     const size_t np = 3 * (size_t)std::max(spmv_grid(A), w->upd_grid) + 1;
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
         (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
@@ -483,8 +519,22 @@ static void launch_spmv_dot_csr(const fespmv_mat* A, CgWork* w, cudaStream_t s) 
                                                          w->q, A->n, w->partials, w->sc);
 }
 
+template <int V>
+static void launch_spmv_dot_df(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    constexpr int U = (V == 4) ? 2 : 4;
+    cg_spmv_dot_df<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_vdf, A->d_val, w->p,
+                                                           w->pdf, w->q, A->n_slices, A->n,
+                                                           w->partials, w->sc);
+}
+
 static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
-    if (A->format == FESPMV_FMT_SLICED) {
+    if (A->d_vdf) {
+        switch (A->vec) {
+            case 1: launch_spmv_dot_df<1>(A, w, s); break;
+            case 4: launch_spmv_dot_df<4>(A, w, s); break;
+            default: launch_spmv_dot_df<2>(A, w, s); break;
+        }
+    } else if (A->format == FESPMV_FMT_SLICED) {
         switch (A->vec) {
             case 1: launch_spmv_dot_sliced<1>(A, w, s); break;
             case 4: launch_spmv_dot_sliced<4>(A, w, s); break;
@@ -501,7 +551,7 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
         }
     }
     cg_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->p, w->q, w->dinv, w->partials, w->sc);
-    cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->sc);
+    cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->pdf, w->sc);
 }
 
 template <typename VT, int V>
@@ -653,7 +703,7 @@ static int enqueue_init(CgRun& r, bool ax) {
     int rc;
     if (ax && (rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
     cg_init<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, w->r, w->p, w->dinv,
-                                          r.o.tol * r.o.tol, w->partials, w->sc);
+                                          r.o.tol * r.o.tol, w->partials, w->sc, w->pdf);
     FESPMV_CUDA(cudaGetLastError());
     r.phase = PH_INIT_WAIT;
     return enqueue_status(r, 0);
@@ -1074,7 +1124,7 @@ static int cg_static_impl(int64_t n, const int64_t* rowptr, const int32_t* colin
     int status = CG_RUNNING;
     for (;;) {
         if (need_ax) static_spmv(m, false, x, q, partials, sc, s);
-        cg_init<<<upd, 256, 0, s>>>(n, b, need_ax ? q : nullptr, r, p, dinv, tol2, partials, sc);
+        cg_init<<<upd, 256, 0, s>>>(n, b, need_ax ? q : nullptr, r, p, dinv, tol2, partials, sc, nullptr);
         FESPMV_CUDA(cudaGetLastError());
         if ((rc = static_read(&h, sc, s))) return rc;
         if (h.status == CG_BADDIAG) {
@@ -1093,7 +1143,7 @@ static int cg_static_impl(int64_t n, const int64_t* rowptr, const int32_t* colin
             for (int k = 0; k < o.check_every; ++k) {
                 static_spmv(m, true, p, q, partials, sc, s);
                 cg_update<<<upd, 256, 0, s>>>(n, x, r, p, q, dinv, partials, sc);
-                cg_pupdate<<<upd, 256, 0, s>>>(n, p, r, dinv, sc);
+                cg_pupdate<<<upd, 256, 0, s>>>(n, p, r, dinv, nullptr, sc);
             }
             FESPMV_CUDA(cudaGetLastError());
             if ((rc = static_read(&h, sc, s))) return rc;

@@ -33,6 +33,7 @@ struct CgWork {
     cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
     int chunk_low[2] = {0, 0};
     double* h_io = nullptr;     // pinned host staging of n doubles (solve server)
+    float2* pdf = nullptr;      // float-pair split of p (handles with FESPMV_PREC_DF64)
     int64_t bytes = 0;          // device bytes held
 };
 

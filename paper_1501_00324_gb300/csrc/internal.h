@@ -102,6 +102,8 @@ struct fespmv_mat {
     uint16_t* d_val16 = nullptr;      // B in bfloat16 bits
     double* d_scale = nullptr;        // S = diag(A)^-1/2 (handle numbering)
     int* d_flag = nullptr;            // set to 1 when diag(A) has a non-positive entry
+    float2* d_vdf = nullptr;          // FP64 values as float pairs (FESPMV_PREC_DF64)
+    float2* d_xdf = nullptr;          // float-pair x scratch (n)
     double* d_xk = nullptr;           // multi-RHS permuted-I/O scratch (32 n doubles each)
     double* d_yk = nullptr;
     int max_lanes_log2 = 0;           // largest log2(lanes per row) over the slices
@@ -126,6 +128,11 @@ int launch_build_scaled(fespmv_mat* A, cudaStream_t s);
 // y = B x with the FP32 (precision FESPMV_PREC_F32) or BF16 copy, handle numbering.
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s);
+// Float-pair FP64 product (FESPMV_PREC_DF64): y = A x with x given as double and split.
+int launch_spmv_df(const fespmv_mat* A, const float2* xs, const double* x, double* y, cudaStream_t s);
+int launch_split(const double* v, float2* out, int64_t len, cudaStream_t s);
+int launch_gather_split(const double* x, const int32_t* idx, double* xp, float2* xs, int64_t n,
+                        cudaStream_t s);
 
 // Handle plumbing (capi.cpp)
 void free_handle(fespmv_mat* A);

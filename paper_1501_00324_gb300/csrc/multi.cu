@@ -47,11 +47,11 @@ __global__ void __launch_bounds__(128) sliced_multi(const uint4* __restrict__ me
         const int32_t* cp = col + off + (int64_t)s * 32;
 #pragma unroll
         for (int e0 = 0; e0 < 32 * V; e0 += 4) {
-            const int4 c4 = *reinterpret_cast<const int4*>(cp + e0);
+            const int4 c4 = ld_stream(reinterpret_cast<const int4*>(cp + e0));
             VT v[4];
 #pragma unroll
             for (int h = 0; h < 4; h += NV) {
-                const VV t = *reinterpret_cast<const VV*>(vp + e0 + h);
+                const VV t = ld_stream(reinterpret_cast<const VV*>(vp + e0 + h));
                 if constexpr (NV == 2) {
                     v[h] = t.x; v[h + 1] = t.y;
                 } else {

@@ -211,3 +211,138 @@ __device__ __forceinline__ float csr_row_sum_low(int64_t row, int sub, int64_t n
 }
 
 }  // namespace fespmv
+
+// ---------------------------------------------------------------- float-pair FP64 product
+// An FP64 value v in the fast range (|v| in [2^-50, 2^50], or 0) is held as two
+// floats hi = fl32(v), lo = fl32(v - hi): 48 significant bits, error <= 2^-48 |v|.
+// Any other value (tiny, huge, Inf, NaN) is marked by hi = NaN and its product is
+// taken in FP64 from the original double (exact slow path).  A product
+// a*x = (ah + al)(xh + xl) is formed on the FP32 pipe with an error-free
+// product (Dekker/Ogita-Rump-Oishi TwoProduct via FMA) and accumulated with an
+// error-free sum (Knuth TwoSum) and a renormalisation after every term, so each
+// term adds at most ~2^-47 of (|a x| + |partial sum|) to the error: a row of L
+// entries stays within ~(L+2) 2^-47 sum|a x|, under 1e-12 for L < 140.
+namespace fespmv {
+
+constexpr float kDfLo = 8.8817841970012523e-16f;   // 2^-50
+constexpr float kDfHi = 1.125899906842624e15f;     // 2^50
+
+struct DfAcc {
+    float hi = 0.0f, lo = 0.0f;
+    double slow = 0.0;
+};
+
+__device__ __forceinline__ void df_add_product(DfAcc& s, float ah, float al, float xh, float xl) {
+    const float p = ah * xh;
+    const float e = fmaf(ah, xh, -p);
+    const float c = fmaf(ah, xl, fmaf(al, xh, e));
+    const float t0 = s.hi + p;
+    const float bp = t0 - s.hi;
+    const float err = (s.hi - (t0 - bp)) + (p - bp);
+    const float t = (s.lo + err) + c;
+    s.hi = t0 + t;
+    s.lo = t - (s.hi - t0);
+}
+
+// (a.hi, a.lo) += (b.hi, b.lo): TwoSum of the high parts, then renormalise.
+__device__ __forceinline__ void df_add(DfAcc& a, float bh, float bl) {
+    const float t0 = a.hi + bh;
+    const float bp = t0 - a.hi;
+    const float err = (a.hi - (t0 - bp)) + (bh - bp);
+    const float t = (a.lo + err) + bl;
+    a.hi = t0 + t;
+    a.lo = t - (a.hi - t0);
+}
+
+__device__ __forceinline__ double df_value(const DfAcc& s) {
+    return ((double)s.hi + (double)s.lo) + s.slow;
+}
+
+__device__ __forceinline__ float2 df_split(double v) {
+    const double a = fabs(v);
+    if (v == 0.0) return make_float2(0.0f, 0.0f);
+    if (!(a >= (double)kDfLo && a <= (double)kDfHi)) return make_float2(__int_as_float(0x7fc00000), 0.0f);
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+template <int V> struct DfChunk;
+template <> struct DfChunk<1> {
+    float2 v[1]; int32_t c[1];
+    __device__ __forceinline__ void load(const float2* vp, const int32_t* cp) {
+        v[0] = ld_stream(vp); c[0] = ld_stream(cp);
+    }
+};
+template <> struct DfChunk<2> {
+    float2 v[2]; int32_t c[2];
+    __device__ __forceinline__ void load(const float2* vp, const int32_t* cp) {
+        float4 a = ld_stream(reinterpret_cast<const float4*>(vp));
+        int2 b = ld_stream(reinterpret_cast<const int2*>(cp));
+        v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w); c[0] = b.x; c[1] = b.y;
+    }
+};
+template <> struct DfChunk<4> {
+    float2 v[4]; int32_t c[4];
+    __device__ __forceinline__ void load(const float2* vp, const int32_t* cp) {
+        float4 a = ld_stream(reinterpret_cast<const float4*>(vp));
+        float4 a2 = ld_stream(reinterpret_cast<const float4*>(vp) + 1);
+        int4 b = ld_stream(reinterpret_cast<const int4*>(cp));
+        v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(a2.x, a2.y); v[3] = make_float2(a2.z, a2.w);
+        c[0] = b.x; c[1] = b.y; c[2] = b.z; c[3] = b.w;
+    }
+};
+
+// One entry: fast path on the FP32 pipe, exact FP64 slow path for marked values.
+__device__ __forceinline__ void df_entry(DfAcc& s, float2 a, int32_t c, const float2* __restrict__ xs,
+                                         const double* __restrict__ x64, const double* __restrict__ a64,
+                                         int64_t pos) {
+    if (c < 0) return;
+    const float2 xv = __ldg(xs + c);
+    if (isnan(a.x) || isnan(xv.x))
+        s.slow = fma(__ldg(a64 + pos), __ldg(x64 + c), s.slow);
+    else
+        df_add_product(s, a.x, a.y, xv.x, xv.y);
+}
+
+template <int V, int U>
+__device__ __forceinline__ double sliced_row_sum_df(const uint4 m, const int32_t* __restrict__ col,
+                                                    const float2* __restrict__ vdf,
+                                                    const double* __restrict__ val,
+                                                    const float2* __restrict__ xs,
+                                                    const double* __restrict__ x64, int lane) {
+    const int64_t off = (int64_t)m.x * 32;
+    const int w = (int)m.y;
+    const int lt = (int)m.w;
+    const int64_t base = off + lane * V;
+    DfAcc s;
+    int st = 0;
+    for (; st + U * V <= w; st += U * V) {
+        DfChunk<V> e[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            e[u].load(vdf + base + (int64_t)(st + u * V) * 32, col + base + (int64_t)(st + u * V) * 32);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                df_entry(s, e[u].v[k], e[u].c[k], xs, x64, val, base + (int64_t)(st + u * V) * 32 + k);
+    }
+    for (; st < w; st += V) {
+        DfChunk<V> e;
+        e.load(vdf + base + (int64_t)st * 32, col + base + (int64_t)st * 32);
+#pragma unroll
+        for (int k = 0; k < V; ++k) df_entry(s, e.v[k], e.c[k], xs, x64, val, base + (int64_t)st * 32 + k);
+    }
+    const int T = 1 << lt;
+    for (int o = T >> 1; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, s.hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, s.lo, o);
+        const double os = __shfl_down_sync(0xffffffffu, s.slow, o);
+        df_add(s, oh, ol);
+        s.slow += os;
+    }
+    return df_value(s);
+}
+
+}  // namespace fespmv

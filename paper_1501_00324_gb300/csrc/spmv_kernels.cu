@@ -53,6 +53,42 @@ __global__ void __launch_bounds__(256) sliced_f64(const uint4* __restrict__ meta
     if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
 }
 
+// ---------------------------------------------------------------- float-pair FP64 product
+
+template <int V, int U>
+__global__ void __launch_bounds__(256) sliced_df64(const uint4* __restrict__ meta,
+                                                   const int32_t* __restrict__ col,
+                                                   const float2* __restrict__ vdf,
+                                                   const double* __restrict__ val,
+                                                   const float2* __restrict__ xs,
+                                                   const double* __restrict__ x,
+                                                   double* __restrict__ y, int64_t n_slices, int64_t n) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_slices) return;
+    const uint4 m = meta[warp];
+    const double sum = sliced_row_sum_df<V, U>(m, col, vdf, val, xs, x, lane);
+    const int lt = (int)m.w;
+    const int64_t row = (int64_t)m.z + (lane >> lt);
+    if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
+}
+
+__global__ void split_df(const double* __restrict__ v, float2* __restrict__ out, int64_t len) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < len) out[i] = df_split(v[i]);
+}
+
+// xp[i] = x[idx[i]] and its float-pair split, in one pass.
+__global__ void gather_split_df(const double* __restrict__ x, const int32_t* __restrict__ idx,
+                                double* __restrict__ xp, float2* __restrict__ xs, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = __ldg(x + idx[i]);
+        xp[i] = v;
+        xs[i] = df_split(v);
+    }
+}
+
 // ---------------------------------------------------------------- low precision (B = S A S)
 
 template <typename VT, int V, int U>
@@ -182,6 +218,39 @@ int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n
     return FESPMV_OK;
 }
 
+int launch_split(const double* v, float2* out, int64_t len, cudaStream_t s) {
+    if (len == 0) return FESPMV_OK;
+    split_df<<<grid_for(len, 256), 256, 0, s>>>(v, out, len);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+int launch_gather_split(const double* x, const int32_t* idx, double* xp, float2* xs, int64_t n,
+                        cudaStream_t s) {
+    if (n == 0) return FESPMV_OK;
+    gather_split_df<<<grid_for(n, 256), 256, 0, s>>>(x, idx, xp, xs, n);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+template <int V>
+static void launch_df(const fespmv_mat* A, const float2* xs, const double* x, double* y, cudaStream_t s) {
+    constexpr int U = (V == 4) ? 2 : 4;
+    sliced_df64<V, U><<<grid_for(A->n_slices * 32, A->block), A->block, 0, s>>>(
+        A->d_meta, A->d_col, A->d_vdf, A->d_val, xs, x, y, A->n_slices, A->n);
+}
+
+int launch_spmv_df(const fespmv_mat* A, const float2* xs, const double* x, double* y, cudaStream_t s) {
+    if (A->n == 0) return FESPMV_OK;
+    switch (A->vec) {
+        case 1: launch_df<1>(A, xs, x, y, s); break;
+        case 4: launch_df<4>(A, xs, x, y, s); break;
+        default: launch_df<2>(A, xs, x, y, s); break;
+    }
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
 int launch_build_scaled(fespmv_mat* A, cudaStream_t s) {
     if (!A->d_scale || A->n == 0) return FESPMV_OK;
     FESPMV_CUDA(cudaMemsetAsync(A->d_flag, 0, sizeof(int), s));
@@ -214,6 +283,10 @@ int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s) {
     if (A->n > 0)
         fill_diag_f64<<<grid_for(A->n, 256), 256, 0, s>>>(vals_in, A->d_diagpos, A->d_diag, A->n);
     FESPMV_CUDA(cudaGetLastError());
+    if (A->d_vdf) {
+        int rc = launch_split(A->d_val, A->d_vdf, A->packed_len, s);
+        if (rc) return rc;
+    }
     return launch_build_scaled(A, s);
 }
 

@@ -82,7 +82,8 @@ def test_batch_many_cubes_device_vectors():
     # 64 cubes, node counts log-uniform in [64, 8000]
     rng = np.random.default_rng(98)
     sizes = np.exp(rng.uniform(np.log(64), np.log(8000), size=64))
-    ps = [fegen.cube_laplace(max(3, round(N ** (1 / 3))), 2000 + i) for i, N in enumerate(sizes)]
+    ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 2000 + i)
+          for i, N in enumerate(sizes)]
     B = as_batch(ps, sigma=256)
     bs = [fegen.random_vector(p.n_rows, 3000 + j) for j, p in enumerate(ps)]
     bd = torch.from_numpy(np.concatenate(bs)).cuda()

@@ -41,7 +41,8 @@ def make(p, **kw):
 
 
 FORMATS = [dict(format=fs.FESPMV_FMT_SLICED, sigma=512), dict(format=fs.FESPMV_FMT_CSR, csr_lanes=4),
-           dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=4, vec=1)]
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=4, vec=1),
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=512, precisions=fs.FESPMV_PREC_DF64)]
 
 
 @pytest.mark.parametrize("fmt", range(len(FORMATS)))
@@ -117,12 +118,13 @@ def test_cg_breakdown_on_indefinite_and_bad_diagonal():
     assert res["status"] == fs.FESPMV_ERR_BREAKDOWN
 
 
-def test_cg_full_size_elasticity_64():
+@pytest.mark.parametrize("prec", [0, fs.FESPMV_PREC_DF64])
+def test_cg_full_size_elasticity_64(prec):
     """The benchmark system (786,432 rows): residual checked by the oracle's product."""
     p = fegen.cube_elasticity(64, 1502)
     u = fegen.manufactured_solution(p)
     b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
-    A = make(p, sigma=1024)
+    A = make(p, sigma=1024, precisions=prec)
     x, res = solve(A, b, tol=1e-10)
     assert res["status"] == 0, res
     assert true_relres(p, x, b) <= 1.01e-10

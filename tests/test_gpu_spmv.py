@@ -70,6 +70,10 @@ KERNELS = [
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, threshold=4),
     dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, block=128),
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=64, threshold=0, reorder=fs.FESPMV_REORDER_NONE),
+    # float-pair FP64 products on the FP32 pipe
+    dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, precisions=fs.FESPMV_PREC_DF64),
+    dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, precisions=fs.FESPMV_PREC_DF64),
+    dict(format=fs.FESPMV_FMT_SLICED, vec=4, sigma=10**9, threshold=4, precisions=fs.FESPMV_PREC_DF64),
 ]
 
 
@@ -171,6 +175,8 @@ def test_edge_cases_empty_ragged_and_nonfinite():
 
 
 @pytest.mark.parametrize("fmt,kw", [(fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2)),
+                                    (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2,
+                                                                precisions=fs.FESPMV_PREC_DF64)),
                                     (fs.FESPMV_FMT_CSR, dict(csr_lanes=4))])
 def test_full_size_elasticity_64(fmt, kw):
     """The benchmark's matrix (64^3 nodes, 786,432 rows, ~34M nnz), every row checked."""
@@ -178,3 +184,27 @@ def test_full_size_elasticity_64(fmt, kw):
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, format=fmt, **kw)
     x = fegen.random_vector(p.n_rows, 1504)
     check_parity(p, apply(A, x), x)
+
+
+@pytest.mark.parametrize("vec", [1, 2, 4])
+def test_float_pair_product_out_of_range_entries(vec):
+    """Values and x entries outside [2^-50, 2^50], and Inf/NaN, take the exact FP64 path."""
+    p = problem("elasticity_9")
+    rng = np.random.default_rng(11)
+    vals = p.values.copy()
+    idx = rng.choice(p.nnz, 40, replace=False)
+    vals[idx[:20]] *= 1e-30
+    vals[idx[20:]] *= 1e30
+    A = fs.spmv_create(p.rowptr, p.colind, vals, p.node_xyz, 3, sigma=64, vec=vec,
+                       precisions=fs.FESPMV_PREC_DF64)
+    x = fegen.random_vector(p.n_rows, 12)
+    x[rng.choice(p.n_rows, 30, replace=False)] *= 1e-200
+    x[rng.choice(p.n_rows, 30, replace=False)] *= 1e200
+    x[rng.choice(p.n_rows, 5, replace=False)] = 0.0
+    check_parity(p, apply(A, x), x, values=vals)
+    xn = x.copy()
+    xn[7] = np.inf
+    xn[19] = np.nan
+    yn = apply(A, xn)
+    yo = oracle.csr_spmv(p.rowptr, p.colind, vals, xn)
+    assert np.array_equal(np.isnan(yn), np.isnan(yo)) and np.array_equal(np.isinf(yn), np.isinf(yo))

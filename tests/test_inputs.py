@@ -110,3 +110,18 @@ def test_generation_is_deterministic():
 def test_inverted_tet_is_rejected():
     with pytest.raises(ValueError):
         fegen.cube_laplace(5, 1, jitter=0.9)
+
+
+def test_valid_seed_redraws_deterministically():
+    calls = []
+
+    def maker(seed):
+        calls.append(seed)
+        if len(calls) < 3:
+            raise ValueError("inverted")
+        return fegen.cube_laplace(4, seed)
+
+    p = fegen.valid_seed(maker, 10)
+    assert calls == [10, 10 + 100003, 10 + 2 * 100003] and p.seed == calls[-1]
+    with pytest.raises(ValueError):
+        fegen.valid_seed(lambda s: fegen.cube_laplace(5, s, jitter=0.9), 1, tries=2)
