@@ -302,7 +302,7 @@ int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts,
  *   opts, res              as for cg_solve (IO flags other than FESPMV_CG_X0 and
  *                          FESPMV_CG_NO_PRECOND are rejected)
  * Same Jacobi-PCG recurrences and kernels as cg_solve on a FESPMV_FMT_CSR handle.
- * The workspace (about 8.3 MB) is one fixed device array inside this library;
+ * The workspace (about 8.8 MB) is one fixed device array inside this library;
  * every GPU that loads the library holds it until the process exits.  The
  * first call on a device resolves that array's address for the device, so make
  * that first call before any stream capture.  Every call shares the array and

@@ -53,31 +53,46 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
     __syncthreads();
 }
 
-// Block sums go to partials[k*gridDim.x + block]; the last block to arrive sums
-// them in block order and returns true (result in thread 0's v).
+// Deterministic grid-wide sum: block sums go to partials[k*gridDim.x + block];
+// the last block to arrive sums them in block order (every thread issues its
+// loads before adding) and returns true (result in thread 0's v).  counters[0]
+// is zero between kernels (the last block resets it).
+constexpr int64_t grid_sum_doubles(int64_t g) { return 3 * g + 8; }
+
 template <int K>
-__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counter) {
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counters) {
     __shared__ bool last;
+    const unsigned G = gridDim.x;
     block_sum<K>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        for (int k = 0; k < K; ++k) partials[k * G + blockIdx.x] = v[k];
         __threadfence();
-        unsigned t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = atomicAdd(&counters[0], 1u) == G - 1;
     }
     __syncthreads();
     if (!last) return false;
+    constexpr int UR = K == 1 ? 8 : (K == 2 ? 4 : 2);
     double t[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) t[k] = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x)
+    for (unsigned i0 = threadIdx.x; i0 < G; i0 += UR * blockDim.x) {
+        double x[UR][K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) t[k] += __ldcg(partials + k * gridDim.x + i);
+        for (int u = 0; u < UR; ++u) {
+            const unsigned i = i0 + u * blockDim.x;
+#pragma unroll
+            for (int k = 0; k < K; ++k) x[u][k] = i < G ? __ldcg(partials + k * G + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u)
+#pragma unroll
+            for (int k = 0; k < K; ++k) t[k] += x[u][k];
+    }
     block_sum<K>(t);
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = t[k];
-    if (threadIdx.x == 0) *counter = 0;
+    if (threadIdx.x == 0) counters[0] = 0;
     return true;
 }
 
@@ -90,7 +105,7 @@ __device__ __forceinline__ void finish_pq(double pq, CgScalars* sc) {
 // ------------------------------------------------------------------ kernels
 
 template <int V, int U>
-__global__ void __launch_bounds__(256) cg_spmv_dot_sliced(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(256, 8) cg_spmv_dot_sliced(const uint4* __restrict__ meta,
                                                           const int32_t* __restrict__ col,
                                                           const double* __restrict__ val,
                                                           const double* __restrict__ p,
@@ -101,17 +116,18 @@ __global__ void __launch_bounds__(256) cg_spmv_dot_sliced(const uint4* __restric
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     double v[1] = {0.0};
-    if (warp < n_slices) {
-        const uint4 m = meta[warp];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = warp; sl < n_slices; sl += nw) {   // persistent warps stride over slices
+        const uint4 m = meta[sl];
         const double sum = sliced_row_sum_f64<V, U>(m, col, val, p, lane);
         const int lt = (int)m.w;
         const int64_t row = (int64_t)m.z + (lane >> lt);
         if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
             q[row] = sum;
-            v[0] = p[row] * sum;
+            v[0] = fma(p[row], sum, v[0]);
         }
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
 template <int V, int U>
@@ -127,17 +143,18 @@ __global__ void __launch_bounds__(256) cg_spmv_dot_df(const uint4* __restrict__ 
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     double v[1] = {0.0};
-    if (warp < n_slices) {
-        const uint4 m = meta[warp];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = warp; sl < n_slices; sl += nw) {   // persistent warps stride over slices
+        const uint4 m = meta[sl];
         const double sum = sliced_row_sum_df<V, U>(m, col, vdf, val, pdf, p, lane);
         const int lt = (int)m.w;
         const int64_t row = (int64_t)m.z + (lane >> lt);
         if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
             q[row] = sum;
-            v[0] = p[row] * sum;
+            v[0] = fma(p[row], sum, v[0]);
         }
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
 template <int L>
@@ -154,10 +171,10 @@ __global__ void cg_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_
         q[row] = sum;
         v[0] = p[row] * sum;
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq(v[0], sc);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
-__global__ void __launch_bounds__(256) cg_update(int64_t n, double* __restrict__ x,
+__global__ void __launch_bounds__(256, 8) cg_update(int64_t n, double* __restrict__ x,
                                                  double* __restrict__ r,
                                                  const double* __restrict__ p,
                                                  const double* __restrict__ q,
@@ -174,7 +191,7 @@ __global__ void __launch_bounds__(256) cg_update(int64_t n, double* __restrict__
         v[0] = fma(ri, dinv[i] * ri, v[0]);
         v[1] = fma(ri, ri, v[1]);
     }
-    if (grid_sum<2>(v, partials, &sc->counter) && threadIdx.x == 0) {
+    if (grid_sum<2>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->iters += 1;
         sc->rr = v[1];
         if (!isfinite(v[0]) || !isfinite(v[1])) sc->status = CG_BREAKDOWN;
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(256) cg_update(int64_t n, double* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) cg_pupdate(int64_t n, double* __restrict__ p,
+__global__ void __launch_bounds__(256, 8) cg_pupdate(int64_t n, double* __restrict__ p,
                                                   const double* __restrict__ r,
                                                   const double* __restrict__ dinv,
                                                   float2* __restrict__ pdf, const CgScalars* sc) {
@@ -238,7 +255,7 @@ __global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restri
         v[1] = fma(ri, ri, v[1]);
         v[2] = fma(bi, bi, v[2]);
     }
-    if (grid_sum<3>(v, partials, &sc->counter) && threadIdx.x == 0) {
+    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->rho = v[0];
         sc->rr = v[1];
         sc->bb = v[2];
@@ -252,7 +269,7 @@ __global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restri
 }
 
 // true_rr = ||b - q||^2 with q = A x.
-__global__ void __launch_bounds__(256) cg_true_residual(int64_t n, const double* __restrict__ b,
+__global__ void __launch_bounds__(256, 8) cg_true_residual(int64_t n, const double* __restrict__ b,
                                                         const double* __restrict__ q,
                                                         double* partials, CgScalars* sc) {
     double v[1] = {0.0};
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(256) cg_true_residual(int64_t n, const double*
         const double d = b[i] - q[i];
         v[0] = fma(d, d, v[0]);
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) sc->true_rr = v[0];
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) sc->true_rr = v[0];
 }
 
 // ------------------------------------------------------------------ refinement kernels
@@ -275,7 +292,7 @@ __device__ __forceinline__ void finish_pq_inner(double pq, CgScalars* sc) {
 }
 
 template <typename VT, int V, int U>
-__global__ void __launch_bounds__(256) cg32_spmv_dot_sliced(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(256, 8) cg32_spmv_dot_sliced(const uint4* __restrict__ meta,
                                                             const int32_t* __restrict__ col,
                                                             const VT* __restrict__ val,
                                                             const float* __restrict__ p,
@@ -286,17 +303,18 @@ __global__ void __launch_bounds__(256) cg32_spmv_dot_sliced(const uint4* __restr
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     double v[1] = {0.0};
-    if (warp < n_slices) {
-        const uint4 m = meta[warp];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = warp; sl < n_slices; sl += nw) {   // persistent warps stride over slices
+        const uint4 m = meta[sl];
         const float sum = sliced_row_sum_low<VT, V, U>(m, col, val, p, lane);
         const int lt = (int)m.w;
         const int64_t row = (int64_t)m.z + (lane >> lt);
         if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
             q[row] = sum;
-            v[0] = (double)p[row] * (double)sum;
+            v[0] = fma((double)p[row], (double)sum, v[0]);
         }
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
 template <typename VT, int L>
@@ -313,10 +331,10 @@ __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int3
         q[row] = sum;
         v[0] = (double)p[row] * (double)sum;
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
-__global__ void __launch_bounds__(256) cg32_update(int64_t n, float* __restrict__ w,
+__global__ void __launch_bounds__(256, 8) cg32_update(int64_t n, float* __restrict__ w,
                                                    float* __restrict__ r,
                                                    const float* __restrict__ p,
                                                    const float* __restrict__ q, double* partials,
@@ -331,7 +349,7 @@ __global__ void __launch_bounds__(256) cg32_update(int64_t n, float* __restrict_
         r[i] = ri;
         v[0] = fma((double)ri, (double)ri, v[0]);
     }
-    if (grid_sum<1>(v, partials, &sc->counter) && threadIdx.x == 0) {
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->iters += 1;
         sc->iters_in += 1;
         sc->rr = v[0];
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(256) cg32_update(int64_t n, float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(256) cg32_pupdate(int64_t n, float* __restrict__ p,
+__global__ void __launch_bounds__(256, 8) cg32_pupdate(int64_t n, float* __restrict__ p,
                                                     const float* __restrict__ r, const CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     const float beta = (float)sc->beta;
@@ -376,7 +394,7 @@ __global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* 
         v[1] = fma((double)rs, (double)rs, v[1]);
         v[2] = fma(bi, bi, v[2]);
     }
-    if (grid_sum<3>(v, partials, &sc->counter) && threadIdx.x == 0) {
+    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->true_rr = v[0];
         sc->rho = v[1];
         sc->bb = v[2];
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* 
 }
 
 // x += S w in FP64.
-__global__ void __launch_bounds__(256) refine_update(int64_t n, double* __restrict__ x,
+__global__ void __launch_bounds__(256, 8) refine_update(int64_t n, double* __restrict__ x,
                                                      const double* __restrict__ scale,
                                                      const float* __restrict__ w) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -406,8 +424,16 @@ __global__ void __launch_bounds__(256) refine_update(int64_t n, double* __restri
 // many runs round-robin, each on its own stream and workspace, so their
 // iterations overlap on the device.
 
+// SLICED CG products run persistent: at most 8 blocks per SM, warps stride over slices.
 static unsigned spmv_grid(const fespmv_mat* A) {
-    if (A->format == FESPMV_FMT_SLICED) return grid_for(A->n_slices * 32, A->block);
+    if (A->format == FESPMV_FMT_SLICED) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned full = grid_for(A->n_slices * 32, A->block);
+        const unsigned cap = (unsigned)sms * (2048u / (unsigned)A->block);
+        return std::max(1u, std::min(full, cap));
+    }
     return grid_for(A->n * A->csr_lanes, A->block);
 }
 
@@ -453,7 +479,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
-    const int64_t np = 3 * std::max<int64_t>(spmv_grid(A), upd) + 1;
+    const int64_t np = grid_sum_doubles(std::max<int64_t>(spmv_grid(A), upd));
     int64_t b = 6 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
@@ -480,7 +506,7 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
         destroy_work(w);
         return rc;
     }
-    const size_t np = 3 * (size_t)std::max(spmv_grid(A), w->upd_grid) + 1;
+    const size_t np = (size_t)grid_sum_doubles(std::max(spmv_grid(A), w->upd_grid));
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
         (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
         destroy_work(w);
@@ -963,9 +989,10 @@ static int cg_solve_impl(fespmv_mat* A, const double* b, double* x, const cg_opt
 // (r, p, q, D^-1, partial sums, scalars) lives in the fixed array below, which
 // every GPU that loads this library holds until the process exits.
 constexpr int64_t kStaticMaxRows = int64_t(1) << 18;     // 262,144 rows
-constexpr int64_t kStaticPartials = 32768;                // >= every grid used below (x3 for K=3)
+constexpr int64_t kStaticPartials = 3 * 32768 + 8;       // grid_sum storage for the largest grid
 constexpr size_t kStaticVecBytes = sizeof(double) * kStaticMaxRows;
-constexpr size_t kStaticBytes = 4 * kStaticVecBytes + sizeof(double) * kStaticPartials + 256;
+constexpr size_t kStaticBytes = 4 * kStaticVecBytes + sizeof(double) * kStaticPartials + 512;
+static_assert(sizeof(CgScalars) <= 512, "the static scratch reserves 512 bytes for the scalars");
 
 static __device__ __align__(256) unsigned char g_cg_static_scratch[kStaticBytes];
 
@@ -1104,7 +1131,7 @@ static int cg_static_impl(int64_t n, const int64_t* rowptr, const int32_t* colin
     FESPMV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned upd = std::max(1u, std::min(grid_for(n, 256), (unsigned)(sms * 8)));
     StaticCsr m{n, rowptr, colind, values, lanes, grid_for(n * lanes, 256)};
-    if ((int64_t)m.spmv_grid > kStaticPartials || 3 * (int64_t)upd > kStaticPartials) {
+    if (grid_sum_doubles(m.spmv_grid) > kStaticPartials || grid_sum_doubles(upd) > kStaticPartials) {
         set_error("grid too large for the static partial-sum buffer");
         return FESPMV_ERR_UNSUPPORTED;
     }

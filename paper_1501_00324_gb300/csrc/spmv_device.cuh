@@ -229,7 +229,6 @@ constexpr float kDfHi = 1.125899906842624e15f;     // 2^50
 
 struct DfAcc {
     float hi = 0.0f, lo = 0.0f;
-    double slow = 0.0;
 };
 
 __device__ __forceinline__ void df_add_product(DfAcc& s, float ah, float al, float xh, float xl) {
@@ -255,15 +254,33 @@ __device__ __forceinline__ void df_add(DfAcc& a, float bh, float bl) {
 }
 
 __device__ __forceinline__ double df_value(const DfAcc& s) {
-    return ((double)s.hi + (double)s.lo) + s.slow;
+    return (double)s.hi + (double)s.lo;
 }
 
+// Split with integer operations (no FP64 pipe): hi = v rounded to nearest even
+// at 24 bits, lo = v - hi rounded to nearest (exact scaling by 2^(e-52)).  Equal
+// to (fl32(v), fl32(v - fl32(v))) for every v in the fast range; 0 -> (0, 0);
+// anything else -> (NaN, 0).
 __device__ __forceinline__ float2 df_split(double v) {
-    const double a = fabs(v);
-    if (v == 0.0) return make_float2(0.0f, 0.0f);
-    if (!(a >= (double)kDfLo && a <= (double)kDfHi)) return make_float2(__int_as_float(0x7fc00000), 0.0f);
-    const float h = __double2float_rn(v);
-    return make_float2(h, __double2float_rn(v - (double)h));
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    if ((u << 1) == 0ull) return make_float2(0.0f, 0.0f);
+    const int e = (int)((u >> 52) & 0x7ffull) - 1023;
+    if (e < -50 || e >= 50) return make_float2(__int_as_float(0x7fc00000), 0.0f);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    unsigned mh = (unsigned)(m >> 29);
+    const long long rem = (long long)(m & 0x1fffffffull);
+    const bool up = rem > (1ll << 28) || (rem == (1ll << 28) && (mh & 1u));
+    int eh = e;
+    if (up && ++mh == (1u << 23)) {   // rounding carried into the exponent
+        mh = 0;
+        ++eh;
+    }
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)(eh + 127) << 23) | mh);
+    const long long d = rem - (up ? (1ll << 29) : 0ll);   // v - hi in units of 2^(e-52)
+    float lo = __ll2float_rn(d) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
+    if (sign) lo = -lo;
+    return make_float2(hi, lo);
 }
 
 template <int V> struct DfChunk;
@@ -293,16 +310,12 @@ template <> struct DfChunk<4> {
     }
 };
 
-// One entry: fast path on the FP32 pipe, exact FP64 slow path for marked values.
-__device__ __forceinline__ void df_entry(DfAcc& s, float2 a, int32_t c, const float2* __restrict__ xs,
-                                         const double* __restrict__ x64, const double* __restrict__ a64,
-                                         int64_t pos) {
+// Fast path for one entry: marked values (NaN high parts) make the row's sum NaN,
+// which sliced_row_sum_df detects and recomputes in FP64.
+__device__ __forceinline__ void df_entry(DfAcc& s, float2 a, int32_t c, const float2* __restrict__ xs) {
     if (c < 0) return;
     const float2 xv = __ldg(xs + c);
-    if (isnan(a.x) || isnan(xv.x))
-        s.slow = fma(__ldg(a64 + pos), __ldg(x64 + c), s.slow);
-    else
-        df_add_product(s, a.x, a.y, xv.x, xv.y);
+    df_add_product(s, a.x, a.y, xv.x, xv.y);
 }
 
 template <int V, int U>
@@ -325,24 +338,37 @@ __device__ __forceinline__ double sliced_row_sum_df(const uint4 m, const int32_t
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int k = 0; k < V; ++k)
-                df_entry(s, e[u].v[k], e[u].c[k], xs, x64, val, base + (int64_t)(st + u * V) * 32 + k);
+            for (int k = 0; k < V; ++k) df_entry(s, e[u].v[k], e[u].c[k], xs);
     }
     for (; st < w; st += V) {
         DfChunk<V> e;
         e.load(vdf + base + (int64_t)st * 32, col + base + (int64_t)st * 32);
 #pragma unroll
-        for (int k = 0; k < V; ++k) df_entry(s, e.v[k], e.c[k], xs, x64, val, base + (int64_t)st * 32 + k);
+        for (int k = 0; k < V; ++k) df_entry(s, e.v[k], e.c[k], xs);
     }
     const int T = 1 << lt;
     for (int o = T >> 1; o > 0; o >>= 1) {
         const float oh = __shfl_down_sync(0xffffffffu, s.hi, o);
         const float ol = __shfl_down_sync(0xffffffffu, s.lo, o);
-        const double os = __shfl_down_sync(0xffffffffu, s.slow, o);
         df_add(s, oh, ol);
-        s.slow += os;
     }
-    return df_value(s);
+    // Rows that met a marked value (or a genuine NaN/Inf) are recomputed in FP64
+    // from the double values: every lane of such a row sums its own entries again.
+    const bool bad = isnan(s.hi) || isnan(s.lo) || isinf(s.hi);
+    const bool row_bad = __shfl_sync(0xffffffffu, bad, lane & ~(T - 1));
+    double r = df_value(s);
+    if (__any_sync(0xffffffffu, row_bad)) {
+        double d = 0.0;
+        if (row_bad)
+            for (int q = 0; q < w; ++q) {
+                const int64_t pos = off + (int64_t)(q / V) * 32 * V + lane * V + q % V;
+                const int32_t c = col[pos];
+                if (c >= 0) d = fma(val[pos], __ldg(x64 + c), d);
+            }
+        for (int o = T >> 1; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if (row_bad) r = d;
+    }
+    return r;
 }
 
 }  // namespace fespmv

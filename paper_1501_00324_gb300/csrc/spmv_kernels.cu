@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) sliced_f64(const uint4* __restrict__ meta
 // ---------------------------------------------------------------- float-pair FP64 product
 
 template <int V, int U>
-__global__ void __launch_bounds__(256) sliced_df64(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(256, 8) sliced_df64(const uint4* __restrict__ meta,
                                                    const int32_t* __restrict__ col,
                                                    const float2* __restrict__ vdf,
                                                    const double* __restrict__ val,
