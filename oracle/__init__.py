@@ -52,6 +52,8 @@ def _lib():
         lib.oracle_csr_spmv.restype = None
         lib.oracle_pcg.argtypes = [i64, P, P, P, P, P, dbl, i32, i32, i32, P, P, P]
         lib.oracle_pcg.restype = i32
+        lib.oracle_pcg_single_reduction.argtypes = [i64, P, P, P, P, P, dbl, i32, i32, i32, P, P, P]
+        lib.oracle_pcg_single_reduction.restype = i32
         lib.oracle_refine.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, i32, P, P, P]
         lib.oracle_refine.restype = i32
         lib.oracle_scaled_values.argtypes = [i64, P, P, P, i32, P]
@@ -85,8 +87,9 @@ def csr_spmv(rowptr, colind, values, x) -> np.ndarray:
 
 
 def pcg(rowptr, colind, values, b, x0=None, tol=1e-10, max_iter=100000, jacobi=True,
-        max_restarts=3):
-    """Jacobi-PCG; returns (x, info) with info = dict(status, iters, relres, true_relres)."""
+        max_restarts=3, single_reduction=False):
+    """Jacobi-PCG; returns (x, info) with info = dict(status, iters, relres, true_relres).
+    single_reduction=True runs the one-reduction (Chronopoulos-Gear) arrangement."""
     rp, ci, va = _csr(rowptr, colind, values)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -94,7 +97,8 @@ def pcg(rowptr, colind, values, b, x0=None, tol=1e-10, max_iter=100000, jacobi=T
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0)
     tr = ctypes.c_double(0)
-    st = _lib().oracle_pcg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, max_iter,
+    fn = _lib().oracle_pcg_single_reduction if single_reduction else _lib().oracle_pcg
+    st = fn(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, max_iter,
                            1 if jacobi else 0, max_restarts, ctypes.byref(it), ctypes.byref(rr),
                            ctypes.byref(tr))
     return x, dict(status=STATUS[st], iters=it.value, relres=rr.value, true_relres=tr.value)

@@ -136,6 +136,94 @@ done:
     return status;
 }
 
+/*
+ * Jacobi-PCG with one reduction per iteration (Chronopoulos and Gear's
+ * rearrangement of the same recurrences): with u = M^-1 r and w = A u,
+ *   gamma = r.u, delta = w.u;  first step: beta = 0, alpha = gamma / delta;
+ *   later: beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev);
+ *   p = u + beta p, s = w + beta s (s = A p), x += alpha p, r -= alpha s.
+ * In exact arithmetic it produces the iterates of oracle_pcg.  Stops when
+ * ||r|| <= tol ||b|| (checked on the r that the next product starts from);
+ * true-residual restarts and status codes as oracle_pcg.
+ */
+int oracle_pcg_single_reduction(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                const double* val, const double* b, double* x, double tol,
+                                int max_iter, int jacobi, int max_restarts, int* iters_out,
+                                double* relres_out, double* true_relres_out) {
+    size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double *r = (double*)malloc(nb), *u = (double*)malloc(nb), *w = (double*)malloc(nb);
+    double *p = (double*)malloc(nb), *sv = (double*)malloc(nb), *dg = (double*)malloc(nb);
+    int status = OR_NOT_CONVERGED, iters = 0;
+    double relres = 0.0, true_relres = 0.0;
+    diagonal(n, rowptr, colind, val, dg);
+    if (jacobi)
+        for (int64_t i = 0; i < n; ++i)
+            if (!(dg[i] > 0.0)) { status = OR_BAD_INPUT; goto done1; }
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        status = OR_CONVERGED;
+        goto done1;
+    }
+    for (int restart = 0; restart <= max_restarts; ++restart) {
+        oracle_csr_spmv(n, rowptr, colind, val, x, w);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - w[i];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = OR_CONVERGED; true_relres = relres; goto done1; }
+        for (int64_t i = 0; i < n; ++i) {
+            u[i] = jacobi ? r[i] / dg[i] : r[i];
+            p[i] = 0.0;
+            sv[i] = 0.0;
+        }
+        double gamma_prev = 0.0, alpha = 0.0;
+        int first = 1, converged = 0;
+        for (;;) {
+            oracle_csr_spmv(n, rowptr, colind, val, u, w);
+            double gamma = dot(n, r, u);
+            double delta = dot(n, w, u);
+            relres = sqrt(dot(n, r, r)) / bnorm;
+            if (!first) ++iters;
+            if (!isfinite(relres) || !isfinite(gamma) || !isfinite(delta)) { status = OR_BREAKDOWN; goto final1; }
+            if (relres <= tol) { converged = 1; break; }
+            if (iters >= max_iter) break;
+            double beta, denom;
+            if (first) {
+                beta = 0.0;
+                denom = delta;
+            } else {
+                beta = gamma / gamma_prev;
+                denom = delta - beta * gamma / alpha;
+            }
+            if (!(denom > 0.0)) { status = OR_BREAKDOWN; goto final1; }
+            alpha = gamma / denom;
+            gamma_prev = gamma;
+            first = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                p[i] = u[i] + beta * p[i];
+                sv[i] = w[i] + beta * sv[i];
+                x[i] = x[i] + alpha * p[i];
+                r[i] = r[i] - alpha * sv[i];
+                u[i] = jacobi ? r[i] / dg[i] : r[i];
+            }
+        }
+        if (!converged) { status = OR_NOT_CONVERGED; break; }
+        oracle_csr_spmv(n, rowptr, colind, val, x, w);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - w[i];
+        true_relres = sqrt(dot(n, r, r)) / bnorm;
+        if (true_relres <= tol) { status = OR_CONVERGED; goto done1; }
+    }
+final1:
+    oracle_csr_spmv(n, rowptr, colind, val, x, w);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - w[i];
+    true_relres = sqrt(dot(n, r, r)) / bnorm;
+done1:
+    if (iters_out) *iters_out = iters;
+    if (relres_out) *relres_out = relres;
+    if (true_relres_out) *true_relres_out = true_relres;
+    free(r); free(u); free(w); free(p); free(sv); free(dg);
+    return status;
+}
+
 /* Round a float to bfloat16 (round to nearest, ties to even), returned as float. */
 static float round_bf16(float f) {
     uint32_t u;

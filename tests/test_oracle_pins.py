@@ -246,6 +246,49 @@ def test_cg_error_decreases_in_A_norm():
     assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
 
 
+@pytest.mark.parametrize("jacobi", [True, False])
+def test_single_reduction_pcg_matches_dense_and_textbook(jacobi):
+    p = fegen.cube_elasticity(4, 31)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    b = fegen.random_vector(p.n_rows, 32)
+    x1, i1 = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12, jacobi=jacobi,
+                        single_reduction=True)
+    x0, i0 = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12, jacobi=jacobi)
+    assert i1["status"] == "converged" and i1["true_relres"] <= 1e-12
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x1 - xd) / np.linalg.norm(xd) <= 10 * np.linalg.cond(A) * 1e-12
+    # same recurrences in exact arithmetic: the step counts agree to rounding
+    assert abs(i1["iters"] - i0["iters"]) <= 0.02 * i0["iters"] + 2
+    # the first iterates agree closely (before rounding differences grow)
+    xa, _ = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=0.0, max_iter=5, jacobi=jacobi,
+                       max_restarts=0)
+    xb, _ = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=0.0, max_iter=5, jacobi=jacobi,
+                       max_restarts=0, single_reduction=True)
+    assert np.linalg.norm(xa - xb) <= 1e-10 * np.linalg.norm(xa)
+
+
+def test_single_reduction_pcg_finite_termination_and_status():
+    n_blocks, n4 = 5, 4
+    rows, cols, vals = [], [], []
+    for b_ in range(n_blocks):
+        i = 2 * b_
+        for (r, c, v) in ((i, i, 2.0), (i, i + 1, 1.0), (i + 1, i, 1.0), (i + 1, i + 1, 2.0)):
+            rows.append(r), cols.append(c), vals.append(v)
+    for k in range(n4):
+        i = 2 * n_blocks + k
+        rows.append(i), cols.append(i), vals.append(4.0)
+    n = 2 * n_blocks + n4
+    order = np.lexsort((cols, rows))
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))])
+    b = fegen.random_vector(n, 3)
+    _, info = oracle.pcg(rowptr, np.array(cols)[order], np.array(vals)[order], b, tol=1e-13,
+                         jacobi=False, max_restarts=0, single_reduction=True)
+    assert info["status"] == "converged" and info["iters"] == 3
+    _, info = oracle.pcg(np.arange(3), np.arange(2), np.array([1.0, -1.0]), np.ones(2),
+                         jacobi=False, single_reduction=True)
+    assert info["status"] == "breakdown"
+
+
 def test_pcg_status_codes():
     # indefinite diagonal: Jacobi rejects it, plain CG breaks down (p.q <= 0)
     rowptr, colind = np.arange(3), np.arange(2)
