@@ -177,6 +177,26 @@ int spmv_update_values(fespmv_mat_t A, const double* values, int32_t flags,
 int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
 
 /*
+ * spmv_autotune -- choose the SLICED layout for this matrix by measurement (the
+ * paper tunes block size and the K2 threshold per matrix by exhaustive timing,
+ * Sec. 6 and Table "bestvalues", and leaves an a-priori rule to future work,
+ * Sec. 9).  Candidates: vec in {1, 2, 4} x threshold in {0, ceil(maxlen/4),
+ * ceil(maxlen/8)} (distinct values, 0 = K1) x block in {128, 256}, each built
+ * from the given CSR with the base options' reorder and sigma, then timed as
+ * `reps` back-to-back FP64 products in the permuted numbering on `stream`.
+ *   opts_inout   in: base options (format forced to SLICED); out: the fastest
+ *                candidate's vec, threshold and block
+ *   reps         products timed per candidate (0 = 20)
+ *   best_us      out (may be NULL): mean microseconds per product of the winner
+ *   n_tried      out (may be NULL): candidates timed
+ * Device memory: one candidate handle at a time plus two vectors.  Errors: as
+ * spmv_create.
+ */
+int spmv_autotune(int64_t n_rows, const int64_t* rowptr, const int32_t* colind, const double* values,
+                  const fespmv_mesh_info* mesh, fespmv_options* opts_inout, int32_t reps,
+                  double* best_us, int32_t* n_tried, fespmv_stream_t stream);
+
+/*
  * spmv_apply_scaled -- y = B x for the low-precision copy B = S A S (S =
  * diag(A)^-1/2) kept with FESPMV_PREC_F32 or FESPMV_PREC_BF16: B's stored
  * values, float x and y, float products and sums.  This is the operator of
@@ -226,6 +246,7 @@ int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
 #define FESPMV_CG_BF16_REFINE  2  /* FP64 refinement around FP32 CG on B = S A S (BF16 values) */
 #define FESPMV_CG_X0           4  /* flag: x holds the initial guess (otherwise x0 = 0) */
 #define FESPMV_CG_NO_PRECOND   8  /* flag: plain CG instead of Jacobi-PCG */
+#define FESPMV_CG_SINGLE_REDUCTION 16 /* flag: single-reduction (Chronopoulos-Gear) PCG, below */
 
 typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2; 0 = 1e-10 */
@@ -265,8 +286,20 @@ typedef struct {
  * scalars kept on the device; the call blocks the host until the solve ends
  * (it polls a status word after each graph).  Dot products are reduced in a
  * fixed order, so repeated solves of the same system give bitwise-equal x.
- * Workspace (6 vectors of n_rows doubles) is allocated on the first call and
+ * Workspace (8 vectors of n_rows doubles) is allocated on the first call and
  * kept by the handle.
+ *
+ * flag FESPMV_CG_SINGLE_REDUCTION (FESPMV_CG_F64 only, else UNSUPPORTED): the
+ * same method in the Chronopoulos-Gear arrangement, whose iterates equal the
+ * ones above in exact arithmetic (u = D^-1 r, w = A u, s = A p):
+ *   r = b - A x0, u = D^-1 r, p = s = 0;
+ *   repeat w = A u; gamma = r.u; delta = w.u;  stop when ||r|| <= tol ||b||;
+ *          beta = gamma / gamma_old (0 at first), alpha = gamma / (delta - beta gamma / alpha_old)
+ *          (gamma / delta at first);  p = u + beta p; s = w + beta s;
+ *          x += alpha p; r -= alpha s; u = D^-1 r.
+ * All three dot products come from one grid reduction fused with the product,
+ * so an iteration is two launches instead of three.  The FP64 product is used
+ * for every handle (no float-pair products on this path).
  *
  * precision FESPMV_CG_F32_REFINE / FESPMV_CG_BF16_REFINE (the handle must hold the
  * FP32 / BF16 copy, FESPMV_PREC_F32 / FESPMV_PREC_BF16 at create): mixed-precision
@@ -279,8 +312,9 @@ typedef struct {
  * the FP64 residual steps.  A refinement step that does not reduce ||r|| ends
  * the solve with FESPMV_ERR_NOT_CONVERGED (the low-precision operator is too
  * far from A for this system: contraction needs cond(B) * u_storage < 1).  Returns FESPMV_OK, FESPMV_ERR_NOT_CONVERGED,
- * FESPMV_ERR_BREAKDOWN (p.Ap <= 0, non-finite scalars or a non-positive
- * diagonal with Jacobi), INVALID_ARG, OOM or CUDA.
+ * FESPMV_ERR_BREAKDOWN (p.Ap <= 0 -- delta - beta gamma / alpha_old <= 0 in the
+ * single-reduction form -- non-finite scalars or a non-positive diagonal with
+ * Jacobi), INVALID_ARG, UNSUPPORTED, OOM or CUDA.
  */
 int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts, cg_result* res,
              fespmv_stream_t stream);

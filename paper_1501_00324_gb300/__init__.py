@@ -52,6 +52,7 @@ FESPMV_CG_F32_REFINE = 1
 FESPMV_CG_BF16_REFINE = 2
 FESPMV_CG_X0 = 4
 FESPMV_CG_NO_PRECOND = 8
+FESPMV_CG_SINGLE_REDUCTION = 16
 
 
 class FespmvError(RuntimeError):
@@ -161,6 +162,10 @@ _lib.batch_cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), _P, _P]
 _lib.batch_cg_solve.restype = ctypes.c_int
 _lib.batch_get_info.argtypes = [_P, ctypes.POINTER(fespmv_info), ctypes.POINTER(_i64)]
 _lib.batch_get_info.restype = ctypes.c_int
+_lib.spmv_autotune.argtypes = [_i64, _P, _P, _P, ctypes.POINTER(fespmv_mesh_info),
+                               ctypes.POINTER(fespmv_options), _i32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(_i32), _P]
+_lib.spmv_autotune.restype = ctypes.c_int
 _lib.fespmv_status_string.argtypes = [ctypes.c_int]
 _lib.fespmv_status_string.restype = ctypes.c_char_p
 _lib.fespmv_last_error.argtypes = []
@@ -295,6 +300,26 @@ def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigm
     _check(_lib.spmv_plan(*args, _ptr(perm), _ptr(meta), _ptr(cols), _ptr(src)))
     return dict(perm=perm[:n], meta=meta[:info.n_slices * 4].reshape(-1, 4),
                 cols=cols[:info.packed_len], srcmap=src[:info.packed_len])
+
+
+def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
+                  reps=0, stream=None) -> dict:
+    """Time candidate layouts; returns dict(vec, threshold, block, sigma, reorder, best_us, tried)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
+    if reorder is None:
+        reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0)
+    mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
+    best = ctypes.c_double(0)
+    tried = _i32(0)
+    _check(_lib.spmv_autotune(len(rowptr) - 1, _ptr(rowptr), _ptr(colind), _ptr(values), ctypes.byref(mesh),
+                              ctypes.byref(opts), reps, ctypes.byref(best), ctypes.byref(tried),
+                              _stream(stream)))
+    return dict(vec=opts.vec, threshold=opts.threshold, block=opts.block, sigma=sigma, reorder=reorder,
+                best_us=best.value, tried=tried.value)
 
 
 def spmv_get_info(A: Matrix) -> dict:

@@ -422,6 +422,85 @@ int spmv_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, const fes
     GUARD_END
 }
 
+int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* values,
+                  const fespmv_mesh_info* mesh, fespmv_options* opts, int32_t reps, double* best_us,
+                  int32_t* n_tried, fespmv_stream_t stream) {
+    GUARD_BEGIN
+    if (!opts || !rowptr || n < 0) { set_error("bad argument"); return FESPMV_ERR_INVALID_ARG; }
+    if (reps <= 0) reps = 20;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = validate_csr(n, rowptr, colind);
+    if (rc) return rc;
+    int64_t maxlen = 0;
+    for (int64_t i = 0; i < n; ++i) maxlen = std::max(maxlen, rowptr[i + 1] - rowptr[i]);
+    std::vector<int> thresholds = {0};
+    for (int64_t d : {4, 8}) {
+        const int t = (int)std::max<int64_t>(1, (maxlen + d - 1) / d);
+        if (t < maxlen && std::find(thresholds.begin(), thresholds.end(), t) == thresholds.end())
+            thresholds.push_back(t);
+    }
+    double* x = nullptr;
+    double* y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&] {
+        if (x) cudaFree(x);
+        if (y) cudaFree(y);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&x, sizeof(double) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        cudaMalloc(&y, sizeof(double) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return cuda_fail(cudaGetLastError(), "spmv_autotune setup");
+    }
+    cudaMemsetAsync(x, 0, sizeof(double) * n, s);
+    fespmv_options best = *opts;
+    best.format = FESPMV_FMT_SLICED;
+    double best_t = 1e300;
+    int tried = 0;
+    for (int vec : {1, 2, 4})
+        for (int thr : thresholds)
+            for (int block : {128, 256}) {
+                fespmv_options o = *opts;
+                o.format = FESPMV_FMT_SLICED;
+                o.vec = vec;
+                o.threshold = thr;
+                o.block = block;
+                o.precisions = FESPMV_PREC_F64;
+                fespmv_mat_t A = nullptr;
+                rc = spmv_create(&A, n, rowptr, colind, values, mesh, &o, stream);
+                if (rc) { cleanup(); return rc; }
+                for (int w = 0; w < 2; ++w) rc |= spmv_apply(A, x, y, FESPMV_IO_PERMUTED, stream);
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps; ++r) rc |= spmv_apply(A, x, y, FESPMV_IO_PERMUTED, stream);
+                cudaEventRecord(e1, s);
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                spmv_destroy(A);
+                if (rc || e != cudaSuccess) {
+                    cleanup();
+                    return rc ? rc : cuda_fail(e, "spmv_autotune timing");
+                }
+                ++tried;
+                const double us = 1e3 * ms / reps;
+                if (us < best_t) {
+                    best_t = us;
+                    best = o;
+                }
+            }
+    cleanup();
+    opts->format = FESPMV_FMT_SLICED;
+    opts->vec = best.vec;
+    opts->threshold = best.threshold;
+    opts->block = best.block;
+    if (best_us) *best_us = best_t;
+    if (n_tried) *n_tried = tried;
+    return FESPMV_OK;
+    GUARD_END
+}
+
 int spmv_get_info(fespmv_mat_t A, fespmv_info* info) {
     if (!A || !info) { set_error("null argument"); return FESPMV_ERR_INVALID_ARG; }
     info->n_rows = A->n;

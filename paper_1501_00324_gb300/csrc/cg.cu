@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(256) cg_init(int64_t n, const double* __restri
         sc->rr = v[1];
         sc->bb = v[2];
         sc->thresh2 = tol2 * v[2];
+        sc->first = 1;
         if (sc->status == CG_BADDIAG) return;
         if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) sc->status = CG_BREAKDOWN;
         else if (v[1] <= sc->thresh2) sc->status = CG_CONVERGED;
@@ -279,6 +280,112 @@ __global__ void __launch_bounds__(256, 8) cg_true_residual(int64_t n, const doub
         v[0] = fma(d, d, v[0]);
     }
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) sc->true_rr = v[0];
+}
+
+// ------------------------------------------------------------------ single-reduction CG
+// Chronopoulos-Gear arrangement (FESPMV_CG_SINGLE_REDUCTION): per iteration one
+// product w = A u fused with gamma = r.u, delta = w.u and r.r (one grid
+// reduction, scalars formed by the last block), then one streaming update
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r.
+
+__device__ __forceinline__ void finish_cg1(double gam, double del, double rr, CgScalars* sc) {
+    sc->rr = rr;
+    if (!sc->first) sc->iters += 1;
+    if (!isfinite(gam) || !isfinite(del) || !isfinite(rr)) {
+        sc->status = CG_BREAKDOWN;
+        return;
+    }
+    if (rr <= sc->thresh2) {
+        sc->status = CG_CONVERGED;
+        return;
+    }
+    if (sc->iters >= sc->max_iter) {
+        sc->status = CG_MAXITER;
+        return;
+    }
+    double beta = 0.0, denom = del;
+    if (!sc->first) {
+        beta = gam / sc->rho;
+        denom = del - beta * gam / sc->alpha;
+    }
+    if (!(denom > 0.0)) {
+        sc->status = CG_BREAKDOWN;
+        return;
+    }
+    sc->alpha = gam / denom;
+    sc->beta = beta;
+    sc->rho = gam;
+    sc->first = 0;
+}
+
+template <int V, int U>
+__global__ void __launch_bounds__(256, 8) cg1_spmv_dots_sliced(const uint4* __restrict__ meta,
+                                                               const int32_t* __restrict__ col,
+                                                               const double* __restrict__ val,
+                                                               const double* __restrict__ u,
+                                                               const double* __restrict__ r,
+                                                               double* __restrict__ w, int64_t n_slices,
+                                                               int64_t n, double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double v[3] = {0.0, 0.0, 0.0};
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = warp; sl < n_slices; sl += nw) {
+        const uint4 m = meta[sl];
+        const double sum = sliced_row_sum_f64<V, U>(m, col, val, u, lane);
+        const int lt = (int)m.w;
+        const int64_t row = (int64_t)m.z + (lane >> lt);
+        if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+            w[row] = sum;
+            const double ur = u[row], rr = r[row];
+            v[0] = fma(rr, ur, v[0]);
+            v[1] = fma(sum, ur, v[1]);
+            v[2] = fma(rr, rr, v[2]);
+        }
+    }
+    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
+}
+
+template <int L>
+__global__ void cg1_spmv_dots_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, const double* __restrict__ u,
+                                  const double* __restrict__ r, double* __restrict__ w, int64_t n,
+                                  double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int sub = (int)(t % L);
+    double v[3] = {0.0, 0.0, 0.0};
+    const double sum = csr_row_sum_f64<L>(row, sub, n, rowptr, col, val, u);
+    if (row < n && sub == 0) {
+        w[row] = sum;
+        const double ur = u[row], rr = r[row];
+        v[0] = rr * ur;
+        v[1] = sum * ur;
+        v[2] = rr * rr;
+    }
+    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
+}
+
+__global__ void __launch_bounds__(256, 8) cg1_update(int64_t n, double* __restrict__ x,
+                                                     double* __restrict__ r, double* __restrict__ u,
+                                                     double* __restrict__ p, double* __restrict__ s,
+                                                     const double* __restrict__ w,
+                                                     const double* __restrict__ dinv, const CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const double a = sc->alpha, b = sc->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double pi = fma(b, p[i], u[i]);
+        const double si = fma(b, s[i], w[i]);
+        p[i] = pi;
+        s[i] = si;
+        x[i] = fma(a, pi, x[i]);
+        const double ri = fma(-a, si, r[i]);
+        r[i] = ri;
+        u[i] = dinv[i] * ri;
+    }
 }
 
 // ------------------------------------------------------------------ refinement kernels
@@ -440,13 +547,14 @@ static unsigned spmv_grid(const fespmv_mat* A) {
 void destroy_work(CgWork* w) {
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->graph_cg1) cudaGraphExecDestroy(w->graph_cg1);
     for (cudaGraphExec_t g : w->graph_low)
         if (g) cudaGraphExecDestroy(g);
     for (cudaEvent_t e : w->ev)
         if (e) cudaEventDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
     void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc,
-                    w->w32, w->r32, w->p32, w->q32, w->pdf};
+                    w->w32, w->r32, w->p32, w->q32, w->pdf, w->u, w->s};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -480,7 +588,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
     const int64_t np = grid_sum_doubles(std::max<int64_t>(spmv_grid(A), upd));
-    int64_t b = 6 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
+    int64_t b = 8 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
     return b;
@@ -499,7 +607,7 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
     }
     w->upd_grid = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
     const size_t nb = sizeof(double) * (size_t)A->n;
-    double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv};
+    double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv, &w->u, &w->s};
     for (double** v : vecs)
         if ((rc = work_alloc(w, (void**)v, nb, "CG vector"))) { destroy_work(w); return rc; }
     if (A->d_vdf && (rc = work_alloc(w, (void**)&w->pdf, sizeof(float2) * (size_t)A->n, "CG float-pair p"))) {
@@ -580,6 +688,41 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->pdf, w->sc);
 }
 
+template <int V>
+static void launch_cg1_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
+    cg1_spmv_dots_sliced<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->u, w->r,
+                                                                 w->q, A->n_slices, A->n, w->partials,
+                                                                 w->sc);
+}
+
+template <int L>
+static void launch_cg1_csr(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    cg1_spmv_dots_csr<L><<<spmv_grid(A), A->block, 0, s>>>(A->d_rowptr, A->d_colind, A->d_val, w->u, w->r,
+                                                           w->q, A->n, w->partials, w->sc);
+}
+
+// One single-reduction iteration: w (= q) = A u with the three dots, then the update.
+static void launch_iteration_cg1(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    if (A->format == FESPMV_FMT_SLICED) {
+        switch (A->vec) {
+            case 1: launch_cg1_sliced<1>(A, w, s); break;
+            case 4: launch_cg1_sliced<4>(A, w, s); break;
+            default: launch_cg1_sliced<2>(A, w, s); break;
+        }
+    } else {
+        switch (A->csr_lanes) {
+            case 1: launch_cg1_csr<1>(A, w, s); break;
+            case 2: launch_cg1_csr<2>(A, w, s); break;
+            case 4: launch_cg1_csr<4>(A, w, s); break;
+            case 8: launch_cg1_csr<8>(A, w, s); break;
+            case 16: launch_cg1_csr<16>(A, w, s); break;
+            default: launch_cg1_csr<32>(A, w, s); break;
+        }
+    }
+    cg1_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->u, w->p, w->s, w->q, w->dinv, w->sc);
+}
+
 template <typename VT, int V>
 static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
     constexpr int U = (V == 4) ? 4 : 8;
@@ -626,8 +769,8 @@ static void launch_inner_iteration(const fespmv_mat* A, CgWork* w, int bf16, cud
 // Graph of `chunk` iterations (kind 0: FP64; 1: FP32 inner; 2: BF16 inner) for
 // this workspace; kernel arguments are the workspace's fixed pointers.
 static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
-    cudaGraphExec_t& slot = kind == 0 ? w->graph : w->graph_low[kind - 1];
-    int& slot_chunk = kind == 0 ? w->graph_chunk : w->chunk_low[kind - 1];
+    cudaGraphExec_t& slot = kind == 0 ? w->graph : (kind == 3 ? w->graph_cg1 : w->graph_low[kind - 1]);
+    int& slot_chunk = kind == 0 ? w->graph_chunk : (kind == 3 ? w->chunk_cg1 : w->chunk_low[kind - 1]);
     if (slot && slot_chunk == chunk) return FESPMV_OK;
     if (slot) {
         cudaGraphExecDestroy(slot);
@@ -637,6 +780,7 @@ static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
     FESPMV_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk; ++i) {
         if (kind == 0) launch_iteration(A, w, w->cap);
+        else if (kind == 3) launch_iteration_cg1(A, w, w->cap);
         else launch_inner_iteration(A, w, kind - 1, w->cap);
     }
     cudaError_t e = cudaStreamEndCapture(w->cap, &g);
@@ -675,9 +819,14 @@ int normalize_options(cg_options& o) {
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.check_every > 4096 ||
         o.precision < FESPMV_CG_F64 || o.precision > FESPMV_CG_BF16_REFINE || o.max_outer < 0 ||
         !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
-        (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND))) {
+        (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND |
+                     FESPMV_CG_SINGLE_REDUCTION))) {
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
+    }
+    if ((o.flags & FESPMV_CG_SINGLE_REDUCTION) && o.precision != FESPMV_CG_F64) {
+        set_error("FESPMV_CG_SINGLE_REDUCTION applies to FESPMV_CG_F64 only");
+        return FESPMV_ERR_UNSUPPORTED;
     }
     return FESPMV_OK;
 }
@@ -714,7 +863,7 @@ static int enqueue_graph(CgRun& r) {
 static int start_graphs(CgRun& r, int kind, int max_iter) {
     int rc = ensure_graph(r.A, r.w, kind, r.o.check_every);
     if (rc) return rc;
-    r.graph = kind == 0 ? r.w->graph : r.w->graph_low[kind - 1];
+    r.graph = kind == 0 ? r.w->graph : (kind == 3 ? r.w->graph_cg1 : r.w->graph_low[kind - 1]);
     r.graphs_left = (int64_t)max_iter / r.o.check_every + 3;
     r.head = 0;
     r.queued = 0;
@@ -727,9 +876,15 @@ static int start_graphs(CgRun& r, int kind, int max_iter) {
 static int enqueue_init(CgRun& r, bool ax) {
     CgWork* w = r.w;
     int rc;
+    const bool cg1 = r.o.flags & FESPMV_CG_SINGLE_REDUCTION;
     if (ax && (rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
-    cg_init<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, w->r, w->p, w->dinv,
-                                          r.o.tol * r.o.tol, w->partials, w->sc, w->pdf);
+    if (cg1) {
+        FESPMV_CUDA(cudaMemsetAsync(w->p, 0, sizeof(double) * (size_t)r.A->n, r.s));
+        FESPMV_CUDA(cudaMemsetAsync(w->s, 0, sizeof(double) * (size_t)r.A->n, r.s));
+    }
+    cg_init<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, w->r, cg1 ? w->u : w->p,
+                                          w->dinv, r.o.tol * r.o.tol, w->partials, w->sc,
+                                          cg1 ? nullptr : w->pdf);
     FESPMV_CUDA(cudaGetLastError());
     r.phase = PH_INIT_WAIT;
     return enqueue_status(r, 0);
@@ -825,7 +980,8 @@ int run_step(CgRun& r, bool block, bool* progress) {
                 r.last.true_rr = 0.0;
                 return finish(r, CG_CONVERGED);
             }
-            if (h.status == CG_RUNNING) return start_graphs(r, 0, r.o.max_iter);
+            if (h.status == CG_RUNNING)
+                return start_graphs(r, (r.o.flags & FESPMV_CG_SINGLE_REDUCTION) ? 3 : 0, r.o.max_iter);
             // converged (or failed) before iterating: confirm on the true residual
             if ((rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
             cg_true_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, w->q, w->partials, w->sc);

@@ -15,7 +15,7 @@ struct CgScalars {
     unsigned int counters[65];   // grid_sum arrival counters: top + 64 groups (zero between kernels)
     unsigned int pad2;
     double thresh_in;   // refinement: inner stop threshold on r_in.r_in
-    int iters_in, pad3; // refinement: inner steps of the current outer step
+    int iters_in, first; // refinement: inner steps of the current outer step; single-reduction: first step
 };
 
 struct CgWork {
@@ -35,6 +35,9 @@ struct CgWork {
     int chunk_low[2] = {0, 0};
     double* h_io = nullptr;     // pinned host staging of n doubles (solve server)
     float2* pdf = nullptr;      // float-pair split of p (handles with FESPMV_PREC_DF64)
+    double *u = nullptr, *s = nullptr;  // single-reduction CG: u = D^-1 r, s = A p
+    cudaGraphExec_t graph_cg1 = nullptr;
+    int chunk_cg1 = 0;
     int64_t bytes = 0;          // device bytes held
 };
 

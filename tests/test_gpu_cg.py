@@ -129,3 +129,72 @@ def test_cg_full_size_elasticity_64(prec):
     assert res["status"] == 0, res
     assert true_relres(p, x, b) <= 1.01e-10
     assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-5
+
+
+SR = fs.FESPMV_CG_SINGLE_REDUCTION
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 3])
+@pytest.mark.parametrize("name", ["cube_laplace_20", "elasticity_8", "shell_5x16x24"])
+def test_single_reduction_cg_matches_oracle(name, fmt):
+    """Chronopoulos-Gear PCG against the oracle's own single-reduction PCG."""
+    p = {"cube_laplace_20": lambda: fegen.cube_laplace(20, 1501),
+         "elasticity_8": lambda: fegen.cube_elasticity(8, 51),
+         "shell_5x16x24": lambda: fegen.shell_laplace(5, 16, 24, 52)}[name]()
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, **FORMATS[fmt])
+    x, res = solve(A, b, tol=1e-10, flags=SR)
+    assert res["status"] == 0, res
+    assert true_relres(p, x, b) <= 1.01e-10
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10, single_reduction=True)
+    assert info["status"] == "converged"
+    assert abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+    from test_oracle_pins import dense_of
+    if p.n_rows <= 3000:
+        cond = np.linalg.cond(dense_of(p.rowptr, p.colind, p.values, p.n_rows))
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= cond * 2e-10
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-6
+
+
+def test_single_reduction_cg_options_and_status_codes():
+    p = fegen.cube_laplace(10, 55)
+    b = fegen.random_vector(p.n_rows, 56)
+    A = make(p, sigma=128)
+    x, res = solve(A, b, tol=1e-12, max_iter=5, max_restarts=-1, flags=SR)
+    assert res["status"] == fs.FESPMV_ERR_NOT_CONVERGED and res["iters"] == 5
+    # the first 5 iterates agree with the oracle's (same recurrences, different rounding)
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12, max_iter=5, single_reduction=True)
+    assert info["iters"] == 5
+    assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
+    x, res = solve(A, b, tol=1e-10, flags=SR | fs.FESPMV_CG_NO_PRECOND)
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10, jacobi=False, single_reduction=True)
+    assert res["status"] == 0 and abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+    res = fs.cg_solve(A, dev(b), dev(x), flags=SR | fs.FESPMV_CG_X0)
+    assert res["status"] == 0 and res["iters"] == 0
+    z = torch.zeros(p.n_rows, dtype=torch.float64, device="cuda")
+    xd = torch.ones_like(z)
+    assert fs.cg_solve(A, z, xd, flags=SR)["status"] == 0 and not xd.any().item()
+    xs = [solve(A, b, check_every=c, flags=SR)[0] for c in (1, 7, 64)]
+    assert all(np.array_equal(xs[0], xi) for xi in xs[1:])
+    x2, _ = solve(A, b, flags=SR)
+    assert np.array_equal(xs[0].view(np.uint64), x2.view(np.uint64))
+    # breakdown on an indefinite matrix; refinement precisions reject the flag
+    B = fs.spmv_create(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0, -1.0]),
+                       format=fs.FESPMV_FMT_CSR)
+    assert solve(B, np.array([1.0, 1.0]), flags=SR | fs.FESPMV_CG_NO_PRECOND)[1]["status"] == \
+        fs.FESPMV_ERR_BREAKDOWN
+    C = make(p, sigma=128, precisions=fs.FESPMV_PREC_F64 | fs.FESPMV_PREC_F32)
+    with pytest.raises(fs.FespmvError):
+        solve(C, b, precision=fs.FESPMV_CG_F32_REFINE, flags=SR)
+
+
+def test_single_reduction_cg_full_size_elasticity_64():
+    p = fegen.cube_elasticity(64, 1502)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, sigma=1024)
+    x, res = solve(A, b, tol=1e-10, flags=SR)
+    assert res["status"] == 0, res
+    assert true_relres(p, x, b) <= 1.01e-10
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-5

@@ -208,3 +208,14 @@ def test_float_pair_product_out_of_range_entries(vec):
     yn = apply(A, xn)
     yo = oracle.csr_spmv(p.rowptr, p.colind, vals, xn)
     assert np.array_equal(np.isnan(yn), np.isnan(yo)) and np.array_equal(np.isinf(yn), np.isinf(yo))
+
+
+def test_autotuner_returns_a_valid_fast_layout():
+    p = problem("shell_6x20x36")
+    t = fs.spmv_autotune(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, reps=5)
+    assert t["tried"] >= 6 and t["best_us"] > 0
+    assert t["vec"] in (1, 2, 4) and t["block"] in (128, 256) and t["threshold"] >= 0
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, vec=t["vec"],
+                       threshold=t["threshold"], block=t["block"])
+    x = fegen.random_vector(p.n_rows, 21)
+    check_parity(p, apply(A, x), x)
