@@ -30,24 +30,24 @@ namespace fespmv {
 // ------------------------------------------------------------------ reductions
 
 // Sum over the block of K values (fixed order); the result is valid in thread 0.
-template <int K>
+// The lane values go to shared memory and one warp adds them: lane l sums
+// entries l, l + 32, ... sequentially, then a shuffle tree.  This takes about
+// a third of the FP64 adds of a shuffle tree in every warp, which matters on a
+// part whose FP64 pipe retires about two lanes per clock per SM.
+template <int K, int MAXB = 256>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
-    __shared__ double sh[K][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double sh[K][MAXB];
+    const int t = threadIdx.x, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
+    for (int k = 0; k < K; ++k) sh[k][t] = v[k];
     __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
+    if (t < 32) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double t = lane < nw ? sh[k][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            v[k] = t;
+            double s = sh[k][t];
+            for (int w = 1; w < nw; ++w) s += sh[k][w * 32 + t];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[k] = s;
         }
     }
     __syncthreads();
@@ -59,11 +59,11 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // is zero between kernels (the last block resets it).
 constexpr int64_t grid_sum_doubles(int64_t g) { return 3 * g + 8; }
 
-template <int K>
+template <int K, int MAXB = 256>
 __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counters) {
     __shared__ bool last;
     const unsigned G = gridDim.x;
-    block_sum<K>(v);
+    block_sum<K, MAXB>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) partials[k * G + blockIdx.x] = v[k];
@@ -89,7 +89,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsig
 #pragma unroll
             for (int k = 0; k < K; ++k) t[k] += x[u][k];
     }
-    block_sum<K>(t);
+    block_sum<K, MAXB>(t);
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = t[k];
     if (threadIdx.x == 0) counters[0] = 0;
@@ -105,7 +105,7 @@ __device__ __forceinline__ void finish_pq(double pq, CgScalars* sc) {
 // ------------------------------------------------------------------ kernels
 
 template <int V, int U>
-__global__ void __launch_bounds__(256, 8) cg_spmv_dot_sliced(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(256, V == 4 ? 6 : 8) cg_spmv_dot_sliced(const uint4* __restrict__ meta,
                                                           const int32_t* __restrict__ col,
                                                           const double* __restrict__ val,
                                                           const double* __restrict__ p,
@@ -171,10 +171,10 @@ __global__ void cg_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_
         q[row] = sum;
         v[0] = p[row] * sum;
     }
-    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
+    if (grid_sum<1, 1024>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
-__global__ void __launch_bounds__(256, 8) cg_update(int64_t n, double* __restrict__ x,
+__global__ void __launch_bounds__(256, 4) cg_update(int64_t n, double* __restrict__ x,
                                                  double* __restrict__ r,
                                                  const double* __restrict__ p,
                                                  const double* __restrict__ q,
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256, 8) cg_update(int64_t n, double* __restric
     }
 }
 
-__global__ void __launch_bounds__(256, 8) cg_pupdate(int64_t n, double* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) cg_pupdate(int64_t n, double* __restrict__ p,
                                                   const double* __restrict__ r,
                                                   const double* __restrict__ dinv,
                                                   float2* __restrict__ pdf, const CgScalars* sc) {
@@ -319,7 +319,7 @@ __device__ __forceinline__ void finish_cg1(double gam, double del, double rr, Cg
 }
 
 template <int V, int U>
-__global__ void __launch_bounds__(256, 8) cg1_spmv_dots_sliced(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(256, 6) cg1_spmv_dots_sliced(const uint4* __restrict__ meta,
                                                                const int32_t* __restrict__ col,
                                                                const double* __restrict__ val,
                                                                const double* __restrict__ u,
@@ -365,10 +365,10 @@ __global__ void cg1_spmv_dots_csr(const int64_t* __restrict__ rowptr, const int3
         v[1] = sum * ur;
         v[2] = rr * rr;
     }
-    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
+    if (grid_sum<3, 1024>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
 }
 
-__global__ void __launch_bounds__(256, 8) cg1_update(int64_t n, double* __restrict__ x,
+__global__ void __launch_bounds__(256, 4) cg1_update(int64_t n, double* __restrict__ x,
                                                      double* __restrict__ r, double* __restrict__ u,
                                                      double* __restrict__ p, double* __restrict__ s,
                                                      const double* __restrict__ w,
@@ -438,7 +438,7 @@ __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int3
         q[row] = sum;
         v[0] = (double)p[row] * (double)sum;
     }
-    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+    if (grid_sum<1, 1024>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
 __global__ void __launch_bounds__(256, 8) cg32_update(int64_t n, float* __restrict__ w,
@@ -544,6 +544,17 @@ static unsigned spmv_grid(const fespmv_mat* A) {
     return grid_for(A->n * A->csr_lanes, A->block);
 }
 
+// A persistent SLICED kernel's grid: spmv_grid, capped at the blocks of `kernel`
+// that are resident at once (kernels holding more than 32 registers fit fewer).
+template <typename Kernel>
+static unsigned resident_grid(const fespmv_mat* A, Kernel kernel) {
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, A->block, 0);
+    return std::max(1u, std::min(spmv_grid(A), (unsigned)(sms * std::max(per_sm, 1))));
+}
+
 void destroy_work(CgWork* w) {
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
@@ -605,7 +616,7 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
         destroy_work(w);
         return cuda_fail(e, "cudaDeviceGetAttribute");
     }
-    w->upd_grid = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
+    w->upd_grid = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 4)));
     const size_t nb = sizeof(double) * (size_t)A->n;
     double** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->b, &w->dinv, &w->u, &w->s};
     for (double** v : vecs)
@@ -642,9 +653,9 @@ static int ensure_workspace(fespmv_mat* A) {
 template <int V>
 static void launch_spmv_dot_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
-    cg_spmv_dot_sliced<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->p,
-                                                               w->q, A->n_slices, A->n, w->partials,
-                                                               w->sc);
+    const unsigned g = resident_grid(A, cg_spmv_dot_sliced<V, U>);
+    cg_spmv_dot_sliced<V, U><<<g, A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->p, w->q, A->n_slices,
+                                                    A->n, w->partials, w->sc);
 }
 
 template <int L>
@@ -691,7 +702,8 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
 template <int V>
 static void launch_cg1_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
-    cg1_spmv_dots_sliced<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->u, w->r,
+    const unsigned g = resident_grid(A, cg1_spmv_dots_sliced<V, U>);
+    cg1_spmv_dots_sliced<V, U><<<g, A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->u, w->r,
                                                                  w->q, A->n_slices, A->n, w->partials,
                                                                  w->sc);
 }
