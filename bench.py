@@ -62,7 +62,7 @@ def parse_args():
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
-    ap.add_argument("--profile-target", choices=["multi", "fp32", "cg", "cg_f32"], default=None,
+    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -338,6 +338,18 @@ def main():
             extra["multi32_fp32"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
+            del X32, Y32
+            # the same with the FP64 matrix and FP64 right-hand sides
+            X64 = torch.rand((n, 32), dtype=torch.float64, device=dev)
+            Y64 = torch.empty_like(X64)
+            fm = lambda: fs.spmv_apply_multi(A, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm()
+            tm64 = timed_steps(fm, max(10, args.steps // 8))
+            tmean = statistics.mean(tm64) * 1e-3
+            extra["multi32_fp64"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
+                                     "us_per_apply": round(tmean * 1e6, 1),
+                                     "us_per_rhs": round(tmean * 1e6 / 32, 2)}
+            del X64, Y64
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
@@ -610,6 +622,10 @@ def profile_piece(fs, torch, A, p, xp, args):
         X = torch.rand((n, 32), dtype=torch.float32, device="cuda")
         Y = torch.empty_like(X)
         f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "multi64":
+        X = torch.rand((n, 32), dtype=torch.float64, device="cuda")
+        Y = torch.empty_like(X)
+        f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
     elif t == "fp32":
         xs = xp.float()
         ys = torch.empty_like(xs)

@@ -1,16 +1,23 @@
 // Products with many right-hand sides sharing one pass over the matrix
 // (spmv_apply_multi in fespmv.h): Y = A X, X and Y row-major n x k, k <= 32.
 //
-// One warp walks one K1 slice (32 rows, one lane per row in the layout of
-// Sec. 5.1).  Instead of each lane reading its own row's entry, the whole warp
-// reads a chunk of the slice (32*V entries: V steps of all 32 rows) with
-// uniform vector loads -- every lane fetches the same 16 bytes, one L1
-// wavefront per load -- and then lane j applies every entry to right-hand side
-// j: acc[row] += a * X[c][j].  A row of X is k contiguous values, so each
-// gather is one coalesced 128 B (FP32) or 256 B (FP64) access, and the matrix
-// is streamed from HBM once for all k columns.  The entry -> row mapping of a
-// chunk is fixed at compile time (row = e / V), so the 32 accumulators stay in
-// registers.
+// The kernel works on X and Y with a padded row stride KW (4, 8, 16 or 32 >= k)
+// in the renumbered space of Sec. 5.2.  A warp covers RW rows of one K1 slice
+// (Sec. 5.1, one lane per row in the stored layout); its lanes form G groups of
+// KW/4 lanes, each lane owning 4 consecutive right-hand sides, and group g owns
+// RW/G consecutive rows of the slice.  Per stored step a group reads the V
+// entries of each of its rows, gathers the KW-wide row of X named by each column
+// index with one 16-byte (FP32) or 32-byte (FP64) load per lane, and applies it
+// with 4 FMAs per lane.  So one warp instruction advances G entries, the matrix
+// streams from HBM once for all k columns, and every gather is a full, aligned
+// line of X.
+//
+// Row-to-row reuse: in an FE matrix the dofs of one node have the same columns,
+// and the locality order keeps them adjacent, so consecutive rows of a group
+// often name the same column at the same step.  A gather is predicated off when
+// the column equals the previous row's at that step; the registers still hold
+// that row of X.  The FMAs of padding entries (column -1) are skipped, so a NaN
+// in X never reaches a row that does not store its column.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -20,81 +27,203 @@
 
 namespace fespmv {
 
-template <typename T> struct U16;   // 16-byte uniform loads
-template <> struct U16<double> { using type = double2; static constexpr int n = 2; };
-template <> struct U16<float> { using type = float4; static constexpr int n = 4; };
+// Four consecutive X values at p, loaded only when `take` is set (otherwise the
+// registers keep their contents).  Read-only path: X is not written here.
+__device__ __forceinline__ void ld_x4(const float* p, bool take, float (&v)[4]) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3])
+        : "r"((int)take), "l"(p));
+}
+__device__ __forceinline__ void ld_x4(const double* p, bool take, double (&v)[4]) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q ld.global.nc.v2.f64 {%0, %1}, [%5];\n\t"
+        "@q ld.global.nc.v2.f64 {%2, %3}, [%5+16];\n\t}"
+        : "+d"(v[0]), "+d"(v[1]), "+d"(v[2]), "+d"(v[3])
+        : "r"((int)take), "l"(p));
+}
 
-template <typename VT, typename XT, int V>
-__global__ void __launch_bounds__(128) sliced_multi(const uint4* __restrict__ meta,
-                                                    const int32_t* __restrict__ col,
-                                                    const VT* __restrict__ val,
-                                                    const XT* __restrict__ X, XT* __restrict__ Y,
-                                                    int64_t n_slices, int64_t n, int k) {
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_slices) return;
-    const uint4 m = meta[warp];
-    const int64_t off = (int64_t)m.x * 32;
-    const int w = (int)m.y;
-    const bool active = lane < k;
-    XT acc[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) acc[r] = XT(0);
-    constexpr int NV = U16<VT>::n;
-    using VV = typename U16<VT>::type;
-    for (int s = 0; s < w; s += V) {
-        const VT* vp = val + off + (int64_t)s * 32;
-        const int32_t* cp = col + off + (int64_t)s * 32;
-#pragma unroll
-        for (int e0 = 0; e0 < 32 * V; e0 += 4) {
-            const int4 c4 = ld_stream(reinterpret_cast<const int4*>(cp + e0));
-            VT v[4];
-#pragma unroll
-            for (int h = 0; h < 4; h += NV) {
-                const VV t = ld_stream(reinterpret_cast<const VV*>(vp + e0 + h));
-                if constexpr (NV == 2) {
-                    v[h] = t.x; v[h + 1] = t.y;
-                } else {
-                    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-                }
-            }
-            const int32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int e = e0 + h;
-                if (cc[h] >= 0 && active)
-                    acc[e / V] = fma((XT)v[h], __ldg(X + (int64_t)cc[h] * k + lane), acc[e / V]);
-            }
-        }
+// V consecutive stream entries (column indices or values) at p.
+template <int V> __device__ __forceinline__ void ld_v(const int32_t* p, int32_t (&c)[V]) {
+    if constexpr (V == 1) {
+        c[0] = ld_stream(p);
+    } else if constexpr (V == 2) {
+        const int2 t = ld_stream(reinterpret_cast<const int2*>(p));
+        c[0] = t.x; c[1] = t.y;
+    } else {
+        const int4 t = ld_stream(reinterpret_cast<const int4*>(p));
+        c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
     }
-    if (active) {
+}
+template <int V> __device__ __forceinline__ void ld_v(const float* p, float (&a)[V]) {
+    if constexpr (V == 1) {
+        a[0] = ld_stream(p);
+    } else if constexpr (V == 2) {
+        const float2 t = ld_stream(reinterpret_cast<const float2*>(p));
+        a[0] = t.x; a[1] = t.y;
+    } else {
+        const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
+        a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+    }
+}
+template <int V> __device__ __forceinline__ void ld_v(const double* p, double (&a)[V]) {
+    if constexpr (V == 1) {
+        a[0] = ld_stream(p);
+    } else {
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int64_t row = (int64_t)m.z + r;
-            if (row < n) Y[row * k + lane] = acc[r];
+        for (int h = 0; h < V; h += 2) {
+            const double2 t = ld_stream(reinterpret_cast<const double2*>(p + h));
+            a[h] = t.x; a[h + 1] = t.y;
         }
     }
 }
 
-// Y[i, :] = X[idx[i], :] for k columns.
+template <typename VT, typename XT, int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__ meta,
+                                                       const int32_t* __restrict__ col,
+                                                       const VT* __restrict__ val,
+                                                       const XT* __restrict__ X, XT* __restrict__ Y,
+                                                       int64_t n_slices, int64_t n) {
+    constexpr int LPG = KW / 4;  // lanes per group
+    constexpr int G = 32 / LPG;  // groups per warp
+    constexpr int R = RW / G;    // rows per group
+    constexpr int WPS = 32 / RW; // warps per slice
+    static_assert(R >= 1 && RW * WPS == 32, "bad multi-RHS tiling");
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t slice = gw / WPS;
+    if (slice >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPG, q = lane % LPG;
+    const uint4 m = meta[slice];
+    const int first_row = (int)(gw % WPS) * RW + g * R;  // first local row of this group
+    const int64_t off = (int64_t)m.x * 32 + (int64_t)first_row * V;
+    const int w = (int)m.y;
+    const int32_t* cp = col + off;
+    const VT* vp = val + off;
+    const XT* Xq = X + 4 * q;
+
+    XT acc[R][4];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = XT(0);
+    XT xr[V][4];
+#pragma unroll
+    for (int t = 0; t < V; ++t)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xr[t][j] = XT(0);
+
+    int32_t c[R][V];
+    VT a[R][V];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        ld_v<V>(cp + i * V, c[i]);
+        ld_v<V>(vp + i * V, a[i]);
+    }
+    for (int s = 0; s < w; s += V) {
+        // next V steps of this group's rows, in flight while this step's gathers run
+        int32_t cn[R][V];
+        VT an[R][V];
+        const bool more = s + V < w;
+        if (more) {
+            const int64_t o = (int64_t)(s + V) * 32;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                ld_v<V>(cp + o + i * V, cn[i]);
+                ld_v<V>(vp + o + i * V, an[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int cc = c[i][t];
+                const bool take = cc >= 0 && (i == 0 || cc != c[i - 1][t]);
+                ld_x4(Xq + (int64_t)cc * KW, take, xr[t]);
+                if (cc >= 0) {
+                    const XT av = (XT)a[i][t];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av, xr[t][j], acc[i][j]);
+                }
+            }
+        if (more) {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int t = 0; t < V; ++t) {
+                    c[i][t] = cn[i][t];
+                    a[i][t] = an[i][t];
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int64_t row = (int64_t)m.z + first_row + i;
+        if (row < n) {
+            XT* yp = Y + row * KW + 4 * q;
+            if constexpr (std::is_same<XT, float>::value) {
+                *reinterpret_cast<float4*>(yp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else {
+                reinterpret_cast<double2*>(yp)[0] = make_double2(acc[i][0], acc[i][1]);
+                reinterpret_cast<double2*>(yp)[1] = make_double2(acc[i][2], acc[i][3]);
+            }
+        }
+    }
+}
+
+// Dst[i, j] = Src[idx[i], j] (idx == nullptr: identity) for j < k, 0 for k <= j < ldd.
 template <typename XT>
-__global__ void gather_rows(const XT* __restrict__ X, const int32_t* __restrict__ idx,
-                            XT* __restrict__ Y, int64_t n, int k) {
+__global__ void gather_rows(const XT* __restrict__ src, int lds, const int32_t* __restrict__ idx,
+                            XT* __restrict__ dst, int ldd, int64_t n, int k) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < n * k) {
-        const int64_t i = t / k;
-        const int j = (int)(t % k);
-        Y[t] = X[(int64_t)idx[i] * k + j];
+    if (t < n * ldd) {
+        const int64_t i = t / ldd;
+        const int j = (int)(t % ldd);
+        const int64_t r = idx ? (int64_t)idx[i] : i;
+        dst[t] = j < k ? src[r * lds + j] : XT(0);
+    }
+}
+
+// Rows per warp: four rows per lane group (row-to-row reuse chains of four: longer
+// chains serialise the gathers of a warp, shorter ones reuse less), at most 32,
+// and small enough that the per-lane registers (accumulators, two sets of V
+// stream entries per row, V rows of X) stay near 100 so that four 128-thread
+// blocks fit on an SM without spilling.
+template <typename VT, typename XT, int V, int KW>
+constexpr int multi_rows_per_warp() {
+    const int sx = (int)sizeof(XT) / 4, sv = (int)sizeof(VT) / 4, groups = 128 / KW;
+    int rw = 4 * groups > 32 ? 32 : 4 * groups;
+    while (rw / 2 >= groups) {
+        const int r = rw / groups;
+        if (r * 4 * sx + 2 * r * V * (1 + sv) + V * 4 * sx <= 104) break;
+        rw /= 2;
+    }
+    return rw;
+}
+
+template <typename VT, typename XT, int V, int KW>
+static void launch_multi_kw(const fespmv_mat* A, const VT* val, const XT* X, XT* Y, cudaStream_t s) {
+    constexpr int RW = multi_rows_per_warp<VT, XT, V, KW>();
+    const unsigned g = grid_for(A->n_slices * (32 / RW) * 32, 128);
+    sliced_multi<VT, XT, V, KW, RW><<<g, 128, 0, s>>>(A->d_meta, A->d_col, val, X, Y, A->n_slices, A->n);
+}
+
+template <typename VT, typename XT, int V>
+static void launch_multi_v(const fespmv_mat* A, const VT* val, const XT* X, XT* Y, int kw, cudaStream_t s) {
+    switch (kw) {
+        case 4: launch_multi_kw<VT, XT, V, 4>(A, val, X, Y, s); break;
+        case 8: launch_multi_kw<VT, XT, V, 8>(A, val, X, Y, s); break;
+        case 16: launch_multi_kw<VT, XT, V, 16>(A, val, X, Y, s); break;
+        default: launch_multi_kw<VT, XT, V, 32>(A, val, X, Y, s); break;
     }
 }
 
 template <typename VT, typename XT>
-static void launch_multi(const fespmv_mat* A, const VT* val, const XT* X, XT* Y, int k, cudaStream_t s) {
-    const unsigned g = grid_for(A->n_slices * 32, 128);
+static void launch_multi(const fespmv_mat* A, const VT* val, const XT* X, XT* Y, int kw, cudaStream_t s) {
     switch (A->vec) {
-        case 1: sliced_multi<VT, XT, 1><<<g, 128, 0, s>>>(A->d_meta, A->d_col, val, X, Y, A->n_slices, A->n, k); break;
-        case 4: sliced_multi<VT, XT, 4><<<g, 128, 0, s>>>(A->d_meta, A->d_col, val, X, Y, A->n_slices, A->n, k); break;
-        default: sliced_multi<VT, XT, 2><<<g, 128, 0, s>>>(A->d_meta, A->d_col, val, X, Y, A->n_slices, A->n, k); break;
+        case 1: launch_multi_v<VT, XT, 1>(A, val, X, Y, kw, s); break;
+        case 4: launch_multi_v<VT, XT, 4>(A, val, X, Y, kw, s); break;
+        default: launch_multi_v<VT, XT, 2>(A, val, X, Y, kw, s); break;
     }
 }
 
@@ -106,25 +235,36 @@ static int ensure_multi_scratch(fespmv_mat* A) {
     return rc;
 }
 
+static int padded_width(int k) {
+    int kw = 4;
+    while (kw < k) kw *= 2;
+    return kw;
+}
+
 template <typename XT>
-static int apply_multi_t(fespmv_mat* A, const XT* X, XT* Y, int k, int precision, int flags,
-                         cudaStream_t s) {
+static int apply_multi_t(fespmv_mat* A, const XT* X, XT* Y, int k, int flags, cudaStream_t s) {
     const bool permute = !(flags & FESPMV_IO_PERMUTED);
+    const int kw = padded_width(k);
+    const size_t align = 4 * sizeof(XT);
+    // the caller's buffers serve directly when they already have the kernel's layout
+    const bool direct = !permute && kw == k && (uintptr_t)X % align == 0 && (uintptr_t)Y % align == 0;
     const XT* xs = X;
     XT* ys = Y;
-    if (permute) {
+    if (!direct) {
         int rc = ensure_multi_scratch(A);
         if (rc) return rc;
         xs = reinterpret_cast<const XT*>(A->d_xk);
         ys = reinterpret_cast<XT*>(A->d_yk);
-        gather_rows<XT><<<grid_for(A->n * k, 256), 256, 0, s>>>(X, A->d_perm, const_cast<XT*>(xs), A->n, k);
+        gather_rows<XT><<<grid_for(A->n * kw, 256), 256, 0, s>>>(X, k, permute ? A->d_perm : nullptr,
+                                                                 const_cast<XT*>(xs), kw, A->n, k);
     }
-    (void)precision;
     if constexpr (std::is_same<XT, double>::value)
-        launch_multi<double, double>(A, A->d_val, xs, ys, k, s);     // FP64 values and sums
+        launch_multi<double, double>(A, A->d_val, xs, ys, kw, s);   // FP64 values and sums
     else
-        launch_multi<float, float>(A, A->d_val32, xs, ys, k, s);     // FP32 copy of S A S
-    if (permute) gather_rows<XT><<<grid_for(A->n * k, 256), 256, 0, s>>>(ys, A->d_pinv, Y, A->n, k);
+        launch_multi<float, float>(A, A->d_val32, xs, ys, kw, s);   // FP32 copy of S A S
+    if (!direct)
+        gather_rows<XT><<<grid_for(A->n * k, 256), 256, 0, s>>>(ys, kw, permute ? A->d_pinv : nullptr, Y, k,
+                                                                A->n, k);
     FESPMV_CUDA(cudaGetLastError());
     return FESPMV_OK;
 }
@@ -152,8 +292,8 @@ extern "C" int spmv_apply_multi(fespmv_mat_t A, const void* X, void* Y, int32_t 
         if (A->n == 0) return FESPMV_OK;
         cudaStream_t s = (cudaStream_t)stream;
         if (precision == FESPMV_PREC_F64)
-            return apply_multi_t<double>(A, (const double*)X, (double*)Y, k, precision, flags, s);
-        return apply_multi_t<float>(A, (const float*)X, (float*)Y, k, precision, flags, s);
+            return apply_multi_t<double>(A, (const double*)X, (double*)Y, k, flags, s);
+        return apply_multi_t<float>(A, (const float*)X, (float*)Y, k, flags, s);
     } catch (...) {
         set_error("unexpected C++ exception");
         return FESPMV_ERR_INVALID_ARG;

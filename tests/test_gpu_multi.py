@@ -21,7 +21,7 @@ def handle(p, **kw):
                           precisions=fs.FESPMV_PREC_F32, **kw)
 
 
-@pytest.mark.parametrize("k", [1, 7, 32])
+@pytest.mark.parametrize("k", [1, 3, 4, 7, 8, 16, 17, 32])
 @pytest.mark.parametrize("vec", [1, 2, 4])
 def test_multi_fp64_parity(k, vec):
     p = fegen.cube_elasticity(7, 110)
@@ -48,11 +48,12 @@ def check_f32(p, X, Y):
         assert np.all(np.abs(Y[:, j].astype(np.float64) - yo) <= 2 * L * 2.0 ** -24 * bound)
 
 
+@pytest.mark.parametrize("k", [5, 12, 32])
+@pytest.mark.parametrize("vec", [1, 2, 4])
 @pytest.mark.parametrize("permuted", [False, True])
-def test_multi_fp32_parity(permuted):
+def test_multi_fp32_parity(permuted, vec, k):
     p = fegen.shell_laplace(5, 16, 30, 112)
-    A = handle(p, sigma=256)
-    k = 32
+    A = handle(p, sigma=256, vec=vec)
     X = np.stack([fegen.random_vector(p.n_rows, 113 + j) for j in range(k)], axis=1).astype(np.float32)
     if permuted:
         P = fs.spmv_export(A, fs.FESPMV_EXPORT_PERM)
@@ -93,3 +94,75 @@ def test_multi_fp32_full_size_elasticity_64():
     fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F32)
     torch.cuda.synchronize()
     check_f32(p, X[:, [0, 13, 31]], Yd.cpu().numpy()[:, [0, 13, 31]])
+
+
+@pytest.mark.parametrize("prec", [fs.FESPMV_PREC_F64, fs.FESPMV_PREC_F32])
+def test_multi_nan_ragged_rows_and_unaligned_buffers(prec):
+    """Padding entries never touch X: a NaN in row c of X poisons exactly the
+    rows that store column c (in that column of Y only); empty rows (FP64) give 0;
+    buffers that are not 16-byte aligned (views offset by one row of k = 5)
+    take the staging path, in both numberings."""
+    n = 37
+    rng = np.random.default_rng(5)
+    lens = np.array([0 if i % 7 == 0 else 1 + i % 5 for i in range(n)])
+    lens[3] = n
+    rows = [np.sort(rng.choice(n, lens[i], replace=False)) for i in range(n)]
+    if prec == fs.FESPMV_PREC_F32:   # the FP32 copy of S A S needs a positive diagonal in every row
+        rows = [np.union1d(r, [i]) for i, r in enumerate(rows)]
+        lens = np.array([len(r) for r in rows])
+    rowptr = np.concatenate([[0], np.cumsum(lens)])
+    cols = np.concatenate(rows).astype(np.int32)
+    vals = rng.uniform(0.5, 2.0, len(cols))
+    A = fs.spmv_create(rowptr, cols, vals, precisions=fs.FESPMV_PREC_F64 | prec, sigma=8, vec=2)
+    P = fs.spmv_export(A, fs.FESPMV_EXPORT_PERM)
+    k = 5
+    dt = torch.float64 if prec == fs.FESPMV_PREC_F64 else torch.float32
+    X = np.stack([fegen.random_vector(n, 120 + j) for j in range(k)], axis=1)
+    X[11, 2] = np.nan
+    for flags in (0, fs.FESPMV_IO_PERMUTED):
+        Xin = X[P] if flags else X
+        big = torch.zeros(n + 1, k, dtype=dt, device="cuda")
+        big[1:] = torch.from_numpy(np.ascontiguousarray(Xin)).to(dt)
+        Ybig = torch.full((n + 1, k), 7.0, dtype=dt, device="cuda")
+        fs.spmv_apply_multi(A, big[1:], Ybig[1:], prec, flags)
+        torch.cuda.synchronize()
+        assert Ybig[0].eq(7.0).all().item()
+        Y = Ybig[1:].double().cpu().numpy()
+        if flags:
+            Yu = np.empty_like(Y)
+            Yu[P] = Y
+            Y = Yu
+        for j in range(k):
+            yo = oracle.csr_spmv(rowptr, cols, vals, X[:, j])
+            assert np.array_equal(np.isnan(Y[:, j]), np.isnan(yo))
+            assert np.all(Y[lens == 0, j] == 0.0)
+            if prec == fs.FESPMV_PREC_F64 and j != 2:
+                bound = oracle.csr_spmv(rowptr, cols, np.abs(vals), np.abs(X[:, j]))
+                assert np.all(np.abs(Y[:, j] - yo) <= 1e-12 * bound)
+
+
+@pytest.mark.parametrize("per_row", [4, 20, 40])
+def test_multi_fp32_random_sparse_rows(per_row):
+    """Random sparse rows of 4, 20 and 40 entries: slices whose rows share no
+    columns (no row-to-row reuse), with many distinct columns per slice."""
+    n = 4096
+    rng = np.random.default_rng(per_row)
+    rows = [np.union1d(rng.choice(n, per_row, replace=False), [i]) for i in range(n)]
+    rowptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+    cols = np.concatenate(rows).astype(np.int32)
+    vals = rng.uniform(-1.0, 1.0, len(cols))
+    vals[cols == np.repeat(np.arange(n), np.diff(rowptr))] = 2.0 * per_row
+
+    class Q:
+        pass
+    q = Q()
+    q.rowptr, q.colind, q.values = rowptr, cols, vals
+    for vec in (1, 2, 4):
+        A = fs.spmv_create(rowptr, cols, vals, precisions=fs.FESPMV_PREC_F32, sigma=64, vec=vec)
+        for k in (3, 32):
+            X = np.stack([fegen.random_vector(n, 130 + j) for j in range(k)], axis=1).astype(np.float32)
+            Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+            Yd = torch.full_like(Xd, float("nan"))
+            fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F32)
+            torch.cuda.synchronize()
+            check_f32(q, X, Yd.cpu().numpy())
