@@ -83,6 +83,12 @@ typedef struct {
     int32_t precisions;  /* FESPMV_PREC_* bitmask; 0 = FP64 only */
     int32_t block;       /* threads per block for the SpMV kernel, multiple of 32, <= 1024
                             (<= 256 for SLICED); 0 = 256 */
+    int32_t tiles;       /* SLICED: x staged through shared memory.  0 = on: runs of up to 8
+                            consecutive slices form tiles whose distinct columns (at most 4096)
+                            are gathered once per product into shared memory, and each stored
+                            entry keeps a 16-bit index into its tile's columns next to the
+                            32-bit column; the FP64 and FP32/BF16 products use them.  Left off
+                            when one slice alone has more distinct columns.  -1 = off. */
 } fespmv_options;
 
 typedef struct {
@@ -99,6 +105,10 @@ typedef struct {
     int64_t device_bytes;    /* device memory owned by the handle */
     int32_t format;
     int32_t vec;
+    int64_t n_tiles;         /* SLICED with tiles: tiles (0 when the products gather x from L1/L2) */
+    int64_t tile_dict_len;   /* concatenated tile column lists */
+    int32_t tile_max_cols;   /* largest tile column list */
+    int32_t pad;
 } fespmv_info;
 
 /*
@@ -219,6 +229,9 @@ int spmv_apply_scaled(fespmv_mat_t A, const float* x, float* y, int32_t precisio
 #define FESPMV_EXPORT_VALUES_F32  6  /* float[packed_len or nnz]: values of B = S A S */
 #define FESPMV_EXPORT_VALUES_BF16 7  /* uint16[packed_len or nnz]: bfloat16 bits of B */
 #define FESPMV_EXPORT_SCALE    8  /* double[n_rows]: S = diag(A)^-1/2, handle numbering */
+#define FESPMV_EXPORT_TILES    9  /* int32[n_tiles*4]: (first slice, slices, column-list offset, D) */
+#define FESPMV_EXPORT_TILE_COLS 10 /* int32[tile_dict_len]: each tile's distinct columns, first-use order */
+#define FESPMV_EXPORT_TILE_INDEX 11 /* uint16[packed_len]: index into the tile's columns; padding = D */
 /* Copy internal array `what` into host buffer `out` of `bytes` bytes (must be at
  * least the array's size).  Synchronises the stream.  Errors: INVALID_ARG,
  * UNSUPPORTED (array not held by this handle), CUDA. */

@@ -29,6 +29,13 @@ Layout of one slice (warp), width w steps (a multiple of V), offset ``off``::
 Padding entries hold value 0 and column -1.  The per-slice metadata row is
 ``(off // 32, w, first_row, log2 T)`` as uint32.
 
+Tiles (this library's x staging, not in the paper): slices are taken in order
+and grouped greedily into runs of at most ``max_slices`` slices whose distinct
+columns number at most ``max_cols``; a tile's dictionary lists its distinct
+columns in order of first use (packed order), and each packed entry stores its
+column's index in that list (padding: the list's length).  A slice that alone
+has more than ``max_cols`` distinct columns means no tiles at all.
+
 The locality order (a design choice of this library, not the paper's) is the
 Morton (Z-order) curve of the node coordinates: each coordinate is mapped to
 q = floor((x - min) / (max - min) * 2097151) (q = 0 on a flat axis), the 21
@@ -179,3 +186,51 @@ def pack(rowptr2, colind2, values2, threshold: int = 0, V: int = 2):
             pmap[a:b] = pos
         off += 32 * w
     return meta, col, val, pmap
+
+
+def tiles(meta: np.ndarray, col: np.ndarray, max_slices: int = 8, max_cols: int = 4096):
+    """Greedy tiles of consecutive slices; returns (tiles int32[n_tiles, 4] =
+    (first slice, slices, dictionary offset, size D), dictionary int32[],
+    index uint16[packed_len]) or None when one slice has too many columns."""
+    meta = np.asarray(meta).reshape(-1, 4)
+    col = np.asarray(col)
+    out_tiles, out_dict = [], []
+    index = np.zeros(len(col), dtype=np.uint16)
+    pos = {}           # column -> index in the open tile's dictionary
+    first, count = 0, 0
+
+    def close():
+        D = len(pos)
+        out_tiles.append((first, count, len(out_dict) - D, D))
+        for t in range(first, first + count):
+            b = int(meta[t, 0]) * 32
+            e = b + 32 * int(meta[t, 1])
+            for p in range(b, e):
+                if col[p] < 0:
+                    index[p] = D
+
+    for sl in range(len(meta)):
+        b = int(meta[sl, 0]) * 32
+        e = b + 32 * int(meta[sl, 1])
+        cols = [int(c) for c in col[b:e] if c >= 0]
+        distinct = set(cols)
+        if len(distinct) > max_cols:
+            return None
+        fresh = distinct - set(pos)
+        if count > 0 and (count == max_slices or len(pos) + len(fresh) > max_cols):
+            close()
+            pos, first, count = {}, sl, 0
+        if count == 0:
+            first = sl
+        for p in range(b, e):
+            c = int(col[p])
+            if c < 0:
+                continue
+            if c not in pos:
+                pos[c] = len(pos)
+                out_dict.append(c)
+            index[p] = pos[c]
+        count += 1
+    if count > 0:
+        close()
+    return (np.array(out_tiles, dtype=np.int32).reshape(-1, 4), np.array(out_dict, dtype=np.int32), index)

@@ -47,6 +47,9 @@ FESPMV_EXPORT_DIAG = 5
 FESPMV_EXPORT_VALUES_F32 = 6
 FESPMV_EXPORT_VALUES_BF16 = 7
 FESPMV_EXPORT_SCALE = 8
+FESPMV_EXPORT_TILES = 9
+FESPMV_EXPORT_TILE_COLS = 10
+FESPMV_EXPORT_TILE_INDEX = 11
 FESPMV_CG_F64 = 0
 FESPMV_CG_F32_REFINE = 1
 FESPMV_CG_BF16_REFINE = 2
@@ -64,7 +67,7 @@ class FespmvError(RuntimeError):
 class fespmv_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("format", "reorder", "sigma", "threshold", "vec", "csr_lanes", "precisions",
-                 "block")]
+                 "block", "tiles")]
 
 
 class fespmv_mesh_info(ctypes.Structure):
@@ -74,7 +77,9 @@ class fespmv_mesh_info(ctypes.Structure):
 class fespmv_info(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_slices", ctypes.c_int64),
                 ("packed_len", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("format", ctypes.c_int32), ("vec", ctypes.c_int32)]
+                ("format", ctypes.c_int32), ("vec", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
+                ("tile_dict_len", ctypes.c_int64), ("tile_max_cols", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class cg_options(ctypes.Structure):
@@ -226,14 +231,14 @@ class Matrix:
 
 def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=FESPMV_FMT_SLICED,
                 reorder=None, sigma=0, threshold=0, vec=0, csr_lanes=0, precisions=0, block=0,
-                stream=None) -> Matrix:
+                tiles=0, stream=None) -> Matrix:
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     values = np.ascontiguousarray(values, dtype=np.float64)
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block)
+    opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block, tiles)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     h = _P()
     n = len(rowptr) - 1
@@ -287,7 +292,7 @@ def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigm
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0, 0)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     info = fespmv_info()
     n = len(rowptr) - 1
@@ -311,7 +316,7 @@ def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorde
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0, 0)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     best = ctypes.c_double(0)
     tried = _i32(0)
@@ -335,17 +340,20 @@ _EXPORT_DTYPES = {FESPMV_EXPORT_PERM: (np.int32, "n_rows"), FESPMV_EXPORT_META: 
                   FESPMV_EXPORT_DIAG: (np.float64, "n_rows"),
                   FESPMV_EXPORT_VALUES_F32: (np.float32, "packed_len"),
                   FESPMV_EXPORT_VALUES_BF16: (np.uint16, "packed_len"),
-                  FESPMV_EXPORT_SCALE: (np.float64, "n_rows")}
+                  FESPMV_EXPORT_SCALE: (np.float64, "n_rows"),
+                  FESPMV_EXPORT_TILES: (np.int32, "tiles"),
+                  FESPMV_EXPORT_TILE_COLS: (np.int32, "tile_dict_len"),
+                  FESPMV_EXPORT_TILE_INDEX: (np.uint16, "packed_len")}
 
 
 def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
     info = spmv_get_info(A)
     dt, key = _EXPORT_DTYPES[what]
-    count = info["n_slices"] * 4 if key == "meta" else info[key]
+    count = {"meta": info["n_slices"] * 4, "tiles": info["n_tiles"] * 4}.get(key) or info.get(key, 0)
     out = np.zeros(max(count, 1), dtype=dt)
     _check(_lib.spmv_export(A.handle, what, _ptr(out), out.nbytes, _stream(stream)))
     out = out[:count]
-    return out.reshape(-1, 4) if key == "meta" else out
+    return out.reshape(-1, 4) if key in ("meta", "tiles") else out
 
 
 def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
@@ -471,7 +479,7 @@ def batch_create(problems, sigma=0, threshold=0, vec=0, precisions=0, block=0, r
         mesh[j] = fespmv_mesh_info(dpn, None if xyz is None else xyz.ctypes.data)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if any_xyz else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, precisions, block)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, precisions, block, 0)
     h = _P()
     _check(_lib.batch_create(ctypes.byref(h), n, _ptr(n_rows), ctypes.cast(rp, _P),
                              ctypes.cast(ci, _P), ctypes.cast(va, _P), ctypes.cast(mesh, _P),

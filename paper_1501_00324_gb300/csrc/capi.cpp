@@ -46,7 +46,8 @@ void free_handle(fespmv_mat* A) {
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
-                    A->d_ys, A->d_xk, A->d_yk, A->d_vdf, A->d_xdf};
+                    A->d_ys, A->d_xk, A->d_yk, A->d_vdf, A->d_xdf, A->d_tiles, A->d_tdict,
+                    A->d_tlidx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;
@@ -106,6 +107,27 @@ int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s) {
     return FESPMV_OK;
 }
 
+// Tile arrays of a SLICED handle (x staged through shared memory); leaves the
+// handle untiled when a slice has more distinct columns than a tile holds.
+static const int kTileSlices = 8, kTileCols = 4096;
+
+int upload_tiles(fespmv_mat* A, const Plan& plan, Tiles& t, cudaStream_t s) {
+    if (!build_tiles(plan.meta, plan.col, A->n, kTileSlices, kTileCols, t)) return FESPMV_OK;
+    A->n_tiles = (int64_t)t.tiles.size() / 4;
+    A->tile_dmax = t.dmax;
+    A->tile_dict_len = (int64_t)t.dict.size();
+    int rc;
+    if ((rc = device_alloc(A, (void**)&A->d_tiles, sizeof(int4) * (size_t)std::max<int64_t>(1, A->n_tiles), "tiles")) ||
+        (rc = device_alloc(A, (void**)&A->d_tdict, sizeof(int32_t) * std::max<size_t>(1, t.dict.size()), "tile columns")) ||
+        (rc = device_alloc(A, (void**)&A->d_tlidx, sizeof(uint16_t) * (size_t)std::max<int64_t>(1, plan.packed_len), "tile indices")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_tiles, t.tiles.data(), sizeof(int32_t) * t.tiles.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_tdict, t.dict.data(), sizeof(int32_t) * t.dict.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_tlidx, t.lidx.data(), sizeof(uint16_t) * t.lidx.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")))
+        return rc;
+    A->tiled = 1;
+    return FESPMV_OK;
+}
+
 static bool pow2_upto32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
 
 static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, const int32_t* colind,
@@ -135,6 +157,9 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     if (!pow2_upto32(o.csr_lanes)) {
         set_error("csr_lanes must be a power of two <= 32 (got %d)", o.csr_lanes);
         return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.tiles < -1 || o.tiles > 0) {
+        set_error("tiles must be 0 (on) or -1 (off) (got %d)", o.tiles); return FESPMV_ERR_INVALID_ARG;
     }
     if (o.block == 0) o.block = 256;
     if (o.block < 32 || o.block > 1024 || o.block % 32) {
@@ -207,6 +232,8 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
                        o.threshold, o.vec, plan));
         TRY(upload_sliced(A, plan, s));
+        Tiles tiles;  // host arrays stay alive until the stream synchronisation below
+        if (o.tiles >= 0) TRY(upload_tiles(A, plan, tiles, s));
         if (A->precisions & FESPMV_PREC_DF64) {
             TRY(device_alloc(A, (void**)&A->d_vdf, sizeof(float2) * plan.packed_len, "float-pair values"));
             TRY(device_alloc(A, (void**)&A->d_xdf, sizeof(float2) * n, "float-pair x"));
@@ -510,6 +537,10 @@ int spmv_get_info(fespmv_mat_t A, fespmv_info* info) {
     info->device_bytes = A->device_bytes;
     info->format = A->format;
     info->vec = A->vec;
+    info->n_tiles = A->tiled ? A->n_tiles : 0;
+    info->tile_dict_len = A->tiled ? A->tile_dict_len : 0;
+    info->tile_max_cols = A->tiled ? A->tile_dmax : 0;
+    info->pad = 0;
     return FESPMV_OK;
 }
 
@@ -532,6 +563,9 @@ int spmv_export(fespmv_mat_t A, int32_t what, void* out, size_t bytes, fespmv_st
         case FESPMV_EXPORT_VALUES_BF16:
             src = A->d_val16; need = 2 * (size_t)(sliced ? A->packed_len : A->nnz); break;
         case FESPMV_EXPORT_SCALE: src = A->d_scale; need = 8 * (size_t)A->n; break;
+        case FESPMV_EXPORT_TILES: src = A->d_tiles; need = 16 * (size_t)A->n_tiles; break;
+        case FESPMV_EXPORT_TILE_COLS: src = A->d_tdict; need = 4 * (size_t)A->tile_dict_len; break;
+        case FESPMV_EXPORT_TILE_INDEX: src = A->d_tlidx; need = 2 * (size_t)A->packed_len; break;
         default: set_error("unknown export %d", what); return FESPMV_ERR_INVALID_ARG;
     }
     if (!src) { set_error("array %d is not held by this handle", what); return FESPMV_ERR_UNSUPPORTED; }

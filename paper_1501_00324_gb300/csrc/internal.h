@@ -33,6 +33,22 @@ struct Plan {
     int64_t packed_len = 0;
 };
 
+// Tiles of consecutive slices for the x-staging kernels: each tile's distinct
+// columns form its dictionary (first-use order); every packed entry carries its
+// 16-bit index into the dictionary, padding the index D of a zero slot.
+struct Tiles {
+    std::vector<int32_t> tiles;     // 4 per tile: first slice, slices, dictionary offset, size D
+    std::vector<int32_t> dict;      // concatenated dictionaries
+    std::vector<uint16_t> lidx;     // per packed entry
+    int dmax = 0;                   // largest D
+};
+
+// Greedy runs of at most max_slices slices, closed before the dictionary would
+// exceed max_cols.  Returns false (and leaves `out` empty) when one slice alone
+// has more than max_cols distinct columns.
+bool build_tiles(const std::vector<uint32_t>& meta, const std::vector<int32_t>& col, int64_t n,
+                 int max_slices, int max_cols, Tiles& out);
+
 // Permuted CSR (stage 1 of planning): P, Pinv, rows in new order with columns
 // renumbered and sorted, each entry's input position, each row's diagonal position.
 struct Permuted {
@@ -107,6 +123,14 @@ struct fespmv_mat {
     double* d_xk = nullptr;           // multi-RHS permuted-I/O scratch (32 n doubles each)
     double* d_yk = nullptr;
     int max_lanes_log2 = 0;           // largest log2(lanes per row) over the slices
+    // x staged through shared memory (SLICED, options.tiles >= 0): Tiles on the device
+    int tiled = 0;                    // 1 when the tile arrays below are in use
+    int64_t n_tiles = 0;
+    int tile_dmax = 0;
+    int64_t tile_dict_len = 0;
+    int4* d_tiles = nullptr;
+    int32_t* d_tdict = nullptr;
+    uint16_t* d_tlidx = nullptr;
     float* d_xs = nullptr;            // float permuted-I/O scratch (n each)
     float* d_ys = nullptr;
 
@@ -120,6 +144,8 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what);
 // Kernel launchers (spmv_kernels.cu); all enqueue on `s` and return FESPMV_OK or
 // FESPMV_ERR_CUDA.
 int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
+int launch_spmv_tiled(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
+int launch_spmv_low_tiled(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
 unsigned grid_for(int64_t work, int block);

@@ -210,6 +210,79 @@ int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
     return FESPMV_OK;
 }
 
+bool build_tiles(const std::vector<uint32_t>& meta, const std::vector<int32_t>& col, int64_t n,
+                 int max_slices, int max_cols, Tiles& out) {
+    const int64_t ns = (int64_t)meta.size() / 4;
+    out = Tiles();
+    out.lidx.assign(col.size(), 0);
+    std::vector<int32_t> tile_of((size_t)n, -1), seen((size_t)n, -1), local((size_t)n, 0);
+    int32_t tile = -1;
+    int D = 0, first = 0, count = 0;
+    auto slice_range = [&](int64_t sl, int64_t& b, int64_t& e) {
+        b = (int64_t)meta[(size_t)sl * 4] * 32;
+        e = b + 32 * (int64_t)meta[(size_t)sl * 4 + 1];
+    };
+    auto close = [&]() {
+        out.tiles.insert(out.tiles.end(), {first, count, (int32_t)(out.dict.size() - (size_t)D), D});
+        out.dmax = std::max(out.dmax, D);
+        for (int64_t sl = first; sl < (int64_t)first + count; ++sl) {  // padding -> zero slot D
+            int64_t b, e;
+            slice_range(sl, b, e);
+            for (int64_t p = b; p < e; ++p)
+                if (col[(size_t)p] < 0) out.lidx[(size_t)p] = (uint16_t)D;
+        }
+    };
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        int64_t b, e;
+        slice_range(sl, b, e);
+        if (count == 0) {  // open a tile
+            ++tile;
+            D = 0;
+            first = (int)sl;
+        }
+        int fresh = 0;  // distinct columns of the slice not yet in the tile
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t c = col[(size_t)p];
+            if (c >= 0 && tile_of[(size_t)c] != tile && seen[(size_t)c] != (int32_t)sl) {
+                seen[(size_t)c] = (int32_t)sl;
+                ++fresh;
+            }
+        }
+        if (count > 0 && (count == max_slices || D + fresh > max_cols)) {
+            close();
+            ++tile;
+            D = 0;
+            first = (int)sl;
+            count = 0;
+            fresh = 0;
+            for (int64_t p = b; p < e; ++p) {
+                const int32_t c = col[(size_t)p];
+                if (c >= 0 && seen[(size_t)c] != (int32_t)(-2 - sl)) {
+                    seen[(size_t)c] = (int32_t)(-2 - sl);
+                    ++fresh;
+                }
+            }
+        }
+        if (fresh > max_cols) {
+            out = Tiles();
+            return false;
+        }
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t c = col[(size_t)p];
+            if (c < 0) continue;
+            if (tile_of[(size_t)c] != tile) {
+                tile_of[(size_t)c] = tile;
+                local[(size_t)c] = D++;
+                out.dict.push_back(c);
+            }
+            out.lidx[(size_t)p] = (uint16_t)local[(size_t)c];
+        }
+        ++count;
+    }
+    if (count > 0) close();
+    return true;
+}
+
 int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
                const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out) {
     Permuted pm;

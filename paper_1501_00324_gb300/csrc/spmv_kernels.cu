@@ -339,6 +339,7 @@ static void dispatch_low(const fespmv_mat* A, const VT* val, const float* x, flo
 
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s) {
     if (A->n == 0) return FESPMV_OK;
+    if (A->tiled) return launch_spmv_low_tiled(A, precision, x, y, s);
     if (precision == FESPMV_PREC_F32)
         dispatch_low<float>(A, A->d_val32, x, y, s);
     else
@@ -358,6 +359,8 @@ int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s)
             case 16: launch_csr<16>(A, x, y, s); break;
             default: launch_csr<32>(A, x, y, s); break;
         }
+    } else if (A->tiled) {
+        return launch_spmv_tiled(A, x, y, s);
     } else {
         switch (A->vec) {
             case 1: launch_sliced<1>(A, x, y, s); break;

@@ -70,6 +70,10 @@ KERNELS = [
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, threshold=4),
     dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, block=128),
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=64, threshold=0, reorder=fs.FESPMV_REORDER_NONE),
+    # x gathered from L1/L2 instead of staged per tile in shared memory
+    dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, threshold=0, tiles=-1),
+    dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, tiles=-1),
+    dict(format=fs.FESPMV_FMT_SLICED, vec=4, sigma=10**9, threshold=4, tiles=-1),
     # float-pair FP64 products on the FP32 pipe
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, precisions=fs.FESPMV_PREC_DF64),
     dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, precisions=fs.FESPMV_PREC_DF64),
@@ -175,6 +179,7 @@ def test_edge_cases_empty_ragged_and_nonfinite():
 
 
 @pytest.mark.parametrize("fmt,kw", [(fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2)),
+                                    (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2, tiles=-1)),
                                     (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2,
                                                                 precisions=fs.FESPMV_PREC_DF64)),
                                     (fs.FESPMV_FMT_CSR, dict(csr_lanes=4))])
@@ -219,3 +224,41 @@ def test_autotuner_returns_a_valid_fast_layout():
                        threshold=t["threshold"], block=t["block"])
     x = fegen.random_vector(p.n_rows, 21)
     check_parity(p, apply(A, x), x)
+
+
+@pytest.mark.parametrize("name,thr,V", [("elasticity_9", 0, 2), ("shell_6x20x36", 3, 1),
+                                        ("cube_laplace_20", 2, 4)])
+def test_tiles_bit_exact_against_oracle(name, thr, V):
+    p = problem(name)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=128,
+                       threshold=thr, vec=V)
+    meta = fs.spmv_export(A, fs.FESPMV_EXPORT_META)
+    col = fs.spmv_export(A, fs.FESPMV_EXPORT_COLS)
+    t, d, idx = layout.tiles(meta, col, 8, 4096)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_TILES), t)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_TILE_COLS), d)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_TILE_INDEX), idx)
+    info = fs.spmv_get_info(A)
+    assert info["n_tiles"] == len(t) and info["tile_max_cols"] == t[:, 3].max()
+    B = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=128, tiles=-1)
+    assert fs.spmv_get_info(B)["n_tiles"] == 0
+
+
+def test_slice_wider_than_a_tile_gathers_from_cache():
+    """A slice with more distinct columns than a tile holds leaves the handle untiled."""
+    n = 8192
+    rng = np.random.default_rng(17)
+    rows = [np.union1d(rng.choice(n, 200, replace=False), [i]) if i < 32 else np.array([i])
+            for i in range(n)]
+    rowptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+    cols = np.concatenate(rows).astype(np.int32)
+    vals = rng.standard_normal(len(cols))
+    A = fs.spmv_create(rowptr, cols, vals, sigma=0)
+    assert fs.spmv_get_info(A)["n_tiles"] == 0
+
+    class Q:
+        pass
+    q = Q()
+    q.rowptr, q.colind, q.values, q.n_rows = rowptr, cols, vals, n
+    x = fegen.random_vector(n, 18)
+    check_parity(q, apply(A, x), x)

@@ -349,3 +349,59 @@ def test_scaled_values_match_dense_scaling(storage):
     yd = B @ x.astype(np.float64)
     L = np.diff(p.rowptr).max()
     assert np.all(np.abs(y - yd) <= (L + 1) * 2.0 ** -24 * (np.abs(B) @ np.abs(x)))
+
+
+def _one_step_slices(cols_per_slice):
+    """meta/col for slices of one step (w = 1) each: slice s holds 32 entries."""
+    meta, col = [], []
+    for s, cs in enumerate(cols_per_slice):
+        meta.append((s, 1, 32 * s, 0))
+        col.extend(list(cs) + [-1] * (32 - len(cs)))
+    return np.array(meta, dtype=np.uint32), np.array(col, dtype=np.int32)
+
+
+def test_tiles_hand_example():
+    # slices with columns {0,1,2}, {2,3}, {4,5,6}, {6}: with max_cols = 5 the first two
+    # share a tile (4 columns), the third would make 7, so it opens a new tile with the fourth
+    meta, col = _one_step_slices([[0, 1, 2], [3, 2], [4, 5, 6], [6]])
+    t, d, idx = layout.tiles(meta, col, max_slices=8, max_cols=5)
+    assert t.tolist() == [[0, 2, 0, 4], [2, 2, 4, 3]]
+    assert d.tolist() == [0, 1, 2, 3, 4, 5, 6]
+    assert idx[:3].tolist() == [0, 1, 2] and idx[32:34].tolist() == [3, 2]
+    assert idx[3] == 4 and idx[64 + 3] == 3          # padding -> the tile's zero slot D
+    # max_slices closes tiles too; a slice wider than max_cols means no tiles
+    t2, _, _ = layout.tiles(meta, col, max_slices=1, max_cols=5)
+    assert t2[:, 1].tolist() == [1, 1, 1, 1]
+    assert layout.tiles(meta, col, max_slices=8, max_cols=2) is None
+
+
+@pytest.mark.parametrize("maker", ["elasticity", "shell"])
+def test_tiles_reconstruct_columns_and_are_greedy(maker):
+    p = fegen.cube_elasticity(6, 71) if maker == "elasticity" else fegen.shell_laplace(4, 12, 16, 72)
+    P = layout.row_permutation(p.rowptr, p.dofs_per_node, p.node_xyz, "morton", 128)
+    rp2, ci2, v2, _ = layout.permute_csr(p.rowptr, p.colind, p.values, P)
+    meta, col, _, _ = layout.pack(rp2, ci2, v2, 3, 2)
+    meta = np.asarray(meta).reshape(-1, 4)
+    max_slices, max_cols = 4, 160
+    t, d, idx = layout.tiles(meta, col, max_slices, max_cols)
+
+    def cols_of(first, count):
+        b = int(meta[first, 0]) * 32
+        e = int(meta[first + count - 1, 0]) * 32 + 32 * int(meta[first + count - 1, 1])
+        return col[b:e], b, e
+
+    assert t[0, 0] == 0 and t[-1, 0] + t[-1, 1] == len(meta)
+    assert np.all(t[1:, 0] == t[:-1, 0] + t[:-1, 1])                     # contiguous, in order
+    for k, (first, count, off, D) in enumerate(t):
+        cs, b, e = cols_of(first, count)
+        real = cs[cs >= 0]
+        u, first_pos = np.unique(real, return_index=True)
+        assert D == len(u) <= max_cols and 1 <= count <= max_slices
+        assert np.array_equal(d[off:off + D], real[np.sort(first_pos)])  # first-use order
+        ii = idx[b:e].astype(np.int64)
+        assert np.array_equal(d[off + ii[cs >= 0]], real)               # index -> column
+        assert np.all(ii[cs < 0] == D)
+        if k + 1 < len(t):                                               # greedy: the next slice
+            nxt, _, _ = cols_of(first + count, 1)                        # would break a limit
+            union = np.union1d(real, nxt[nxt >= 0])
+            assert count == max_slices or len(union) > max_cols
