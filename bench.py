@@ -44,8 +44,9 @@ METRIC = "SpMV effective HBM GB/s (% of ~8 TB/s); CG solves/s and p50/p99 latenc
 WORKLOAD = "cube_elasticity_64"
 NOMINAL_HBM_GBS = 8000.0
 PROFILES = os.path.join(ROOT, "profiles")
-KERNEL_SRCS = [os.path.join(ROOT, "paper_1501_00324_gb300", "csrc", f)
-               for f in ("spmv_kernels.cu", "spmv_device.cuh")]
+KERNEL_SRCS = {k: [os.path.join(ROOT, "paper_1501_00324_gb300", "csrc", f) for f in fs]
+               for k, fs in {"sliced": ("spmv_kernels.cu", "spmv_device.cuh"),
+                             "tiled": ("tiled.cu", "tiled_device.cuh", "spmv_device.cuh")}.items()}
 
 
 def parse_args():
@@ -58,6 +59,8 @@ def parse_args():
     ap.add_argument("--vec", type=int, default=2)
     ap.add_argument("--threshold", type=int, default=0)
     ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--tiles", type=int, choices=[0, -1], default=0,
+                    help="0: x staged through shared memory per tile of slices; -1: x gathered from L1/L2")
     ap.add_argument("--kernel", choices=["f64", "df64"], default="f64",
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
@@ -87,24 +90,25 @@ def measured_peaks():
         return None
 
 
-def kernel_hash():
+def kernel_hash(family="sliced"):
     h = hashlib.sha256()
-    for f in KERNEL_SRCS:
+    for f in KERNEL_SRCS[family]:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+def profile_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary profiles/<name>_cube_elasticity_64.md
+    (name: tiled_f64, sliced_f64, sliced_df64), if it matches this source."""
     try:
-        text = open(os.path.join(PROFILES, f"sliced_{kernel}_cube_elasticity_64.md")).read()
+        text = open(os.path.join(PROFILES, f"{name}_cube_elasticity_64.md")).read()
     except OSError:
         return None, "no ncu summary committed"
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not h or not b:
         return None, "summary lacks traffic figures"
-    if h.group(1) != kernel_hash():
+    if h.group(1) != kernel_hash(name.split("_")[0]):
         return None, "kernel changed since the ncu capture"
     return float(b.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum"
 
@@ -260,7 +264,7 @@ def main():
     x = fegen.random_vector(n, 1504)
     t0 = time.perf_counter()
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.vec,
-                       threshold=args.threshold, block=args.block,
+                       threshold=args.threshold, block=args.block, tiles=args.tiles,
                        precisions=(0 if args.only_spmv else fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
                        | (fs.FESPMV_PREC_DF64 if args.kernel == "df64" else 0))
     create_s = time.perf_counter() - t0
@@ -350,6 +354,14 @@ def main():
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
             del X64, Y64
+            # the same FE product with x gathered from L1/L2 (no tiles), for comparison
+            if info["n_tiles"] > 0:
+                G = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                                   vec=args.vec, threshold=args.threshold, block=args.block, tiles=-1)
+                fg = lambda: fs.spmv_apply(G, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+                fg()
+                extra["fe_global_gather_gbs"] = round(mb / (back_to_back(fg, args.steps) * 1e-3) / 1e9, 1)
+                fs.spmv_destroy(G)
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
@@ -373,6 +385,8 @@ def main():
                             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
             if hasattr(fs, "cg_solve"):
                 extra["cg"] = bench_cg(fs, torch, A, p, args.cg_solves, fs.FESPMV_CG_F64)
+                extra["cg_single_reduction"] = bench_cg(fs, torch, A, p, args.cg_solves, fs.FESPMV_CG_F64,
+                                                        flags=fs.FESPMV_CG_SINGLE_REDUCTION)
                 extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                   fs.FESPMV_CG_F32_REFINE)
             if args.batch_meshes > 0:
@@ -387,7 +401,12 @@ def main():
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = mb / t_mean / 1e9
-    traffic, traffic_src = profile_traffic(args.kernel)
+    tiled = info["n_tiles"] > 0 and args.kernel == "f64"
+    kname = "tiled_f64" if tiled else f"sliced_{args.kernel}"
+    traffic, traffic_src = profile_traffic(kname)
+    # bytes the layout actually moves: values + 16-bit indices + tile column lists (+ x, y)
+    layout_bytes = (info["packed_len"] * 10 + info["tile_dict_len"] * 4 + n * 16 if tiled
+                    else info["packed_len"] * 12 + n * 16)
 
     if rank == 0:
         cpu = None
@@ -403,8 +422,10 @@ def main():
             "dtype": "f64" if args.kernel == "f64" else "df64 (float pairs, fp32 FMA)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": n, "nnz": nnz,
-                       "kernel": f"sliced_{args.kernel} V={info['vec']} threshold={args.threshold} "
-                                 f"sigma={args.sigma} block={args.block}",
+                       "kernel": (f"tiled_f64 (x staged in shared memory, {info['n_tiles']} tiles of <= 8 "
+                                  f"slices, 16-bit column indices)" if tiled else f"sliced_{args.kernel}")
+                                 + f" V={info['vec']} threshold={args.threshold} sigma={args.sigma}"
+                                 + ("" if tiled else f" block={args.block}"),
                        "order": "Morton nodes, windowed length sort, sorted columns",
                        "l2": "inputs larger than L2: the 414 MB matrix streams from HBM every "
                              "step (x stays L2-resident, as in CG); steps enqueued back to back",
@@ -418,7 +439,10 @@ def main():
                          "traffic": traffic, "traffic_source": traffic_src,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks
                          else "fallback 6.8 TB/s",
-                         "bytes_per_launch": mb},
+                         "bytes_per_launch": mb,
+                         "layout_bytes_per_launch": layout_bytes,
+                         "note": "achieved = algorithmic bytes (FP64 values, int32 indices, x, y) / time; "
+                                 "the tiled layout moves layout_bytes_per_launch"},
             "gpu_launches": args.steps * (2 if args.kernel == "df64" else 1),
             "step_with_l2_flush": {"ms": round(statistics.mean(times_flushed), 4),
                                    "gbs": round(mb / (statistics.mean(times_flushed) * 1e-3) / 1e9, 1),
@@ -568,8 +592,13 @@ def bench_batched(fs, torch, args):
     ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 2000 + i)
           for i, N in enumerate(sizes)]
     gen_s = time.perf_counter() - t0
+    # rows-per-warp (K2 threshold), vector width and block from the autotuner, run on the
+    # largest mesh with the batch's kernels (x gathered from cache, no tiles)
+    big = max(ps, key=lambda q: q.n_rows)
+    tune = fs.spmv_autotune(big.rowptr, big.colind, big.values, big.node_xyz, 1, sigma=1024, reps=5, tiles=-1)
     t0 = time.perf_counter()
-    B = fs.batch_create([(p.rowptr, p.colind, p.values, p.node_xyz, 1) for p in ps], sigma=1024)
+    B = fs.batch_create([(p.rowptr, p.colind, p.values, p.node_xyz, 1) for p in ps], sigma=1024,
+                        vec=tune["vec"], threshold=tune["threshold"], block=tune["block"])
     create_s = time.perf_counter() - t0
     bs = [fegen.random_vector(p.n_rows, 5000 + j) for j, p in enumerate(ps)]
     bd = torch.from_numpy(np.concatenate(bs)).cuda()
@@ -606,6 +635,7 @@ def bench_batched(fs, torch, args):
         for A in mats:
             fs.spmv_destroy(A)
     return {"meshes": len(ps), "rows_total": info["n_rows"], "padded_rows": info["padded_rows"],
+            "autotune": {k: tune[k] for k in ("vec", "threshold", "block", "best_us", "tried")},
             "nnz_total": info["nnz"], "gen_s": round(gen_s, 1), "create_s": round(create_s, 1),
             "batched_s": round(batch_s, 4), "solves_per_s": round(len(ps) / batch_s, 1),
             "max_outer": max(r["outer"] for r in res), "max_inner_iters": max(r["iters"] for r in res),
@@ -645,7 +675,7 @@ def profile_piece(fs, torch, A, p, xp, args):
     print(f"profile target {t}: {args.steps} runs done", flush=True)
 
 
-def bench_cg(fs, torch, A, p, n_solves, precision):
+def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
     """CG solves to 1e-10 on the same matrix (b = A u*, u* manufactured)."""
     import fegen
     u = fegen.manufactured_solution(p)
@@ -653,12 +683,12 @@ def bench_cg(fs, torch, A, p, n_solves, precision):
     bd = torch.empty_like(ud)
     fs.spmv_apply(A, ud, bd)
     lat, iters, outer, rel = [], [], [], []
-    fs.cg_solve(A, bd, torch.zeros_like(bd), tol=1e-10, precision=precision)   # warm: graphs
+    fs.cg_solve(A, bd, torch.zeros_like(bd), tol=1e-10, precision=precision, flags=flags)   # warm: graphs
     for _ in range(n_solves):
         xs = torch.zeros_like(bd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = fs.cg_solve(A, bd, xs, tol=1e-10, precision=precision)
+        res = fs.cg_solve(A, bd, xs, tol=1e-10, precision=precision, flags=flags)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0)
         iters.append(res["iters"])
@@ -667,6 +697,7 @@ def bench_cg(fs, torch, A, p, n_solves, precision):
         assert res["status"] == 0, res
     lat_ms = sorted(1e3 * t for t in lat)
     return {"precision": {0: "f64", 1: "f32_refine", 2: "bf16_refine"}[precision], "tol": 1e-10,
+            "variant": "single_reduction" if flags & fs.FESPMV_CG_SINGLE_REDUCTION else "textbook",
             "solves": n_solves, "outer": outer[0], "true_relres_max": max(rel),
             "solves_per_s": round(n_solves / sum(lat), 3),
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),

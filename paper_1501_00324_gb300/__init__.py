@@ -308,7 +308,7 @@ def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigm
 
 
 def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
-                  reps=0, stream=None) -> dict:
+                  reps=0, tiles=0, stream=None) -> dict:
     """Time candidate layouts; returns dict(vec, threshold, block, sigma, reorder, best_us, tried)."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
@@ -316,7 +316,7 @@ def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorde
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0, 0)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0, tiles)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     best = ctypes.c_double(0)
     tried = _i32(0)

@@ -23,6 +23,7 @@
 
 #include "internal.h"
 #include "spmv_device.cuh"
+#include "tiled_device.cuh"
 #include "cg_run.h"
 
 namespace fespmv {
@@ -126,6 +127,40 @@ __global__ void __launch_bounds__(256, V == 4 ? 6 : 8) cg_spmv_dot_sliced(const 
             q[row] = sum;
             v[0] = fma(p[row], sum, v[0]);
         }
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
+}
+
+// The same products with x staged through shared memory per tile (handles with
+// tiles): one block per tile, the block reduction at the end as above.
+template <int V, int U>
+__global__ void __launch_bounds__(kTiledBlock) cg_spmv_dot_tiled(const uint4* __restrict__ meta,
+                                                                 const uint16_t* __restrict__ lidx,
+                                                                 const double* __restrict__ val,
+                                                                 const int4* __restrict__ tiles,
+                                                                 const int32_t* __restrict__ dict,
+                                                                 const double* __restrict__ p,
+                                                                 double* __restrict__ q, int64_t n,
+                                                                 int64_t n_tiles, double* partials,
+                                                                 CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    double* xs = reinterpret_cast<double*>(tile_smem);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {   // persistent blocks stride over tiles
+        const int4 tl = stage_tile<double>(tiles + t, dict, p, xs);
+        if (wid < tl.y) {
+            const uint4 m = meta[tl.x + wid];
+            const double sum = tiled_row_sum<double, V, U>(m, lidx, val, xs, lane);
+            const int lt = (int)m.w;
+            const int64_t row = (int64_t)m.z + (lane >> lt);
+            if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+                q[row] = sum;
+                v[0] = fma(p[row], sum, v[0]);
+            }
+        }
+        __syncthreads();  // the next tile overwrites xs
     }
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
@@ -347,6 +382,42 @@ __global__ void __launch_bounds__(256, 6) cg1_spmv_dots_sliced(const uint4* __re
     if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
 }
 
+template <int V, int U>
+__global__ void __launch_bounds__(kTiledBlock) cg1_spmv_dots_tiled(const uint4* __restrict__ meta,
+                                                                   const uint16_t* __restrict__ lidx,
+                                                                   const double* __restrict__ val,
+                                                                   const int4* __restrict__ tiles,
+                                                                   const int32_t* __restrict__ dict,
+                                                                   const double* __restrict__ u,
+                                                                   const double* __restrict__ r,
+                                                                   double* __restrict__ w, int64_t n,
+                                                                   int64_t n_tiles, double* partials,
+                                                                   CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    double* xs = reinterpret_cast<double*>(tile_smem);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int4 tl = stage_tile<double>(tiles + t, dict, u, xs);
+        if (wid < tl.y) {
+            const uint4 m = meta[tl.x + wid];
+            const double sum = tiled_row_sum<double, V, U>(m, lidx, val, xs, lane);
+            const int lt = (int)m.w;
+            const int64_t row = (int64_t)m.z + (lane >> lt);
+            if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+                w[row] = sum;
+                const double ur = u[row], rr = r[row];
+                v[0] = fma(rr, ur, v[0]);
+                v[1] = fma(sum, ur, v[1]);
+                v[2] = fma(rr, rr, v[2]);
+            }
+        }
+        __syncthreads();
+    }
+    if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) finish_cg1(v[0], v[1], v[2], sc);
+}
+
 template <int L>
 __global__ void cg1_spmv_dots_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                   const double* __restrict__ val, const double* __restrict__ u,
@@ -424,6 +495,38 @@ __global__ void __launch_bounds__(256, 8) cg32_spmv_dot_sliced(const uint4* __re
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
+template <typename VT, int V, int U>
+__global__ void __launch_bounds__(kTiledBlock) cg32_spmv_dot_tiled(const uint4* __restrict__ meta,
+                                                                   const uint16_t* __restrict__ lidx,
+                                                                   const VT* __restrict__ val,
+                                                                   const int4* __restrict__ tiles,
+                                                                   const int32_t* __restrict__ dict,
+                                                                   const float* __restrict__ p,
+                                                                   float* __restrict__ q, int64_t n,
+                                                                   int64_t n_tiles, double* partials,
+                                                                   CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    float* xs = reinterpret_cast<float*>(tile_smem);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int4 tl = stage_tile<float>(tiles + t, dict, p, xs);
+        if (wid < tl.y) {
+            const uint4 m = meta[tl.x + wid];
+            const float sum = tiled_row_sum<VT, V, U>(m, lidx, val, xs, lane);
+            const int lt = (int)m.w;
+            const int64_t row = (int64_t)m.z + (lane >> lt);
+            if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+                q[row] = sum;
+                v[0] = fma((double)p[row], (double)sum, v[0]);
+            }
+        }
+        __syncthreads();
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+}
+
 template <typename VT, int L>
 __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                   const VT* __restrict__ val, const float* __restrict__ p,
@@ -441,7 +544,7 @@ __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int3
     if (grid_sum<1, 1024>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
-__global__ void __launch_bounds__(256, 8) cg32_update(int64_t n, float* __restrict__ w,
+__global__ void __launch_bounds__(256, 4) cg32_update(int64_t n, float* __restrict__ w,
                                                    float* __restrict__ r,
                                                    const float* __restrict__ p,
                                                    const float* __restrict__ q, double* partials,
@@ -470,7 +573,7 @@ __global__ void __launch_bounds__(256, 8) cg32_update(int64_t n, float* __restri
     }
 }
 
-__global__ void __launch_bounds__(256, 8) cg32_pupdate(int64_t n, float* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) cg32_pupdate(int64_t n, float* __restrict__ p,
                                                     const float* __restrict__ r, const CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     const float beta = (float)sc->beta;
@@ -544,6 +647,17 @@ static unsigned spmv_grid(const fespmv_mat* A) {
     return grid_for(A->n * A->csr_lanes, A->block);
 }
 
+// A persistent tiled kernel's grid: the blocks of `kernel` resident at once (with
+// its shared memory), at most one per tile.
+template <typename Kernel>
+static unsigned tiled_grid(const fespmv_mat* A, Kernel kernel, size_t smem) {
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTiledBlock, smem);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(A->n_tiles, (int64_t)sms * std::max(per_sm, 1)));
+}
+
 // A persistent SLICED kernel's grid: spmv_grid, capped at the blocks of `kernel`
 // that are resident at once (kernels holding more than 32 registers fit fewer).
 template <typename Kernel>
@@ -598,7 +712,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
-    const int64_t np = grid_sum_doubles(std::max<int64_t>(spmv_grid(A), upd));
+    const int64_t np = grid_sum_doubles(std::max<int64_t>({(int64_t)spmv_grid(A), upd, A->tiled ? A->n_tiles : 0}));
     int64_t b = 8 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
@@ -625,7 +739,10 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
         destroy_work(w);
         return rc;
     }
-    const size_t np = (size_t)grid_sum_doubles(std::max(spmv_grid(A), w->upd_grid));
+    // one partial per block of the largest reduction grid: the persistent products, the
+    // vector updates, or one block per tile
+    const size_t np = (size_t)grid_sum_doubles(
+        std::max<int64_t>({(int64_t)spmv_grid(A), (int64_t)w->upd_grid, A->tiled ? A->n_tiles : 0}));
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
         (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
         destroy_work(w);
@@ -653,6 +770,14 @@ static int ensure_workspace(fespmv_mat* A) {
 template <int V>
 static void launch_spmv_dot_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
+    if (A->tiled) {
+        const size_t smem = sizeof(double) * (A->tile_dmax + 1);
+        const unsigned g = tiled_grid(A, cg_spmv_dot_tiled<V, U>, smem);
+        cg_spmv_dot_tiled<V, U><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_val, A->d_tiles,
+                                                             A->d_tdict, w->p, w->q, A->n, A->n_tiles,
+                                                             w->partials, w->sc);
+        return;
+    }
     const unsigned g = resident_grid(A, cg_spmv_dot_sliced<V, U>);
     cg_spmv_dot_sliced<V, U><<<g, A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->p, w->q, A->n_slices,
                                                     A->n, w->partials, w->sc);
@@ -702,6 +827,14 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
 template <int V>
 static void launch_cg1_sliced(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     constexpr int U = (V == 1) ? 8 : (V == 2 ? 4 : 2);
+    if (A->tiled) {
+        const size_t smem = sizeof(double) * (A->tile_dmax + 1);
+        const unsigned g = tiled_grid(A, cg1_spmv_dots_tiled<V, U>, smem);
+        cg1_spmv_dots_tiled<V, U><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_val, A->d_tiles,
+                                                               A->d_tdict, w->u, w->r, w->q, A->n,
+                                                               A->n_tiles, w->partials, w->sc);
+        return;
+    }
     const unsigned g = resident_grid(A, cg1_spmv_dots_sliced<V, U>);
     cg1_spmv_dots_sliced<V, U><<<g, A->block, 0, s>>>(A->d_meta, A->d_col, A->d_val, w->u, w->r,
                                                                  w->q, A->n_slices, A->n, w->partials,
@@ -738,6 +871,15 @@ static void launch_iteration_cg1(const fespmv_mat* A, CgWork* w, cudaStream_t s)
 template <typename VT, int V>
 static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
     constexpr int U = (V == 4) ? 4 : 8;
+    if (A->tiled) {
+        constexpr int UT = (V == 1) ? 8 : (V == 2 ? 4 : 2);
+        const size_t smem = sizeof(float) * (A->tile_dmax + 1);
+        const unsigned g = tiled_grid(A, cg32_spmv_dot_tiled<VT, V, UT>, smem);
+        cg32_spmv_dot_tiled<VT, V, UT><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, val, A->d_tiles,
+                                                                    A->d_tdict, w->p32, w->q32, A->n,
+                                                                    A->n_tiles, w->partials, w->sc);
+        return;
+    }
     cg32_spmv_dot_sliced<VT, V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, val, w->p32,
                                                                      w->q32, A->n_slices, A->n,
                                                                      w->partials, w->sc);

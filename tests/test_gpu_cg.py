@@ -42,7 +42,8 @@ def make(p, **kw):
 
 FORMATS = [dict(format=fs.FESPMV_FMT_SLICED, sigma=512), dict(format=fs.FESPMV_FMT_CSR, csr_lanes=4),
            dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=4, vec=1),
-           dict(format=fs.FESPMV_FMT_SLICED, sigma=512, precisions=fs.FESPMV_PREC_DF64)]
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=512, precisions=fs.FESPMV_PREC_DF64),
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=512, tiles=-1)]
 
 
 @pytest.mark.parametrize("fmt", range(len(FORMATS)))
@@ -134,7 +135,7 @@ def test_cg_full_size_elasticity_64(prec):
 SR = fs.FESPMV_CG_SINGLE_REDUCTION
 
 
-@pytest.mark.parametrize("fmt", [0, 1, 3])
+@pytest.mark.parametrize("fmt", [0, 1, 3, 4])
 @pytest.mark.parametrize("name", ["cube_laplace_20", "elasticity_8", "shell_5x16x24"])
 def test_single_reduction_cg_matches_oracle(name, fmt):
     """Chronopoulos-Gear PCG against the oracle's own single-reduction PCG."""

@@ -31,7 +31,8 @@ def make(p, prec_bits, **kw):
 
 
 FORMATS = [dict(format=fs.FESPMV_FMT_SLICED, sigma=256), dict(format=fs.FESPMV_FMT_CSR, csr_lanes=4),
-           dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=3, vec=4)]
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=64, threshold=3, vec=4),
+           dict(format=fs.FESPMV_FMT_SLICED, sigma=256, tiles=-1)]
 
 
 @pytest.mark.parametrize("fmt", range(len(FORMATS)))
