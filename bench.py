@@ -74,6 +74,8 @@ def parse_args():
     ap.add_argument("--serve-full", action="store_true",
                     help="the full serving pool: 48 meshes of 5k..3M rows (else 12 of 5k..300k)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--shell", type=int, default=1,
+                    help="1: also measure the 24x256x512 shell Laplacian (FP64/BF16 products, refined CG)")
     ap.add_argument("--batch-meshes", type=int, default=256,
                     help="cubes in the batched solve (node counts log-uniform in [1k, 200k]); 0 skips")
     return ap.parse_args()
@@ -320,25 +322,26 @@ def main():
         extra = {}
         if not args.only_spmv:
             # product in the input numbering (permute x in, y out)
+            # (every extra product below is timed back to back, like the headline: each
+            # matrix is larger than L2, so it streams from HBM on every launch)
             y_user = torch.empty_like(xd)
-            t_user = timed_steps(lambda: fs.spmv_apply(A, xd, y_user), max(10, args.steps // 4))
-            extra["fe_input_numbering_gbs"] = round(mb / (statistics.mean(t_user) * 1e-3) / 1e9, 1)
+            fu = lambda: fs.spmv_apply(A, xd, y_user)  # noqa: E731
+            fu()
+            extra["fe_input_numbering_gbs"] = round(mb / (back_to_back(fu, args.steps) * 1e-3) / 1e9, 1)
             # low-precision products of B = S A S (the refined CG's inner operator)
             xs = xp.float()
             ys = torch.empty_like(xs)
             for name, prec, vb in (("fp32", fs.FESPMV_PREC_F32, 4), ("bf16", fs.FESPMV_PREC_BF16, 2)):
                 f = lambda: fs.spmv_apply_scaled(A, xs, ys, prec, fs.FESPMV_IO_PERMUTED)  # noqa: E731
                 f()
-                tl = timed_steps(f, max(10, args.steps // 4))
-                extra[f"{name}_spmv_gbs"] = round(nnz * (vb + 4) + n * 8) / (statistics.mean(tl) * 1e-3) / 1e9
-                extra[f"{name}_spmv_gbs"] = round(extra[f"{name}_spmv_gbs"], 1)
+                tl = back_to_back(f, args.steps)
+                extra[f"{name}_spmv_gbs"] = round((nnz * (vb + 4) + n * 8) / (tl * 1e-3) / 1e9, 1)
             # 32 right-hand sides in one pass over the FP32 matrix (row-major n x 32)
             X32 = torch.rand((n, 32), dtype=torch.float32, device=dev)
             Y32 = torch.empty_like(X32)
             fm = lambda: fs.spmv_apply_multi(A, X32, Y32, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
             fm()
-            tm32 = timed_steps(fm, max(10, args.steps // 8))
-            tmean = statistics.mean(tm32) * 1e-3
+            tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
             extra["multi32_fp32"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
@@ -348,8 +351,7 @@ def main():
             Y64 = torch.empty_like(X64)
             fm = lambda: fs.spmv_apply_multi(A, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
             fm()
-            tm64 = timed_steps(fm, max(10, args.steps // 8))
-            tmean = statistics.mean(tm64) * 1e-3
+            tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
             extra["multi32_fp64"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
@@ -367,9 +369,9 @@ def main():
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
                                    csr_lanes=lanes)
                 fs.spmv_apply(B, xd, y_user)
-                tb = timed_steps(lambda: fs.spmv_apply(B, xd, y_user), max(10, args.steps // 4))
+                tb = back_to_back(lambda: fs.spmv_apply(B, xd, y_user), args.steps)  # noqa: B023
                 extra[f"csr_{'scalar' if lanes == 1 else f'vector{lanes}'}_gbs"] = round(
-                    mb / (statistics.mean(tb) * 1e-3) / 1e9, 1)
+                    mb / (tb * 1e-3) / 1e9, 1)
                 fs.spmv_destroy(B)
             # end to end with host buffers (pinned), copies inside the timed region
             xh = torch.from_numpy(x).pin_memory().numpy()
@@ -389,6 +391,8 @@ def main():
                                                         flags=fs.FESPMV_CG_SINGLE_REDUCTION)
                 extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                   fs.FESPMV_CG_F32_REFINE)
+            if args.shell:
+                extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
                 extra["batched"] = bench_batched(fs, torch, args)
             if args.serve_seconds > 0 and hasattr(fs, "srv_create"):
@@ -581,6 +585,49 @@ def bench_serving(fs, torch, args):
             "seconds": T, "overload": dict(rate_per_s=args.serve_rate, **over), "steady": steady}
 
 
+def bench_shell(fs, torch, args):
+    """The heart-like shell Laplacian (24 x 256 x 512 nodes, 3.1M rows, ~15 entries per row,
+    fibre-rotated 9:1 conductivity): FP64 and BF16/FP32 products of the tiled layout, and
+    CG to 1e-10 in FP64 and with BF16 / FP32 values inside FP64 refinement."""
+    import fegen
+    t0 = time.perf_counter()
+    p = fegen.shell_laplace(24, 256, 512, 1503)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=1024,
+                       precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+    create_s = time.perf_counter() - t0
+    n, nnz = p.n_rows, p.nnz
+    x = torch.rand(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    xs, ys = x.float(), torch.empty(n, dtype=torch.float32, device="cuda")
+
+    def per_launch(fn, k=20):
+        fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k * 1e-3
+
+    t64 = per_launch(lambda: fs.spmv_apply(A, x, y, fs.FESPMV_IO_PERMUTED))
+    t32 = per_launch(lambda: fs.spmv_apply_scaled(A, xs, ys, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED))
+    t16 = per_launch(lambda: fs.spmv_apply_scaled(A, xs, ys, fs.FESPMV_PREC_BF16, fs.FESPMV_IO_PERMUTED))
+    out = {"rows": n, "nnz": nnz, "gen_s": round(gen_s, 1), "create_s": round(create_s, 1),
+           "n_tiles": fs.spmv_get_info(A)["n_tiles"],
+           "f64_spmv_gbs": round((nnz * 12 + n * 16) / t64 / 1e9, 1),
+           "f32_spmv_gbs": round((nnz * 8 + n * 8) / t32 / 1e9, 1),
+           "bf16_spmv_gbs": round((nnz * 6 + n * 8) / t16 / 1e9, 1)}
+    for name, prec in (("cg_f64", fs.FESPMV_CG_F64), ("cg_f32_refine", fs.FESPMV_CG_F32_REFINE),
+                       ("cg_bf16_refine", fs.FESPMV_CG_BF16_REFINE)):
+        out[name] = bench_cg(fs, torch, A, p, 2, prec)
+    fs.spmv_destroy(A)
+    return out
+
+
 def bench_batched(fs, torch, args):
     """Many independent cube Laplacians (node counts log-uniform in [1k, 200k]) solved
     together by batch_cg_solve (FP32 inner CG, FP64 refinement, tol 1e-10), against
@@ -683,7 +730,11 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
     bd = torch.empty_like(ud)
     fs.spmv_apply(A, ud, bd)
     lat, iters, outer, rel = [], [], [], []
-    fs.cg_solve(A, bd, torch.zeros_like(bd), tol=1e-10, precision=precision, flags=flags)   # warm: graphs
+    name = {0: "f64", 1: "f32_refine", 2: "bf16_refine"}[precision]
+    warm = fs.cg_solve(A, bd, torch.zeros_like(bd), tol=1e-10, precision=precision, flags=flags)  # graphs
+    if warm["status"] != 0:   # e.g. BF16 refinement stagnating: cond(B) * 2^-8 >= 1
+        return {"precision": name, "tol": 1e-10, "status": fs.status_string(warm["status"]),
+                "iters": warm["iters"], "outer": warm["outer"], "true_relres": warm["true_relres"]}
     for _ in range(n_solves):
         xs = torch.zeros_like(bd)
         torch.cuda.synchronize()
@@ -696,7 +747,7 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
         rel.append(res["true_relres"])
         assert res["status"] == 0, res
     lat_ms = sorted(1e3 * t for t in lat)
-    return {"precision": {0: "f64", 1: "f32_refine", 2: "bf16_refine"}[precision], "tol": 1e-10,
+    return {"precision": name, "tol": 1e-10,
             "variant": "single_reduction" if flags & fs.FESPMV_CG_SINGLE_REDUCTION else "textbook",
             "solves": n_solves, "outer": outer[0], "true_relres_max": max(rel),
             "solves_per_s": round(n_solves / sum(lat), 3),

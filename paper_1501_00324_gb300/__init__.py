@@ -247,6 +247,10 @@ def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=F
     return Matrix(h, n, int(rowptr[-1]))
 
 
+def status_string(status: int) -> str:
+    return _lib.fespmv_status_string(status).decode()
+
+
 def spmv_destroy(A: Matrix):
     if A.handle:
         _lib.spmv_destroy(A.handle)
