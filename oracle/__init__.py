@@ -56,6 +56,8 @@ def _lib():
         lib.oracle_pcg_single_reduction.restype = i32
         lib.oracle_refine.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, i32, P, P, P]
         lib.oracle_refine.restype = i32
+        lib.oracle_refine_reliable.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, P, P, P]
+        lib.oracle_refine_reliable.restype = i32
         lib.oracle_scaled_values.argtypes = [i64, P, P, P, i32, P]
         lib.oracle_scaled_values.restype = i32
         lib.oracle_csr_spmv_f32.argtypes = [i64, P, P, P, P, P]
@@ -147,3 +149,20 @@ def refine(rowptr, colind, values, b, x0=None, tol=1e-10, inner_tol=1e-3, max_ou
                               max_outer, max_inner, {"f32": 0, "bf16": 1}[storage],
                               ctypes.byref(o), ctypes.byref(i), ctypes.byref(tr))
     return x, dict(status=STATUS[st], outer=o.value, inner=i.value, true_relres=tr.value)
+
+
+def refine_reliable(rowptr, colind, values, b, x0=None, tol=1e-10, delta=0.1, max_iter=20000,
+                    storage="f32"):
+    """One float/bfloat16 CG on S A S with FP64 reliable updates (no restarts);
+    info: status, updates (residual replacements), iters (CG steps), true_relres."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    u = ctypes.c_int(0)
+    i = ctypes.c_int(0)
+    tr = ctypes.c_double(0)
+    st = _lib().oracle_refine_reliable(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, delta, max_iter,
+                                       {"f32": 0, "bf16": 1}[storage], ctypes.byref(u), ctypes.byref(i),
+                                       ctypes.byref(tr))
+    return x, dict(status=STATUS[st], updates=u.value, iters=i.value, true_relres=tr.value)

@@ -21,6 +21,11 @@
  *                     S = diag(A)^(-1/2), with B stored in FP32 or BF16 and FP64
  *                     dot products.  The paper runs FP64 only (Sec. 2); this
  *                     is the mixed-precision layer built on top of it.
+ *   oracle_refine_reliable  the same pieces without restarts: one low-precision
+ *                     CG whose recurrence residual is replaced by the FP64 true
+ *                     residual (and x updated in FP64) each time it has fallen
+ *                     by a factor delta ("reliable updates", Sleijpen and van
+ *                     der Vorst 1996); the search direction is kept.
  *
  * The paper gives no code for CG; these routines follow the standard
  * algorithm step by step.
@@ -370,5 +375,111 @@ done:
     if (inner_out) *inner_out = inner_total;
     if (true_relres_out) *true_relres_out = relres;
     free(s); free(r); free(t); free(bv); free(rs); free(w); free(ri); free(p); free(q);
+    return status;
+}
+
+/*
+ * Mixed-precision CG with reliable updates (no restarts).
+ *   S, B as in oracle_refine.  x = x0;  r = b - A x (FP64);  rs = float(S r)
+ *   w = 0;  r_in = rs;  p = rs;  rho = r_in.r_in;  m = ||rs||;  c = ||r|| / ||rs||
+ *   repeat (at most max_iter steps):
+ *       q = B p;  alpha = rho / (p.q)            (p.q <= 0: breakdown)
+ *       w += alpha p;  r_in -= alpha q;  rho' = r_in.r_in
+ *       if sqrt(rho') <= delta m  or  c sqrt(rho') <= tol ||b||:      (reliable update)
+ *           x += S w (FP64);  w = 0;  r = b - A x (FP64)
+ *           stop when ||r|| <= tol ||b||;  stop (stagnation) when ||r|| did not
+ *             decrease since the previous update
+ *           r_in = float(S r);  rho' = r_in.r_in;  m = ||r_in||;  c = ||r|| / ||r_in||
+ *       beta = rho' / rho;  rho = rho';  p = r_in + beta p
+ * Vectors w, r_in, p, q are float, products float, dot products FP64 (as in
+ * oracle_refine).  Returns 0 converged, 1 not converged (max_iter), 2 breakdown or
+ * stagnation; updates_out counts reliable updates, iters_out CG steps.
+ */
+int oracle_refine_reliable(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                           const double* b, double* x, double tol, double delta, int max_iter,
+                           int storage, int* updates_out, int* iters_out, double* true_relres_out) {
+    int64_t nnz = rowptr[n];
+    double* s = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    float* bv = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    float* w = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* ri = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* p = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* q = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    int status = 1, updates = 0, iters = 0;
+    double relres = 0.0, bnorm, rho, m, c, prev;
+    diagonal(n, rowptr, colind, val, t);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(t[i] > 0.0)) { status = 2; goto done; }
+        s[i] = 1.0 / sqrt(t[i]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            float f = (float)(s[i] * val[k] * s[colind[k]]);
+            bv[k] = storage == 1 ? round_bf16(f) : f;
+        }
+    bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        status = 0;
+        goto done;
+    }
+    /* true residual, scaled and rounded: the start and every reliable update */
+    oracle_csr_spmv(n, rowptr, colind, val, x, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    relres = sqrt(dot(n, r, r)) / bnorm;
+    if (relres <= tol) { status = 0; goto done; }
+    for (int64_t i = 0; i < n; ++i) {
+        ri[i] = (float)(s[i] * r[i]);
+        w[i] = 0.0f;
+        p[i] = ri[i];
+    }
+    rho = dot_f(n, ri, ri);
+    m = sqrt(rho);
+    c = relres * bnorm / m;
+    prev = relres;
+    while (iters < max_iter) {
+        spmv_f32(n, rowptr, colind, bv, p, q);
+        double pq = dot_f(n, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = 2; goto done; }
+        float alpha = (float)(rho / pq);
+        for (int64_t i = 0; i < n; ++i) w[i] = w[i] + alpha * p[i];
+        for (int64_t i = 0; i < n; ++i) ri[i] = ri[i] - alpha * q[i];
+        ++iters;
+        double rho_new = dot_f(n, ri, ri);
+        if (!isfinite(rho_new)) { status = 2; goto done; }
+        if (sqrt(rho_new) <= delta * m || c * sqrt(rho_new) <= tol * bnorm) {
+            ++updates;
+            for (int64_t i = 0; i < n; ++i) {
+                x[i] = x[i] + s[i] * (double)w[i];
+                w[i] = 0.0f;
+            }
+            oracle_csr_spmv(n, rowptr, colind, val, x, t);
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+            relres = sqrt(dot(n, r, r)) / bnorm;
+            if (relres <= tol) { status = 0; goto done; }
+            if (!(relres < prev)) { status = 2; goto done; }
+            prev = relres;
+            for (int64_t i = 0; i < n; ++i) ri[i] = (float)(s[i] * r[i]);
+            rho_new = dot_f(n, ri, ri);
+            m = sqrt(rho_new);
+            c = relres * bnorm / m;
+        }
+        float beta = (float)(rho_new / rho);
+        rho = rho_new;
+        for (int64_t i = 0; i < n; ++i) p[i] = ri[i] + beta * p[i];
+    }
+    /* iteration limit: fold in the last correction and report the true residual */
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + s[i] * (double)w[i];
+    oracle_csr_spmv(n, rowptr, colind, val, x, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    relres = sqrt(dot(n, r, r)) / bnorm;
+    status = relres <= tol ? 0 : 1;
+done:
+    if (updates_out) *updates_out = updates;
+    if (iters_out) *iters_out = iters;
+    if (true_relres_out) *true_relres_out = relres;
+    free(s); free(r); free(t); free(bv); free(w); free(ri); free(p); free(q);
     return status;
 }

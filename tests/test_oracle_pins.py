@@ -405,3 +405,55 @@ def test_tiles_reconstruct_columns_and_are_greedy(maker):
             nxt, _, _ = cols_of(first + count, 1)                        # would break a limit
             union = np.union1d(real, nxt[nxt >= 0])
             assert count == max_slices or len(union) > max_cols
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_reliable_refinement_reaches_dense_solution(storage):
+    p = fegen.cube_laplace(7, 31)
+    b = fegen.random_vector(p.n_rows, 32)
+    x, info = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10, storage=storage)
+    assert info["status"] == "converged" and info["true_relres"] <= 1e-10
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= np.linalg.cond(A) * 1e-10
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1.01e-10   # recomputed densely
+    # about log(1e-10) / log(delta) replacements
+    assert 8 <= info["updates"] <= 16
+
+
+def test_reliable_refinement_keeps_the_krylov_space():
+    """No restarts: the float CG with residual replacement needs close to as many steps
+    as FP64 Jacobi-PCG (the same method in exact arithmetic, since CG on S A S is
+    Jacobi-PCG on A; float rounding delays it somewhat), while restarted refinement,
+    at any inner tolerance, needs clearly more."""
+    p = fegen.cube_elasticity(6, 33)
+    b = fegen.random_vector(p.n_rows, 34)
+    _, rel = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    _, pcg = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    assert rel["status"] == "converged" and pcg["status"] == "converged"
+    assert pcg["iters"] <= rel["iters"] <= 1.3 * pcg["iters"] + 5
+    for inner_tol in (1e-1, 1e-2, 1e-3):
+        _, rst = oracle.refine(p.rowptr, p.colind, p.values, b, tol=1e-10, inner_tol=inner_tol)
+        assert rst["inner"] > 1.3 * rel["iters"]
+
+
+def test_reliable_refinement_special_cases():
+    # diagonal matrix: B = S A S = I up to rounding, so CG needs a step per update
+    n = 50
+    rowptr = np.arange(n + 1)
+    colind = np.arange(n, dtype=np.int32)
+    vals = np.linspace(1.0, 100.0, n)
+    b = fegen.random_vector(n, 35)
+    x, info = oracle.refine_reliable(rowptr, colind, vals, b, tol=1e-12)
+    assert info["status"] == "converged" and info["iters"] <= 4
+    assert np.allclose(x, b / vals, rtol=1e-11, atol=0)
+    # b = 0 gives x = 0 at once; a non-positive diagonal is rejected
+    x0, i0 = oracle.refine_reliable(rowptr, colind, vals, np.zeros(n))
+    assert i0["status"] == "converged" and i0["iters"] == 0 and not x0.any()
+    _, bad = oracle.refine_reliable(rowptr, colind, -vals, b)
+    assert bad["status"] == "breakdown"
+    # iteration limit
+    p = fegen.cube_laplace(8, 36)
+    bb = fegen.random_vector(p.n_rows, 37)
+    _, lim = oracle.refine_reliable(p.rowptr, p.colind, p.values, bb, tol=1e-12, max_iter=3)
+    assert lim["status"] == "not_converged" and lim["iters"] == 3
