@@ -391,6 +391,8 @@ def main():
                                                         flags=fs.FESPMV_CG_SINGLE_REDUCTION)
                 extra["cg_f32_refine"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                   fs.FESPMV_CG_F32_REFINE)
+                extra["cg_f32_reliable"] = bench_cg(fs, torch, A, p, args.cg_solves,
+                                                    fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
             if args.shell:
                 extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
@@ -534,7 +536,7 @@ def bench_serving(fs, torch, args):
             if now < a:
                 time.sleep(a - now)
             tickets.append(fs.srv_submit(S, ids[m], rhs[m][k], tol=tol,
-                                         precision=fs.FESPMV_CG_F32_REFINE))
+                                         precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE))
         fs.srv_cancel_queued(S)
         lat, served = [], 0
         for t in tickets:
@@ -546,7 +548,7 @@ def bench_serving(fs, torch, args):
         st = fs.srv_get_stats(S)
         fs.srv_destroy(S)
         out = summarize(trace, lat, served, elapsed)
-        out.update({"precision": "f32_refine", "peak_active": st["peak_active"],
+        out.update({"precision": "f32_reliable", "peak_active": st["peak_active"],
                     "peak_workspace_gb": round(st["peak_workspace_bytes"] / 2 ** 30, 2)})
         return out
 
@@ -621,9 +623,10 @@ def bench_shell(fs, torch, args):
            "f64_spmv_gbs": round((nnz * 12 + n * 16) / t64 / 1e9, 1),
            "f32_spmv_gbs": round((nnz * 8 + n * 8) / t32 / 1e9, 1),
            "bf16_spmv_gbs": round((nnz * 6 + n * 8) / t16 / 1e9, 1)}
-    for name, prec in (("cg_f64", fs.FESPMV_CG_F64), ("cg_f32_refine", fs.FESPMV_CG_F32_REFINE),
-                       ("cg_bf16_refine", fs.FESPMV_CG_BF16_REFINE)):
-        out[name] = bench_cg(fs, torch, A, p, 2, prec)
+    for name, prec, fl in (("cg_f64", fs.FESPMV_CG_F64, 0), ("cg_f32_refine", fs.FESPMV_CG_F32_REFINE, 0),
+                           ("cg_f32_reliable", fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE),
+                           ("cg_bf16_reliable", fs.FESPMV_CG_BF16_REFINE, fs.FESPMV_CG_RELIABLE)):
+        out[name] = bench_cg(fs, torch, A, p, 2, prec, flags=fl)
     fs.spmv_destroy(A)
     return out
 
@@ -748,7 +751,9 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
         assert res["status"] == 0, res
     lat_ms = sorted(1e3 * t for t in lat)
     return {"precision": name, "tol": 1e-10,
-            "variant": "single_reduction" if flags & fs.FESPMV_CG_SINGLE_REDUCTION else "textbook",
+            "variant": ("single_reduction" if flags & fs.FESPMV_CG_SINGLE_REDUCTION else
+                        "reliable_updates" if flags & fs.FESPMV_CG_RELIABLE else
+                        "restarted_refinement" if precision else "textbook"),
             "solves": n_solves, "outer": outer[0], "true_relres_max": max(rel),
             "solves_per_s": round(n_solves / sum(lat), 3),
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),

@@ -260,6 +260,7 @@ int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
 #define FESPMV_CG_X0           4  /* flag: x holds the initial guess (otherwise x0 = 0) */
 #define FESPMV_CG_NO_PRECOND   8  /* flag: plain CG instead of Jacobi-PCG */
 #define FESPMV_CG_SINGLE_REDUCTION 16 /* flag: single-reduction (Chronopoulos-Gear) PCG, below */
+#define FESPMV_CG_RELIABLE     32 /* flag: refined precisions without restarts (reliable updates), below */
 
 typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2; 0 = 1e-10 */
@@ -322,7 +323,18 @@ typedef struct {
  *           the product, FP64 dot products, until ||B w - S r|| <= inner_tol ||S r||
  *           or max_iter inner steps;  x += S w in FP64.
  * diag(B) = 1, so Jacobi on B is the identity.  iters counts inner steps, outer
- * the FP64 residual steps.  A refinement step that does not reduce ||r|| ends
+ * the FP64 residual steps.
+ *
+ * flag FESPMV_CG_RELIABLE (refined precisions only, else UNSUPPORTED): one inner
+ * CG without restarts.  Each time the inner residual has fallen by inner_tol
+ * (default 0.1 with this flag) (or
+ * its estimate ||r|| ~ c ||r_in||, c = ||r|| / ||S r|| at the last update, reaches
+ * tol ||b||) the correction is folded in, x += S w, r = b - A x is recomputed in
+ * FP64 and replaces the inner residual (r_in = S r in float), and the search
+ * direction is kept: p = r_in + beta p with beta = r_in.r_in / rho ("reliable
+ * updates", Sleijpen and van der Vorst 1996).  The solve stops at the first update
+ * whose ||r|| <= tol ||b||, or with NOT_CONVERGED when ||r|| did not decrease since
+ * the previous update or after max_iter inner steps in total.  outer counts updates.  A refinement step that does not reduce ||r|| ends
  * the solve with FESPMV_ERR_NOT_CONVERGED (the low-precision operator is too
  * far from A for this system: contraction needs cond(B) * u_storage < 1).  Returns FESPMV_OK, FESPMV_ERR_NOT_CONVERGED,
  * FESPMV_ERR_BREAKDOWN (p.Ap <= 0 -- delta - beta gamma / alpha_old <= 0 in the

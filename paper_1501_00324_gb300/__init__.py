@@ -56,6 +56,7 @@ FESPMV_CG_BF16_REFINE = 2
 FESPMV_CG_X0 = 4
 FESPMV_CG_NO_PRECOND = 8
 FESPMV_CG_SINGLE_REDUCTION = 16
+FESPMV_CG_RELIABLE = 32
 
 
 class FespmvError(RuntimeError):

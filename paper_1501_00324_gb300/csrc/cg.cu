@@ -584,13 +584,18 @@ __global__ void __launch_bounds__(256, 4) cg32_pupdate(int64_t n, float* __restr
 
 // Outer step: r = b - Ax (FP64; Ax = q or 0), rhs = float(S r); inner state
 // w = 0, r_in = p = rhs.  Sums: r.r (outer), rhs.rhs (inner rho), b.b.
+// Reliable updates (keep_p): the same residual replaces the inner recurrence
+// residual but p is kept; beta = rho' / rho for the p update that follows, the
+// inner step count runs on, and the inner stop threshold is the smaller
+// reduction of delta^2 rho' and the estimate c^2 rho' <= tol^2 b.b, where
+// c = ||r|| / ||S r|| (the scaled residual's norm against the true one).
 __global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* __restrict__ b,
                                                        const double* __restrict__ q,
                                                        const double* __restrict__ scale,
                                                        float* __restrict__ w, float* __restrict__ r_in,
                                                        float* __restrict__ p, double tol2,
-                                                       double inner_tol2, double* partials,
-                                                       CgScalars* sc) {
+                                                       double inner_tol2, int reliable, int keep_p,
+                                                       double* partials, CgScalars* sc) {
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -599,18 +604,23 @@ __global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* 
         const float rs = (float)(scale[i] * ri);
         w[i] = 0.0f;
         r_in[i] = rs;
-        p[i] = rs;
+        if (!keep_p) p[i] = rs;
         v[0] = fma(ri, ri, v[0]);
         v[1] = fma((double)rs, (double)rs, v[1]);
         v[2] = fma(bi, bi, v[2]);
     }
     if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->true_rr = v[0];
+        if (keep_p) sc->beta = v[1] / sc->rho;
         sc->rho = v[1];
         sc->bb = v[2];
         sc->thresh2 = tol2 * v[2];
-        sc->thresh_in = inner_tol2 * v[1];
-        sc->iters_in = 0;
+        if (reliable) {
+            sc->thresh_in = fmax(inner_tol2 * v[1], v[0] > 0.0 ? tol2 * v[2] * v[1] / v[0] : 0.0);
+        } else {
+            sc->thresh_in = inner_tol2 * v[1];
+            sc->iters_in = 0;
+        }
         if (!isfinite(v[0]) || !isfinite(v[1])) sc->status = CG_BREAKDOWN;
         else if (v[0] <= sc->thresh2) sc->status = CG_CONVERGED;
         else sc->status = CG_RUNNING;
@@ -969,17 +979,21 @@ int normalize_options(cg_options& o) {
     if (o.max_restarts < 0) o.max_restarts = 0;
     if (o.check_every == 0) o.check_every = 16;
     if (o.max_outer == 0) o.max_outer = 60;
-    if (o.inner_tol == 0.0) o.inner_tol = 1e-2;
+    if (o.inner_tol == 0.0) o.inner_tol = (o.flags & FESPMV_CG_RELIABLE) ? 1e-1 : 1e-2;
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.check_every > 4096 ||
         o.precision < FESPMV_CG_F64 || o.precision > FESPMV_CG_BF16_REFINE || o.max_outer < 0 ||
         !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
         (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND |
-                     FESPMV_CG_SINGLE_REDUCTION))) {
+                     FESPMV_CG_SINGLE_REDUCTION | FESPMV_CG_RELIABLE))) {
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
     }
     if ((o.flags & FESPMV_CG_SINGLE_REDUCTION) && o.precision != FESPMV_CG_F64) {
         set_error("FESPMV_CG_SINGLE_REDUCTION applies to FESPMV_CG_F64 only");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    if ((o.flags & FESPMV_CG_RELIABLE) && o.precision == FESPMV_CG_F64) {
+        set_error("FESPMV_CG_RELIABLE applies to the refined precisions only");
         return FESPMV_ERR_UNSUPPORTED;
     }
     return FESPMV_OK;
@@ -1047,10 +1061,15 @@ static int enqueue_init(CgRun& r, bool ax) {
 static int enqueue_residual(CgRun& r, bool ax) {
     CgWork* w = r.w;
     int rc;
+    const int reliable = (r.o.flags & FESPMV_CG_RELIABLE) ? 1 : 0;
+    const int keep_p = reliable && r.outer > 0;
     if (ax && (rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
     refine_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, ax ? w->q : nullptr, r.A->d_scale, w->w32,
                                                   w->r32, w->p32, r.o.tol * r.o.tol,
-                                                  r.o.inner_tol * r.o.inner_tol, w->partials, w->sc);
+                                                  r.o.inner_tol * r.o.inner_tol, reliable, keep_p,
+                                                  w->partials, w->sc);
+    // reliable update: the kept direction takes the replaced residual, p = r_in + beta p
+    if (keep_p) cg32_pupdate<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->p32, w->r32, w->sc);
     FESPMV_CUDA(cudaGetLastError());
     r.phase = PH_RES_WAIT;
     return enqueue_status(r, 0);
@@ -1186,6 +1205,7 @@ int run_step(CgRun& r, bool block, bool* progress) {
             }
             if (h.status == CG_CONVERGED || h.status == CG_BREAKDOWN) return finish(r, h.status);
             if (r.outer >= r.o.max_outer) return finish(r, CG_MAXITER);
+            if ((r.o.flags & FESPMV_CG_RELIABLE) && h.iters >= r.o.max_iter) return finish(r, CG_MAXITER);
             if (!(h.true_rr < r.prev)) {  // no progress: the low-precision operator is too far from A
                 set_error("refinement stagnated: ||b - A x|| did not decrease");
                 return finish(r, CG_MAXITER);

@@ -129,3 +129,80 @@ def test_f32_refinement_full_size_elasticity_64():
     assert res["status"] == 0, res
     r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
     assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
+
+
+REL = fs.FESPMV_CG_RELIABLE
+
+
+@pytest.mark.parametrize("name", ["cube_laplace_20", "elasticity_8", "shell_5x16x24"])
+@pytest.mark.parametrize("fmt", [0, 1, 3])
+def test_reliable_refinement_matches_oracle(name, fmt):
+    """FP32 CG with reliable updates against the oracle's: true residual, solution,
+    step and update counts (float sums in another order: counts within 10 % + 5)."""
+    p = {"cube_laplace_20": lambda: fegen.cube_laplace(20, 1501),
+         "elasticity_8": lambda: fegen.cube_elasticity(8, 74),
+         "shell_5x16x24": lambda: fegen.shell_laplace(5, 16, 24, 75)}[name]()
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, fs.FESPMV_PREC_F32, **FORMATS[fmt])
+    x, res = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=REL, inner_tol=0.1)
+    assert res["status"] == 0, res
+    r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
+    xo, info = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10, delta=0.1)
+    assert info["status"] == "converged"
+    assert abs(res["iters"] - info["iters"]) <= 0.1 * info["iters"] + 5
+    assert abs(res["outer"] - info["updates"]) <= 3
+    from test_oracle_pins import dense_of
+    if p.n_rows <= 3000:
+        cond = np.linalg.cond(dense_of(p.rowptr, p.colind, p.values, p.n_rows))
+        assert np.linalg.norm(x - xo) <= cond * 2e-10 * np.linalg.norm(xo)
+    # fewer steps than restarted refinement on the same system
+    _, rr = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE)
+    assert res["iters"] < rr["iters"]
+
+
+def test_reliable_refinement_limits_and_options():
+    p = fegen.cube_laplace(10, 76)
+    b = fegen.random_vector(p.n_rows, 77)
+    A = make(p, fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+    x, res = solve(A, b, tol=1e-12, precision=fs.FESPMV_CG_F32_REFINE, flags=REL, max_iter=7)
+    assert res["status"] == fs.FESPMV_ERR_NOT_CONVERGED and res["iters"] == 7
+    # the same first 7 steps as the oracle's (no update reached yet at delta = 1e-6)
+    x7, res7 = solve(A, b, tol=1e-12, precision=fs.FESPMV_CG_F32_REFINE, flags=REL, max_iter=7,
+                     inner_tol=1e-6)
+    xo, io = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-12, delta=1e-6, max_iter=7)
+    assert io["status"] == "not_converged" and io["updates"] == 0
+    assert np.linalg.norm(x7 - xo) <= 1e-5 * np.linalg.norm(xo)
+    # BF16 with reliable updates (default delta 0.1) on a small system converges, as the
+    # oracle's does; with delta 0.01 both stop without converging (B in bfloat16 is too
+    # far from S A S for updates that rare)
+    xb, rb = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_BF16_REFINE, flags=REL)
+    _, ob = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10, delta=0.1, storage="bf16")
+    assert rb["status"] == 0 and ob["status"] == "converged"
+    _, rb2 = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_BF16_REFINE, flags=REL, inner_tol=1e-2,
+                   max_iter=3000)
+    _, ob2 = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10, delta=1e-2, storage="bf16",
+                                    max_iter=3000)
+    assert rb2["status"] != 0 and ob2["status"] != "converged"
+    # b = 0; FP64 refuses the flag; graph sizes reach the same iterate
+    z = torch.zeros(p.n_rows, dtype=torch.float64, device="cuda")
+    xz = torch.ones_like(z)
+    assert fs.cg_solve(A, z, xz, precision=fs.FESPMV_CG_F32_REFINE, flags=REL)["status"] == 0
+    assert not xz.any().item()
+    with pytest.raises(fs.FespmvError):
+        solve(A, b, precision=fs.FESPMV_CG_F64, flags=REL)
+    xs = [solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=REL, check_every=c)[0]
+          for c in (1, 16)]
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_reliable_refinement_full_size_elasticity_64():
+    p = fegen.cube_elasticity(64, 1502)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, fs.FESPMV_PREC_F32, sigma=1024)
+    x, res = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=REL, inner_tol=0.1)
+    assert res["status"] == 0, res
+    r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
