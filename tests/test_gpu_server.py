@@ -44,18 +44,21 @@ def test_results_in_the_mix_equal_results_alone():
         m = int(rng.integers(len(ps)))
         b = fegen.random_vector(ps[m].n_rows, 1000 + k)
         tol = [1e-8, 1e-10][k % 2]
-        prec = [fs.FESPMV_CG_F64, fs.FESPMV_CG_F32_REFINE][(k // 2) % 2]
-        reqs.append((m, b, tol, prec))
-    tickets = [fs.srv_submit(S, ids[m], b, tol=tol, precision=prec) for (m, b, tol, prec) in reqs]
-    results = [fs.srv_poll(S, t, ps[m].n_rows) for t, (m, _, _, _) in zip(tickets, reqs)]
+        # FP64, restarted FP32 refinement, FP32 with reliable updates, single-reduction FP64
+        prec, fl = [(fs.FESPMV_CG_F64, 0), (fs.FESPMV_CG_F32_REFINE, 0),
+                    (fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE),
+                    (fs.FESPMV_CG_F64, fs.FESPMV_CG_SINGLE_REDUCTION)][(k // 2) % 4]
+        reqs.append((m, b, tol, prec, fl))
+    tickets = [fs.srv_submit(S, ids[m], b, tol=tol, precision=prec, flags=fl) for (m, b, tol, prec, fl) in reqs]
+    results = [fs.srv_poll(S, t, ps[m].n_rows) for t, (m, *_rest) in zip(tickets, reqs)]
     st = fs.srv_get_stats(S)
     assert st["completed"] == 24 and st["peak_active"] > 1
-    for (m, b, tol, prec), (rc, x, res, tm) in zip(reqs, results):
+    for (m, b, tol, prec, fl), (rc, x, res, tm) in zip(reqs, results):
         assert rc == 0, res
         p = ps[m]
         r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
         assert np.linalg.norm(r) <= tol * 1.01 * np.linalg.norm(b)
-        xa, ra = alone(mats[m], b, tol=tol, precision=prec)
+        xa, ra = alone(mats[m], b, tol=tol, precision=prec, flags=fl)
         assert np.array_equal(x.view(np.uint64), xa.view(np.uint64))
         assert res["iters"] == ra["iters"] and res["outer"] == ra["outer"]
         assert tm["t_total_s"] >= tm["t_solve_s"] > 0
