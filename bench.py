@@ -364,6 +364,15 @@ def main():
                 fg()
                 extra["fe_global_gather_gbs"] = round(mb / (back_to_back(fg, args.steps) * 1e-3) / 1e9, 1)
                 fs.spmv_destroy(G)
+            # float-pair products (FP32 pipe, FP64 fallback; within the 1e-12 bound): the
+            # same tiled layout off the FP64 pipe -- reported beside the FP64 headline
+            if info["n_tiles"] > 0 and args.kernel == "f64":
+                Fd = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                                    vec=args.vec, threshold=args.threshold, precisions=fs.FESPMV_PREC_DF64)
+                ff = lambda: fs.spmv_apply(Fd, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+                ff()
+                extra["fe_float_pair_gbs"] = round(mb / (back_to_back(ff, args.steps) * 1e-3) / 1e9, 1)
+                fs.spmv_destroy(Fd)
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
                 B = fs.spmv_create(p.rowptr, p.colind, p.values, format=fs.FESPMV_FMT_CSR,
@@ -653,33 +662,38 @@ def bench_batched(fs, torch, args):
     bs = [fegen.random_vector(p.n_rows, 5000 + j) for j, p in enumerate(ps)]
     bd = torch.from_numpy(np.concatenate(bs)).cuda()
     xd = torch.zeros_like(bd)
-    fs.batch_cg_solve(B, bd, xd, tol=1e-10)            # warm: graph capture
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(3):
-        xd.zero_()
+    def batch_time(flags):
+        fs.batch_cg_solve(B, bd, xd, tol=1e-10, flags=flags)            # warm: graph capture
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, res = fs.batch_cg_solve(B, bd, xd, tol=1e-10)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-    assert rc == 0
-    batch_s = min(times)
+        times = []
+        for _ in range(3):
+            xd.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, res = fs.batch_cg_solve(B, bd, xd, tol=1e-10, flags=flags)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        assert rc == 0
+        return min(times), res
+
+    batch_rel_s, res_rel = batch_time(fs.FESPMV_CG_RELIABLE)
+    batch_s, res = batch_time(0)
     info = fs.batch_get_info(B)
     fs.batch_destroy(B)
     seq = {}
-    for name, prec in (("f32_refine", fs.FESPMV_CG_F32_REFINE), ("f64", fs.FESPMV_CG_F64)):
+    for name, prec, fl in (("f32_reliable", fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE),
+                           ("f32_refine", fs.FESPMV_CG_F32_REFINE, 0), ("f64", fs.FESPMV_CG_F64, 0)):
         mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=1024,
                                precisions=fs.FESPMV_PREC_F32) for p in ps]
         bds = [torch.from_numpy(b).cuda() for b in bs]
         xs = [torch.zeros_like(b) for b in bds]
         for A, b, x in zip(mats, bds, xs):              # warm: graphs per handle
-            fs.cg_solve(A, b, x, tol=1e-10, precision=prec)
+            fs.cg_solve(A, b, x, tol=1e-10, precision=prec, flags=fl)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for A, b, x in zip(mats, bds, xs):
             x.zero_()
-            fs.cg_solve(A, b, x, tol=1e-10, precision=prec)
+            fs.cg_solve(A, b, x, tol=1e-10, precision=prec, flags=fl)
         torch.cuda.synchronize()
         seq[name] = round(time.perf_counter() - t0, 4)
         for A in mats:
@@ -687,11 +701,15 @@ def bench_batched(fs, torch, args):
     return {"meshes": len(ps), "rows_total": info["n_rows"], "padded_rows": info["padded_rows"],
             "autotune": {k: tune[k] for k in ("vec", "threshold", "block", "best_us", "tried")},
             "nnz_total": info["nnz"], "gen_s": round(gen_s, 1), "create_s": round(create_s, 1),
-            "batched_s": round(batch_s, 4), "solves_per_s": round(len(ps) / batch_s, 1),
-            "max_outer": max(r["outer"] for r in res), "max_inner_iters": max(r["iters"] for r in res),
+            "batched_reliable_s": round(batch_rel_s, 4),
+            "solves_per_s": round(len(ps) / batch_rel_s, 1),
+            "max_updates": max(r["outer"] for r in res_rel), "max_iters": max(r["iters"] for r in res_rel),
+            "batched_restarted_s": round(batch_s, 4),
+            "restarted_max_outer": max(r["outer"] for r in res),
+            "restarted_max_inner_iters": max(r["iters"] for r in res),
             "one_after_another_s": seq,
-            "speedup_vs_sequential_f32": round(seq["f32_refine"] / batch_s, 2),
-            "speedup_vs_sequential_f64": round(seq["f64"] / batch_s, 2)}
+            "speedup_vs_sequential_f32_reliable": round(seq["f32_reliable"] / batch_rel_s, 2),
+            "speedup_vs_sequential_f64": round(seq["f64"] / batch_rel_s, 2)}
 
 
 def profile_piece(fs, torch, A, p, xp, args):

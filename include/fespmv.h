@@ -411,6 +411,9 @@ int batch_spmv(fespmv_batch_t B, const double* x, double* y, fespmv_stream_t str
  * refinement step runs one batched FP64 residual, then inner FP32 iterations
  * of all problems still refining, as CUDA graphs of check_every iterations
  * (five launches per iteration for the whole batch), then x_j += S w_j.
+ * With FESPMV_CG_RELIABLE each problem keeps its search direction across the
+ * FP64 residual steps (reliable updates, as in cg_solve; inner_tol defaults
+ * to 0.1 and max_iter bounds each problem's total inner steps).
  * Scalars are per problem; finished problems are skipped by every kernel.
  *   b, x     concatenated vectors (device, or host with FESPMV_IO_HOST);
  *            x: initial guess with FESPMV_CG_X0, else zero; overwritten

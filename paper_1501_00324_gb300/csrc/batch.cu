@@ -188,17 +188,18 @@ __global__ void __launch_bounds__(256) b_residual(int64_t np, const double* __re
                                                   float* __restrict__ p32,
                                                   const int32_t* __restrict__ warp_prob,
                                                   double* __restrict__ part, int64_t ngroups,
-                                                  const BScal* __restrict__ sc) {
+                                                  int reliable, const BScal* __restrict__ sc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
     const int64_t g = i >> 5;
-    if (sc[warp_prob[g]].status_out != CG_RUNNING) return;
+    const BScal& s = sc[warp_prob[g]];
+    if (s.status_out != CG_RUNNING) return;
     const double bi = b[i];
     const double ri = q ? bi - q[i] : bi;
     const float rs = (float)(scale[i] * ri);
     w[i] = 0.0f;
     r32[i] = rs;
-    p32[i] = rs;
+    if (!(reliable && s.outer > 0)) p32[i] = rs;   // reliable updates keep the direction
     const double c0 = warp_sum(ri * ri);
     const double c1 = warp_sum((double)rs * (double)rs);
     const double c2 = warp_sum(bi * bi);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256) b_residual(int64_t np, const double* __re
 
 __global__ void b_finalize_res(const double* __restrict__ part, int64_t ngroups,
                                const int64_t* __restrict__ pwarp, BScal* sc, double tol2,
-                               double in2) {
+                               double in2, int reliable) {
     const int j = blockIdx.x;
     if (sc[j].status_out != CG_RUNNING) return;
     const double rr = block_range_sum(part, pwarp[j], pwarp[j + 1]);
@@ -226,12 +227,18 @@ __global__ void b_finalize_res(const double* __restrict__ part, int64_t ngroups,
         if (!isfinite(rr) || !isfinite(rhs2)) s.status_out = CG_BREAKDOWN;
         else if (rr <= s.thresh2) s.status_out = CG_CONVERGED;
         else if (s.outer >= s.max_outer) s.status_out = CG_MAXITER;
+        else if (reliable && s.iters >= s.max_iter) s.status_out = CG_MAXITER;
         else if (!(rr < s.prev)) s.status_out = CG_MAXITER;   // stagnation
         else {
             s.prev = rr;
+            if (reliable) {   // replace the residual, keep p: p = r_in + beta p follows
+                s.beta = s.outer > 0 ? rhs2 / s.rho : 0.0;
+                s.thresh_in = fmax(in2 * rhs2, rr > 0.0 ? tol2 * bb * rhs2 / rr : 0.0);
+            } else {
+                s.thresh_in = in2 * rhs2;
+                s.iters_in = 0;
+            }
             s.rho = rhs2;
-            s.thresh_in = in2 * rhs2;
-            s.iters_in = 0;
             s.status_in = CG_RUNNING;
         }
     }
@@ -584,13 +591,18 @@ static int batch_solve_impl(fespmv_batch* B, const double* b, double* x, const c
     }
     FESPMV_CUDA(cudaMemcpyAsync(B->sc, B->h_sc, sizeof(BScal) * B->count, cudaMemcpyHostToDevice, s));
     const double tol2 = o.tol * o.tol, in2 = o.inner_tol * o.inner_tol;
+    const int reliable = (o.flags & FESPMV_CG_RELIABLE) ? 1 : 0;
     const int64_t max_graphs = (int64_t)o.max_iter / o.check_every + 3;
     for (int step = 0;; ++step) {
         const bool ax = x0 || step > 0;
         if (ax && (rc = launch_spmv(M, B->x, B->q, s))) return rc;
         b_residual<<<grid_for(np, 256), 256, 0, s>>>(np, B->b, ax ? B->q : nullptr, M->d_scale, B->w32,
-                                                     B->r32, B->p32, B->d_warp_prob, B->part, ng, B->sc);
-        b_finalize_res<<<B->count, 256, 0, s>>>(B->part, ng, B->d_pwarp, B->sc, tol2, in2);
+                                                     B->r32, B->p32, B->d_warp_prob, B->part, ng, reliable,
+                                                     B->sc);
+        b_finalize_res<<<B->count, 256, 0, s>>>(B->part, ng, B->d_pwarp, B->sc, tol2, in2, reliable);
+        // reliable updates: the kept directions take the replaced residuals (beta = 0 at the
+        // first step, where p = r_in already)
+        if (reliable) b_pupdate32<<<grid_for(np, 256), 256, 0, s>>>(np, B->p32, B->r32, B->d_warp_prob, B->sc);
         FESPMV_CUDA(cudaGetLastError());
         if ((rc = read_bsc(B, s))) return rc;
         bool any = false;

@@ -192,6 +192,41 @@ __global__ void __launch_bounds__(256) cg_spmv_dot_df(const uint4* __restrict__ 
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
 }
 
+template <int V, int U>
+__global__ void __launch_bounds__(kTiledBlock) cg_spmv_dot_tiled_df(const uint4* __restrict__ meta,
+                                                                    const uint16_t* __restrict__ lidx,
+                                                                    const float2* __restrict__ vdf,
+                                                                    const double* __restrict__ val,
+                                                                    const int32_t* __restrict__ col,
+                                                                    const int4* __restrict__ tiles,
+                                                                    const int32_t* __restrict__ dict,
+                                                                    const double* __restrict__ p,
+                                                                    const float2* __restrict__ pdf,
+                                                                    double* __restrict__ q, int64_t n,
+                                                                    int64_t n_tiles, double* partials,
+                                                                    CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    float2* xs = reinterpret_cast<float2*>(tile_smem);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int4 tl = stage_tile<float2>(tiles + t, dict, pdf, xs);
+        if (wid < tl.y) {
+            const uint4 m = meta[tl.x + wid];
+            const double sum = tiled_row_sum_df<V, U>(m, lidx, vdf, val, col, xs, p, lane);
+            const int lt = (int)m.w;
+            const int64_t row = (int64_t)m.z + (lane >> lt);
+            if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
+                q[row] = sum;
+                v[0] = fma(p[row], sum, v[0]);
+            }
+        }
+        __syncthreads();
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq(v[0], sc);
+}
+
 template <int L>
 __global__ void cg_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ p,
@@ -802,6 +837,14 @@ static void launch_spmv_dot_csr(const fespmv_mat* A, CgWork* w, cudaStream_t s) 
 template <int V>
 static void launch_spmv_dot_df(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     constexpr int U = (V == 4) ? 2 : 4;
+    if (A->tiled) {
+        const size_t smem = sizeof(float2) * (A->tile_dmax + 1);
+        const unsigned g = tiled_grid(A, cg_spmv_dot_tiled_df<V, U>, smem);
+        cg_spmv_dot_tiled_df<V, U><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_vdf, A->d_val,
+                                                                A->d_col, A->d_tiles, A->d_tdict, w->p, w->pdf,
+                                                                w->q, A->n, A->n_tiles, w->partials, w->sc);
+        return;
+    }
     cg_spmv_dot_df<V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, A->d_vdf, A->d_val, w->p,
                                                            w->pdf, w->q, A->n_slices, A->n,
                                                            w->partials, w->sc);

@@ -146,6 +146,7 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what);
 int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
 int launch_spmv_tiled(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
 int launch_spmv_low_tiled(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
+int launch_spmv_df_tiled(const fespmv_mat* A, const float2* xdf, const double* x, double* y, cudaStream_t s);
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
 unsigned grid_for(int64_t work, int block);

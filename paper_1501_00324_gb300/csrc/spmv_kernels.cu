@@ -242,6 +242,7 @@ static void launch_df(const fespmv_mat* A, const float2* xs, const double* x, do
 
 int launch_spmv_df(const fespmv_mat* A, const float2* xs, const double* x, double* y, cudaStream_t s) {
     if (A->n == 0) return FESPMV_OK;
+    if (A->tiled) return launch_spmv_df_tiled(A, xs, x, y, s);
     switch (A->vec) {
         case 1: launch_df<1>(A, xs, x, y, s); break;
         case 4: launch_df<4>(A, xs, x, y, s); break;

@@ -43,6 +43,43 @@ __global__ void __launch_bounds__(kTiledBlock) sliced_tiled(const uint4* __restr
     if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
 }
 
+// y = A x with float-pair products (FESPMV_PREC_DF64 handles), x pairs staged per tile.
+template <int V, int U>
+__global__ void __launch_bounds__(kTiledBlock) sliced_tiled_df(const uint4* __restrict__ meta,
+                                                               const uint16_t* __restrict__ lidx,
+                                                               const float2* __restrict__ vdf,
+                                                               const double* __restrict__ val,
+                                                               const int32_t* __restrict__ col,
+                                                               const int4* __restrict__ tiles,
+                                                               const int32_t* __restrict__ dict,
+                                                               const float2* __restrict__ xdf,
+                                                               const double* __restrict__ x,
+                                                               double* __restrict__ y, int64_t n) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    float2* xs = reinterpret_cast<float2*>(tile_smem);
+    const int4 tl = stage_tile<float2>(tiles + blockIdx.x, dict, xdf, xs);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid >= tl.y) return;
+    const uint4 m = meta[tl.x + wid];
+    const double sum = tiled_row_sum_df<V, U>(m, lidx, vdf, val, col, xs, x, lane);
+    const int lt = (int)m.w;
+    const int64_t row = (int64_t)m.z + (lane >> lt);
+    if ((lane & ((1 << lt) - 1)) == 0 && row < n) y[row] = sum;
+}
+
+int launch_spmv_df_tiled(const fespmv_mat* A, const float2* xdf, const double* x, double* y, cudaStream_t s) {
+    if (A->n == 0) return FESPMV_OK;
+    const size_t smem = sizeof(float2) * (size_t)(A->tile_dmax + 1);
+    const unsigned g = (unsigned)A->n_tiles;
+    switch (A->vec) {
+        case 1: sliced_tiled_df<1, 8><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_vdf, A->d_val, A->d_col, A->d_tiles, A->d_tdict, xdf, x, y, A->n); break;
+        case 4: sliced_tiled_df<4, 2><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_vdf, A->d_val, A->d_col, A->d_tiles, A->d_tdict, xdf, x, y, A->n); break;
+        default: sliced_tiled_df<2, 4><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, A->d_vdf, A->d_val, A->d_col, A->d_tiles, A->d_tdict, xdf, x, y, A->n); break;
+    }
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
 template <typename VT, int V>
 static void launch_tiled_t(const fespmv_mat* A, const VT* val, const typename SumOf<VT>::type* x,
                            typename SumOf<VT>::type* y, cudaStream_t s) {

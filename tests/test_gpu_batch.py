@@ -111,3 +111,30 @@ def test_batch_rejects_bad_input():
     with pytest.raises(fs.FespmvError) as e:
         fs.batch_create([(p.rowptr, p.colind, p.values, None, 1), (p.rowptr, bad, p.values, None, 1)])
     assert e.value.status == fs.FESPMV_ERR_BAD_CSR and "problem 1" in str(e.value)
+
+
+def test_batch_reliable_updates_match_single_solves():
+    """Reliable updates in the batch: every problem meets the tolerance (oracle residual),
+    takes about the steps of the oracle's reliable-update solve, and fewer steps than the
+    batch's restarted refinement."""
+    rng = np.random.default_rng(99)
+    sizes = np.exp(rng.uniform(np.log(200), np.log(6000), size=24))
+    ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 4000 + i)
+          for i, N in enumerate(sizes)] + [fegen.cube_elasticity(6, 4100), fegen.shell_laplace(4, 12, 16, 4101)]
+    B = as_batch(ps, sigma=256)
+    bs = [fegen.random_vector(p.n_rows, 5000 + j) for j, p in enumerate(ps)]
+    b = np.concatenate(bs)
+    x = np.zeros_like(b)
+    rc, res = fs.batch_cg_solve(B, b, x, tol=1e-10, flags=fs.FESPMV_CG_RELIABLE)
+    assert rc == 0
+    x2 = np.zeros_like(b)
+    rc2, res2 = fs.batch_cg_solve(B, b, x2, tol=1e-10)
+    assert rc2 == 0
+    for j, p in enumerate(ps):
+        xj = x[B.offsets[j]:B.offsets[j + 1]]
+        r = bs[j] - oracle.csr_spmv(p.rowptr, p.colind, p.values, xj)
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bs[j])
+        _, io = oracle.refine_reliable(p.rowptr, p.colind, p.values, bs[j], tol=1e-10, delta=0.1)
+        assert io["status"] == "converged"
+        assert abs(res[j]["iters"] - io["iters"]) <= 0.1 * io["iters"] + 5
+    assert sum(r["iters"] for r in res) < sum(r["iters"] for r in res2)

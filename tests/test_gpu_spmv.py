@@ -78,6 +78,7 @@ KERNELS = [
     dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, precisions=fs.FESPMV_PREC_DF64),
     dict(format=fs.FESPMV_FMT_SLICED, vec=1, sigma=64, threshold=2, precisions=fs.FESPMV_PREC_DF64),
     dict(format=fs.FESPMV_FMT_SLICED, vec=4, sigma=10**9, threshold=4, precisions=fs.FESPMV_PREC_DF64),
+    dict(format=fs.FESPMV_FMT_SLICED, vec=2, sigma=256, precisions=fs.FESPMV_PREC_DF64, tiles=-1),
 ]
 
 
@@ -191,8 +192,9 @@ def test_full_size_elasticity_64(fmt, kw):
     check_parity(p, apply(A, x), x)
 
 
+@pytest.mark.parametrize("tiles", [0, -1])
 @pytest.mark.parametrize("vec", [1, 2, 4])
-def test_float_pair_product_out_of_range_entries(vec):
+def test_float_pair_product_out_of_range_entries(vec, tiles):
     """Values and x entries outside [2^-50, 2^50], and Inf/NaN, take the exact FP64 path."""
     p = problem("elasticity_9")
     rng = np.random.default_rng(11)
@@ -201,7 +203,7 @@ def test_float_pair_product_out_of_range_entries(vec):
     vals[idx[:20]] *= 1e-30
     vals[idx[20:]] *= 1e30
     A = fs.spmv_create(p.rowptr, p.colind, vals, p.node_xyz, 3, sigma=64, vec=vec,
-                       precisions=fs.FESPMV_PREC_DF64)
+                       precisions=fs.FESPMV_PREC_DF64, tiles=tiles)
     x = fegen.random_vector(p.n_rows, 12)
     x[rng.choice(p.n_rows, 30, replace=False)] *= 1e-200
     x[rng.choice(p.n_rows, 30, replace=False)] *= 1e200
