@@ -177,11 +177,13 @@ def dist_setup():
 
 
 def reduce_max(value, world):
+    """Max over ranks (NCCL on GPUs; the same call over gloo on CPU processes)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -244,8 +246,11 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:   # host-only ranks (the reference arm, or tests of this path on CPU)
+            dist.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, world, rank)
         if world > 1:

@@ -142,7 +142,10 @@ void spmv_destroy(fespmv_mat_t A);
  *   x, y  n_rows doubles each, device memory unless FESPMV_IO_HOST; x and y must
  *         not overlap.  Without FESPMV_IO_PERMUTED they are in the numbering of
  *         the CSR given to spmv_create; a SLICED handle then permutes x on the way
- *         in and y on the way out (two gathers of n_rows entries).
+ *         in and y on the way out (two gathers of n_rows entries).  With
+ *         FESPMV_IO_HOST and page-locked (pinned, mapped) host buffers in the input
+ *         numbering, those permutations read x and write y in place over the host
+ *         link (no staging copies); pageable buffers are copied through staging.
  * Result per entry: the exact sum over the stored entries of the row, rounded
  * with a different association than a left-to-right sum (componentwise error
  * well under 1e-12 * sum_j |A_ij x_j|).  Errors: INVALID_ARG, CUDA.

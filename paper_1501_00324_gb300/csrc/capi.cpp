@@ -304,6 +304,17 @@ static int ensure_host_staging(fespmv_mat* A) {
     return FESPMV_OK;
 }
 
+// Device address of a pinned (page-locked, mapped) host buffer, or nullptr for
+// pageable memory and anything else.
+static void* mapped_view(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv_stream_t stream) {
     GUARD_BEGIN
     if (!A || (A->n > 0 && (!x || !y))) { set_error("null argument"); return FESPMV_ERR_INVALID_ARG; }
@@ -314,6 +325,21 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
     if (A->n == 0) return FESPMV_OK;
     const double* xd = x;
     double* yd = y;
+    if ((flags & FESPMV_IO_HOST) && A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED) &&
+        !A->d_vdf) {
+        // pinned host buffers: the permutations read x and write y in place over the host link
+        const double* xv = static_cast<const double*>(mapped_view(x));
+        double* yv = static_cast<double*>(mapped_view(y));
+        if (xv && yv) {
+            int rc;
+            if ((rc = launch_scatter(xv, A->d_pinv, A->d_xp, A->n, s)) ||
+                (rc = launch_spmv(A, A->d_xp, A->d_yp, s)) ||
+                (rc = launch_gather(A->d_yp, A->d_pinv, yv, A->n, s)))
+                return rc;
+            FESPMV_CUDA(cudaStreamSynchronize(s));
+            return FESPMV_OK;
+        }
+    }
     if (flags & FESPMV_IO_HOST) {
         int rc = ensure_host_staging(A);
         if (rc) return rc;

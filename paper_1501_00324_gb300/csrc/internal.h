@@ -148,6 +148,7 @@ int launch_spmv_tiled(const fespmv_mat* A, const double* x, double* y, cudaStrea
 int launch_spmv_low_tiled(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_spmv_df_tiled(const fespmv_mat* A, const float2* xdf, const double* x, double* y, cudaStream_t s);
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
+int launch_scatter(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
 unsigned grid_for(int64_t work, int block);
 // Rebuilds S and the FP32/BF16 copies of S A S from the FP64 values (if held).

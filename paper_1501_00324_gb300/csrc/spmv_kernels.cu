@@ -174,6 +174,15 @@ __global__ void gather_f64(const double* __restrict__ in, const int32_t* __restr
     if (i < n) out[i] = __ldg(in + idx[i]);
 }
 
+// out[idx[i]] = in[i]: reads `in` in order (a pinned host buffer read in place
+// streams over the host link in full lines), scatters into device memory.  One
+// entry per thread: the link's latency wants many requests in flight.
+__global__ void scatter_f64(const double* __restrict__ in, const int32_t* __restrict__ idx,
+                            double* __restrict__ out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[idx[i]] = in[i];
+}
+
 __global__ void gather_f32(const float* __restrict__ in, const int32_t* __restrict__ idx,
                            float* __restrict__ out, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -207,6 +216,13 @@ unsigned grid_for(int64_t work, int block) {
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s) {
     if (n == 0) return FESPMV_OK;
     gather_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+int launch_scatter(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s) {
+    if (n == 0) return FESPMV_OK;
+    scatter_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
     FESPMV_CUDA(cudaGetLastError());
     return FESPMV_OK;
 }

@@ -264,3 +264,26 @@ def test_slice_wider_than_a_tile_gathers_from_cache():
     q.rowptr, q.colind, q.values, q.n_rows = rowptr, cols, vals, n
     x = fegen.random_vector(n, 18)
     check_parity(q, apply(A, x), x)
+
+
+@pytest.mark.parametrize("k", [1, 5, 10, 13])
+def test_pinned_host_buffers_are_read_and_written_in_place(k):
+    """Page-locked host x and y (the in-place permutation path) give the same bits as
+    device vectors; pageable host buffers (staging copies) too."""
+    p = problem("elasticity_9")
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, **KERNELS[k])
+    x = fegen.random_vector(p.n_rows, 31)
+    yd = apply(A, x)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.full((p.n_rows,), float("nan"), dtype=torch.float64).pin_memory()
+    fs.spmv_apply(A, xh.numpy(), yh.numpy())
+    assert np.array_equal(yh.numpy().view(np.uint64), yd.view(np.uint64))
+    y2 = np.zeros(p.n_rows)
+    fs.spmv_apply(A, x, y2)
+    assert np.array_equal(y2.view(np.uint64), yd.view(np.uint64))
+    # pinned views that are not 16-byte aligned (one double in)
+    xb = torch.zeros(p.n_rows + 1, dtype=torch.float64).pin_memory()
+    yb = torch.full((p.n_rows + 1,), 7.0, dtype=torch.float64).pin_memory()
+    xb[1:] = torch.from_numpy(x)
+    fs.spmv_apply(A, xb.numpy()[1:], yb.numpy()[1:])
+    assert np.array_equal(yb.numpy()[1:].view(np.uint64), yd.view(np.uint64)) and yb[0].item() == 7.0
