@@ -113,25 +113,16 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
 #pragma unroll
         for (int j = 0; j < 4; ++j) xr[t][j] = XT(0);
 
-    int32_t c[R][V];
-    VT a[R][V];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        ld_v<V>(cp + i * V, c[i]);
-        ld_v<V>(vp + i * V, a[i]);
-    }
     for (int s = 0; s < w; s += V) {
-        // next V steps of this group's rows, in flight while this step's gathers run
-        int32_t cn[R][V];
-        VT an[R][V];
-        const bool more = s + V < w;
-        if (more) {
-            const int64_t o = (int64_t)(s + V) * 32;
+        // this group's rows at V steps; more warps in flight (registers freed by not
+        // double-buffering these loads) hide their latency better than a prefetch
+        int32_t c[R][V];
+        VT a[R][V];
+        const int64_t o = (int64_t)s * 32;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                ld_v<V>(cp + o + i * V, cn[i]);
-                ld_v<V>(vp + o + i * V, an[i]);
-            }
+        for (int i = 0; i < R; ++i) {
+            ld_v<V>(cp + o + i * V, c[i]);
+            ld_v<V>(vp + o + i * V, a[i]);
         }
 #pragma unroll
         for (int i = 0; i < R; ++i)
@@ -146,15 +137,6 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
                     for (int j = 0; j < 4; ++j) acc[i][j] = fma(av, xr[t][j], acc[i][j]);
                 }
             }
-        if (more) {
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-#pragma unroll
-                for (int t = 0; t < V; ++t) {
-                    c[i][t] = cn[i][t];
-                    a[i][t] = an[i][t];
-                }
-        }
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -186,16 +168,16 @@ __global__ void gather_rows(const XT* __restrict__ src, int lds, const int32_t* 
 
 // Rows per warp: four rows per lane group (row-to-row reuse chains of four: longer
 // chains serialise the gathers of a warp, shorter ones reuse less), at most 32,
-// and small enough that the per-lane registers (accumulators, two sets of V
-// stream entries per row, V rows of X) stay near 100 so that four 128-thread
-// blocks fit on an SM without spilling.
+// and small enough that the per-lane registers (accumulators, V stream entries
+// per row, V rows of X) stay near 100 so that four 128-thread blocks fit on an SM
+// without spilling.
 template <typename VT, typename XT, int V, int KW>
 constexpr int multi_rows_per_warp() {
     const int sx = (int)sizeof(XT) / 4, sv = (int)sizeof(VT) / 4, groups = 128 / KW;
     int rw = 4 * groups > 32 ? 32 : 4 * groups;
     while (rw / 2 >= groups) {
         const int r = rw / groups;
-        if (r * 4 * sx + 2 * r * V * (1 + sv) + V * 4 * sx <= 104) break;
+        if (r * 4 * sx + r * V * (1 + sv) + V * 4 * sx <= 104) break;
         rw /= 2;
     }
     return rw;
