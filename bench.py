@@ -360,6 +360,15 @@ def main():
             extra["multi32_fp64"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
+            # the same with float-pair products (a handle holding the pairs)
+            Fm = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                                vec=args.vec, precisions=fs.FESPMV_PREC_DF64)
+            fm = lambda: fs.spmv_apply_multi(Fm, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm()
+            tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
+            extra["multi32_fp64_float_pairs"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
+                                                 "us_per_apply": round(tmean * 1e6, 1)}
+            fs.spmv_destroy(Fm)
             del X64, Y64
             # the same FE product with x gathered from L1/L2 (no tiles), for comparison
             if info["n_tiles"] > 0:

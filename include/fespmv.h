@@ -162,7 +162,10 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
  *              arithmetic); input numbering unless FESPMV_IO_PERMUTED
  * Needs a SLICED handle built with threshold 0 (one lane per row).  Each entry
  * of Y is the sum of its row's products in the order of the row's stored
- * entries (one FMA chain per row and column).
+ * entries (one FMA chain per row and column).  With FESPMV_PREC_F64 on a handle
+ * holding float pairs (FESPMV_PREC_DF64) the products and sums are float pairs
+ * on the FP32 pipe (as spmv_apply's), rows meeting values outside the pairs'
+ * range summed again in FP64: within the same 1e-12 componentwise bound.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM (scratch for the input numbering), CUDA.
  */
 int spmv_apply_multi(fespmv_mat_t A, const void* X, void* Y, int32_t k, int32_t precision,

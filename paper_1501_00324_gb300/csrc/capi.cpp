@@ -47,7 +47,7 @@ void free_handle(fespmv_mat* A) {
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
                     A->d_ys, A->d_xk, A->d_yk, A->d_vdf, A->d_xdf, A->d_tiles, A->d_tdict,
-                    A->d_tlidx};
+                    A->d_tlidx, A->d_xkdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;

@@ -122,6 +122,7 @@ struct fespmv_mat {
     float2* d_xdf = nullptr;          // float-pair x scratch (n)
     double* d_xk = nullptr;           // multi-RHS permuted-I/O scratch (32 n doubles each)
     double* d_yk = nullptr;
+    float2* d_xkdf = nullptr;         // multi-RHS X as float pairs (handles with FESPMV_PREC_DF64)
     int max_lanes_log2 = 0;           // largest log2(lanes per row) over the slices
     // x staged through shared memory (SLICED, options.tiles >= 0): Tiles on the device
     int tiled = 0;                    // 1 when the tile arrays below are in use

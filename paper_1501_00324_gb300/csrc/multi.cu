@@ -153,6 +153,128 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
     }
 }
 
+// ---------------------------------------------------------------- FP64 by float pairs
+// FESPMV_PREC_DF64 handles: the same lane groups and row-to-row reuse, with every
+// product and sum as float pairs on the FP32 pipe (df_add_product: the pair
+// product with its FMA error terms, double-float sums), X split into pairs.  One
+// DFMA per stored entry and right-hand side is what bounds the FP64 kernel above
+// (GB300 retires ~1.9 FP64 lanes per clock per SM); the FP32 pipe is ~58x wider.
+// Rows whose pair sums meet a marked pair (a value or an X entry outside the
+// pairs' range, NaN, Inf) are summed again in FP64 from val, col and X64.
+
+// Four float pairs at p (32 bytes), loaded only when `take` is set.
+__device__ __forceinline__ void ld_x4_pairs(const float2* p, bool take, float2 (&v)[4]) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %8, 0;\n\t"
+        "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%9];\n\t"
+        "@q ld.global.nc.v4.f32 {%4, %5, %6, %7}, [%9+16];\n\t}"
+        : "+f"(v[0].x), "+f"(v[0].y), "+f"(v[1].x), "+f"(v[1].y), "+f"(v[2].x), "+f"(v[2].y),
+          "+f"(v[3].x), "+f"(v[3].y)
+        : "r"((int)take), "l"(p));
+}
+
+template <int V>
+__device__ __forceinline__ void ld_v_pairs(const float2* p, float2 (&a)[V]) {
+    if constexpr (V == 1) {
+        a[0] = ld_stream(p);
+    } else {
+#pragma unroll
+        for (int h = 0; h < V; h += 2) {
+            const float4 t = ld_stream(reinterpret_cast<const float4*>(p + h));
+            a[h] = make_float2(t.x, t.y);
+            a[h + 1] = make_float2(t.z, t.w);
+        }
+    }
+}
+
+template <int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi_df(const uint4* __restrict__ meta,
+                                                          const int32_t* __restrict__ col,
+                                                          const float2* __restrict__ vdf,
+                                                          const double* __restrict__ val,
+                                                          const float2* __restrict__ Xdf,
+                                                          const double* __restrict__ X64,
+                                                          double* __restrict__ Y, int64_t n_slices,
+                                                          int64_t n) {
+    constexpr int LPG = KW / 4, G = 32 / LPG, R = RW / G, WPS = 32 / RW;
+    static_assert(R >= 1 && RW * WPS == 32, "bad multi-RHS tiling");
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t slice = gw / WPS;
+    if (slice >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPG, q = lane % LPG;
+    const uint4 m = meta[slice];
+    const int first_row = (int)(gw % WPS) * RW + g * R;
+    const int64_t off = (int64_t)m.x * 32 + (int64_t)first_row * V;
+    const int w = (int)m.y;
+    const int32_t* cp = col + off;
+    const float2* vp = vdf + off;
+    const float2* Xq = Xdf + 4 * q;
+
+    DfAcc acc[R][4];
+    float2 xr[V][4];
+#pragma unroll
+    for (int t = 0; t < V; ++t)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xr[t][j] = make_float2(0.f, 0.f);
+    for (int s = 0; s < w; s += V) {
+        int32_t c[R][V];
+        float2 a[R][V];
+        const int64_t o = (int64_t)s * 32;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            ld_v<V>(cp + o + i * V, c[i]);
+            ld_v_pairs<V>(vp + o + i * V, a[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int cc = c[i][t];
+                const bool take = cc >= 0 && (i == 0 || cc != c[i - 1][t]);
+                ld_x4_pairs(Xq + (int64_t)cc * KW, take, xr[t]);
+                if (cc >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) df_add_product(acc[i][j], a[i][t].x, a[i][t].y, xr[t][j].x, xr[t][j].y);
+                }
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int64_t row = (int64_t)m.z + first_row + i;
+        double yv[4];
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            bad |= isnan(acc[i][j].hi) || isnan(acc[i][j].lo) || isinf(acc[i][j].hi);
+            yv[j] = df_value(acc[i][j]);
+        }
+        if (bad) {   // this lane's four sums of the row again, in FP64
+#pragma unroll
+            for (int j = 0; j < 4; ++j) yv[j] = 0.0;
+            for (int s2 = 0; s2 < w; ++s2) {
+                const int64_t pos = (int64_t)m.x * 32 + (int64_t)(s2 / V) * 32 * V + (int64_t)(first_row + i) * V + s2 % V;
+                const int32_t cc = col[pos];
+                if (cc >= 0) {
+                    const double av = val[pos];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) yv[j] = fma(av, X64[(int64_t)cc * KW + 4 * q + j], yv[j]);
+                }
+            }
+        }
+        if (row < n) {
+            double* yp = Y + row * KW + 4 * q;
+            reinterpret_cast<double2*>(yp)[0] = make_double2(yv[0], yv[1]);
+            reinterpret_cast<double2*>(yp)[1] = make_double2(yv[2], yv[3]);
+        }
+    }
+}
+
+// X in pairs (df_split: marked pairs for values outside the fast range).
+__global__ void split_rows(const double* __restrict__ X, float2* __restrict__ Xdf, int64_t len) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < len) Xdf[t] = df_split(X[t]);
+}
+
 // Dst[i, j] = Src[idx[i], j] (idx == nullptr: identity) for j < k, 0 for k <= j < ldd.
 template <typename XT>
 __global__ void gather_rows(const XT* __restrict__ src, int lds, const int32_t* __restrict__ idx,
@@ -209,6 +331,41 @@ static void launch_multi(const fespmv_mat* A, const VT* val, const XT* X, XT* Y,
     }
 }
 
+template <int V, int KW>
+static void launch_multi_df_kw(const fespmv_mat* A, const float2* Xdf, const double* X, double* Y,
+                               cudaStream_t s) {
+    constexpr int RW = multi_rows_per_warp<double, double, V, KW>();
+    const unsigned g = grid_for(A->n_slices * (32 / RW) * 32, 128);
+    sliced_multi_df<V, KW, RW><<<g, 128, 0, s>>>(A->d_meta, A->d_col, A->d_vdf, A->d_val, Xdf, X, Y,
+                                                 A->n_slices, A->n);
+}
+
+template <int V>
+static void launch_multi_df_v(const fespmv_mat* A, const float2* Xdf, const double* X, double* Y, int kw,
+                              cudaStream_t s) {
+    switch (kw) {
+        case 4: launch_multi_df_kw<V, 4>(A, Xdf, X, Y, s); break;
+        case 8: launch_multi_df_kw<V, 8>(A, Xdf, X, Y, s); break;
+        case 16: launch_multi_df_kw<V, 16>(A, Xdf, X, Y, s); break;
+        default: launch_multi_df_kw<V, 32>(A, Xdf, X, Y, s); break;
+    }
+}
+
+static int launch_multi_df(fespmv_mat* A, const double* X, double* Y, int kw, cudaStream_t s) {
+    if (!A->d_xkdf) {
+        int rc = device_alloc(A, (void**)&A->d_xkdf, sizeof(float2) * 32 * (size_t)A->n, "multi-RHS pair scratch");
+        if (rc) return rc;
+    }
+    const int64_t len = A->n * kw;
+    split_rows<<<grid_for(len, 256), 256, 0, s>>>(X, A->d_xkdf, len);
+    switch (A->vec) {
+        case 1: launch_multi_df_v<1>(A, A->d_xkdf, X, Y, kw, s); break;
+        case 4: launch_multi_df_v<4>(A, A->d_xkdf, X, Y, kw, s); break;
+        default: launch_multi_df_v<2>(A, A->d_xkdf, X, Y, kw, s); break;
+    }
+    return FESPMV_OK;
+}
+
 static int ensure_multi_scratch(fespmv_mat* A) {
     if (A->d_xk) return FESPMV_OK;
     const size_t bytes = sizeof(double) * 32 * (size_t)A->n;
@@ -240,10 +397,16 @@ static int apply_multi_t(fespmv_mat* A, const XT* X, XT* Y, int k, int flags, cu
         gather_rows<XT><<<grid_for(A->n * kw, 256), 256, 0, s>>>(X, k, permute ? A->d_perm : nullptr,
                                                                  const_cast<XT*>(xs), kw, A->n, k);
     }
-    if constexpr (std::is_same<XT, double>::value)
-        launch_multi<double, double>(A, A->d_val, xs, ys, kw, s);   // FP64 values and sums
-    else
+    if constexpr (std::is_same<XT, double>::value) {
+        if (A->d_vdf) {                                              // FP64 by float pairs
+            int rc = launch_multi_df(A, xs, ys, kw, s);
+            if (rc) return rc;
+        } else {
+            launch_multi<double, double>(A, A->d_val, xs, ys, kw, s);  // FP64 values and sums
+        }
+    } else {
         launch_multi<float, float>(A, A->d_val32, xs, ys, kw, s);   // FP32 copy of S A S
+    }
     if (!direct)
         gather_rows<XT><<<grid_for(A->n * k, 256), 256, 0, s>>>(ys, kw, permute ? A->d_pinv : nullptr, Y, k,
                                                                 A->n, k);

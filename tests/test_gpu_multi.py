@@ -21,11 +21,15 @@ def handle(p, **kw):
                           precisions=fs.FESPMV_PREC_F32, **kw)
 
 
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("k", [1, 3, 4, 7, 8, 16, 17, 32])
 @pytest.mark.parametrize("vec", [1, 2, 4])
-def test_multi_fp64_parity(k, vec):
+def test_multi_fp64_parity(k, vec, pairs):
+    """FP64 products by DFMA, or (handles with FESPMV_PREC_DF64) by float pairs on the
+    FP32 pipe: both within the FP64 bound."""
     p = fegen.cube_elasticity(7, 110)
-    A = handle(p, vec=vec, sigma=128)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, vec=vec, sigma=128,
+                       precisions=fs.FESPMV_PREC_F32 | (fs.FESPMV_PREC_DF64 if pairs else 0))
     X = np.stack([fegen.random_vector(p.n_rows, 111 + j) for j in range(k)], axis=1)
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     Yd = torch.full_like(Xd, float("nan"))
@@ -166,3 +170,30 @@ def test_multi_fp32_random_sparse_rows(per_row):
             fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F32)
             torch.cuda.synchronize()
             check_f32(q, X, Yd.cpu().numpy())
+
+
+def test_multi_float_pairs_out_of_range_and_nan():
+    """Entries of A or X outside the float pairs' range, and NaN, take the FP64 path."""
+    p = fegen.cube_elasticity(7, 140)
+    rng = np.random.default_rng(141)
+    vals = p.values.copy()
+    idx = rng.choice(p.nnz, 30, replace=False)
+    vals[idx[:15]] *= 1e-30
+    vals[idx[15:]] *= 1e30
+    A = fs.spmv_create(p.rowptr, p.colind, vals, p.node_xyz, 3, sigma=128, precisions=fs.FESPMV_PREC_DF64)
+    k = 8
+    X = np.stack([fegen.random_vector(p.n_rows, 142 + j) for j in range(k)], axis=1)
+    X[rng.choice(p.n_rows, 20, replace=False), 3] *= 1e200
+    X[rng.choice(p.n_rows, 20, replace=False), 5] *= 1e-200
+    X[9, 6] = np.nan
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Yd = torch.full_like(Xd, float("nan"))
+    fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F64)
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy()
+    for j in range(k):
+        yo = oracle.csr_spmv(p.rowptr, p.colind, vals, X[:, j])
+        assert np.array_equal(np.isnan(Y[:, j]), np.isnan(yo))
+        ok = ~np.isnan(yo)
+        bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(vals), np.abs(X[:, j]))
+        assert np.all(np.abs(Y[ok, j] - yo[ok]) <= 1e-12 * bound[ok])
