@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256, V == 4 ? 6 : 8) cg_spmv_dot_sliced(const 
 }
 
 // The same products with x staged through shared memory per tile (handles with
-// tiles): one block per tile, the block reduction at the end as above.
+// tiles): persistent blocks stride over the tiles, staging each tile's x then
+// walking its slices, and reduce once at the end as above.
 template <int V, int U>
 __global__ void __launch_bounds__(kTiledBlock) cg_spmv_dot_tiled(const uint4* __restrict__ meta,
                                                                  const uint16_t* __restrict__ lidx,
@@ -785,7 +786,7 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
         return rc;
     }
     // one partial per block of the largest reduction grid: the persistent products, the
-    // vector updates, or one block per tile
+    // vector updates, or the tiled products (at most one block per tile)
     const size_t np = (size_t)grid_sum_doubles(
         std::max<int64_t>({(int64_t)spmv_grid(A), (int64_t)w->upd_grid, A->tiled ? A->n_tiles : 0}));
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
