@@ -197,11 +197,13 @@ int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
  * paper tunes block size and the K2 threshold per matrix by exhaustive timing,
  * Sec. 6 and Table "bestvalues", and leaves an a-priori rule to future work,
  * Sec. 9).  Candidates: vec in {1, 2, 4} x threshold in {0, ceil(maxlen/4),
- * ceil(maxlen/8)} (distinct values, 0 = K1) x block in {128, 256}, each built
- * from the given CSR with the base options' reorder and sigma, then timed as
- * `reps` back-to-back FP64 products in the permuted numbering on `stream`.
+ * ceil(maxlen/8)} (distinct values, 0 = K1) x layout in {x staged per tile (when
+ * the base options' tiles is 0), x gathered from cache with 128 or 256 threads
+ * per block}, each built from the given CSR with the base options' reorder and
+ * sigma, then timed as `reps` back-to-back FP64 products in the permuted
+ * numbering on `stream`.
  *   opts_inout   in: base options (format forced to SLICED); out: the fastest
- *                candidate's vec, threshold and block
+ *                candidate's vec, threshold, block and tiles
  *   reps         products timed per candidate (0 = 20)
  *   best_us      out (may be NULL): mean microseconds per product of the winner
  *   n_tried      out (may be NULL): candidates timed

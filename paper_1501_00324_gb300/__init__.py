@@ -314,7 +314,7 @@ def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigm
 
 def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
                   reps=0, tiles=0, stream=None) -> dict:
-    """Time candidate layouts; returns dict(vec, threshold, block, sigma, reorder, best_us, tried)."""
+    """Time candidate layouts; returns dict(vec, threshold, block, tiles, sigma, reorder, best_us, tried)."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     values = np.ascontiguousarray(values, dtype=np.float64)
@@ -328,8 +328,8 @@ def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorde
     _check(_lib.spmv_autotune(len(rowptr) - 1, _ptr(rowptr), _ptr(colind), _ptr(values), ctypes.byref(mesh),
                               ctypes.byref(opts), reps, ctypes.byref(best), ctypes.byref(tried),
                               _stream(stream)))
-    return dict(vec=opts.vec, threshold=opts.threshold, block=opts.block, sigma=sigma, reorder=reorder,
-                best_us=best.value, tried=tried.value)
+    return dict(vec=opts.vec, threshold=opts.threshold, block=opts.block, tiles=opts.tiles, sigma=sigma,
+                reorder=reorder, best_us=best.value, tried=tried.value)
 
 
 def spmv_get_info(A: Matrix) -> dict:

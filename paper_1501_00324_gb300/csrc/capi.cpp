@@ -512,14 +512,22 @@ int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const
     best.format = FESPMV_FMT_SLICED;
     double best_t = 1e300;
     int tried = 0;
+    // layouts: x staged per tile (block fixed by the tiled kernels), or gathered from
+    // cache with 128 or 256 threads per block; tiles only when the base options allow them
+    struct Shape { int tiles, block; };
+    std::vector<Shape> shapes;
+    if (opts->tiles >= 0) shapes.push_back({0, 256});
+    shapes.push_back({-1, 128});
+    shapes.push_back({-1, 256});
     for (int vec : {1, 2, 4})
         for (int thr : thresholds)
-            for (int block : {128, 256}) {
+            for (const Shape& sh : shapes) {
                 fespmv_options o = *opts;
                 o.format = FESPMV_FMT_SLICED;
                 o.vec = vec;
                 o.threshold = thr;
-                o.block = block;
+                o.block = sh.block;
+                o.tiles = sh.tiles;
                 o.precisions = FESPMV_PREC_F64;
                 fespmv_mat_t A = nullptr;
                 rc = spmv_create(&A, n, rowptr, colind, values, mesh, &o, stream);
@@ -548,6 +556,7 @@ int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const
     opts->vec = best.vec;
     opts->threshold = best.threshold;
     opts->block = best.block;
+    opts->tiles = best.tiles;
     if (best_us) *best_us = best_t;
     if (n_tried) *n_tried = tried;
     return FESPMV_OK;

@@ -220,10 +220,14 @@ def test_float_pair_product_out_of_range_entries(vec, tiles):
 def test_autotuner_returns_a_valid_fast_layout():
     p = problem("shell_6x20x36")
     t = fs.spmv_autotune(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, reps=5)
-    assert t["tried"] >= 6 and t["best_us"] > 0
-    assert t["vec"] in (1, 2, 4) and t["block"] in (128, 256) and t["threshold"] >= 0
+    assert t["tried"] >= 9 and t["best_us"] > 0
+    assert t["vec"] in (1, 2, 4) and t["block"] in (128, 256) and t["threshold"] >= 0 and t["tiles"] in (0, -1)
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, vec=t["vec"],
-                       threshold=t["threshold"], block=t["block"])
+                       threshold=t["threshold"], block=t["block"], tiles=t["tiles"])
+    assert fs.spmv_get_info(A)["n_tiles"] > 0 or t["tiles"] == -1
+    # with tiles off in the base options only cache-gather layouts are tried
+    u = fs.spmv_autotune(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, reps=3, tiles=-1)
+    assert u["tiles"] == -1 and u["tried"] < t["tried"]
     x = fegen.random_vector(p.n_rows, 21)
     check_parity(p, apply(A, x), x)
 
@@ -287,3 +291,24 @@ def test_pinned_host_buffers_are_read_and_written_in_place(k):
     xb[1:] = torch.from_numpy(x)
     fs.spmv_apply(A, xb.numpy()[1:], yb.numpy()[1:])
     assert np.array_equal(yb.numpy()[1:].view(np.uint64), yd.view(np.uint64)) and yb[0].item() == 7.0
+
+
+def test_full_size_shell_24x256x512():
+    """The shell workload (3,145,728 rows, ~46 M nnz, more tiles than the cube): every
+    row of the tiled FP64 product, and of the FP32 product of S A S, against the oracle."""
+    p = fegen.shell_laplace(24, 256, 512, 1503)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=1024,
+                       precisions=fs.FESPMV_PREC_F32)
+    assert fs.spmv_get_info(A)["n_tiles"] > 0
+    x = fegen.random_vector(p.n_rows, 1505)
+    check_parity(p, apply(A, x), x)
+    bv = oracle.scaled_values(p.rowptr, p.colind, p.values, "f32")
+    x32 = x.astype(np.float32)
+    xd = dev(x32)
+    yd = torch.empty_like(xd)
+    fs.spmv_apply_scaled(A, xd, yd, fs.FESPMV_PREC_F32)
+    torch.cuda.synchronize()
+    yo = oracle.csr_spmv_f32(p.rowptr, p.colind, bv, x32)
+    bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(bv).astype(np.float64), np.abs(x32).astype(np.float64))
+    L = np.diff(p.rowptr).max()
+    assert np.all(np.abs(yd.cpu().numpy().astype(np.float64) - yo) <= 2 * L * 2.0 ** -24 * bound)
