@@ -56,7 +56,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sigma", type=int, default=1024)
-    ap.add_argument("--vec", type=int, default=2)
+    ap.add_argument("--vec", type=int, default=1,
+                    help="entries per lane per load of the headline handle (1: least padding)")
+    ap.add_argument("--extras-vec", type=int, default=4,
+                    help="vector width of the handle the low-precision and multi-RHS extras use")
     ap.add_argument("--threshold", type=int, default=0)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--tiles", type=int, choices=[0, -1], default=0,
@@ -333,18 +336,24 @@ def main():
             fu = lambda: fs.spmv_apply(A, xd, y_user)  # noqa: E731
             fu()
             extra["fe_input_numbering_gbs"] = round(mb / (back_to_back(fu, args.steps) * 1e-3) / 1e9, 1)
+            # low-precision and multi-RHS extras on a handle with wider lane loads (these
+            # kernels are not on the FP64 pipe, where the headline's V = 1 saves padding)
+            E = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                               vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+            xe = torch.empty_like(xd)
+            fs.spmv_permute(E, xd, xe, 0)
             # low-precision products of B = S A S (the refined CG's inner operator)
-            xs = xp.float()
+            xs = xe.float()
             ys = torch.empty_like(xs)
             for name, prec, vb in (("fp32", fs.FESPMV_PREC_F32, 4), ("bf16", fs.FESPMV_PREC_BF16, 2)):
-                f = lambda: fs.spmv_apply_scaled(A, xs, ys, prec, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+                f = lambda: fs.spmv_apply_scaled(E, xs, ys, prec, fs.FESPMV_IO_PERMUTED)  # noqa: E731
                 f()
                 tl = back_to_back(f, args.steps)
                 extra[f"{name}_spmv_gbs"] = round((nnz * (vb + 4) + n * 8) / (tl * 1e-3) / 1e9, 1)
             # 32 right-hand sides in one pass over the FP32 matrix (row-major n x 32)
             X32 = torch.rand((n, 32), dtype=torch.float32, device=dev)
             Y32 = torch.empty_like(X32)
-            fm = lambda: fs.spmv_apply_multi(A, X32, Y32, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm = lambda: fs.spmv_apply_multi(E, X32, Y32, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
             fm()
             tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
             extra["multi32_fp32"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
@@ -354,7 +363,7 @@ def main():
             # the same with the FP64 matrix and FP64 right-hand sides
             X64 = torch.rand((n, 32), dtype=torch.float64, device=dev)
             Y64 = torch.empty_like(X64)
-            fm = lambda: fs.spmv_apply_multi(A, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm = lambda: fs.spmv_apply_multi(E, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
             fm()
             tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
             extra["multi32_fp64"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
@@ -362,13 +371,14 @@ def main():
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
             # the same with float-pair products (a handle holding the pairs)
             Fm = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
-                                vec=args.vec, precisions=fs.FESPMV_PREC_DF64)
+                                vec=args.extras_vec, precisions=fs.FESPMV_PREC_DF64)
             fm = lambda: fs.spmv_apply_multi(Fm, X64, Y64, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
             fm()
             tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
             extra["multi32_fp64_float_pairs"] = {"gbs": round((nnz * 12 + n * 32 * 16) / tmean / 1e9, 1),
                                                  "us_per_apply": round(tmean * 1e6, 1)}
             fs.spmv_destroy(Fm)
+            fs.spmv_destroy(E)
             del X64, Y64
             # the same FE product with x gathered from L1/L2 (no tiles), for comparison
             if info["n_tiles"] > 0:
@@ -727,9 +737,15 @@ def bench_batched(fs, torch, args):
 
 
 def profile_piece(fs, torch, A, p, xp, args):
-    """Warm-up then `steps` launches of one piece, for ncu launch lists and captures."""
+    """Warm-up then `steps` launches of one piece, for ncu launch lists and captures.
+    The multi-RHS and FP32 pieces run on the extras' handle (vector width
+    --extras-vec), the CG pieces on the headline handle, as in the timed run."""
     n = p.n_rows
     t = args.profile_target
+    if t in ("multi", "multi64", "fp32"):
+        A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                           vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32)
+        xp = torch.rand_like(xp)          # any x in this handle's numbering
     if t == "multi":
         X = torch.rand((n, 32), dtype=torch.float32, device="cuda")
         Y = torch.empty_like(X)
