@@ -466,7 +466,7 @@ def main():
                                  + f" V={info['vec']} threshold={args.threshold} sigma={args.sigma}"
                                  + ("" if tiled else f" block={args.block}"),
                        "order": "Morton nodes, windowed length sort, sorted columns",
-                       "l2": "inputs larger than L2: the 414 MB matrix streams from HBM every "
+                       "l2": f"inputs larger than L2: the {layout_bytes / 1e6:.0f} MB layout streams from HBM every "
                              "step (x stays L2-resident, as in CG); steps enqueued back to back",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "create_s": round(create_s, 2),
