@@ -261,6 +261,26 @@ int spmv_plan(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
               const fespmv_mesh_info* mesh, const fespmv_options* opts, fespmv_info* info,
               int32_t* perm, uint32_t* meta, int32_t* cols, int64_t* srcmap);
 
+/*
+ * spmv_plan_tiles -- the tiles spmv_create builds (options.tiles = 0) for a packed
+ * layout from spmv_plan, on the host, with no device work: runs of at most 8
+ * consecutive slices whose distinct columns number at most 4096, each tile's
+ * columns in order of first use, each stored entry's 16-bit index into its tile's
+ * list (padding: the list's length).  Not in the paper: this library's x staging.
+ *   n_rows        rows of the matrix (every column index is -1 or in [0, n_rows))
+ *   meta, cols    spmv_plan's slice metadata (n_slices x 4) and packed columns
+ *   tiles         out: int32[4 * n_slices] or NULL: (first slice, slices, list offset, D)
+ *   tile_cols     out: int32[packed_len] or NULL: the concatenated column lists
+ *   index         out: uint16[packed_len] or NULL
+ *   n_tiles, n_tile_cols   out: counts; 0 and 0 when one slice alone has more
+ *                 than 4096 distinct columns (the handle then gathers x from cache)
+ * Errors: INVALID_ARG (a slice outside the packed arrays, a column out of range),
+ * OOM (host).
+ */
+int spmv_plan_tiles(int64_t n_rows, int64_t n_slices, const uint32_t* meta, int64_t packed_len,
+                    const int32_t* cols, int32_t* tiles, int32_t* tile_cols, uint16_t* index,
+                    int64_t* n_tiles, int64_t* n_tile_cols);
+
 /* ---- conjugate gradients ----------------------------------------------------------- */
 #define FESPMV_CG_F64          0  /* FP64 Jacobi-PCG on the handle's FP64 values */
 #define FESPMV_CG_F32_REFINE   1  /* FP64 refinement around FP32 CG on B = S A S (FP32 values) */

@@ -141,6 +141,8 @@ _lib.spmv_export.restype = ctypes.c_int
 _lib.spmv_plan.argtypes = [_i64, _P, _P, ctypes.POINTER(fespmv_mesh_info),
                            ctypes.POINTER(fespmv_options), ctypes.POINTER(fespmv_info), _P, _P, _P, _P]
 _lib.spmv_plan.restype = ctypes.c_int
+_lib.spmv_plan_tiles.argtypes = [_i64, _i64, _P, _i64, _P, _P, _P, _P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+_lib.spmv_plan_tiles.restype = ctypes.c_int
 _lib.cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), ctypes.POINTER(cg_result), _P]
 _lib.cg_solve.restype = ctypes.c_int
 _lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
@@ -310,6 +312,23 @@ def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigm
     _check(_lib.spmv_plan(*args, _ptr(perm), _ptr(meta), _ptr(cols), _ptr(src)))
     return dict(perm=perm[:n], meta=meta[:info.n_slices * 4].reshape(-1, 4),
                 cols=cols[:info.packed_len], srcmap=src[:info.packed_len])
+
+
+def spmv_plan_tiles(n_rows, meta, cols):
+    """Host-only tiles of a packed layout from spmv_plan: (tiles int32[n, 4], tile
+    columns int32, index uint16[packed_len]), or None when a slice is too wide."""
+    meta = np.ascontiguousarray(meta, dtype=np.uint32).reshape(-1)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    ns, plen = len(meta) // 4, len(cols)
+    tiles = np.zeros(max(4 * ns, 1), np.int32)
+    tcols = np.zeros(max(plen, 1), np.int32)
+    index = np.zeros(max(plen, 1), np.uint16)
+    nt, nc = _i64(0), _i64(0)
+    _check(_lib.spmv_plan_tiles(n_rows, ns, _ptr(meta), plen, _ptr(cols), _ptr(tiles), _ptr(tcols),
+                                _ptr(index), ctypes.byref(nt), ctypes.byref(nc)))
+    if nt.value == 0 and ns > 0:
+        return None
+    return tiles[:4 * nt.value].reshape(-1, 4), tcols[:nc.value], index[:plen]
 
 
 def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,

@@ -475,6 +475,38 @@ int spmv_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, const fes
     GUARD_END
 }
 
+int spmv_plan_tiles(int64_t n, int64_t n_slices, const uint32_t* meta, int64_t packed_len,
+                    const int32_t* cols, int32_t* tiles, int32_t* tile_cols, uint16_t* index,
+                    int64_t* n_tiles, int64_t* n_tile_cols) {
+    GUARD_BEGIN
+    if (n < 0 || n_slices < 0 || packed_len < 0 || !n_tiles || !n_tile_cols ||
+        (n_slices > 0 && !meta) || (packed_len > 0 && !cols)) {
+        set_error("bad argument"); return FESPMV_ERR_INVALID_ARG;
+    }
+    for (int64_t sl = 0; sl < n_slices; ++sl) {
+        const int64_t b = (int64_t)meta[sl * 4] * 32, e = b + 32 * (int64_t)meta[sl * 4 + 1];
+        if (e > packed_len) { set_error("slice %lld outside the packed arrays", (long long)sl); return FESPMV_ERR_INVALID_ARG; }
+    }
+    for (int64_t q = 0; q < packed_len; ++q)
+        if (cols[q] < -1 || (int64_t)cols[q] >= n) {
+            set_error("column %d at position %lld out of range", cols[q], (long long)q);
+            return FESPMV_ERR_INVALID_ARG;
+        }
+    std::vector<uint32_t> m(meta, meta + 4 * n_slices);
+    std::vector<int32_t> c(cols, cols + packed_len);
+    Tiles t;
+    *n_tiles = 0;
+    *n_tile_cols = 0;
+    if (!build_tiles(m, c, n, kTileSlices, kTileCols, t)) return FESPMV_OK;
+    *n_tiles = (int64_t)t.tiles.size() / 4;
+    *n_tile_cols = (int64_t)t.dict.size();
+    if (tiles) std::memcpy(tiles, t.tiles.data(), sizeof(int32_t) * t.tiles.size());
+    if (tile_cols) std::memcpy(tile_cols, t.dict.data(), sizeof(int32_t) * t.dict.size());
+    if (index) std::memcpy(index, t.lidx.data(), sizeof(uint16_t) * t.lidx.size());
+    return FESPMV_OK;
+    GUARD_END
+}
+
 int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* values,
                   const fespmv_mesh_info* mesh, fespmv_options* opts, int32_t reps, double* best_us,
                   int32_t* n_tried, fespmv_stream_t stream) {

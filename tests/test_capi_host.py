@@ -132,3 +132,31 @@ def test_planner_edge_cases():
         rp2, ci2, v2, vmap = layout.permute_csr(rowptr, cols, np.ones(len(cols)), P)
         meta, col, _, pmap = layout.pack(rp2, ci2, v2, thr, V)
         assert np.array_equal(got["meta"], meta) and np.array_equal(got["cols"], col)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_host_tiles_match_oracle_bit_exactly(case):
+    """The tile builder (x staging) against oracle.layout.tiles, on spmv_plan's layout."""
+    make, reorder, sigma, threshold, V = CASES[case]
+    p = make()
+    got = fs.spmv_plan(p.rowptr, p.colind, p.node_xyz if reorder == "morton" else None,
+                       p.dofs_per_node, fs.FESPMV_REORDER_MORTON if reorder == "morton"
+                       else fs.FESPMV_REORDER_NONE, sigma, threshold, V)
+    t = fs.spmv_plan_tiles(p.n_rows, got["meta"], got["cols"])
+    o = layout.tiles(got["meta"], got["cols"], 8, 4096)
+    assert np.array_equal(t[0], o[0]) and np.array_equal(t[1], o[1]) and np.array_equal(t[2], o[2])
+
+
+def test_host_tiles_wide_slice_and_bad_input():
+    n = 20000
+    rng = np.random.default_rng(61)
+    rows = [np.sort(rng.choice(n, 200, replace=False)) if i < 32 else np.array([i]) for i in range(n)]
+    rowptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+    cols = np.concatenate(rows).astype(np.int32)
+    got = fs.spmv_plan(rowptr, cols, sigma=0)
+    assert fs.spmv_plan_tiles(n, got["meta"], got["cols"]) is None
+    assert layout.tiles(got["meta"], got["cols"], 8, 4096) is None
+    bad = got["cols"].copy()
+    bad[3] = n
+    _expect(fs.FESPMV_ERR_INVALID_ARG, fs.spmv_plan_tiles, n, got["meta"], bad)
+    _expect(fs.FESPMV_ERR_INVALID_ARG, fs.spmv_plan_tiles, n, got["meta"], got["cols"][:10])
