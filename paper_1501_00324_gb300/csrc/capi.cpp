@@ -112,7 +112,8 @@ int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s) {
 static const int kTileSlices = 8, kTileCols = 4096;
 
 int upload_tiles(fespmv_mat* A, const Plan& plan, Tiles& t, cudaStream_t s) {
-    if (!build_tiles(plan.meta, plan.col, A->n, kTileSlices, kTileCols, t)) return FESPMV_OK;
+    if (plan.n_slices == 0 || !build_tiles(plan.meta, plan.col, A->n, kTileSlices, kTileCols, t))
+        return FESPMV_OK;
     A->n_tiles = (int64_t)t.tiles.size() / 4;
     A->tile_dmax = t.dmax;
     A->tile_dict_len = (int64_t)t.dict.size();
