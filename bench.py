@@ -68,6 +68,8 @@ def parse_args():
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
+    ap.add_argument("--multi-cg", type=int, default=1,
+                    help="time cg_solve_multi with 32 right-hand sides on the workload matrix")
     ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
@@ -426,6 +428,8 @@ def main():
                                                   fs.FESPMV_CG_F32_REFINE)
                 extra["cg_f32_reliable"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                     fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
+            if hasattr(fs, "cg_solve_multi") and args.multi_cg:
+                extra["cg_multi32"] = bench_cg_multi(fs, torch, p, args)
             if args.shell:
                 extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
@@ -807,6 +811,52 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 2),
             "iters": iters}
+
+
+def bench_cg_multi(fs, torch, p, args):
+    """32 right-hand sides of the same matrix solved to 1e-10 in lockstep
+    (cg_solve_multi): FP32 values with FP64 reliable updates (timed over a few
+    solves after a warm-up that builds the graphs), and FP64 (one solve)."""
+    import fegen
+    E = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.extras_vec,
+                       precisions=fs.FESPMV_PREC_F32)
+    k = 32
+    B = np.stack([fegen.random_vector(p.n_rows, 1700 + j) for j in range(k)], axis=1)
+    B[:, 0] = manufactured_rhs(fs, torch, E, p)
+    Bd = torch.from_numpy(B).cuda()
+    out = {}
+    for name, precision, flags, reps in (("f32_reliable", fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE,
+                                          args.cg_solves), ("f64", fs.FESPMV_CG_F64, 0, 1)):
+        if reps > 1:
+            fs.cg_solve_multi(E, Bd, torch.zeros_like(Bd), tol=1e-10, precision=precision, flags=flags)
+        lat = []
+        for _ in range(reps):
+            Xd = torch.zeros_like(Bd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, res = fs.cg_solve_multi(E, Bd, Xd, tol=1e-10, precision=precision, flags=flags)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0)
+            assert rc == 0, [r for r in res if r["status"] != 0][:2]
+        iters = [r["iters"] for r in res]
+        t = float(np.median(lat))
+        out[name] = {"rhs": k, "tol": 1e-10, "solves_per_s": round(k / t, 2),
+                     "ms_per_32_solves": round(t * 1e3, 1),
+                     "us_per_iteration_all_rhs": round(t * 1e6 / max(iters), 1),
+                     "iters_max": max(iters), "iters_min": min(iters),
+                     "true_relres_max": max(r["true_relres"] for r in res),
+                     "repeats": reps}
+    fs.spmv_destroy(E)
+    return out
+
+
+def manufactured_rhs(fs, torch, A, p):
+    """b = A u* for the manufactured u*, computed by the library's own FP64 product."""
+    import fegen
+    ud = torch.from_numpy(fegen.manufactured_solution(p)).cuda()
+    bd = torch.empty_like(ud)
+    fs.spmv_apply(A, ud, bd)
+    return bd.cpu().numpy()
 
 
 if __name__ == "__main__":

@@ -402,6 +402,44 @@ int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* co
                         const double* values, const double* b, double* x, int32_t csr_lanes,
                         const cg_options* opts, cg_result* res, fespmv_stream_t stream);
 
+/*
+ * cg_solve_multi -- solve A x_j = b_j for k right-hand sides of one matrix by k
+ * Jacobi-PCG solves run in lockstep (the solver of cg_solve, Sec. 2.1, once per
+ * column), so that each iteration streams the matrix once for all columns with
+ * the multi-RHS product of spmv_apply_multi.  The paper solves one system at a
+ * time; this entry point is the library's batching of right-hand sides.
+ *   B, X   n_rows x k doubles, row-major (row i holds b_i1 .. b_ik), device unless
+ *          FESPMV_IO_HOST, permuted numbering with FESPMV_IO_PERMUTED; X holds the
+ *          initial guesses with FESPMV_CG_X0 and is overwritten with the solutions.
+ *   k      1 .. 32
+ *   opts   as cg_solve: precision FESPMV_CG_F64 or FESPMV_CG_F32_REFINE (flag
+ *          FESPMV_CG_RELIABLE allowed); BF16 and FESPMV_CG_SINGLE_REDUCTION return
+ *          UNSUPPORTED.  max_iter bounds each column's iterations in total.
+ *   res    NULL or k records, one per column.
+ * Each column has its own scalars and stopping test, and its dot products are
+ * reduced in a fixed order of their own: a column's x is bitwise the same
+ * whatever the other columns hold (for the same padded width: k rounded up to
+ * 4, 8, 16 or 32).
+ *   FESPMV_CG_F64: every stop of the recurrence (||r|| <= tol ||b||) is checked
+ *   against the FP64 residual b - A x; above tol the column restarts from x
+ *   (max_restarts times).  relres and true_relres are both that FP64 residual.
+ *   FESPMV_CG_F32_REFINE: the iterative refinement (or, with FESPMV_CG_RELIABLE,
+ *   the reliable updates) of cg_solve, per column, with one difference: a column
+ *   whose inner residual has fallen by inner_tol keeps iterating until the next
+ *   FP64 outer step (or until it has fallen by inner_tol^3 with reliable updates,
+ *   inner_tol^2 without), and those steps come every 8 * check_every inner
+ *   iterations (or as soon as no column is iterating); an inner CG also stops
+ *   once its residual estimates ||b - A x|| <= tol ||b||.
+ * Needs a SLICED handle with one lane per row (threshold 0; UNSUPPORTED
+ * otherwise) and, for the refinement, the FP32 copy (FESPMV_PREC_F32).  The
+ * workspace (seven n_rows x kw arrays of doubles) is allocated on the first call
+ * and grows with kw; the call blocks the host until every column has stopped.
+ * Returns FESPMV_OK when every column converged, else the first column's
+ * NOT_CONVERGED or BREAKDOWN (a non-positive diagonal: BREAKDOWN for all).
+ */
+int cg_solve_multi(fespmv_mat_t A, const double* B, double* X, int32_t k, const cg_options* opts,
+                   cg_result* res, fespmv_stream_t stream);
+
 /* ---- batches of independent FE problems ------------------------------------------- */
 typedef struct fespmv_batch* fespmv_batch_t;
 

@@ -145,6 +145,8 @@ _lib.spmv_plan_tiles.argtypes = [_i64, _i64, _P, _i64, _P, _P, _P, _P, ctypes.PO
 _lib.spmv_plan_tiles.restype = ctypes.c_int
 _lib.cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), ctypes.POINTER(cg_result), _P]
 _lib.cg_solve.restype = ctypes.c_int
+_lib.cg_solve_multi.argtypes = [_P, _P, _P, _i32, ctypes.POINTER(cg_options), _P, _P]
+_lib.cg_solve_multi.restype = ctypes.c_int
 _lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
 _lib.srv_create.restype = ctypes.c_int
 _lib.srv_register.argtypes = [_P, _P, ctypes.POINTER(_i32)]
@@ -394,6 +396,22 @@ def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, fl
     if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
         _check(rc)
     return {k: getattr(r, k) for k, _ in cg_result._fields_}
+
+
+def cg_solve_multi(A: Matrix, B, X, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
+                   max_restarts=0, check_every=0, max_outer=0, inner_tol=0.0, stream=None):
+    """Solve A X = B for B of shape (n_rows, k), k <= 32, column by column in lockstep;
+    returns (status, list of k per-column result dicts).  numpy arrays are host I/O."""
+    if isinstance(B, np.ndarray):
+        flags |= FESPMV_IO_HOST
+    k = B.shape[1] if B.ndim == 2 else 1
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
+    res = (cg_result * k)()
+    rc = _lib.cg_solve_multi(A.handle, _ptr(B), _ptr(X), k, ctypes.byref(o), ctypes.cast(res, _P),
+                             _stream(stream))
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return rc, [{f: getattr(r, f) for f, _ in cg_result._fields_} for r in res]
 
 
 class Server:

@@ -43,6 +43,7 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what) {
 void free_handle(fespmv_mat* A) {
     if (!A) return;
     free_cg(A);
+    free_multi_cg(A);
     void* ptrs[] = {A->d_rowptr, A->d_colind, A->d_val, A->d_meta, A->d_col, A->d_perm, A->d_pinv,
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,

@@ -78,7 +78,8 @@ int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind);
 }  // namespace fespmv
 
 namespace fespmv {
-struct CgWork;  // cg.cu
+struct CgWork;     // cg.cu
+struct MultiWork;  // multi_cg.cu
 }
 
 // The opaque handle.
@@ -136,6 +137,7 @@ struct fespmv_mat {
     float* d_ys = nullptr;
 
     fespmv::CgWork* cg = nullptr;     // CG workspace, allocated by the first cg_solve
+    fespmv::MultiWork* mcg = nullptr; // multi-RHS CG workspace, allocated by the first cg_solve_multi
 };
 
 namespace fespmv {
@@ -163,12 +165,26 @@ int launch_split(const double* v, float2* out, int64_t len, cudaStream_t s);
 int launch_gather_split(const double* x, const int32_t* idx, double* xp, float2* xs, int64_t n,
                         cudaStream_t s);
 
+// Multi-RHS kernels (multi.cu), X and Y row-major with row stride kw (4, 8, 16 or 32),
+// handle numbering.  launch_multi_dot: Q = A P with the FP64 (f64) or FP32 copy
+// of S A S, plus per-block FP64 sums of p_ij q_ij at part[block * kw + j]; returns
+// its grid (with part == nullptr it only returns the grid).
+unsigned launch_multi_dot(const fespmv_mat* A, const void* P, void* Q, int kw, bool f64, double* part,
+                          cudaStream_t s);
+// Y = A X in FP64 (float pairs on FESPMV_PREC_DF64 handles).
+int launch_multi_f64(fespmv_mat* A, const double* X, double* Y, int kw, cudaStream_t s);
+// dst[i, j] = src[idx[i], j] (idx null: identity) for j < k, 0 for k <= j < ldd.
+void launch_gather_rows_f64(const double* src, int lds, const int32_t* idx, double* dst, int ldd, int64_t n,
+                            int k, cudaStream_t s);
+int multi_width(int k);   // the padded width kw for k columns
+
 // Handle plumbing (capi.cpp)
 void free_handle(fespmv_mat* A);
 int alloc_scaled(fespmv_mat* A, int64_t len);
 int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s);
 
-// CG (cg.cu)
+// CG (cg.cu) and the multi-RHS CG (multi_cg.cu)
 void free_cg(fespmv_mat* A);
+void free_multi_cg(fespmv_mat* A);
 
 }  // namespace fespmv

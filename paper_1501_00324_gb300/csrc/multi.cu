@@ -20,6 +20,7 @@
 // in X never reaches a row that does not store its column.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -78,21 +79,20 @@ template <int V> __device__ __forceinline__ void ld_v(const double* p, double (&
     }
 }
 
+// One warp's unit of work: RW rows of one slice (unit gw = slice * 32/RW + part),
+// all KW columns; stores the rows of Y and leaves the sums in acc (per group
+// row i, this lane's 4 columns).
 template <typename VT, typename XT, int V, int KW, int RW>
-__global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__ meta,
-                                                       const int32_t* __restrict__ col,
-                                                       const VT* __restrict__ val,
-                                                       const XT* __restrict__ X, XT* __restrict__ Y,
-                                                       int64_t n_slices, int64_t n) {
+__device__ __forceinline__ void multi_unit(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
+                                           const VT* __restrict__ val, const XT* __restrict__ X,
+                                           XT* __restrict__ Y, int64_t gw, int64_t n, int lane,
+                                           XT (&acc)[RW / (32 / (KW / 4))][4]) {
     constexpr int LPG = KW / 4;  // lanes per group
     constexpr int G = 32 / LPG;  // groups per warp
     constexpr int R = RW / G;    // rows per group
     constexpr int WPS = 32 / RW; // warps per slice
     static_assert(R >= 1 && RW * WPS == 32, "bad multi-RHS tiling");
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t slice = gw / WPS;
-    if (slice >= n_slices) return;
-    const int lane = threadIdx.x & 31;
     const int g = lane / LPG, q = lane % LPG;
     const uint4 m = meta[slice];
     const int first_row = (int)(gw % WPS) * RW + g * R;  // first local row of this group
@@ -102,7 +102,6 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
     const VT* vp = val + off;
     const XT* Xq = X + 4 * q;
 
-    XT acc[R][4];
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -151,6 +150,64 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
             }
         }
     }
+}
+
+template <typename VT, typename XT, int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__ meta,
+                                                       const int32_t* __restrict__ col,
+                                                       const VT* __restrict__ val,
+                                                       const XT* __restrict__ X, XT* __restrict__ Y,
+                                                       int64_t n_slices, int64_t n) {
+    constexpr int R = RW / (32 / (KW / 4));
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (gw >= n_slices * (32 / RW)) return;
+    XT acc[R][4];
+    multi_unit<VT, XT, V, KW, RW>(meta, col, val, X, Y, gw, n, threadIdx.x & 31, acc);
+}
+
+// The product of the lockstep CG of cg_solve_multi: Q = A P as sliced_multi
+// computes it, and for every column j the sum of p_ij q_ij over the rows this
+// block covered, in FP64, at part[blockIdx.x * KW + j].  The grid is resident
+// (persistent): each warp strides over the units, so the partial sums stay few.
+template <typename VT, typename XT, int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi_dot(const uint4* __restrict__ meta,
+                                                           const int32_t* __restrict__ col,
+                                                           const VT* __restrict__ val,
+                                                           const XT* __restrict__ P, XT* __restrict__ Q,
+                                                           int64_t n_slices, int64_t n,
+                                                           double* __restrict__ part) {
+    constexpr int LPG = KW / 4, G = 32 / LPG, R = RW / G, WPS = 32 / RW;
+    __shared__ double sh[4][KW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int g = lane / LPG, q = lane % LPG;
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t units = n_slices * WPS;
+    for (int64_t gw = (int64_t)blockIdx.x * 4 + wib; gw < units; gw += (int64_t)gridDim.x * 4) {
+        XT acc[R][4];
+        multi_unit<VT, XT, V, KW, RW>(meta, col, val, P, Q, gw, n, lane, acc);
+        const int64_t row0 = (int64_t)meta[gw / WPS].z + (int)(gw % WPS) * RW + g * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (row0 + i < n) {
+                XT pv[4] = {XT(0), XT(0), XT(0), XT(0)};
+                ld_x4(P + (row0 + i) * KW + 4 * q, true, pv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d[j] = fma((double)pv[j], (double)acc[i][j], d[j]);
+            }
+        }
+    }
+    // lanes with the same q hold the same columns: sum over the warp's groups
+#pragma unroll
+    for (int o = LPG; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
+    if (g == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[wib][4 * q + j] = d[j];
+    __syncthreads();
+    if (threadIdx.x < KW)
+        part[(int64_t)blockIdx.x * KW + threadIdx.x] =
+            ((sh[0][threadIdx.x] + sh[1][threadIdx.x]) + sh[2][threadIdx.x]) + sh[3][threadIdx.x];
 }
 
 // ---------------------------------------------------------------- FP64 by float pairs
@@ -331,6 +388,45 @@ static void launch_multi(const fespmv_mat* A, const VT* val, const XT* X, XT* Y,
     }
 }
 
+// The product-and-dot kernel: its grid is the blocks resident at once (at most
+// one block per four units); with part == nullptr nothing is launched.
+template <typename VT, typename XT, int V, int KW>
+static unsigned multi_dot_kw(const fespmv_mat* A, const VT* val, const XT* P, XT* Q, double* part,
+                             cudaStream_t s) {
+    constexpr int RW = multi_rows_per_warp<VT, XT, V, KW>();
+    auto kernel = sliced_multi_dot<VT, XT, V, KW, RW>;
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    const int64_t units = A->n_slices * (32 / RW);
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (units + 3) / 4));
+    if (part) kernel<<<grid, 128, 0, s>>>(A->d_meta, A->d_col, val, P, Q, A->n_slices, A->n, part);
+    return grid;
+}
+
+template <typename VT, typename XT, int V>
+static unsigned multi_dot_v(const fespmv_mat* A, const VT* val, const XT* P, XT* Q, int kw, double* part,
+                            cudaStream_t s) {
+    switch (kw) {
+        case 4: return multi_dot_kw<VT, XT, V, 4>(A, val, P, Q, part, s);
+        case 8: return multi_dot_kw<VT, XT, V, 8>(A, val, P, Q, part, s);
+        case 16: return multi_dot_kw<VT, XT, V, 16>(A, val, P, Q, part, s);
+        default: return multi_dot_kw<VT, XT, V, 32>(A, val, P, Q, part, s);
+    }
+}
+
+template <typename VT, typename XT>
+static unsigned multi_dot(const fespmv_mat* A, const VT* val, const XT* P, XT* Q, int kw, double* part,
+                          cudaStream_t s) {
+    switch (A->vec) {
+        case 1: return multi_dot_v<VT, XT, 1>(A, val, P, Q, kw, part, s);
+        case 4: return multi_dot_v<VT, XT, 4>(A, val, P, Q, kw, part, s);
+        default: return multi_dot_v<VT, XT, 2>(A, val, P, Q, kw, part, s);
+    }
+}
+
 template <int V, int KW>
 static void launch_multi_df_kw(const fespmv_mat* A, const float2* Xdf, const double* X, double* Y,
                                cudaStream_t s) {
@@ -413,6 +509,26 @@ static int apply_multi_t(fespmv_mat* A, const XT* X, XT* Y, int k, int flags, cu
     FESPMV_CUDA(cudaGetLastError());
     return FESPMV_OK;
 }
+
+unsigned launch_multi_dot(const fespmv_mat* A, const void* P, void* Q, int kw, bool f64, double* part,
+                          cudaStream_t s) {
+    if (f64)
+        return multi_dot<double, double>(A, A->d_val, (const double*)P, (double*)Q, kw, part, s);
+    return multi_dot<float, float>(A, A->d_val32, (const float*)P, (float*)Q, kw, part, s);
+}
+
+int launch_multi_f64(fespmv_mat* A, const double* X, double* Y, int kw, cudaStream_t s) {
+    if (A->d_vdf) return launch_multi_df(A, X, Y, kw, s);
+    launch_multi<double, double>(A, A->d_val, X, Y, kw, s);
+    return FESPMV_OK;
+}
+
+void launch_gather_rows_f64(const double* src, int lds, const int32_t* idx, double* dst, int ldd, int64_t n,
+                            int k, cudaStream_t s) {
+    gather_rows<double><<<grid_for(n * ldd, 256), 256, 0, s>>>(src, lds, idx, dst, ldd, n, k);
+}
+
+int multi_width(int k) { return padded_width(k); }
 
 }  // namespace fespmv
 
