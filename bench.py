@@ -70,7 +70,7 @@ def parse_args():
                     help="time the FE product only (for profiling runs)")
     ap.add_argument("--multi-cg", type=int, default=1,
                     help="time cg_solve_multi with 32 right-hand sides on the workload matrix")
-    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32"], default=None,
+    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -746,7 +746,7 @@ def profile_piece(fs, torch, A, p, xp, args):
     --extras-vec), the CG pieces on the headline handle, as in the timed run."""
     n = p.n_rows
     t = args.profile_target
-    if t in ("multi", "multi64", "fp32"):
+    if t in ("multi", "multi64", "fp32", "cg_multi"):
         A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
                            vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32)
         xp = torch.rand_like(xp)          # any x in this handle's numbering
@@ -758,6 +758,12 @@ def profile_piece(fs, torch, A, p, xp, args):
         X = torch.rand((n, 32), dtype=torch.float64, device="cuda")
         Y = torch.empty_like(X)
         f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "cg_multi":
+        B = torch.rand((n, 32), dtype=torch.float64, device="cuda")
+        X = torch.zeros_like(B)
+        # 48 inner iterations (three graphs of 16) of the 32-RHS FP32 CG with reliable updates
+        f = lambda: fs.cg_solve_multi(A, B, X, tol=1e-30, max_iter=48,  # noqa: E731
+                                      precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
     elif t == "fp32":
         xs = xp.float()
         ys = torch.empty_like(xs)

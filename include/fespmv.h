@@ -417,7 +417,9 @@ int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* co
  *          UNSUPPORTED.  max_iter bounds each column's iterations in total.
  *   res    NULL or k records, one per column.
  * Each column has its own scalars and stopping test, and its dot products are
- * reduced in a fixed order of their own: a column's x is bitwise the same
+ * reduced in a fixed order of their own (p.q: each lane sums the products of its
+ * at most 4 rows of a warp's unit in the vectors' precision, and those sums are
+ * added in FP64; the other dots in FP64): a column's x is bitwise the same
  * whatever the other columns hold (for the same padded width: k rounded up to
  * 4, 8, 16 or 32).
  *   FESPMV_CG_F64: every stop of the recurrence (||r|| <= tol ||b||) is checked

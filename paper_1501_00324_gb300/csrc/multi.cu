@@ -167,10 +167,16 @@ __global__ void __launch_bounds__(128, 4) sliced_multi(const uint4* __restrict__
 
 // The product of the lockstep CG of cg_solve_multi: Q = A P as sliced_multi
 // computes it, and for every column j the sum of p_ij q_ij over the rows this
-// block covered, in FP64, at part[blockIdx.x * KW + j].  The grid is resident
-// (persistent): each warp strides over the units, so the partial sums stay few.
+// block covered at part[blockIdx.x * KW + j].  Each lane sums the products of
+// its (at most 4) rows of a unit in the vectors' precision and accumulates those
+// sums in FP64: FP32 inner vectors then spend one conversion and one FP64 add per
+// unit and column instead of two conversions and a DFMA per row (the FP64 pipe,
+// which the conversions also occupy, was 45 % busy); the FP32 bound (6 blocks of
+// 128 threads per SM) gives it the occupancy of the plain product.
+// The grid is resident (persistent): each warp strides over the units, so the
+// partial sums stay few.
 template <typename VT, typename XT, int V, int KW, int RW>
-__global__ void __launch_bounds__(128, 4) sliced_multi_dot(const uint4* __restrict__ meta,
+__global__ void __launch_bounds__(128, sizeof(XT) == 4 ? 6 : 4) sliced_multi_dot(const uint4* __restrict__ meta,
                                                            const int32_t* __restrict__ col,
                                                            const VT* __restrict__ val,
                                                            const XT* __restrict__ P, XT* __restrict__ Q,
@@ -186,15 +192,18 @@ __global__ void __launch_bounds__(128, 4) sliced_multi_dot(const uint4* __restri
         XT acc[R][4];
         multi_unit<VT, XT, V, KW, RW>(meta, col, val, P, Q, gw, n, lane, acc);
         const int64_t row0 = (int64_t)meta[gw / WPS].z + (int)(gw % WPS) * RW + g * R;
+        XT t[4] = {XT(0), XT(0), XT(0), XT(0)};
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             if (row0 + i < n) {
                 XT pv[4] = {XT(0), XT(0), XT(0), XT(0)};
                 ld_x4(P + (row0 + i) * KW + 4 * q, true, pv);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) d[j] = fma((double)pv[j], (double)acc[i][j], d[j]);
+                for (int j = 0; j < 4; ++j) t[j] = fma(pv[j], acc[i][j], t[j]);
             }
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] += (double)t[j];
     }
     // lanes with the same q hold the same columns: sum over the warp's groups
 #pragma unroll
