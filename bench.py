@@ -563,8 +563,10 @@ def bench_serving(fs, torch, args):
                 "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
                 "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None}
 
-    def run_server(trace):
+    def run_server(trace, group=0):
         S = fs.srv_create(48 << 30, 64)
+        if group:
+            fs.srv_set_grouping(S, group)
         ids = [fs.srv_register(S, A) for A in mats]
         tickets = []
         start = time.perf_counter()
@@ -587,6 +589,8 @@ def bench_serving(fs, torch, args):
         out = summarize(trace, lat, served, elapsed)
         out.update({"precision": "f32_reliable", "peak_active": st["peak_active"],
                     "peak_workspace_gb": round(st["peak_workspace_bytes"] / 2 ** 30, 2)})
+        if group:
+            out["grouping"] = "lockstep multi-RHS groups, width by matrix size (srv_set_grouping -1)"
         return out
 
     def run_single(trace):
@@ -609,12 +613,13 @@ def bench_serving(fs, torch, args):
         out["precision"] = "f64"
         return out
 
-    over = {"server": run_server(trace), "one_at_a_time": run_single(trace)}
+    over = {"server": run_server(trace), "server_grouped": run_server(trace, -1),
+            "one_at_a_time": run_single(trace)}
     # a second arrival stream at 80 % of the one-at-a-time capacity, where queues stay short
     rate2 = 0.8 * max(1.0, over["one_at_a_time"]["solves_per_s"])
     trace2 = make_trace(rate2, 1507)
     steady = {"rate_per_s": round(rate2, 1), "server": run_server(trace2),
-              "one_at_a_time": run_single(trace2)}
+              "server_grouped": run_server(trace2, -1), "one_at_a_time": run_single(trace2)}
     for A in mats:
         fs.spmv_destroy(A)
     return {"pool": {"meshes": n_mesh, "rows_min": min(p.n_rows for p in pool),

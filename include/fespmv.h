@@ -508,6 +508,7 @@ typedef struct {
 typedef struct {
     int64_t submitted, completed, queued, active, peak_active;
     int64_t workspace_bytes, peak_workspace_bytes;
+    int64_t grouped;      /* requests admitted to lockstep groups (srv_set_grouping) */
 } srv_stats;
 
 /*
@@ -528,6 +529,37 @@ typedef struct {
  * Errors: INVALID_ARG, OOM.
  */
 int srv_create(fespmv_server_t* out, int64_t workspace_budget_bytes, int32_t max_active);
+
+/*
+ * srv_set_grouping -- solve the requests on one matrix together, as the columns
+ * of a lockstep multi-RHS CG (the algorithm of cg_solve_multi), so that one pass
+ * over the matrix serves all of them.  Each registered matrix gets at most one
+ * group at a time, of a fixed width:
+ *   width  0 = off (default: every request takes the single path above);
+ *          4, 8, 16 or 32 = that many columns for every matrix;
+ *          -1 = by size: 32 columns while n_rows * 32 <= 2^21, halved until
+ *          n_rows * width <= 2^21, at least 4.
+ * A group pays off when it holds two or more right-hand sides, so a request takes
+ * it when at least two requests of its matrix wait in the queue or the group
+ * already holds two (a lone request takes the single path, which is faster for
+ * one right-hand side).  It joins a free column of its matrix's group (wherever it
+ * stands in the queue: a full group does not hold up other requests), starts at the group's
+ * next FP64 outer step (they come every 8 * check_every inner iterations, or at
+ * once when no column iterates) and finishes at the outer step that finds it
+ * converged, stopped or broken down; its column is then free for the next
+ * request.  Its x is bitwise equal to cg_solve_multi's for that right-hand side
+ * alone with the group's width (e.g. k = width with the other columns zero), and
+ * within the tolerance of cg_solve's; which path a request takes depends on the
+ * load, so with grouping on a result equals one of the two solves alone.  A group counts as one solve toward
+ * max_active and holds group workspace (seven n_rows x width arrays of doubles)
+ * in the budget; an idle group is kept for reuse and released when the budget
+ * needs room.  Requests a group cannot take (FESPMV_CG_BF16_REFINE,
+ * FESPMV_CG_SINGLE_REDUCTION, options other than those of its matrix's running
+ * group: precision, flags, check_every; a handle that cg_solve_multi rejects)
+ * take the single path.  Affects requests admitted after the call.  Errors:
+ * INVALID_ARG (bad width).
+ */
+int srv_set_grouping(fespmv_server_t S, int32_t width);
 
 /* Make handle A solvable by the server; *matrix_id names it in srv_submit.  The
  * handle stays the caller's: it must outlive the server and must not be used

@@ -104,7 +104,7 @@ class srv_timing(ctypes.Structure):
 class srv_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "queued", "active",
                                               "peak_active", "workspace_bytes",
-                                              "peak_workspace_bytes")]
+                                              "peak_workspace_bytes", "grouped")]
 
 
 def _load():
@@ -149,6 +149,8 @@ _lib.cg_solve_multi.argtypes = [_P, _P, _P, _i32, ctypes.POINTER(cg_options), _P
 _lib.cg_solve_multi.restype = ctypes.c_int
 _lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
 _lib.srv_create.restype = ctypes.c_int
+_lib.srv_set_grouping.argtypes = [_P, _i32]
+_lib.srv_set_grouping.restype = ctypes.c_int
 _lib.srv_register.argtypes = [_P, _P, ctypes.POINTER(_i32)]
 _lib.srv_register.restype = ctypes.c_int
 _lib.srv_submit.argtypes = [_P, _i32, _P, ctypes.POINTER(cg_options), ctypes.POINTER(_i64)]
@@ -431,6 +433,11 @@ def srv_create(workspace_budget_bytes: int, max_active: int) -> Server:
     h = _P()
     _check(_lib.srv_create(ctypes.byref(h), workspace_budget_bytes, max_active))
     return Server(h, {})
+
+
+def srv_set_grouping(S: Server, width: int):
+    """Solve requests on one matrix together in lockstep groups (0 off, 4/8/16/32, -1 by size)."""
+    _check(_lib.srv_set_grouping(S.handle, width))
 
 
 def srv_register(S: Server, A: Matrix) -> int:

@@ -38,16 +38,19 @@
 
 #include "cg_run.h"
 #include "internal.h"
+#include "multi_group.h"
 
 namespace fespmv {
 
 struct MScal {
     double rho, alpha, beta, rr_in, thresh_in, thresh_due, rr, bb, thresh2, prev;
+    double tol2, in2;   // this column's tol^2 and inner_tol^2
     int iters, iters_in, status_in, status_out, outer, max_iter, max_outer;
-    int due;   // the inner residual has fallen by inner_tol: replace it at the next outer step
-    int act;   // this outer step acts on the column: 1 its inner CG has stopped, 2 it is due
-               // and still iterating (its p already follows the last residual), 0 neither
-    int pad;
+    int due;    // the inner residual has fallen by inner_tol: replace it at the next outer step
+    int act;    // this outer step acts on the column: 1 its inner CG has stopped, 2 it is due
+                // and still iterating (its p already follows the last residual), 3 it is new
+                // (x = x0, nothing to fold in), 0 none of these
+    int fresh;  // set for a column whose first outer step is still to come
 };
 
 struct MultiWork {
@@ -58,7 +61,7 @@ struct MultiWork {
     int64_t part_len = 0;
     MScal* sc = nullptr;
     MScal* h_sc = nullptr;                       // pinned mirror
-    int64_t grown_bytes = 0;                     // device bytes of the width-dependent arrays
+    int64_t bytes = 0;                           // device bytes held
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     int g_kw = 0, g_f64 = -1, g_pre = -1, g_chunk = 0;
@@ -364,8 +367,8 @@ __global__ void __launch_bounds__(kUpdBlock) mc_residual(int64_t n, const double
 // when it estimates ||b - A x|| <= tol ||b|| (||r|| ~ ||r_in|| ||r|| / ||S r|| at
 // this step).  FP64 (f64): the inner CG runs to tol ||b|| on its own recurrence;
 // rho = r.z.
-__global__ void mc_finalize_res(const double* __restrict__ part, int64_t nb, int kw, MScal* sc, double tol2,
-                                double in2, int reliable, int f64) {
+__global__ void mc_finalize_res(const double* __restrict__ part, int64_t nb, int kw, MScal* sc, int reliable,
+                                int f64) {
     const int c = blockIdx.x;
     if (!sc[c].act) return;
     const double rr = column_sum(part, nb, kw, c);
@@ -374,10 +377,12 @@ __global__ void mc_finalize_res(const double* __restrict__ part, int64_t nb, int
     const double rz = column_sum(part + 3 * nb * kw, nb, kw, c);
     if (threadIdx.x == 0) {
         MScal& s = sc[c];
+        const double tol2 = s.tol2, in2 = s.in2;
         s.rr = rr;
         s.bb = bb;
         s.thresh2 = tol2 * bb;
         s.due = 0;
+        s.fresh = 0;
         s.status_in = CG_CONVERGED;    // idle unless another inner phase starts below
         if (!isfinite(rr) || !isfinite(rhs2) || !isfinite(rz)) s.status_out = CG_BREAKDOWN;
         else if (rr <= s.thresh2) s.status_out = CG_CONVERGED;
@@ -409,14 +414,15 @@ __global__ void mc_finalize_res(const double* __restrict__ part, int64_t nb, int
     }
 }
 
-// x += S w (refinement) or x += w (FP64) for the columns the outer step acts on.
+// x += S w (refinement) or x += w (FP64) for the columns the outer step acts on
+// (not the new ones: their w is another column's leftover).
 template <typename T, int KW>
 __global__ void __launch_bounds__(kUpdBlock) mc_xupdate(int64_t n, double* __restrict__ x,
                                                         const double* __restrict__ scale, const T* __restrict__ w,
                                                         const MScal* __restrict__ sc) {
     constexpr int LPG = KW / 4;
     __shared__ int s_run[KW];
-    if (threadIdx.x < KW) s_run[threadIdx.x] = sc[threadIdx.x].act != 0;
+    if (threadIdx.x < KW) s_run[threadIdx.x] = sc[threadIdx.x].act == 1 || sc[threadIdx.x].act == 2;
     __syncthreads();
     const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int qd = (int)(first % LPG);
@@ -438,13 +444,13 @@ __global__ void __launch_bounds__(kUpdBlock) mc_xupdate(int64_t n, double* __res
     }
 }
 
-// The columns this outer step acts on; with `count`, their outer steps are counted.
-__global__ void mc_mark_act(int kw, int count, MScal* sc) {
+// The columns this outer step acts on; the finished inner phases are counted.
+__global__ void mc_mark_act(int kw, MScal* sc) {
     const int c = threadIdx.x;
     if (c < kw) {
         MScal& s = sc[c];
-        s.act = s.status_out != CG_RUNNING ? 0 : s.status_in != CG_RUNNING ? 1 : s.due ? 2 : 0;
-        if (count && s.act) s.outer += 1;
+        s.act = s.status_out != CG_RUNNING ? 0 : s.fresh ? 3 : s.status_in != CG_RUNNING ? 1 : s.due ? 2 : 0;
+        if (s.act == 1 || s.act == 2) s.outer += 1;
     }
 }
 
@@ -555,52 +561,71 @@ static void destroy_multi_work(MultiWork* w) {
     delete w;
 }
 
-// Workspace for width kw (grown when a wider solve comes): x, b, q64 (FP64) and
-// w, r, p, q (8-byte entries, used as float by the refinement), n x kw each.
-static int ensure_multi_work(fespmv_mat* A, int kw, int64_t part_len) {
-    MultiWork* w = A->mcg;
-    if (w && w->kw >= kw && w->part_len >= part_len) return FESPMV_OK;
-    if (w) {
-        for (void* p : {(void*)w->x, (void*)w->b, (void*)w->q64, w->w, w->r, w->p, w->q, (void*)w->part})
-            if (p) cudaFree(p);
-        A->device_bytes -= w->grown_bytes;
-        w->x = w->b = w->q64 = nullptr;
-        w->w = w->r = w->p = w->q = nullptr;
-        w->part = nullptr;
-        w->grown_bytes = 0;
-        if (w->graph) {
-            cudaGraphExecDestroy(w->graph);
-            w->graph = nullptr;
-        }
-    } else {
-        w = new MultiWork();
-        A->mcg = w;
-        int rc;
-        if ((rc = device_alloc(A, (void**)&w->dinv, sizeof(double) * (size_t)A->n, "multi-RHS dinv")) ||
-            (rc = device_alloc(A, (void**)&w->sc, sizeof(MScal) * 32, "multi-RHS scalars")))
-            return rc;
-        FESPMV_CUDA(cudaMallocHost((void**)&w->h_sc, sizeof(MScal) * 32));
-        FESPMV_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+static int mw_alloc(MultiWork* w, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu bytes) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FESPMV_ERR_OOM : FESPMV_ERR_CUDA;
     }
-    const int kn = std::max(kw, w->kw);
-    const int64_t pl = std::max(part_len, w->part_len);
-    const size_t bytes = sizeof(double) * (size_t)A->n * kn;
-    const int64_t before = A->device_bytes;
+    w->bytes += (int64_t)bytes;
+    return FESPMV_OK;
+}
+
+// Partial sums for either precision's grids at width kw.
+static int64_t multi_part_len(const fespmv_mat* A, int kw) {
+    const unsigned g32 = launch_multi_dot(A, nullptr, nullptr, kw, false, nullptr, nullptr);
+    const unsigned g64 = launch_multi_dot(A, nullptr, nullptr, kw, true, nullptr, nullptr);
+    return (int64_t)std::max({g32, g64, 4 * update_grid(A->n, kw)}) * kw;
+}
+
+// Workspace of a lockstep solve of width kw: x, b, A x (FP64) and w, r, p, q (8-byte
+// entries, used as float by the refinement), n x kw each; 1/diag; partial sums;
+// per-column scalars (device and pinned host); a stream for graph capture.
+static int create_multi_work(const fespmv_mat* A, int kw, MultiWork** out) {
+    *out = nullptr;
+    MultiWork* w = new MultiWork();
+    const size_t bytes = sizeof(double) * (size_t)A->n * kw;
+    const int64_t pl = multi_part_len(A, kw);
     int rc;
-    if ((rc = device_alloc(A, (void**)&w->x, bytes, "multi-RHS x")) ||
-        (rc = device_alloc(A, (void**)&w->b, bytes, "multi-RHS b")) ||
-        (rc = device_alloc(A, (void**)&w->q64, bytes, "multi-RHS A x")) ||
-        (rc = device_alloc(A, &w->w, bytes, "multi-RHS w")) || (rc = device_alloc(A, &w->r, bytes, "multi-RHS r")) ||
-        (rc = device_alloc(A, &w->p, bytes, "multi-RHS p")) || (rc = device_alloc(A, &w->q, bytes, "multi-RHS q")) ||
-        (rc = device_alloc(A, (void**)&w->part, sizeof(double) * (size_t)pl, "multi-RHS partial sums"))) {
-        w->grown_bytes = A->device_bytes - before;
-        w->kw = 0;
-        w->part_len = 0;
+    if ((rc = mw_alloc(w, (void**)&w->x, bytes, "multi-RHS x")) ||
+        (rc = mw_alloc(w, (void**)&w->b, bytes, "multi-RHS b")) ||
+        (rc = mw_alloc(w, (void**)&w->q64, bytes, "multi-RHS A x")) ||
+        (rc = mw_alloc(w, &w->w, bytes, "multi-RHS w")) || (rc = mw_alloc(w, &w->r, bytes, "multi-RHS r")) ||
+        (rc = mw_alloc(w, &w->p, bytes, "multi-RHS p")) || (rc = mw_alloc(w, &w->q, bytes, "multi-RHS q")) ||
+        (rc = mw_alloc(w, (void**)&w->dinv, sizeof(double) * (size_t)A->n, "multi-RHS dinv")) ||
+        (rc = mw_alloc(w, (void**)&w->part, sizeof(double) * (size_t)pl, "multi-RHS partial sums")) ||
+        (rc = mw_alloc(w, (void**)&w->sc, sizeof(MScal) * 32, "multi-RHS scalars"))) {
+        destroy_multi_work(w);
         return rc;
     }
-    w->grown_bytes = A->device_bytes - before;
-    w->kw = kn;
+    cudaError_t e = cudaMallocHost((void**)&w->h_sc, sizeof(MScal) * 32);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        destroy_multi_work(w);
+        return cuda_fail(e, "multi-RHS workspace");
+    }
+    w->kw = kw;
     w->part_len = pl;
+    *out = w;
+    return FESPMV_OK;
+}
+
+// The handle's own workspace (cg_solve_multi), grown to width kw.
+static int ensure_handle_work(fespmv_mat* A, int kw) {
+    if (A->mcg && A->mcg->kw >= kw) return FESPMV_OK;
+    if (A->mcg) {
+        A->device_bytes -= A->mcg->bytes;
+        destroy_multi_work(A->mcg);
+        A->mcg = nullptr;
+    }
+    MultiWork* w = nullptr;
+    int rc = create_multi_work(A, kw, &w);
+    if (rc) return rc;
+    A->mcg = w;
+    A->device_bytes += w->bytes;
     return FESPMV_OK;
 }
 
@@ -633,55 +658,135 @@ static int read_scalars(MultiWork* w, int kw, cudaStream_t s) {
     return FESPMV_OK;
 }
 
+// 1/diag (Jacobi of the FP64 solve; 1 with NO_PRECOND) and the check of diag(A) > 0
+// that Jacobi and S = D^-1/2 need.  Returns FESPMV_ERR_BREAKDOWN for a bad diagonal.
+static int prepare_diag(const fespmv_mat* A, MultiWork* w, Shape sh, cudaStream_t s) {
+    int* bad = reinterpret_cast<int*>(w->part);   // scratch: the partial sums are rewritten later
+    FESPMV_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    mc_dinv<<<grid_for(A->n, 256), 256, 0, s>>>(A->n, A->d_diag, w->dinv, (!sh.f64 || sh.pre) ? 1 : 0, bad);
+    FESPMV_CUDA(cudaGetLastError());
+    int h_bad = 0;
+    FESPMV_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    if (h_bad) {
+        set_error("the diagonal has a non-positive or non-finite entry");
+        return FESPMV_ERR_BREAKDOWN;
+    }
+    return FESPMV_OK;
+}
+
+// Scalars of a column before its first outer step.
+static MScal new_column(const cg_options& o, bool f64) {
+    MScal z;
+    std::memset(&z, 0, sizeof(z));
+    z.status_out = CG_RUNNING;
+    z.status_in = CG_CONVERGED;
+    z.fresh = 1;
+    z.prev = INFINITY;
+    z.tol2 = o.tol * o.tol;
+    z.in2 = o.inner_tol * o.inner_tol;
+    z.max_iter = o.max_iter;
+    z.max_outer = f64 ? o.max_restarts + 1 : o.max_outer;   // FP64: the first solve and its restarts
+    return z;
+}
+
+static cg_result column_result(const MScal& h, bool f64) {
+    cg_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.status = h.status_out == CG_CONVERGED ? FESPMV_OK
+             : h.status_out == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
+    r.iters = h.iters;
+    r.restarts = f64 ? std::max(h.outer - 1, 0) : 0;
+    r.outer = f64 ? 0 : h.outer;
+    r.relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    r.true_relres = r.relres;
+    return r;
+}
+
+// One outer step for the columns it acts on (see mc_mark_act): fold the inner
+// corrections into x, r = b - A x in FP64 (ax: A x computed; else x = 0), the
+// convergence tests and the start of the next inner phases.
+static int enqueue_outer(fespmv_mat* A, MultiWork* w, Shape sh, int reliable, bool ax, unsigned upd_grid,
+                         cudaStream_t s) {
+    const int kw = sh.kw;
+    mc_mark_act<<<1, 32, 0, s>>>(kw, w->sc);
+    if (sh.f64) xupdate_t<double>(A, w, kw, false, upd_grid, s);
+    else xupdate_t<float>(A, w, kw, true, upd_grid, s);
+    if (ax) {
+        int rc = launch_multi_f64(A, w->x, w->q64, kw, s);
+        if (rc) return rc;
+    }
+    if (sh.f64) {
+        if (sh.pre) outer_t<double, true>(A, w, kw, ax, 0, upd_grid, s);
+        else outer_t<double, false>(A, w, kw, ax, 0, upd_grid, s);
+    } else {
+        outer_t<float, false>(A, w, kw, ax, reliable, upd_grid, s);
+    }
+    mc_finalize_res<<<kw, 256, 0, s>>>(w->part, upd_grid, kw, w->sc, reliable, sh.f64 ? 1 : 0);
+    // reliable updates: the kept directions take the replaced residuals
+    if (reliable) replaced_pupdate(A, w, kw, upd_grid, s);
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+// Where a column stands after a scalar read: still iterating, or waiting for an
+// outer step (due, or its inner CG stopped).
+static void column_flags(const MScal& h, bool& iterating, bool& acted) {
+    iterating |= h.status_in == CG_RUNNING;
+    acted |= h.status_out == CG_RUNNING && (h.status_in != CG_RUNNING || h.due);
+}
+
+// Options shared by cg_solve_multi and the server's groups.
+static int check_multi_options(const fespmv_mat* A, const cg_options& o, const char* who) {
+    if (o.flags & FESPMV_CG_SINGLE_REDUCTION) {
+        set_error("%s: FESPMV_CG_SINGLE_REDUCTION is not supported", who);
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    if (o.precision == FESPMV_CG_BF16_REFINE) {
+        set_error("%s: FESPMV_CG_BF16_REFINE is not supported (FP64 or FP32 refinement)", who);
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    if (A->format != FESPMV_FMT_SLICED || A->max_lanes_log2 != 0) {
+        set_error("%s needs a SLICED handle with one lane per row (threshold 0)", who);
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    return check_precision(A, o.precision);
+}
+
+static Shape shape_of(int kw, const cg_options& o) {
+    const bool f64 = o.precision == FESPMV_CG_F64;
+    return Shape{kw, f64, f64 && !(o.flags & FESPMV_CG_NO_PRECOND)};
+}
+
 static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, const cg_options* opts,
                             cg_result* res, cudaStream_t s) {
     cg_options o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     int rc = normalize_options(o);
-    if (rc) return rc;
-    if (o.flags & FESPMV_CG_SINGLE_REDUCTION) {
-        set_error("cg_solve_multi: FESPMV_CG_SINGLE_REDUCTION is not supported");
-        return FESPMV_ERR_UNSUPPORTED;
-    }
-    if (o.precision == FESPMV_CG_BF16_REFINE) {
-        set_error("cg_solve_multi: FESPMV_CG_BF16_REFINE is not supported (FP64 or FP32 refinement)");
-        return FESPMV_ERR_UNSUPPORTED;
-    }
-    if ((rc = check_precision(A, o.precision))) return rc;
+    if (rc || (rc = check_multi_options(A, o, "cg_solve_multi"))) return rc;
     if (A->n == 0) {   // empty system: every column is solved by x = 0
         if (res)
             for (int j = 0; j < k; ++j) std::memset(&res[j], 0, sizeof(cg_result));
         return FESPMV_OK;
     }
-    const bool f64 = o.precision == FESPMV_CG_F64;
-    const Shape sh{multi_width(k), f64, f64 && !(o.flags & FESPMV_CG_NO_PRECOND)};
+    const Shape sh = shape_of(multi_width(k), o);
+    const bool f64 = sh.f64;
     const int kw = sh.kw;
     const int64_t n = A->n;
-    const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, f64, nullptr, s);
+    const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, f64, nullptr, nullptr);
     const unsigned upd_grid = update_grid(n, kw);
-    const int64_t part_len = (int64_t)std::max(dot_grid, 4 * upd_grid) * 32;
-    if ((rc = ensure_multi_work(A, kw, part_len))) return rc;
+    if ((rc = ensure_handle_work(A, kw))) return rc;
     MultiWork* w = A->mcg;
     if ((rc = multi_graph(A, w, sh, o.check_every, dot_grid, upd_grid))) return rc;
-
-    // the diagonal: Jacobi of the FP64 solve, or the positivity that S = D^-1/2 needs
-    int* bad = reinterpret_cast<int*>(w->sc);   // scalars are initialised below
-    FESPMV_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    mc_dinv<<<grid_for(std::max<int64_t>(n, 1), 256), 256, 0, s>>>(n, A->d_diag, w->dinv, (!f64 || sh.pre) ? 1 : 0,
-                                                                   bad);
-    FESPMV_CUDA(cudaGetLastError());
-    int h_bad = 0;
-    FESPMV_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FESPMV_CUDA(cudaStreamSynchronize(s));
-    if (h_bad) {
-        set_error("cg_solve_multi: the diagonal has a non-positive or non-finite entry");
+    if ((rc = prepare_diag(A, w, sh, s))) {
         if (res)
             for (int j = 0; j < k; ++j) {
                 std::memset(&res[j], 0, sizeof(cg_result));
-                res[j].status = FESPMV_ERR_BREAKDOWN;
+                res[j].status = rc;
             }
-        return FESPMV_ERR_BREAKDOWN;
+        set_error("cg_solve_multi: the diagonal has a non-positive or non-finite entry");
+        return rc;
     }
 
     // b (and x0) into the handle's numbering, row stride kw
@@ -708,18 +813,8 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
     // inner vectors start at zero: kept directions and frozen columns read defined values
     for (void* v : {w->w, w->r, w->p, w->q})
         FESPMV_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * (size_t)n * kw, s));
-    for (int j = 0; j < kw; ++j) {
-        MScal z;
-        std::memset(&z, 0, sizeof(z));
-        z.status_out = CG_RUNNING;
-        z.status_in = CG_CONVERGED;
-        z.prev = INFINITY;
-        z.max_iter = o.max_iter;
-        z.max_outer = f64 ? o.max_restarts + 1 : o.max_outer;   // FP64: the first solve and its restarts
-        w->h_sc[j] = z;
-    }
+    for (int j = 0; j < kw; ++j) w->h_sc[j] = new_column(o, f64);
     FESPMV_CUDA(cudaMemcpyAsync(w->sc, w->h_sc, sizeof(MScal) * kw, cudaMemcpyHostToDevice, s));
-    const double tol2 = o.tol * o.tol, in2 = o.inner_tol * o.inner_tol;
     const int reliable = (o.flags & FESPMV_CG_RELIABLE) ? 1 : 0;
     // Outer steps come on a fixed grid of `period` inner iterations (and when no
     // column is iterating, the next grid point is taken at once: the idle steps in
@@ -728,24 +823,7 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
     const int64_t period = (int64_t)o.check_every * kOuterChunks;
     int64_t it = 0;   // inner iterations on the grid
     for (int step = 0;; ++step) {
-        mc_mark_act<<<1, 32, 0, s>>>(kw, step > 0 ? 1 : 0, w->sc);
-        if (step > 0) {
-            if (f64) xupdate_t<double>(A, w, kw, false, upd_grid, s);
-            else xupdate_t<float>(A, w, kw, true, upd_grid, s);
-        }
-        const bool ax = x0 || step > 0;
-        if (ax && (rc = launch_multi_f64(A, w->x, w->q64, kw, s))) return rc;
-        if (f64) {
-            if (sh.pre) outer_t<double, true>(A, w, kw, ax, 0, upd_grid, s);
-            else outer_t<double, false>(A, w, kw, ax, 0, upd_grid, s);
-        } else {
-            outer_t<float, false>(A, w, kw, ax, reliable, upd_grid, s);
-        }
-        mc_finalize_res<<<kw, 256, 0, s>>>(w->part, upd_grid, kw, w->sc, tol2, in2, reliable, f64 ? 1 : 0);
-        // reliable updates: the kept directions take the replaced residuals (beta = 0 at the
-        // first step, where p = r_in already)
-        if (reliable) replaced_pupdate(A, w, kw, upd_grid, s);
-        FESPMV_CUDA(cudaGetLastError());
+        if ((rc = enqueue_outer(A, w, sh, reliable, x0 || step > 0, upd_grid, s))) return rc;
         if ((rc = read_scalars(w, kw, s))) return rc;
         bool running = false;
         for (int j = 0; j < kw; ++j) running |= w->h_sc[j].status_in == CG_RUNNING;
@@ -755,11 +833,7 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
             it += o.check_every;
             if ((rc = read_scalars(w, kw, s))) return rc;
             bool iterating = false, acted = false;
-            for (int j = 0; j < kw; ++j) {
-                const MScal& h = w->h_sc[j];
-                iterating |= h.status_in == CG_RUNNING;
-                acted |= h.status_out == CG_RUNNING && (h.status_in != CG_RUNNING || h.due);
-            }
+            for (int j = 0; j < kw; ++j) column_flags(w->h_sc[j], iterating, acted);
             if (!iterating) {
                 it = (it + period - 1) / period * period;
                 break;
@@ -775,27 +849,259 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
     FESPMV_CUDA(cudaStreamSynchronize(s));
     int worst = FESPMV_OK;
     for (int j = 0; j < k; ++j) {
-        const MScal& h = w->h_sc[j];
-        const int st = h.status_out == CG_CONVERGED ? FESPMV_OK
-                     : h.status_out == CG_BREAKDOWN ? FESPMV_ERR_BREAKDOWN : FESPMV_ERR_NOT_CONVERGED;
-        if (st != FESPMV_OK && worst == FESPMV_OK) worst = st;
-        if (res) {
-            res[j].status = st;
-            res[j].iters = h.iters;
-            res[j].restarts = f64 ? std::max(h.outer - 1, 0) : 0;
-            res[j].outer = f64 ? 0 : h.outer;
-            res[j].relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-            res[j].true_relres = res[j].relres;
-        }
+        const cg_result r = column_result(w->h_sc[j], f64);
+        if (r.status != FESPMV_OK && worst == FESPMV_OK) worst = r.status;
+        if (res) res[j] = r;
     }
     if (worst != FESPMV_OK) set_error("cg_solve_multi: at least one right-hand side did not converge");
     return worst;
 }
 
+// ------------------------------------------------------------------ groups of the solve server
+
+// out[i] = M[pinv[i], c] (row stride kw): one column of x in the input numbering.
+__global__ void mc_extract_column(const double* __restrict__ M, int kw, int c, const int32_t* __restrict__ pinv,
+                                  double* __restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = M[(int64_t)pinv[i] * kw + c];
+}
+
+// M[i, c] = in[perm[i]] (in == nullptr: 0): one column of b, or x = 0.
+__global__ void mc_insert_column(const double* __restrict__ in, const int32_t* __restrict__ perm,
+                                 double* __restrict__ M, int kw, int c, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) M[i * kw + c] = in ? in[perm[i]] : 0.0;
+}
+
 }  // namespace
+
+struct GroupColumn {
+    int state = 0;            // 0 free, 1 waiting for an outer step, 2 solving
+    int64_t tag = 0;
+    std::vector<double> b;
+    cg_options o{};
+};
+
+struct MultiGroup {
+    fespmv_mat* A = nullptr;
+    MultiWork* w = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    Shape sh{};
+    int reliable = 0, precision = 0, flags = 0, chunk = 16;
+    int64_t period = 0, it = 0;
+    unsigned upd_grid = 0;
+    int phase = 0;            // 0 nothing enqueued, 1 an outer step, 2 a graph of inner iterations
+    std::vector<GroupColumn> cols;
+    double* d_io = nullptr;   // one column in or out (n doubles)
+};
+
+namespace {
+
+void group_free(MultiGroup* g) {
+    if (!g) return;
+    if (g->s) cudaStreamSynchronize(g->s);
+    destroy_multi_work(g->w);
+    if (g->d_io) cudaFree(g->d_io);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->s) cudaStreamDestroy(g->s);
+    delete g;
+}
+
+// Inject the waiting columns, enqueue an outer step and the read of the scalars.
+int group_start_outer(MultiGroup* g) {
+    fespmv_mat* A = g->A;
+    MultiWork* w = g->w;
+    const int kw = g->sh.kw;
+    const unsigned gr = grid_for(A->n, 256);
+    for (int c = 0; c < kw; ++c) {
+        GroupColumn& col = g->cols[(size_t)c];
+        if (col.state != 1) continue;
+        FESPMV_CUDA(cudaMemcpyAsync(g->d_io, col.b.data(), sizeof(double) * (size_t)A->n, cudaMemcpyHostToDevice,
+                                    g->s));
+        mc_insert_column<<<gr, 256, 0, g->s>>>(g->d_io, A->d_perm, w->b, kw, c, A->n);
+        mc_insert_column<<<gr, 256, 0, g->s>>>(nullptr, A->d_perm, w->x, kw, c, A->n);
+        w->h_sc[c] = new_column(col.o, g->sh.f64);
+        FESPMV_CUDA(cudaMemcpyAsync(w->sc + c, &w->h_sc[c], sizeof(MScal), cudaMemcpyHostToDevice, g->s));
+        col.state = 2;
+    }
+    int rc = enqueue_outer(A, w, g->sh, g->reliable, true, g->upd_grid, g->s);
+    if (rc) return rc;
+    FESPMV_CUDA(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(MScal) * kw, cudaMemcpyDeviceToHost, g->s));
+    FESPMV_CUDA(cudaEventRecord(g->ev, g->s));
+    g->phase = 1;
+    return FESPMV_OK;
+}
+
+}  // namespace
+
+// ---- the server's interface (multi_group.h)
+
+int group_width_auto(const fespmv_mat* A) {
+    int kw = 32;
+    while (kw > 4 && A->n * (int64_t)kw > ((int64_t)1 << 21)) kw /= 2;
+    return kw;
+}
+
+int64_t group_bytes(const fespmv_mat* A, int kw) {
+    return (int64_t)sizeof(double) * (7 * kw + 2) * A->n + (int64_t)sizeof(double) * multi_part_len(A, kw) +
+           (int64_t)sizeof(MScal) * 32;
+}
+
+int group_create(fespmv_mat* A, int kw, const cg_options& o, MultiGroup** out) {
+    *out = nullptr;
+    int rc = check_multi_options(A, o, "solve group");
+    if (rc) return rc;
+    if (A->n == 0) {
+        set_error("solve group: empty matrix");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    MultiGroup* g = new MultiGroup();
+    g->A = A;
+    g->sh = shape_of(kw, o);
+    g->reliable = (o.flags & FESPMV_CG_RELIABLE) ? 1 : 0;
+    g->precision = o.precision;
+    g->flags = o.flags & (FESPMV_CG_RELIABLE | FESPMV_CG_NO_PRECOND);
+    g->chunk = o.check_every;
+    g->period = (int64_t)o.check_every * kOuterChunks;
+    g->cols.resize((size_t)kw);
+    g->upd_grid = update_grid(A->n, kw);
+    const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, g->sh.f64, nullptr, nullptr);
+    cudaError_t e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_io, sizeof(double) * (size_t)A->n);
+    if (e != cudaSuccess) {
+        group_free(g);
+        return cuda_fail(e, "solve group");
+    }
+    if ((rc = create_multi_work(A, kw, &g->w)) || (rc = multi_graph(A, g->w, g->sh, g->chunk, dot_grid, g->upd_grid)) ||
+        (rc = prepare_diag(A, g->w, g->sh, g->s))) {
+        group_free(g);
+        return rc;
+    }
+    // inner vectors start at zero (columns that never ran still pass through the product)
+    for (void* v : {g->w->w, g->w->r, g->w->p, g->w->q}) {
+        e = cudaMemsetAsync(v, 0, sizeof(double) * (size_t)A->n * kw, g->s);
+        if (e != cudaSuccess) {
+            group_free(g);
+            return cuda_fail(e, "cudaMemsetAsync");
+        }
+    }
+    // every column starts finished and idle
+    MScal idle;
+    std::memset(&idle, 0, sizeof(idle));
+    idle.status_out = CG_CONVERGED;
+    idle.status_in = CG_CONVERGED;
+    for (int c = 0; c < kw; ++c) g->w->h_sc[c] = idle;
+    e = cudaMemcpyAsync(g->w->sc, g->w->h_sc, sizeof(MScal) * kw, cudaMemcpyHostToDevice, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    if (e != cudaSuccess) {
+        group_free(g);
+        return cuda_fail(e, "solve group");
+    }
+    *out = g;
+    return FESPMV_OK;
+}
+
+void group_destroy(MultiGroup* g) { group_free(g); }
+
+int64_t group_device_bytes(const MultiGroup* g) {
+    return g->w->bytes + (int64_t)sizeof(double) * g->A->n;
+}
+
+bool group_matches(const MultiGroup* g, const cg_options& o) {
+    return g->precision == o.precision && g->flags == (o.flags & (FESPMV_CG_RELIABLE | FESPMV_CG_NO_PRECOND)) &&
+           g->chunk == o.check_every;
+}
+
+int group_free_columns(const MultiGroup* g) {
+    int k = 0;
+    for (const GroupColumn& c : g->cols) k += c.state == 0;
+    return k;
+}
+
+int group_width_of(const MultiGroup* g) { return g->sh.kw; }
+
+bool group_empty(const MultiGroup* g) {
+    return g->phase == 0 && group_free_columns(g) == (int)g->cols.size();
+}
+
+int group_add(MultiGroup* g, int64_t tag, const double* b, const cg_options& o) {
+    for (GroupColumn& c : g->cols)
+        if (c.state == 0) {
+            c.state = 1;
+            c.tag = tag;
+            c.b.assign(b, b + g->A->n);
+            c.o = o;
+            return FESPMV_OK;
+        }
+    set_error("solve group: no free column");
+    return FESPMV_ERR_INVALID_ARG;
+}
+
+int group_step(MultiGroup* g, bool* progress, std::vector<GroupDone>& done) {
+    *progress = false;
+    const int kw = g->sh.kw;
+    if (g->phase == 0) {
+        bool waiting = false;
+        for (const GroupColumn& c : g->cols) waiting |= c.state == 1;
+        if (!waiting) return FESPMV_OK;
+        *progress = true;
+        return group_start_outer(g);
+    }
+    cudaError_t q = cudaEventQuery(g->ev);
+    if (q == cudaErrorNotReady) return FESPMV_OK;
+    if (q != cudaSuccess) return cuda_fail(q, "solve group");
+    *progress = true;
+    const MScal* h = g->w->h_sc;
+    const bool after_graph = g->phase == 2;
+    if (after_graph) {
+        g->it += g->chunk;
+    } else {   // the columns this outer step finished: x out, results
+        for (int c = 0; c < kw; ++c) {
+            GroupColumn& col = g->cols[(size_t)c];
+            if (col.state != 2 || h[c].status_out == CG_RUNNING) continue;
+            GroupDone d;
+            d.tag = col.tag;
+            d.res = column_result(h[c], g->sh.f64);
+            d.x.resize((size_t)g->A->n);
+            mc_extract_column<<<grid_for(g->A->n, 256), 256, 0, g->s>>>(g->w->x, kw, c, g->A->d_pinv, g->d_io,
+                                                                         g->A->n);
+            FESPMV_CUDA(cudaMemcpyAsync(d.x.data(), g->d_io, sizeof(double) * (size_t)g->A->n,
+                                        cudaMemcpyDeviceToHost, g->s));
+            FESPMV_CUDA(cudaStreamSynchronize(g->s));
+            done.push_back(std::move(d));
+            col.state = 0;
+            col.b.clear();
+            col.b.shrink_to_fit();
+        }
+    }
+    bool iterating = false, acted = false, waiting = false;
+    for (int c = 0; c < kw; ++c) {
+        const GroupColumn& col = g->cols[(size_t)c];
+        if (col.state == 2) column_flags(h[c], iterating, acted);
+        waiting |= col.state == 1;
+    }
+    if (!iterating) {
+        if (!acted && !waiting) {   // nothing left: the next column starts a fresh grid
+            g->phase = 0;
+            g->it = 0;
+            return FESPMV_OK;
+        }
+        g->it = (g->it + g->period - 1) / g->period * g->period;
+        return group_start_outer(g);
+    }
+    if (after_graph && g->it % g->period == 0 && (acted || waiting)) return group_start_outer(g);
+    FESPMV_CUDA(cudaGraphLaunch(g->w->graph, g->s));
+    FESPMV_CUDA(cudaMemcpyAsync(g->w->h_sc, g->w->sc, sizeof(MScal) * kw, cudaMemcpyDeviceToHost, g->s));
+    FESPMV_CUDA(cudaEventRecord(g->ev, g->s));
+    g->phase = 2;
+    return FESPMV_OK;
+}
 
 void free_multi_cg(fespmv_mat* A) {
     if (A && A->mcg) {
+        A->device_bytes -= A->mcg->bytes;
         destroy_multi_work(A->mcg);
         A->mcg = nullptr;
     }
@@ -811,10 +1117,6 @@ extern "C" int cg_solve_multi(fespmv_mat_t A, const double* B, double* X, int32_
         if (!A || k < 1 || k > 32 || (A->n > 0 && (!B || !X))) {
             set_error("cg_solve_multi: bad argument");
             return FESPMV_ERR_INVALID_ARG;
-        }
-        if (A->format != FESPMV_FMT_SLICED || A->max_lanes_log2 != 0) {
-            set_error("cg_solve_multi needs a SLICED handle with one lane per row (threshold 0)");
-            return FESPMV_ERR_UNSUPPORTED;
         }
         return solve_multi_impl(A, B, X, k, opts, res, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {

@@ -11,6 +11,17 @@
 // device while matrices stay resident.  A solve in the mix runs exactly the
 // kernels, grids and reduction order of cg_solve alone, so its result is
 // bitwise the same.
+//
+// With grouping on (srv_set_grouping), requests on the same matrix are solved
+// together as the columns of a lockstep multi-RHS CG (one group per matrix, a
+// fixed width per matrix): one pass over the matrix serves every column.  A
+// request takes the group when at least two of its matrix wait or the group
+// already holds two (a lone right-hand side is faster on the single path).  It
+// joins a free column at the group's next outer step and leaves at the outer
+// step that finishes it, so columns are refilled while the group runs; its x is
+// bitwise the same as cg_solve_multi of that right-hand side alone with the
+// group's width.  Requests the groups cannot take (BF16, the single-reduction
+// flag, options other than the group's) take the single path.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -21,6 +32,7 @@
 #include <vector>
 
 #include "cg_run.h"
+#include "multi_group.h"
 
 namespace fespmv {
 
@@ -39,6 +51,7 @@ struct Request {
     cg_options o{};
     cg_result res{};
     int state = RQ_QUEUED;
+    bool in_slot = false;       // running on the single path (not in a group)
     int rc = FESPMV_OK;
     std::string error;
     double t_submit = 0, t_start = 0, t_done = 0;
@@ -56,6 +69,8 @@ struct MatrixEntry {
     std::vector<CgWork*> idle;  // finished workspaces kept for reuse (their graphs too)
     int64_t bytes = 0;          // workspace bytes for this matrix
     double last_used = 0.0;
+    MultiGroup* group = nullptr;  // lockstep group of this matrix (grouping on)
+    int64_t group_bytes = 0;
 };
 
 }  // namespace
@@ -66,6 +81,8 @@ struct fespmv_server {
     int64_t budget = 0;
     int64_t used = 0;           // workspace bytes held (busy + idle)
     int max_active = 0;
+    int group_width = 0;        // 0: no groups; -1: per matrix by size; else the width
+    bool admit_dirty = true;    // something changed since admission last found nothing to start
     std::vector<fespmv::MatrixEntry> mats;
     std::deque<fespmv::Request*> queue;
     std::unordered_map<int64_t, fespmv::Request*> tickets;
@@ -77,7 +94,7 @@ struct fespmv_server {
     bool stop = false;
     int64_t next_ticket = 1;
     // statistics
-    int64_t submitted = 0, completed = 0, peak_active = 0, peak_bytes = 0;
+    int64_t submitted = 0, completed = 0, peak_active = 0, peak_bytes = 0, grouped = 0;
 };
 
 namespace fespmv {
@@ -92,21 +109,138 @@ static void release_work(fespmv_server* S, MatrixEntry& m, CgWork* w) {
 static bool make_room(fespmv_server* S, int64_t need) {
     while (S->used + need > S->budget) {
         MatrixEntry* victim = nullptr;
-        for (MatrixEntry& m : S->mats)
-            if (!m.idle.empty() && (!victim || m.last_used < victim->last_used)) victim = &m;
+        for (MatrixEntry& m : S->mats) {
+            const bool spare = !m.idle.empty() || (m.group && group_empty(m.group));
+            if (spare && (!victim || m.last_used < victim->last_used)) victim = &m;
+        }
         if (!victim) return false;
-        CgWork* w = victim->idle.back();
-        victim->idle.pop_back();
-        S->used -= w->bytes;
-        destroy_work(w);
+        if (!victim->idle.empty()) {
+            CgWork* w = victim->idle.back();
+            victim->idle.pop_back();
+            S->used -= w->bytes;
+            destroy_work(w);
+        } else {
+            group_destroy(victim->group);
+            victim->group = nullptr;
+            S->used -= victim->group_bytes;
+            victim->group_bytes = 0;
+        }
     }
     return true;
 }
 
-// Try to start the request at the head of the queue.  Lock held.
+static int active_groups(const fespmv_server* S) {
+    int k = 0;
+    for (const MatrixEntry& m : S->mats) k += m.group && !group_empty(m.group);
+    return k;
+}
+
+static void finish_request(fespmv_server* S, Request* q, int rc) {
+    q->rc = rc;
+    if (rc != FESPMV_OK) q->error = fespmv_last_error();
+    q->state = RQ_DONE;
+    q->t_done = now_s();
+    S->cv_done.notify_all();
+}
+
+// Requests a group can take: FP64 or FP32 refinement, no flags but reliable
+// updates and NO_PRECOND.
+static bool groupable(const fespmv_server* S, const MatrixEntry& m, const Request* q) {
+    if (S->group_width == 0 || m.A->format != FESPMV_FMT_SLICED || m.A->max_lanes_log2 != 0 || m.A->n == 0)
+        return false;
+    if (q->o.precision != FESPMV_CG_F64 && q->o.precision != FESPMV_CG_F32_REFINE) return false;
+    if (q->o.flags & ~(FESPMV_CG_RELIABLE | FESPMV_CG_NO_PRECOND | FESPMV_IO_HOST)) return false;
+    return !m.group || group_empty(m.group) || group_matches(m.group, q->o);
+}
+
+// Try to put queue entry `q` into its matrix's group.  Returns 1 when admitted
+// (or failed for good), 0 when it must wait.  Lock held.
+static int admit_to_group(fespmv_server* S, Request* q) {
+    MatrixEntry& m = S->mats[(size_t)q->matrix];
+    if (m.group && group_empty(m.group) && !group_matches(m.group, q->o)) {
+        group_destroy(m.group);   // an idle group with other options: rebuild it
+        m.group = nullptr;
+        S->used -= m.group_bytes;
+        m.group_bytes = 0;
+    }
+    if (!m.group) {
+        if ((int)S->active.size() + active_groups(S) >= S->max_active) return 0;
+        const int kw = S->group_width > 0 ? S->group_width : group_width_auto(m.A);
+        const int64_t need = group_bytes(m.A, kw);
+        if (need > S->budget) {   // never fits: take the single path instead
+            return -1;
+        }
+        if (!make_room(S, need)) return 0;
+        MultiGroup* g = nullptr;
+        int rc = group_create(m.A, kw, q->o, &g);
+        if (rc) {
+            finish_request(S, q, rc);
+            return 1;
+        }
+        m.group = g;
+        m.group_bytes = group_device_bytes(g);
+        S->used += m.group_bytes;
+        if (S->used > S->peak_bytes) S->peak_bytes = S->used;
+    }
+    if (group_empty(m.group) && (int)S->active.size() + active_groups(S) >= S->max_active) return 0;
+    if (group_free_columns(m.group) == 0) return 0;
+    int rc = group_add(m.group, q->ticket, q->b.data(), q->o);
+    if (rc) {
+        finish_request(S, q, rc);
+        return 1;
+    }
+    m.last_used = now_s();
+    q->state = RQ_RUNNING;
+    q->t_start = now_s();
+    q->b.clear();
+    q->b.shrink_to_fit();
+    const int64_t act = (int64_t)S->active.size() + active_groups(S);
+    if (act > S->peak_active) S->peak_active = act;
+    return 1;
+}
+
+// Admit what can start now.  Requests for groups are taken wherever they stand in
+// the queue (a full group does not hold up the others); the single path starts
+// the first of its requests in arrival order.  Lock held.
+static bool admit_single(fespmv_server* S, std::deque<Request*>::iterator pos);
+
+// Columns of m's group in use (waiting or solving).
+static int group_load(const MatrixEntry& m) {
+    return m.group ? (int)group_width_of(m.group) - group_free_columns(m.group) : 0;
+}
+
 static bool admit_one(fespmv_server* S) {
-    if (S->queue.empty() || (int)S->active.size() >= S->max_active) return false;
-    Request* q = S->queue.front();
+    // a group pays off when it holds two or more right-hand sides: requests take it
+    // when at least two of their matrix wait in the queue or its group already
+    // holds two; a lone request takes the single path
+    std::vector<int> waiting(S->mats.size(), 0);
+    if (S->group_width != 0)
+        for (const Request* q : S->queue)
+            if (groupable(S, S->mats[(size_t)q->matrix], q)) ++waiting[(size_t)q->matrix];
+    bool single_blocked = false;
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        Request* q = *it;
+        const MatrixEntry& m = S->mats[(size_t)q->matrix];
+        int r = -1;
+        if (groupable(S, m, q) && (waiting[(size_t)q->matrix] >= 2 || group_load(m) >= 2))
+            r = admit_to_group(S, q);
+        if (r == 1) {
+            if (q->state == RQ_RUNNING) ++S->grouped;
+            S->queue.erase(it);
+            return true;
+        }
+        if (r == 0) continue;
+        if (single_blocked) continue;
+        if (admit_single(S, it)) return true;
+        single_blocked = true;
+    }
+    return false;
+}
+
+// Try to start queue entry *pos on the single path.  Lock held.
+static bool admit_single(fespmv_server* S, std::deque<Request*>::iterator pos) {
+    if ((int)S->active.size() + active_groups(S) >= S->max_active) return false;
+    Request* q = *pos;
     MatrixEntry& m = S->mats[(size_t)q->matrix];
     CgWork* w = nullptr;
     if (!m.idle.empty()) {
@@ -122,14 +256,14 @@ static bool admit_one(fespmv_server* S) {
             q->error = fespmv_last_error();
             q->state = RQ_DONE;
             q->t_done = now_s();
-            S->queue.pop_front();
+            S->queue.erase(pos);
             S->cv_done.notify_all();
             return true;
         }
         S->used += w->bytes;
         if (S->used > S->peak_bytes) S->peak_bytes = S->used;
     }
-    S->queue.pop_front();
+    S->queue.erase(pos);
     Slot slot;
     slot.req = q;
     slot.w = w;
@@ -140,6 +274,7 @@ static bool admit_one(fespmv_server* S) {
         cudaStreamCreateWithFlags(&slot.s, cudaStreamNonBlocking);
     }
     q->state = RQ_RUNNING;
+    q->in_slot = true;
     q->t_start = now_s();
     CgRun& r = slot.run;
     r.A = m.A;
@@ -159,7 +294,8 @@ static bool admit_one(fespmv_server* S) {
         r.phase = PH_DONE;
     }
     S->active.push_back(slot);
-    if ((int64_t)S->active.size() > S->peak_active) S->peak_active = (int64_t)S->active.size();
+    const int64_t act = (int64_t)S->active.size() + active_groups(S);
+    if (act > S->peak_active) S->peak_active = act;
     return true;
 }
 
@@ -167,18 +303,36 @@ static void scheduler(fespmv_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lock(S->mu);
     for (;;) {
-        while (admit_one(S)) {
+        // a scan of a long queue that finds nothing is repeated only after a
+        // submission, a finished solve or column, or freed memory
+        if (S->admit_dirty) {
+            S->admit_dirty = false;
+            while (admit_one(S)) {
+            }
         }
-        if (S->stop && S->active.empty() && S->queue.empty()) break;
-        if (S->active.empty()) {
+        const bool groups_busy = active_groups(S) > 0;
+        if (S->stop && S->active.empty() && S->queue.empty() && !groups_busy) break;
+        if (S->active.empty() && !groups_busy) {
             S->cv_work.wait(lock);
             continue;
         }
-        // advance every active solve without holding the lock
+        // advance every active solve without holding the lock (groups are touched by
+        // this thread only)
         std::vector<Slot> work;
         work.swap(S->active);
+        std::vector<MatrixEntry*> groups;
+        for (MatrixEntry& m : S->mats)
+            if (m.group && !group_empty(m.group)) groups.push_back(&m);
         lock.unlock();
         bool any = false;
+        std::vector<GroupDone> gdone;
+        std::vector<std::pair<MatrixEntry*, int>> gfail;
+        for (MatrixEntry* m : groups) {
+            bool progress = false;
+            int rc = group_step(m->group, &progress, gdone);
+            if (rc) gfail.emplace_back(m, rc);
+            any |= progress;
+        }
         std::vector<Slot> still, done;
         for (Slot& sl : work) {
             bool progress = false;
@@ -208,6 +362,38 @@ static void scheduler(fespmv_server* S) {
             }
         }
         lock.lock();
+        for (GroupDone& d : gdone) {
+            auto t = S->tickets.find(d.tag);
+            if (t == S->tickets.end()) continue;
+            Request* q = t->second;
+            q->res = d.res;
+            q->x = std::move(d.x);
+            q->rc = d.res.status;
+            if (q->rc != FESPMV_OK) q->error = "the solve did not converge";
+            q->t_done = now_s();
+            q->state = RQ_DONE;
+            ++S->completed;
+        }
+        for (auto& f : gfail) {   // a CUDA error in a group: its requests fail, the group goes
+            const std::string err = fespmv_last_error();
+            for (auto& kv : S->tickets) {
+                Request* q = kv.second;
+                if (q->state == RQ_RUNNING && q->matrix == (int)(f.first - S->mats.data()) && !q->in_slot) {
+                    q->rc = f.second;
+                    q->error = err;
+                    q->state = RQ_DONE;
+                    q->t_done = now_s();
+                }
+            }
+            group_destroy(f.first->group);
+            f.first->group = nullptr;
+            S->used -= f.first->group_bytes;
+            f.first->group_bytes = 0;
+        }
+        if (!gdone.empty() || !gfail.empty()) {
+            S->cv_done.notify_all();
+            S->admit_dirty = true;
+        }
         for (Slot& sl : done) {
             sl.req->state = RQ_DONE;
             ++S->completed;
@@ -215,8 +401,11 @@ static void scheduler(fespmv_server* S) {
             S->free_streams.push_back(sl.s);
         }
         for (Slot& sl : still) S->active.push_back(sl);
-        if (!done.empty()) S->cv_done.notify_all();
-        if (!any && done.empty()) {
+        if (!done.empty()) {
+            S->cv_done.notify_all();
+            S->admit_dirty = true;
+        }
+        if (!any && done.empty() && gdone.empty()) {
             // nothing ready: wait briefly (new submissions wake us at once)
             S->cv_work.wait_for(lock, std::chrono::microseconds(20));
         }
@@ -251,6 +440,17 @@ int srv_create(fespmv_server_t* out, int64_t workspace_budget_bytes, int32_t max
         set_error("srv_create: could not start the scheduler thread");
         return FESPMV_ERR_OOM;
     }
+}
+
+int srv_set_grouping(fespmv_server_t S, int32_t width) {
+    if (!S || !(width == 0 || width == -1 || width == 4 || width == 8 || width == 16 || width == 32)) {
+        set_error("srv_set_grouping: width must be 0, -1, 4, 8, 16 or 32");
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->group_width = width;
+    S->admit_dirty = true;
+    return FESPMV_OK;
 }
 
 int srv_register(fespmv_server_t S, fespmv_mat_t A, int32_t* matrix_id) {
@@ -307,6 +507,7 @@ int srv_submit(fespmv_server_t S, int32_t matrix_id, const double* b, const cg_o
         q->t_submit = now_s();
         S->tickets[q->ticket] = q;
         S->queue.push_back(q);
+        S->admit_dirty = true;
         ++S->submitted;
         *ticket = q->ticket;
         S->cv_work.notify_one();
@@ -359,10 +560,11 @@ int srv_get_stats(fespmv_server_t S, srv_stats* st) {
     st->submitted = S->submitted;
     st->completed = S->completed;
     st->queued = (int64_t)S->queue.size();
-    st->active = (int64_t)S->active.size();
+    st->active = (int64_t)S->active.size() + active_groups(S);
     st->peak_active = S->peak_active;
     st->workspace_bytes = S->used;
     st->peak_workspace_bytes = S->peak_bytes;
+    st->grouped = S->grouped;
     return FESPMV_OK;
 }
 
@@ -395,8 +597,10 @@ void srv_destroy(fespmv_server_t S) {
         S->cv_work.notify_all();
     }
     if (S->thread.joinable()) S->thread.join();
-    for (MatrixEntry& m : S->mats)
+    for (MatrixEntry& m : S->mats) {
         for (CgWork* w : m.idle) destroy_work(w);
+        if (m.group) group_destroy(m.group);
+    }
     for (cudaStream_t s : S->free_streams) cudaStreamDestroy(s);
     for (auto& kv : S->tickets) delete kv.second;
     delete S;

@@ -127,3 +127,114 @@ def test_cancel_queued():
     codes = [fs.srv_poll(S, t, p.n_rows)[0] for t in tickets]
     assert codes.count(fs.FESPMV_ERR_CANCELLED) == n and codes.count(0) == 20 - n
     fs.srv_destroy(S)
+
+
+def multi_alone(A, b, width, **kw):
+    """cg_solve_multi of b alone with `width` columns (the others zero)."""
+    B = np.zeros((len(b), width))
+    B[:, 0] = b
+    Bd = torch.from_numpy(B).cuda()
+    Xd = torch.zeros_like(Bd)
+    rc, res = fs.cg_solve_multi(A, Bd, Xd, **kw)
+    torch.cuda.synchronize()
+    return Xd.cpu().numpy()[:, 0].copy(), res[0]
+
+
+def same(x, res, xa, ra):
+    return (np.array_equal(x.view(np.uint64), xa.view(np.uint64)) and res["iters"] == ra["iters"]
+            and res["outer"] == ra["outer"])
+
+
+@pytest.mark.parametrize("width", [8, -1])
+def test_grouped_results_equal_the_lockstep_solve_alone(width):
+    """With grouping on, requests on one matrix share lockstep groups; each result
+    equals (bit for bit) cg_solve_multi of that right-hand side alone with the
+    group's width, or cg_solve alone when it took the single path (a lone request,
+    or the single-reduction flag, which groups do not take)."""
+    ps = problems()
+    mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=256,
+                           precisions=fs.FESPMV_PREC_F32) for p in ps]
+    S = fs.srv_create(1 << 30, 6)
+    fs.srv_set_grouping(S, width)
+    ids = [fs.srv_register(S, A) for A in mats]
+    rng = np.random.default_rng(91)
+    reqs = []
+    for k in range(40):
+        m = int(rng.integers(len(ps)))
+        b = fegen.random_vector(ps[m].n_rows, 3000 + k)
+        tol = [1e-8, 1e-10][k % 2]
+        single = k % 5 == 4
+        prec, fl = ((fs.FESPMV_CG_F64, fs.FESPMV_CG_SINGLE_REDUCTION) if single else
+                    (fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE))
+        reqs.append((m, b, tol, prec, fl, single))
+    tickets = [fs.srv_submit(S, ids[m], b, tol=tol, precision=prec, flags=fl)
+               for (m, b, tol, prec, fl, _) in reqs]
+    results = [fs.srv_poll(S, t, ps[r[0]].n_rows) for t, r in zip(tickets, reqs)]
+    st = fs.srv_get_stats(S)
+    assert st["completed"] == 40 and st["grouped"] >= 8
+    n_grouped = 0
+    for (m, b, tol, prec, fl, single), (rc, x, res, tm) in zip(reqs, results):
+        assert rc == 0, res
+        p = ps[m]
+        r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        assert np.linalg.norm(r) <= tol * 1.01 * np.linalg.norm(b)
+        xa, ra = alone(mats[m], b, tol=tol, precision=prec, flags=fl)
+        if single:
+            assert same(x, res, xa, ra)
+            continue
+        kw = width if width > 0 else 32          # these matrices are small: 32 columns
+        xm, rm = multi_alone(mats[m], b, kw, tol=tol, precision=prec, flags=fl)
+        assert same(x, res, xm, rm) or same(x, res, xa, ra)
+        n_grouped += same(x, res, xm, rm)
+    assert n_grouped == st["grouped"]
+    fs.srv_destroy(S)
+
+
+@pytest.mark.parametrize("precision,flags", [(fs.FESPMV_CG_F64, 0), (fs.FESPMV_CG_F32_REFINE, 0),
+                                             (fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE)])
+def test_late_arrivals_join_running_groups(precision, flags):
+    """Requests that arrive while a group runs take the columns that finished
+    solves free, at the group's outer steps (every 8 * check_every = 32 inner
+    iterations here): more requests than columns, results as alone."""
+    p = fegen.cube_elasticity(9, 92)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=256, precisions=fs.FESPMV_PREC_F32)
+    S = fs.srv_create(1 << 30, 4)
+    fs.srv_set_grouping(S, 4)
+    mid = fs.srv_register(S, A)
+    bs = [fegen.random_vector(p.n_rows, 4000 + k) for k in range(14)]
+    tols = [[1e-8, 1e-10, 1e-6][k % 3] for k in range(14)]
+    kw = dict(precision=precision, flags=flags, check_every=4)
+    tickets = [fs.srv_submit(S, mid, bs[k], tol=tols[k], **kw) for k in range(7)]
+    time.sleep(0.005)
+    tickets += [fs.srv_submit(S, mid, bs[k], tol=tols[k], **kw) for k in range(7, 14)]
+    n_grouped = 0
+    for k, t in enumerate(tickets):
+        rc, x, res, tm = fs.srv_poll(S, t, p.n_rows)
+        assert rc == 0, res
+        xm, rm = multi_alone(A, bs[k], 4, tol=tols[k], **kw)
+        xa, ra = alone(A, bs[k], tol=tols[k], **kw)
+        assert same(x, res, xm, rm) or same(x, res, xa, ra), k
+        n_grouped += same(x, res, xm, rm)
+    st = fs.srv_get_stats(S)
+    assert st["completed"] == 14 and n_grouped == st["grouped"] >= 8   # more than one group's worth
+    fs.srv_destroy(S)
+
+
+def test_grouping_falls_back_to_the_single_path():
+    """A budget too small for a group, and a width of 0 again: the requests take the
+    single path and equal cg_solve alone; a bad width is rejected."""
+    p = fegen.cube_laplace(12, 93)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256)
+    S = fs.srv_create(80 * p.n_rows + (1 << 20), 4)   # room for one single workspace only
+    with pytest.raises(fs.FespmvError):
+        fs.srv_set_grouping(S, 12)
+    fs.srv_set_grouping(S, 32)
+    mid = fs.srv_register(S, A)
+    bs = [fegen.random_vector(p.n_rows, 5000 + k) for k in range(5)]
+    tickets = [fs.srv_submit(S, mid, b) for b in bs]
+    for b, t in zip(bs, tickets):
+        rc, x, res, tm = fs.srv_poll(S, t, p.n_rows)
+        assert rc == 0
+        xa, ra = alone(A, b)
+        assert np.array_equal(x.view(np.uint64), xa.view(np.uint64))
+    fs.srv_destroy(S)
