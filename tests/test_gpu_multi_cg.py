@@ -78,6 +78,46 @@ def test_multi_cg_f64_matches_oracle(name, k):
             assert np.linalg.norm(X[:, j] - xo) / np.linalg.norm(xo) <= cond * 2e-10
 
 
+@pytest.mark.parametrize("variant", ["float_pair_handle", "no_precond"])
+def test_multi_cg_f64_variants(variant):
+    """FP64 on a handle holding float pairs (its outer residual products use them) and
+    FP64 without Jacobi (the oracle's unpreconditioned CG): per column within tolerance,
+    iteration counts within 2 % (+2) of the oracle's."""
+    p = fegen.cube_elasticity(8, 395)
+    B = rhs(p, 6, 396)
+    pairs = variant == "float_pair_handle"
+    A = make(p, prec=fs.FESPMV_PREC_DF64 if pairs else 0)
+    flags = 0 if pairs else fs.FESPMV_CG_NO_PRECOND
+    rc, X, res = solve(A, B, tol=1e-10, flags=flags)
+    assert rc == fs.FESPMV_OK
+    for j in range(6):
+        assert res[j]["status"] == 0, (j, res[j])
+        assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+        _, info = oracle.pcg(p.rowptr, p.colind, p.values, B[:, j], tol=1e-10, jacobi=pairs)
+        assert abs(res[j]["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2, (j, res[j], info)
+
+
+@pytest.mark.parametrize("check_every", [1, 3, 64])
+def test_multi_cg_graph_chunks(check_every):
+    """Graphs of 1, 3 and 64 inner iterations (outer-step grids of 8, 24 and 512): the
+    same per-column convergence; the FP64 recurrence is the same whatever the chunk."""
+    p = fegen.cube_laplace(11, 397)
+    B = rhs(p, 5, 398)
+    A = make(p)
+    rc, X, res = solve(A, B, tol=1e-10, check_every=check_every)
+    _, X16, res16 = solve(A, B, tol=1e-10)
+    assert rc == 0
+    for j in range(5):
+        assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+        assert res[j]["iters"] == res16[j]["iters"]
+        assert np.array_equal(X[:, j].view(np.uint64), X16[:, j].view(np.uint64))
+    rc, X, res = solve(A, B, tol=1e-10, check_every=check_every, precision=fs.FESPMV_CG_F32_REFINE,
+                       flags=fs.FESPMV_CG_RELIABLE)
+    assert rc == 0
+    for j in range(5):
+        assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+
+
 @pytest.mark.parametrize("reliable", [False, True])
 @pytest.mark.parametrize("k", [3, 8, 32])
 def test_multi_cg_f32_refinement_reaches_fp64_tolerance(k, reliable):
