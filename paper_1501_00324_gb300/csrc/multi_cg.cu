@@ -1,6 +1,9 @@
 // Conjugate gradients for many right-hand sides of one matrix (cg_solve_multi in
-// fespmv.h): k <= 32 independent Jacobi-PCG solves A x_j = b_j run in lockstep, so
-// that every iteration streams the matrix once for all of them.
+// fespmv.h): k <= 32 independent Jacobi-PCG solves A x_j = b_j (the solver of
+// the paper's Newton step, Sec. 2.1, once per column) run in lockstep, so that
+// every iteration streams the matrix once for all of them.  The same lockstep
+// solve, with columns filled and emptied while it runs, serves the solve
+// server's groups (multi_group.h).
 //
 // The solves share nothing but the product: each column has its own scalars
 // (alpha, beta, rho, thresholds, status), the vectors are row-major n x kw blocks
@@ -24,10 +27,12 @@
 //
 // In lockstep the columns reach their refinement points at different
 // iterations.  A column whose inner residual has fallen by inner_tol is marked
-// due and keeps iterating; outer steps come every kOuterChunks graph launches
-// (or at once when no column is iterating) and act only on the columns that are
-// due or whose inner CG has stopped.  No column waits for the others, and the
-// grid of outer steps is fixed, so the independence above still holds.
+// due and keeps iterating (until it has fallen by inner_tol^3 with reliable
+// updates, inner_tol^2 without: further the float recurrence drifts from the
+// true residual); outer steps come every kOuterChunks graph launches (or at once
+// when no column is iterating) and act only on the columns that are due or whose
+// inner CG has stopped.  No column waits for the others, and the grid of outer
+// steps is fixed, so the independence above still holds.
 #include <cuda_runtime.h>
 
 #include <algorithm>
