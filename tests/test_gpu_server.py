@@ -238,3 +238,30 @@ def test_grouping_falls_back_to_the_single_path():
         xa, ra = alone(A, b)
         assert np.array_equal(x.view(np.uint64), xa.view(np.uint64))
     fs.srv_destroy(S)
+
+
+def test_grouped_cancel_and_errors_are_per_request():
+    """With grouping on: cancelling the queue leaves the requests already in groups
+    to finish; a matrix whose diagonal is not positive fails its requests (the
+    group cannot be built), the others are served."""
+    p = fegen.cube_laplace(14, 94)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, precisions=fs.FESPMV_PREC_F32)
+    vals = p.values.copy()
+    rows = np.repeat(np.arange(p.n_rows), np.diff(p.rowptr))
+    vals[(rows == 5) & (p.colind == 5)] = -2.0
+    Bad = fs.spmv_create(p.rowptr, p.colind, vals, p.node_xyz, 1, sigma=256)
+    S = fs.srv_create(1 << 30, 2)
+    fs.srv_set_grouping(S, 4)
+    ia, ib = fs.srv_register(S, A), fs.srv_register(S, Bad)
+    bad_tickets = [fs.srv_submit(S, ib, fegen.random_vector(p.n_rows, 6000 + k)) for k in range(3)]
+    tickets = [fs.srv_submit(S, ia, fegen.random_vector(p.n_rows, 6100 + k), precision=fs.FESPMV_CG_F32_REFINE,
+                             flags=fs.FESPMV_CG_RELIABLE) for k in range(40)]
+    n = fs.srv_cancel_queued(S)
+    codes = [fs.srv_poll(S, t, p.n_rows)[0] for t in tickets]
+    assert codes.count(fs.FESPMV_ERR_CANCELLED) == n and codes.count(0) == 40 - n
+    assert all(fs.srv_poll(S, t, p.n_rows)[0] in (fs.FESPMV_ERR_BREAKDOWN, fs.FESPMV_ERR_CANCELLED)
+               for t in bad_tickets)
+    # the server keeps serving after the cancellation and the failures
+    t = fs.srv_submit(S, ia, fegen.random_vector(p.n_rows, 6200))
+    assert fs.srv_poll(S, t, p.n_rows)[0] == 0
+    fs.srv_destroy(S)
