@@ -66,6 +66,8 @@ def _lib():
         lib.fegen_assemble.restype = i32
         lib.fegen_dirichlet.argtypes = [i64, P, P, P, P]
         lib.fegen_dirichlet.restype = i64
+        lib.fegen_elements.argtypes = [i32, i32, i32, i32, i32, P, P, P, dbl, dbl, dbl, P, P, P]
+        lib.fegen_elements.restype = i32
         _lib_handle = lib
     return _lib_handle
 
@@ -88,6 +90,9 @@ class FEProblem:
     n_elems: int
     grid: tuple                 # node grid dims
     seed: int
+    # with elements=True: the element quantities the matrix is the sum of (tet order)
+    elem_nodes: np.ndarray = None   # int32 [n_elems, 4], node numbers (new numbering)
+    elem_mats: np.ndarray = None    # float64 [n_elems, 4*dpn, 4*dpn], row/col dpn*vertex + comp
 
     @property
     def nnz(self) -> int:
@@ -99,7 +104,7 @@ class FEProblem:
 
 
 def _assemble(name, kind, dims, periodic2, xyz_grid, rng_perm, coef, d_iso, d_ani, nu,
-              dir_grid_mask, seed, dirichlet=True):
+              dir_grid_mask, seed, dirichlet=True, elements=False):
     n0, n1, n2 = dims
     nn = n0 * n1 * n2
     lib = _lib()
@@ -137,9 +142,19 @@ def _assemble(name, kind, dims, periodic2, xyz_grid, rng_perm, coef, d_iso, d_an
     if not dirichlet:
         row_mask = np.zeros_like(row_mask)
     n_elems = 6 * (n0 - 1) * (n1 - 1) * (n2 if periodic2 else n2 - 1)
+    elem_nodes = elem_mats = None
+    if elements:
+        ne = 4 * dpn
+        elem_nodes = np.zeros((n_elems, 4), dtype=np.int32)
+        elem_mats = np.zeros((n_elems, ne, ne), dtype=np.float64)
+        rc = lib.fegen_elements(kind, n0, n1, n2, periodic2, _ptr(xyz_c), _ptr(newid), _ptr(coef_c),
+                                d_iso, d_ani, nu, _ptr(elem_nodes), _ptr(elem_mats), _ptr(bad))
+        if rc != 0:
+            raise RuntimeError(f"fegen_elements failed ({rc})")
     return FEProblem(name=name, n_rows=n_rows, rowptr=rowptr, colind=colind, values=values,
                      node_xyz=node_xyz, dofs_per_node=dpn, dirichlet=row_mask,
-                     n_elems=n_elems, grid=tuple(dims), seed=seed)
+                     n_elems=n_elems, grid=tuple(dims), seed=seed, elem_nodes=elem_nodes,
+                     elem_mats=elem_mats)
 
 
 def _cube_grid(n, rng, jitter):
@@ -156,18 +171,18 @@ def _cube_grid(n, rng, jitter):
 
 
 def cube_laplace(n: int = 20, seed: int = 1501, jitter: float = 0.2, permute: bool = True,
-                 dirichlet: bool = True) -> FEProblem:
+                 dirichlet: bool = True, elements: bool = False) -> FEProblem:
     """P1 Laplace stiffness on the unit cube (n^3 nodes), Dirichlet on z=0."""
     rng = np.random.default_rng(seed)
     xyz, idx = _cube_grid(n, rng, jitter)
     perm = rng.permutation(n ** 3) if permute else np.arange(n ** 3)
     zmask = np.round(idx[:, 2]) == 0
     return _assemble(f"cube_laplace_{n}", 0, (n, n, n), 0, xyz, perm, None, 1.0, 0.0, 0.0,
-                     zmask, seed, dirichlet)
+                     zmask, seed, dirichlet, elements)
 
 
 def cube_elasticity(n: int = 64, seed: int = 1502, jitter: float = 0.2, nu: float = 0.3,
-                    permute: bool = True, dirichlet: bool = True) -> FEProblem:
+                    permute: bool = True, dirichlet: bool = True, elements: bool = False) -> FEProblem:
     """P1 linear elasticity (3 dof/node) on the unit cube, clamped on z=0."""
     rng = np.random.default_rng(seed)
     xyz, idx = _cube_grid(n, rng, jitter)
@@ -176,7 +191,7 @@ def cube_elasticity(n: int = 64, seed: int = 1502, jitter: float = 0.2, nu: floa
     E = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=n_tets))
     zmask = np.round(idx[:, 2]) == 0
     return _assemble(f"cube_elasticity_{n}", 2, (n, n, n), 0, xyz, perm, E, 0.0, 0.0, nu,
-                     zmask, seed, dirichlet)
+                     zmask, seed, dirichlet, elements)
 
 
 # shell geometry (cm): inner and outer semi-axes of the prolate spheroid, theta range
@@ -194,7 +209,7 @@ def _shell_map(r, th, ph):
 
 def shell_laplace(nr: int = 24, nt: int = 256, nph: int = 512, seed: int = 1503,
                   jitter: float = 0.15, permute: bool = True, dirichlet: bool = True,
-                  d_iso: float = 1.0, d_ani: float = 8.0) -> FEProblem:
+                  d_iso: float = 1.0, d_ani: float = 8.0, elements: bool = False) -> FEProblem:
     """Anisotropic P1 Laplace on a heart-like thick prolate-spheroidal shell."""
     rng = np.random.default_rng(seed)
     ir, it, ip = np.meshgrid(np.arange(nr, dtype=np.float64), np.arange(nt, dtype=np.float64),
@@ -225,7 +240,7 @@ def shell_laplace(nr: int = 24, nt: int = 256, nph: int = 512, seed: int = 1503,
     fib /= np.linalg.norm(fib, axis=1, keepdims=True)
     base = np.round(idx[:, 1]) == 0
     return _assemble(f"shell_laplace_{nr}x{nt}x{nph}", 1, (nr, nt, nph), 1, xyz, perm,
-                     fib.ravel(), d_iso, d_ani, 0.0, base, seed, dirichlet)
+                     fib.ravel(), d_iso, d_ani, 0.0, base, seed, dirichlet, elements)
 
 
 def valid_seed(maker, seed: int, tries: int = 16):

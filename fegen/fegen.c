@@ -346,6 +346,48 @@ int fegen_assemble(int kind, int n0, int n1, int n2, int periodic2, const double
 }
 
 /*
+ * The element quantities behind fegen_assemble, in the same tet order (cell
+ * major, 6 tets per cell): each tet's 4 node numbers (new numbering) in
+ * elem_nodes[4 * tet + a], and its element matrix (ne x ne, ne = 4 * dofs per
+ * node, row/column dpn * a + c for component c of vertex a) in
+ * Ke[tet * ne * ne ...].  Returns 0, or -3 with *bad_tet for a degenerate tet.
+ */
+int fegen_elements(int kind, int n0, int n1, int n2, int periodic2, const double* xyz,
+                   const int32_t* newid, const double* coef, double d_iso, double d_ani,
+                   double nu, int32_t* elem_nodes, double* Ke, int64_t* bad_tet) {
+    int dpn = (kind == 2) ? 3 : 1;
+    int ne = 4 * dpn;
+    int64_t nc2 = n_cells2(n2, periodic2);
+    int64_t ncells = (int64_t)(n0 - 1) * (n1 - 1) * nc2;
+    int64_t bad = -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t cell = 0; cell < ncells; ++cell) {
+        int c0 = (int)(cell / ((int64_t)(n1 - 1) * nc2));
+        int c1 = (int)((cell / nc2) % (n1 - 1));
+        int c2 = (int)(cell % nc2);
+        for (int t = 0; t < 6; ++t) {
+            int64_t tet = cell * 6 + t;
+            int64_t g[4];
+            double x[4][3];
+            tet_nodes(c0, c1, c2, t, n1, n2, periodic2, g);
+            for (int a = 0; a < 4; ++a) {
+                elem_nodes[tet * 4 + a] = newid[g[a]];
+                for (int d = 0; d < 3; ++d) x[a][d] = xyz[g[a] * 3 + d];
+            }
+            double sd = element_matrix(kind, x, kind == 1 ? coef + cell * 3 : NULL,
+                                       kind == 2 ? coef[tet] : 0.0, d_iso, d_ani, nu, t,
+                                       Ke + tet * ne * ne);
+            if (sd == 0.0) {
+#pragma omp critical
+                bad = tet;
+            }
+        }
+    }
+    if (bad >= 0) { *bad_tet = bad; return -3; }
+    return 0;
+}
+
+/*
  * Homogeneous Dirichlet conditions by symmetric elimination: every row r with
  * mask[r] != 0 becomes the identity row; every entry (i, j) with exactly one of
  * i, j constrained is dropped from the pattern.  Compacts the CSR in place and

@@ -6,6 +6,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 mixed-precision refinement; ``layout.py`` holds the numpy definitions of the
 row/column permutation and the warp-slice packing.
 
+``oracle.c`` also assembles global values and vectors from element quantities
+(the sum of the element contributions to each entry, Sec. 4).
+
 Pins (tests that tie the oracle to something other than itself) live in
 ``tests/test_oracle_pins.py``: dense brute-force products, the paper's worked
 permutation example (Sec. 5.2/5.3), zero row sums of Neumann Laplacians,
@@ -64,6 +67,10 @@ def _lib():
         lib.oracle_csr_spmv_f32.restype = None
         lib.oracle_round_bf16.argtypes = [ctypes.c_float]
         lib.oracle_round_bf16.restype = ctypes.c_float
+        lib.oracle_assemble_matrix.argtypes = [i64, P, P, i64, i32, i32, P, P, P, P]
+        lib.oracle_assemble_matrix.restype = i32
+        lib.oracle_assemble_vector.argtypes = [i64, i64, i32, i32, P, P, P, P]
+        lib.oracle_assemble_vector.restype = None
         _lib_handle = lib
     return _lib_handle
 
@@ -166,3 +173,33 @@ def refine_reliable(rowptr, colind, values, b, x0=None, tol=1e-10, delta=0.1, ma
                                        {"f32": 0, "bf16": 1}[storage], ctypes.byref(u), ctypes.byref(i),
                                        ctypes.byref(tr))
     return x, dict(status=STATUS[st], updates=u.value, iters=i.value, true_relres=tr.value)
+
+
+def assemble_matrix(rowptr, colind, elem_nodes, elem_mats, dofs_per_node, mask=None) -> np.ndarray:
+    """Global values (CSR order of the given pattern) as the sums of the element
+    contributions in ascending element order; masked rows are identity rows and
+    entries with a masked row or column get no contribution (Sec. 4)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    en = np.ascontiguousarray(elem_nodes, dtype=np.int32)
+    ke = np.ascontiguousarray(elem_mats, dtype=np.float64)
+    n = len(rp) - 1
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    out = np.zeros(int(rp[-1]), dtype=np.float64)
+    rc = _lib().oracle_assemble_matrix(n, _p(rp), _p(ci), en.shape[0], en.shape[1], dofs_per_node, _p(en),
+                                       _p(ke), None if mk is None else _p(mk), _p(out))
+    if rc != 0:
+        raise ValueError("an element contribution has no stored position in the pattern")
+    return out
+
+
+def assemble_vector(n_rows, elem_nodes, elem_vecs, dofs_per_node, mask=None) -> np.ndarray:
+    """Global vector as the sums of the element vectors' entries, ascending element
+    order; 0 on masked rows (Sec. 4)."""
+    en = np.ascontiguousarray(elem_nodes, dtype=np.int32)
+    re = np.ascontiguousarray(elem_vecs, dtype=np.float64)
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    out = np.zeros(n_rows, dtype=np.float64)
+    _lib().oracle_assemble_vector(n_rows, en.shape[0], en.shape[1], dofs_per_node, _p(en), _p(re),
+                                  None if mk is None else _p(mk), _p(out))
+    return out

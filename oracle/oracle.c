@@ -27,6 +27,14 @@
  *                     by a factor delta ("reliable updates", Sleijpen and van
  *                     der Vorst 1996); the search direction is kept.
  *
+ *   oracle_assemble_matrix / oracle_assemble_vector
+ *                     the global stiffness values and a global residual vector
+ *                     from element quantities: every global entry is the sum of
+ *                     the element contributions to it (Sec. 4 writes this as
+ *                     the row sums K^elem 1 of a matrix with one row per global
+ *                     non-zero), here summed in ascending element order, with
+ *                     homogeneous Dirichlet rows eliminated symmetrically.
+ *
  * The paper gives no code for CG; these routines follow the standard
  * algorithm step by step.
  */
@@ -482,4 +490,76 @@ done:
     if (true_relres_out) *true_relres_out = relres;
     free(s); free(r); free(t); free(bv); free(w); free(ri); free(p); free(q);
     return status;
+}
+
+/* Position of column j in row i of a CSR with ascending columns, or -1. */
+static int64_t csr_find(const int64_t* rowptr, const int32_t* colind, int64_t i, int32_t j) {
+    int64_t lo = rowptr[i], hi = rowptr[i + 1] - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (colind[mid] == j) return mid;
+        if (colind[mid] < j) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+/*
+ * Global values in CSR order from element matrices.  Element e has npe nodes
+ * elem_nodes[e * npe + a] and dpn dofs per node (dof = dpn * node + c); its
+ * matrix Ke[e] is m x m, m = npe * dpn, row/column dpn * a + c.  For every
+ * stored entry (I, J):
+ *   values = 0 + Ke[e1](.,.) + Ke[e2](.,.) + ...   over the elements holding both
+ *   dofs, in ascending element order;
+ * a row with mask[I] set is the identity row (its diagonal 1, nothing else
+ * stored), and contributions to entries with a masked row or column are dropped
+ * (symmetric elimination of homogeneous Dirichlet conditions; mask may be NULL).
+ * Returns 0, or -1 when a contribution to an unmasked entry has no stored
+ * position, or a masked row has no diagonal.
+ */
+int oracle_assemble_matrix(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t n_elems,
+                           int npe, int dpn, const int32_t* elem_nodes, const double* Ke,
+                           const uint8_t* mask, double* values) {
+    const int m = npe * dpn;
+    for (int64_t p = 0; p < rowptr[n]; ++p) values[p] = 0.0;
+    for (int64_t e = 0; e < n_elems; ++e)
+        for (int a = 0; a < npe; ++a)
+            for (int ci = 0; ci < dpn; ++ci) {
+                const int64_t I = (int64_t)dpn * elem_nodes[e * npe + a] + ci;
+                if (mask && mask[I]) continue;
+                for (int b = 0; b < npe; ++b)
+                    for (int cj = 0; cj < dpn; ++cj) {
+                        const int32_t J = dpn * elem_nodes[e * npe + b] + cj;
+                        if (mask && mask[J]) continue;
+                        const int64_t p = csr_find(rowptr, colind, I, J);
+                        if (p < 0) return -1;
+                        values[p] += Ke[e * m * m + (int64_t)(dpn * a + ci) * m + dpn * b + cj];
+                    }
+            }
+    if (mask)
+        for (int64_t i = 0; i < n; ++i)
+            if (mask[i]) {
+                const int64_t p = csr_find(rowptr, colind, i, (int32_t)i);
+                if (p < 0) return -1;
+                values[p] = 1.0;
+            }
+    return 0;
+}
+
+/*
+ * A global vector from element vectors Re[e] (m entries, dpn * a + c):
+ *   r_I = 0 + Re[e1](.) + Re[e2](.) + ...   over the elements holding dof I, in
+ *   ascending element order; r_I = 0 on masked rows (mask may be NULL).
+ */
+void oracle_assemble_vector(int64_t n, int64_t n_elems, int npe, int dpn, const int32_t* elem_nodes,
+                            const double* Re, const uint8_t* mask, double* r) {
+    const int m = npe * dpn;
+    for (int64_t i = 0; i < n; ++i) r[i] = 0.0;
+    for (int64_t e = 0; e < n_elems; ++e)
+        for (int a = 0; a < npe; ++a)
+            for (int c = 0; c < dpn; ++c) {
+                const int64_t I = (int64_t)dpn * elem_nodes[e * npe + a] + c;
+                if (mask && mask[I]) continue;
+                r[I] += Re[e * m + dpn * a + c];
+            }
 }

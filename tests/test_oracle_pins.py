@@ -457,3 +457,68 @@ def test_reliable_refinement_special_cases():
     bb = fegen.random_vector(p.n_rows, 37)
     _, lim = oracle.refine_reliable(p.rowptr, p.colind, p.values, bb, tol=1e-12, max_iter=3)
     assert lim["status"] == "not_converged" and lim["iters"] == 3
+
+
+# ---------------------------------------------------------------- assembly (Sec. 4)
+
+@pytest.mark.parametrize("maker", [lambda d: fegen.cube_laplace(6, 21, dirichlet=d, elements=True),
+                                   lambda d: fegen.cube_elasticity(5, 22, dirichlet=d, elements=True),
+                                   lambda d: fegen.shell_laplace(3, 8, 10, 23, dirichlet=d, elements=True)])
+@pytest.mark.parametrize("dirichlet", [True, False])
+def test_assembly_equals_the_generators_rowwise_assembly(maker, dirichlet):
+    """The oracle sums element contributions element by element; the generator
+    sums them row by row (its own traversal of the tets around each node, then
+    the symmetric elimination).  Both add in ascending element order, so the
+    values agree bit for bit."""
+    p = maker(dirichlet)
+    mask = p.dirichlet if dirichlet else None
+    v = oracle.assemble_matrix(p.rowptr, p.colind, p.elem_nodes, p.elem_mats, p.dofs_per_node, mask)
+    assert np.array_equal(v.view(np.uint64), p.values.view(np.uint64))
+
+
+def test_assembly_hand_example():
+    """Two elements on nodes {0,1,2} and {1,2,3} (scalar dofs): entries shared by
+    both are the sums, the others one element's value; node 3 constrained."""
+    en = np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32)
+    K1 = np.array([[4., -1., -2.], [-1., 5., -3.], [-2., -3., 6.]])
+    K2 = np.array([[7., -4., -1.], [-4., 8., -2.], [-1., -2., 9.]])
+    rows = [[0, 1, 2], [0, 1, 2, 3], [0, 1, 2, 3], [1, 2, 3]]
+    rowptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    colind = np.concatenate(rows).astype(np.int32)
+    v = oracle.assemble_matrix(rowptr, colind, en, np.stack([K1, K2]), 1)
+    dense = np.zeros((4, 4))
+    for r, cs in enumerate(rows):
+        for k, c in enumerate(cs):
+            dense[r, c] = v[rowptr[r] + k]
+    expect = np.array([[4., -1., -2., 0.],
+                       [-1., 5. + 7., -3. - 4., -1.],
+                       [-2., -3. - 4., 6. + 8., -2.],
+                       [0., -1., -2., 9.]])
+    assert np.array_equal(dense, expect)
+    mask = np.array([0, 0, 0, 1], dtype=np.uint8)
+    rows_m = [[0, 1, 2], [0, 1, 2], [0, 1, 2], [3]]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows_m])]).astype(np.int64)
+    vm = oracle.assemble_matrix(rp, np.concatenate(rows_m).astype(np.int32), en, np.stack([K1, K2]), 1, mask)
+    assert np.array_equal(vm, [4., -1., -2., -1., 12., -7., -2., -7., 14., 1.])
+    r = oracle.assemble_vector(4, en, np.array([[1., 2., 3.], [10., 20., 30.]]), 1, mask)
+    assert np.array_equal(r, [1., 12., 23., 0.])
+    with pytest.raises(ValueError):   # a contribution with no stored position
+        oracle.assemble_matrix(rp, np.concatenate(rows_m).astype(np.int32), en, np.stack([K1, K2]), 1)
+
+
+@pytest.mark.parametrize("maker", [lambda: fegen.cube_elasticity(5, 24, elements=True),
+                                   lambda: fegen.shell_laplace(3, 8, 10, 25, elements=True)])
+def test_vector_assembly_of_element_products_is_the_global_product(maker):
+    """Linearity: assembling the element vectors K_e u_e gives K u (u zero on the
+    constrained dofs), up to rounding."""
+    p = maker()
+    u = fegen.random_vector(p.n_rows, 26)
+    u[p.dirichlet.astype(bool)] = 0.0
+    dpn = p.dofs_per_node
+    idx = (dpn * p.elem_nodes[:, :, None] + np.arange(dpn)[None, None, :]).reshape(p.n_elems, -1)
+    re = np.einsum("eij,ej->ei", p.elem_mats, u[idx])
+    r = oracle.assemble_vector(p.n_rows, p.elem_nodes, re, dpn, p.dirichlet)
+    ku = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    ku[p.dirichlet.astype(bool)] = 0.0
+    bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(u))
+    assert np.all(np.abs(r - ku) <= 1e-13 * (bound + 1e-300) * 30)
