@@ -442,6 +442,64 @@ int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* co
 int cg_solve_multi(fespmv_mat_t A, const double* B, double* X, int32_t k, const cg_options* opts,
                    cg_result* res, fespmv_stream_t stream);
 
+/* ---- assembly as a sparse product (Sec. 4) ------------------------------------------ */
+typedef struct fespmv_assembly* fespmv_assembly_t;
+
+/*
+ * assembly_create -- the map that lets the GPU assemble A's values from element
+ * matrices, and global vectors from element vectors, in A's own storage.  Sec. 4
+ * writes assembly without atomics as the row sums K^elem 1 of a matrix with one
+ * row per global non-zero listing the element contributions to it; here those
+ * rows are A's value positions (its packed slices, or the CSR order), each
+ * listing its contributions in ascending element order, so that the assembled
+ * values equal 0 + c_1 + c_2 + ... summed on the host in element order and
+ * loaded with spmv_update_values, bit for bit.
+ *   A                 a handle (SLICED or CSR) created from the pattern below
+ *   rowptr, colind    the host CSR pattern given to spmv_create (ascending columns)
+ *   n_elems, nodes_per_elem, dofs_per_node
+ *                     the elements; dof = dofs_per_node * node + c (the same
+ *                     dofs_per_node for every node)
+ *   elem_nodes        host int32[n_elems * nodes_per_elem]: node numbers of the
+ *                     input numbering (0 .. n_rows / dofs_per_node - 1)
+ *   dirichlet         host uint8[n_rows] or NULL: rows eliminated symmetrically
+ *                     (their stored diagonal becomes 1; entries with a marked row
+ *                     or column receive no contribution)
+ * The map is built on the host (threads over nodes) and kept on the device:
+ * 8 bytes per value position, 4 per contribution (n_elems * m^2 at most,
+ * m = nodes_per_elem * dofs_per_node), 4 per element-vector entry.  Errors:
+ * INVALID_ARG (sizes, node numbers, n_elems * m^2 >= 2^32, a pattern with
+ * another nnz than A's), BAD_CSR (an element contributes to an unmarked entry
+ * the pattern does not store; a marked row stores no diagonal), OOM, CUDA.
+ */
+int assembly_create(fespmv_assembly_t* out, fespmv_mat_t A, const int64_t* rowptr, const int32_t* colind,
+                    int64_t n_elems, int32_t nodes_per_elem, int32_t dofs_per_node, const int32_t* elem_nodes,
+                    const uint8_t* dirichlet, fespmv_stream_t stream);
+
+/*
+ * assembly_matrix -- A's values := the sums of the element matrices'
+ * contributions (one thread per value position adds its list), the marked rows'
+ * unit diagonals, then A's diagonal, float-pair copy and S with the FP32 / BF16
+ * copies of S A S refreshed as spmv_update_values does.
+ *   Ke   double[n_elems * m * m], element e's matrix row-major at e * m * m, row and
+ *        column dofs_per_node * a + c for component c of local node a; device memory,
+ *        or host with FESPMV_IO_HOST (copied to a device buffer kept by the map;
+ *        the call then returns after the copy).
+ */
+int assembly_matrix(fespmv_assembly_t P, const double* Ke, int32_t flags, fespmv_stream_t stream);
+
+/*
+ * assembly_vector -- r_I := the sums of the element vectors' entries for dof I in
+ * ascending element order, 0 on marked rows (the residual vector of Sec. 4).
+ *   Re   device double[n_elems * m], element e's vector at e * m (dofs_per_node * a + c)
+ *   r    device double[n_rows]: input numbering, or the handle's with
+ *        FESPMV_IO_PERMUTED (SLICED handles)
+ */
+int assembly_vector(fespmv_assembly_t P, const double* Re, double* r, int32_t flags, fespmv_stream_t stream);
+
+/* Contributions held and device bytes of the map. */
+int assembly_get_info(fespmv_assembly_t P, int64_t* n_contributions, int64_t* device_bytes);
+void assembly_destroy(fespmv_assembly_t P);
+
 /* ---- batches of independent FE problems ------------------------------------------- */
 typedef struct fespmv_batch* fespmv_batch_t;
 

@@ -147,6 +147,16 @@ _lib.cg_solve.argtypes = [_P, _P, _P, ctypes.POINTER(cg_options), ctypes.POINTER
 _lib.cg_solve.restype = ctypes.c_int
 _lib.cg_solve_multi.argtypes = [_P, _P, _P, _i32, ctypes.POINTER(cg_options), _P, _P]
 _lib.cg_solve_multi.restype = ctypes.c_int
+_lib.assembly_create.argtypes = [ctypes.POINTER(_P), _P, _P, _P, _i64, _i32, _i32, _P, _P, _P]
+_lib.assembly_create.restype = ctypes.c_int
+_lib.assembly_matrix.argtypes = [_P, _P, _i32, _P]
+_lib.assembly_matrix.restype = ctypes.c_int
+_lib.assembly_vector.argtypes = [_P, _P, _P, _i32, _P]
+_lib.assembly_vector.restype = ctypes.c_int
+_lib.assembly_get_info.argtypes = [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+_lib.assembly_get_info.restype = ctypes.c_int
+_lib.assembly_destroy.argtypes = [_P]
+_lib.assembly_destroy.restype = None
 _lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
 _lib.srv_create.restype = ctypes.c_int
 _lib.srv_set_grouping.argtypes = [_P, _i32]
@@ -414,6 +424,53 @@ def cg_solve_multi(A: Matrix, B, X, tol=1e-10, max_iter=0, precision=FESPMV_CG_F
     if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
         _check(rc)
     return rc, [{f: getattr(r, f) for f, _ in cg_result._fields_} for r in res]
+
+
+class Assembly:
+    """An element-to-entry map (assembly_create); destroy it with assembly_destroy."""
+
+    def __init__(self, handle, A, n_rows):
+        self.handle = handle
+        self.A = A              # keeps the matrix handle alive
+        self.n_rows = n_rows
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.assembly_destroy(self.handle)
+            self.handle = None
+
+
+def assembly_create(A: Matrix, rowptr, colind, elem_nodes, dofs_per_node=1, dirichlet=None,
+                    stream=None) -> Assembly:
+    """elem_nodes: (n_elems, nodes_per_elem) int array of input node numbers."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    en = np.ascontiguousarray(elem_nodes, dtype=np.int32)
+    mk = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    h = _P()
+    _check(_lib.assembly_create(ctypes.byref(h), A.handle, _ptr(rowptr), _ptr(colind), en.shape[0],
+                                en.shape[1] if en.ndim == 2 else 1, dofs_per_node, _ptr(en), _ptr(mk),
+                                _stream(stream)))
+    return Assembly(h, A, A.n_rows)
+
+
+def assembly_matrix(P: Assembly, elem_mats, flags=0, stream=None):
+    """A's values from element matrices (torch CUDA tensor, or numpy for host I/O)."""
+    if isinstance(elem_mats, np.ndarray):
+        elem_mats = np.ascontiguousarray(elem_mats, dtype=np.float64)
+        flags |= FESPMV_IO_HOST
+    _check(_lib.assembly_matrix(P.handle, _ptr(elem_mats), flags, _stream(stream)))
+
+
+def assembly_vector(P: Assembly, elem_vecs, r, flags=0, stream=None):
+    _check(_lib.assembly_vector(P.handle, _ptr(elem_vecs), _ptr(r), flags, _stream(stream)))
+    return r
+
+
+def assembly_get_info(P: Assembly) -> dict:
+    nc, nb = _i64(), _i64()
+    _check(_lib.assembly_get_info(P.handle, ctypes.byref(nc), ctypes.byref(nb)))
+    return {"contributions": nc.value, "device_bytes": nb.value}
 
 
 class Server:
