@@ -68,9 +68,11 @@ def parse_args():
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
+    ap.add_argument("--assembly", type=int, default=1,
+                    help="time the assembly of the workload matrix from its element matrices")
     ap.add_argument("--multi-cg", type=int, default=1,
                     help="time cg_solve_multi with 32 right-hand sides on the workload matrix")
-    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi"], default=None,
+    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "assembly"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -430,6 +432,8 @@ def main():
                                                     fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
             if hasattr(fs, "cg_solve_multi") and args.multi_cg:
                 extra["cg_multi32"] = bench_cg_multi(fs, torch, p, args)
+            if hasattr(fs, "assembly_create") and args.assembly:
+                extra["assembly"] = bench_assembly(fs, torch, args, back_to_back)
             if args.shell:
                 extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
@@ -763,6 +767,13 @@ def profile_piece(fs, torch, A, p, xp, args):
         X = torch.rand((n, 32), dtype=torch.float64, device="cuda")
         Y = torch.empty_like(X)
         f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F64, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "assembly":
+        # the workload's element matrices summed into A's values (assembly as a sparse product)
+        import fegen
+        q = fegen.cube_elasticity(64, 1502, elements=True)
+        P = fs.assembly_create(A, q.rowptr, q.colind, q.elem_nodes, 3, q.dirichlet)
+        Ke = torch.from_numpy(q.elem_mats).cuda()
+        f = lambda: fs.assembly_matrix(P, Ke)  # noqa: E731
     elif t == "cg_multi":
         B = torch.rand((n, 32), dtype=torch.float64, device="cuda")
         X = torch.zeros_like(B)
@@ -858,6 +869,55 @@ def bench_cg_multi(fs, torch, p, args):
                      "true_relres_max": max(r["true_relres"] for r in res),
                      "repeats": reps}
     fs.spmv_destroy(E)
+    return out
+
+
+def bench_assembly(fs, torch, args, back_to_back):
+    """Assembly as a sparse product (Sec. 4) of the workload matrix from its 1.5 M
+    element matrices (12 x 12) into the headline layout, against refreshing the same
+    handle from host-assembled CSR-order values already on the device
+    (spmv_update_values: the value map of the reordering) -- both calls also rebuild
+    the diagonal, S and the FP32/BF16 copies."""
+    import fegen
+    t0 = time.perf_counter()
+    p = fegen.cube_elasticity(64, 1502, elements=True)
+    gen_s = time.perf_counter() - t0
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.vec,
+                       threshold=args.threshold, block=args.block, tiles=args.tiles,
+                       precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+    t0 = time.perf_counter()
+    P = fs.assembly_create(A, p.rowptr, p.colind, p.elem_nodes, 3, p.dirichlet)
+    plan_s = time.perf_counter() - t0
+    info = fs.assembly_get_info(P)
+    Ke = torch.from_numpy(p.elem_mats).cuda()
+    vals = torch.from_numpy(p.values).cuda()
+    fa = lambda: fs.assembly_matrix(P, Ke)  # noqa: E731
+    fu = lambda: fs.spmv_update_values(A, vals)  # noqa: E731
+    fa()
+    fu()
+    k = max(10, args.steps // 10)
+    ta = back_to_back(fa, k) * 1e-3
+    tu = back_to_back(fu, k) * 1e-3
+    fa()
+    torch.cuda.synchronize()
+    ok = np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_VALUES).view(np.uint64),
+                        fs.spmv_export(fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3,
+                                                      sigma=args.sigma, vec=args.vec, threshold=args.threshold,
+                                                      block=args.block, tiles=args.tiles),
+                                       fs.FESPMV_EXPORT_VALUES).view(np.uint64))
+    sl = fs.spmv_get_info(A)["packed_len"]
+    nc = info["contributions"]
+    out = {"elements": p.n_elems, "element_matrix": "12 x 12", "contributions": nc,
+           "value_positions": sl, "plan_s": round(plan_s, 2), "gen_s": round(gen_s, 1),
+           "assembly_us": round(ta * 1e6, 1),
+           "assembly_gbs": round((nc * 12 + sl * 16) / ta / 1e9, 1),
+           "update_values_us": round(tu * 1e6, 1),
+           "bitwise_equal_to_csr_handle": bool(ok),
+           "bytes_note": "assembly_gbs counts element-matrix reads and 4-byte indices per contribution, "
+                         "offsets and the value write per position"}
+    del Ke, vals
+    fs.assembly_destroy(P)
+    fs.spmv_destroy(A)
     return out
 
 

@@ -454,6 +454,12 @@ def assembly_create(A: Matrix, rowptr, colind, elem_nodes, dofs_per_node=1, diri
     return Assembly(h, A, A.n_rows)
 
 
+def assembly_destroy(P: Assembly):
+    if P.handle:
+        _lib.assembly_destroy(P.handle)
+        P.handle = None
+
+
 def assembly_matrix(P: Assembly, elem_mats, flags=0, stream=None):
     """A's values from element matrices (torch CUDA tensor, or numpy for host I/O)."""
     if isinstance(elem_mats, np.ndarray):
