@@ -68,6 +68,8 @@ def parse_args():
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
+    ap.add_argument("--ablation", type=int, default=0,
+                    help="the layout ablation (CSR, slices, sort, Morton order, tiles) on two workloads")
     ap.add_argument("--assembly", type=int, default=1,
                     help="time the assembly of the workload matrix from its element matrices")
     ap.add_argument("--multi-cg", type=int, default=1,
@@ -434,6 +436,8 @@ def main():
                 extra["cg_multi32"] = bench_cg_multi(fs, torch, p, args)
             if hasattr(fs, "assembly_create") and args.assembly:
                 extra["assembly"] = bench_assembly(fs, torch, args, back_to_back)
+            if args.ablation:
+                extra["ablation"] = bench_ablation(fs, torch, args, back_to_back)
             if args.shell:
                 extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
@@ -905,6 +909,7 @@ def bench_assembly(fs, torch, args, back_to_back):
                                                       sigma=args.sigma, vec=args.vec, threshold=args.threshold,
                                                       block=args.block, tiles=args.tiles),
                                        fs.FESPMV_EXPORT_VALUES).view(np.uint64))
+    newton = newton_steps(fs, torch, p, A, P, Ke)
     sl = fs.spmv_get_info(A)["packed_len"]
     nc = info["contributions"]
     out = {"elements": p.n_elems, "element_matrix": "12 x 12", "contributions": nc,
@@ -913,11 +918,110 @@ def bench_assembly(fs, torch, args, back_to_back):
            "assembly_gbs": round((nc * 12 + sl * 16) / ta / 1e9, 1),
            "update_values_us": round(tu * 1e6, 1),
            "bitwise_equal_to_csr_handle": bool(ok),
+           "newton_like_steps": newton,
            "bytes_note": "assembly_gbs counts element-matrix reads and 4-byte indices per contribution, "
                          "offsets and the value write per position"}
     del Ke, vals
     fs.assembly_destroy(P)
     fs.spmv_destroy(A)
+    return out
+
+
+def newton_steps(fs, torch, p, A, P, Ke, steps=4):
+    """A Newton-like sequence on a fixed pattern (the loop of Sec. 2.1): every step
+    assembles new values and a new right-hand side on the GPU from element
+    quantities (here the element matrices scaled by 1 + 0.05 k and the element
+    vectors K_e u_k of a slowly varying field u_k), then solves K dx = R to 1e-10
+    (FP32 values with FP64 reliable updates) warm-started from the previous step's
+    solution, against the same solve started from zero."""
+    import fegen
+    dpn = p.dofs_per_node
+    idx = torch.from_numpy((dpn * p.elem_nodes[:, :, None] + np.arange(dpn)[None, None, :])
+                           .reshape(p.n_elems, -1).astype(np.int64)).cuda()
+    u0 = torch.from_numpy(fegen.manufactured_solution(p)).cuda()
+    du = torch.from_numpy(fegen.random_vector(p.n_rows, 1790)).cuda() * 1e-3
+    mask = torch.from_numpy(p.dirichlet.astype(bool)).cuda()
+    b = torch.empty_like(u0)
+    x = torch.zeros_like(u0)
+    rows = []
+    for k in range(steps):
+        Kk = Ke * (1.0 + 0.05 * k)
+        uk = (u0 + k * du).masked_fill(mask, 0.0)
+        Rk = torch.einsum("eij,ej->ei", Kk, uk[idx]).contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs.assembly_matrix(P, Kk)
+        fs.assembly_vector(P, Rk, b)
+        torch.cuda.synchronize()
+        t_asm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rw = fs.cg_solve(A, b, x, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE,
+                         flags=fs.FESPMV_CG_RELIABLE | (fs.FESPMV_CG_X0 if k > 0 else 0))
+        torch.cuda.synchronize()
+        t_warm = time.perf_counter() - t0
+        xc = torch.zeros_like(u0)
+        rc = fs.cg_solve(A, b, xc, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
+        rows.append({"step": k, "assemble_ms": round(t_asm * 1e3, 2), "solve_ms": round(t_warm * 1e3, 1),
+                     "iters_warm": rw["iters"], "iters_cold": rc["iters"],
+                     "true_relres": rw["true_relres"], "status": rw["status"]})
+        del Kk, Rk
+    return rows
+
+
+def bench_ablation(fs, torch, args, back_to_back):
+    """What each step of the layout buys (the paper's ablation, Sec. 7), FP64 products
+    on the 64^3 elasticity and the shell matrices: CSR baselines, then warp slices in
+    the generator's (random) node numbering without and with the paper's global length
+    sort, Morton locality order, windowed sort, and x staged per tile with 16-bit
+    indices.  Each line: algorithmic GB/s of the product, the host planning time and
+    the value refresh (spmv_update_values) in products: the reordering cost alpha of
+    Sec. 6."""
+    import fegen
+    out = {}
+    CSR, NONE, MORTON = fs.FESPMV_FMT_CSR, fs.FESPMV_REORDER_NONE, fs.FESPMV_REORDER_MORTON
+    for wname, maker in (("cube_elasticity_64", lambda: fegen.cube_elasticity(64, 1502)),
+                         ("shell_24x256x512", lambda: fegen.shell_laplace(24, 256, 512, 1503))):
+        p = maker()
+        n, nnz = p.n_rows, p.nnz
+        mb = nnz * 12 + n * 16
+        vals = torch.from_numpy(p.values).cuda()
+        x = torch.from_numpy(fegen.random_vector(n, 1791)).cuda()
+        variants = [
+            ("csr_scalar", dict(format=CSR, csr_lanes=1)),
+            ("csr_vector4", dict(format=CSR, csr_lanes=4)),
+            ("slices, generator numbering, no sort", dict(reorder=NONE, sigma=0, tiles=-1, vec=1)),
+            ("slices, generator numbering, global length sort", dict(reorder=NONE, sigma=n, tiles=-1, vec=1)),
+            ("slices, Morton order, no sort", dict(reorder=MORTON, sigma=0, tiles=-1, vec=1)),
+            ("slices, Morton order, sort windows of 1024", dict(reorder=MORTON, sigma=1024, tiles=-1, vec=1)),
+            ("+ x staged per tile, 16-bit indices", dict(reorder=MORTON, sigma=1024, vec=1)),
+        ]
+        rows = []
+        for name, kw in variants:
+            t0 = time.perf_counter()
+            A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, **kw)
+            create_s = time.perf_counter() - t0
+            sliced = kw.get("format", fs.FESPMV_FMT_SLICED) != CSR
+            xp = torch.empty_like(x)
+            if sliced:
+                fs.spmv_permute(A, x, xp, 0)
+            else:
+                xp.copy_(x)
+            yp = torch.empty_like(x)
+            flags = fs.FESPMV_IO_PERMUTED if sliced else 0
+            fa = lambda: fs.spmv_apply(A, xp, yp, flags)  # noqa: E731
+            fu = lambda: fs.spmv_update_values(A, vals)  # noqa: E731
+            fa()
+            fu()
+            ta = back_to_back(fa, max(20, args.steps // 4))
+            tu = back_to_back(fu, 10)
+            info = fs.spmv_get_info(A)
+            rows.append({"variant": name, "gbs": round(mb / (ta * 1e-3) / 1e9, 1), "us": round(ta * 1e3, 1),
+                         "padding": round(info["packed_len"] / nnz - 1.0, 4) if sliced else 0.0,
+                         "tiles": info["n_tiles"], "plan_s": round(create_s, 2),
+                         "refresh_products": round(tu / ta, 2)})
+            fs.spmv_destroy(A)
+        out[wname] = {"rows": n, "nnz": nnz, "variants": rows}
+        del vals
     return out
 
 

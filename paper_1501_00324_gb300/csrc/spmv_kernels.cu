@@ -142,17 +142,20 @@ __device__ __forceinline__ void store_low(float b, float* f32, uint16_t* b16, in
 template <int V>
 __global__ void build_scaled_sliced(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
                                    const double* __restrict__ val, const double* __restrict__ scale,
-                                   float* f32, uint16_t* b16, int64_t n_slices) {
+                                   float* __restrict__ f32, uint16_t* __restrict__ b16, int64_t n_slices) {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_slices) return;
     const uint4 m = meta[warp];
     const int64_t off = (int64_t)m.x * 32;
     const int64_t row = (int64_t)m.z + (lane >> m.w);
+    const double sr = scale[row];
+    // steps are independent: unrolled, a warp keeps several column -> scale gathers in flight
+#pragma unroll 4
     for (int st = 0; st < (int)m.y; ++st) {
         const int64_t pos = off + (int64_t)(st / V) * 32 * V + lane * V + st % V;
         const int32_t c = col[pos];
-        const float b = c >= 0 ? (float)((scale[row] * val[pos]) * scale[c]) : 0.0f;
+        const float b = c >= 0 ? (float)((sr * val[pos]) * scale[c]) : 0.0f;
         store_low(b, f32, b16, pos);
     }
 }
