@@ -50,6 +50,8 @@ __global__ void asm_values(const int64_t* __restrict__ kp, const uint32_t* __res
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= len) return;
     double v = 0.0;
+    // the loads of several contributions go out together; the sum stays in list order
+#pragma unroll 4
     for (int64_t k = kp[p], e = kp[p + 1]; k < e; ++k) v += __ldg(Ke + kidx[k]);
     val[p] = v;
 }
@@ -73,6 +75,7 @@ __global__ void asm_vector(const int64_t* __restrict__ vp, const uint32_t* __res
     if (r >= n) return;
     const int64_t I = idx ? (int64_t)idx[r] : r;
     double v = 0.0;
+#pragma unroll 4
     for (int64_t k = vp[I], e = vp[I + 1]; k < e; ++k) v += __ldg(Re + vidx[k]);
     out[r] = v;
 }
