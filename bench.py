@@ -402,6 +402,9 @@ def main():
                 ff = lambda: fs.spmv_apply(Fd, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
                 ff()
                 extra["fe_float_pair_gbs"] = round(mb / (back_to_back(ff, args.steps) * 1e-3) / 1e9, 1)
+                if hasattr(fs, "cg_solve"):
+                    # FP64-accurate Jacobi-PCG whose products run as float pairs on the FP32 pipe
+                    extra["cg_float_pair_products"] = bench_cg(fs, torch, Fd, p, args.cg_solves, fs.FESPMV_CG_F64)
                 fs.spmv_destroy(Fd)
             # CSR baselines on the input CSR
             for lanes in (1, 4, 8):
