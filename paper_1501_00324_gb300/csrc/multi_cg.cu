@@ -891,12 +891,17 @@ struct MultiGroup {
     fespmv_mat* A = nullptr;
     MultiWork* w = nullptr;
     cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;     // the outer step's scalars are back
     Shape sh{};
     int reliable = 0, precision = 0, flags = 0, chunk = 16;
     int64_t period = 0, it = 0;
     unsigned upd_grid = 0;
-    int phase = 0;            // 0 nothing enqueued, 1 an outer step, 2 a graph of inner iterations
+    int phase = 0;            // 0 nothing enqueued, 1 an outer step, 2 graphs of inner iterations
+    // graphs in flight (at most 2, oldest at qhead): their scalars, events and end points
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    MScal* h_slot[2] = {nullptr, nullptr};
+    int64_t q_end[2] = {0, 0};
+    int nq = 0, qhead = 0;
     std::vector<GroupColumn> cols;
     double* d_io = nullptr;   // one column in or out (n doubles)
 };
@@ -909,8 +914,34 @@ void group_free(MultiGroup* g) {
     destroy_multi_work(g->w);
     if (g->d_io) cudaFree(g->d_io);
     if (g->ev) cudaEventDestroy(g->ev);
+    for (int k = 0; k < 2; ++k) {
+        if (g->gev[k]) cudaEventDestroy(g->gev[k]);
+        if (g->h_slot[k]) cudaFreeHost(g->h_slot[k]);
+    }
     if (g->s) cudaStreamDestroy(g->s);
     delete g;
+}
+
+// Queue graphs of inner iterations, up to two in flight.  A graph may start at a
+// grid point only once the graph ending there has been examined (the outer-step
+// decision is taken on its scalars); between grid points a graph is queued before
+// the previous one's scalars are back, which keeps the GPU busy.  A queued graph
+// that turns out to follow the last column's stop changes nothing.
+int group_top_up(MultiGroup* g) {
+    const int kw = g->sh.kw;
+    int64_t tail = g->nq ? g->q_end[(g->qhead + g->nq - 1) % 2] : g->it;
+    while (g->nq < 2) {
+        if (tail % g->period == 0 && tail != g->it) break;
+        const int slot = (g->qhead + g->nq) % 2;
+        FESPMV_CUDA(cudaGraphLaunch(g->w->graph, g->s));
+        FESPMV_CUDA(cudaMemcpyAsync(g->h_slot[slot], g->w->sc, sizeof(MScal) * kw, cudaMemcpyDeviceToHost, g->s));
+        FESPMV_CUDA(cudaEventRecord(g->gev[slot], g->s));
+        tail += g->chunk;
+        g->q_end[slot] = tail;
+        ++g->nq;
+    }
+    g->phase = 2;
+    return FESPMV_OK;
 }
 
 // Inject the waiting columns, enqueue an outer step and the read of the scalars.
@@ -974,6 +1005,10 @@ int group_create(fespmv_mat* A, int kw, const cg_options& o, MultiGroup** out) {
     const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, g->sh.f64, nullptr, nullptr);
     cudaError_t e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&g->gev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&g->h_slot[k], sizeof(MScal) * 32);
+    }
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_io, sizeof(double) * (size_t)A->n);
     if (e != cudaSuccess) {
         group_free(g);
@@ -1054,15 +1089,20 @@ int group_step(MultiGroup* g, bool* progress, std::vector<GroupDone>& done) {
         *progress = true;
         return group_start_outer(g);
     }
-    cudaError_t q = cudaEventQuery(g->ev);
+    const int slot = g->qhead;
+    cudaError_t q = cudaEventQuery(g->phase == 1 ? g->ev : g->gev[slot]);
     if (q == cudaErrorNotReady) return FESPMV_OK;
     if (q != cudaSuccess) return cuda_fail(q, "solve group");
     *progress = true;
-    const MScal* h = g->w->h_sc;
+    const MScal* h;
     const bool after_graph = g->phase == 2;
     if (after_graph) {
-        g->it += g->chunk;
+        h = g->h_slot[slot];
+        g->it = g->q_end[slot];
+        g->qhead = (g->qhead + 1) % 2;
+        --g->nq;
     } else {   // the columns this outer step finished: x out, results
+        h = g->w->h_sc;
         for (int c = 0; c < kw; ++c) {
             GroupColumn& col = g->cols[(size_t)c];
             if (col.state != 2 || h[c].status_out == CG_RUNNING) continue;
@@ -1088,6 +1128,8 @@ int group_step(MultiGroup* g, bool* progress, std::vector<GroupDone>& done) {
         waiting |= col.state == 1;
     }
     if (!iterating) {
+        // graphs still queued change nothing now; stream order runs them before what follows
+        g->nq = 0;
         if (!acted && !waiting) {   // nothing left: the next column starts a fresh grid
             g->phase = 0;
             g->it = 0;
@@ -1096,12 +1138,9 @@ int group_step(MultiGroup* g, bool* progress, std::vector<GroupDone>& done) {
         g->it = (g->it + g->period - 1) / g->period * g->period;
         return group_start_outer(g);
     }
+    // a graph that ends on a grid point is examined before anything is queued past it
     if (after_graph && g->it % g->period == 0 && (acted || waiting)) return group_start_outer(g);
-    FESPMV_CUDA(cudaGraphLaunch(g->w->graph, g->s));
-    FESPMV_CUDA(cudaMemcpyAsync(g->w->h_sc, g->w->sc, sizeof(MScal) * kw, cudaMemcpyDeviceToHost, g->s));
-    FESPMV_CUDA(cudaEventRecord(g->ev, g->s));
-    g->phase = 2;
-    return FESPMV_OK;
+    return group_top_up(g);
 }
 
 void free_multi_cg(fespmv_mat* A) {
