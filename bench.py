@@ -695,10 +695,12 @@ def bench_batched(fs, torch, args):
     ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 2000 + i)
           for i, N in enumerate(sizes)]
     gen_s = time.perf_counter() - t0
-    # rows-per-warp (K2 threshold), vector width and block from the autotuner, run on the
-    # largest mesh with the batch's kernels (x gathered from cache, no tiles)
-    big = max(ps, key=lambda q: q.n_rows)
-    tune = fs.spmv_autotune(big.rowptr, big.colind, big.values, big.node_xyz, 1, sigma=1024, reps=5, tiles=-1)
+    # rows-per-warp (K2 threshold), vector width and block from the autotuner, run with the
+    # batch's kernels (x gathered from cache, no tiles; FP32 products, those of the solve) on
+    # the block-diagonal matrix of the eight largest meshes: large enough that the
+    # candidates differ by more than the launch noise
+    tune = fs.spmv_autotune(*block_diagonal(sorted(ps, key=lambda q: -q.n_rows)[:8]), 1, sigma=1024,
+                            reps=20, tiles=-1, precisions=fs.FESPMV_PREC_F32)
     t0 = time.perf_counter()
     B = fs.batch_create([(p.rowptr, p.colind, p.values, p.node_xyz, 1) for p in ps], sigma=1024,
                         vec=tune["vec"], threshold=tune["threshold"], block=tune["block"])
@@ -840,6 +842,21 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 2),
             "iters": iters}
+
+
+def block_diagonal(ps):
+    """(rowptr, colind, values, node_xyz) of the block-diagonal matrix of the scalar problems
+    ps, each mesh's nodes shifted apart so that a locality order keeps the meshes apart."""
+    rps, cis, vas, xyz, r0, c0 = [np.zeros(1, dtype=np.int64)], [], [], [], 0, 0
+    for i, q in enumerate(ps):
+        rps.append(q.rowptr[1:] + r0)
+        cis.append(q.colind + c0)
+        vas.append(q.values)
+        xyz.append(q.node_xyz + np.array([2.0 * i, 0.0, 0.0]))
+        r0 += q.nnz
+        c0 += q.n_rows
+    return (np.concatenate(rps), np.concatenate(cis).astype(np.int32), np.concatenate(vas),
+            np.concatenate(xyz))
 
 
 def bench_cg_multi(fs, torch, p, args):

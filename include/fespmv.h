@@ -200,8 +200,10 @@ int spmv_get_info(fespmv_mat_t A, fespmv_info* info);
  * ceil(maxlen/8)} (distinct values, 0 = K1) x layout in {x staged per tile (when
  * the base options' tiles is 0), x gathered from cache with 128 or 256 threads
  * per block}, each built from the given CSR with the base options' reorder and
- * sigma, then timed as `reps` back-to-back FP64 products in the permuted
- * numbering on `stream`.
+ * sigma, then timed as `reps` back-to-back products in the permuted numbering on
+ * `stream`: products of the FP32 copy of S A S when the base options' precisions
+ * hold FESPMV_PREC_F32 (else of the BF16 copy when they hold FESPMV_PREC_BF16: the
+ * refined CG's inner product), FP64 products otherwise.
  *   opts_inout   in: base options (format forced to SLICED); out: the fastest
  *                candidate's vec, threshold, block and tiles
  *   reps         products timed per candidate (0 = 20)

@@ -346,15 +346,16 @@ def spmv_plan_tiles(n_rows, meta, cols):
 
 
 def spmv_autotune(rowptr, colind, values, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
-                  reps=0, tiles=0, stream=None) -> dict:
-    """Time candidate layouts; returns dict(vec, threshold, block, tiles, sigma, reorder, best_us, tried)."""
+                  reps=0, tiles=0, precisions=0, stream=None) -> dict:
+    """Time candidate layouts (products in FP32/BF16 when precisions names that copy, else
+    FP64); returns dict(vec, threshold, block, tiles, sigma, reorder, best_us, tried)."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     values = np.ascontiguousarray(values, dtype=np.float64)
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, 0, 0, tiles)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, 0, 0, 0, precisions, 0, tiles)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     best = ctypes.c_double(0)
     tried = _i32(0)

@@ -546,6 +546,15 @@ int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const
     best.format = FESPMV_FMT_SLICED;
     double best_t = 1e300;
     int tried = 0;
+    // the products are timed in the precision the caller will run: the FP32 (or BF16)
+    // copy of S A S when the base options keep one, else FP64
+    const int tprec = (opts->precisions & FESPMV_PREC_F32) ? FESPMV_PREC_F32
+                    : (opts->precisions & FESPMV_PREC_BF16) ? FESPMV_PREC_BF16 : 0;
+    auto product = [&](fespmv_mat_t A) {
+        return tprec ? spmv_apply_scaled(A, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y), tprec,
+                                         FESPMV_IO_PERMUTED, stream)
+                     : spmv_apply(A, x, y, FESPMV_IO_PERMUTED, stream);
+    };
     // layouts: x staged per tile (block fixed by the tiled kernels), or gathered from
     // cache with 128 or 256 threads per block; tiles only when the base options allow them
     struct Shape { int tiles, block; };
@@ -562,13 +571,13 @@ int spmv_autotune(int64_t n, const int64_t* rowptr, const int32_t* colind, const
                 o.threshold = thr;
                 o.block = sh.block;
                 o.tiles = sh.tiles;
-                o.precisions = FESPMV_PREC_F64;
+                o.precisions = FESPMV_PREC_F64 | tprec;
                 fespmv_mat_t A = nullptr;
                 rc = spmv_create(&A, n, rowptr, colind, values, mesh, &o, stream);
                 if (rc) { cleanup(); return rc; }
-                for (int w = 0; w < 2; ++w) rc |= spmv_apply(A, x, y, FESPMV_IO_PERMUTED, stream);
+                for (int w = 0; w < 2; ++w) rc |= product(A);
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < reps; ++r) rc |= spmv_apply(A, x, y, FESPMV_IO_PERMUTED, stream);
+                for (int r = 0; r < reps; ++r) rc |= product(A);
                 cudaEventRecord(e1, s);
                 cudaError_t e = cudaEventSynchronize(e1);
                 float ms = 0.0f;

@@ -230,6 +230,14 @@ def test_autotuner_returns_a_valid_fast_layout():
     assert u["tiles"] == -1 and u["tried"] < t["tried"]
     x = fegen.random_vector(p.n_rows, 21)
     check_parity(p, apply(A, x), x)
+    # timed in the low precision the options name: the winner is a valid FP32 layout
+    for prec in (fs.FESPMV_PREC_F32, fs.FESPMV_PREC_BF16):
+        w = fs.spmv_autotune(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, reps=3, tiles=-1,
+                             precisions=prec)
+        assert w["tiles"] == -1 and w["tried"] == u["tried"] and w["best_us"] > 0
+        B = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=256, vec=w["vec"],
+                           threshold=w["threshold"], block=w["block"], tiles=-1, precisions=prec)
+        assert fs.spmv_get_info(B)["vec"] == w["vec"]
 
 
 @pytest.mark.parametrize("name,thr,V", [("elasticity_9", 0, 2), ("shell_6x20x36", 3, 1),
