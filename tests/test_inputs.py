@@ -125,3 +125,52 @@ def test_valid_seed_redraws_deterministically():
     assert calls == [10, 10 + 100003, 10 + 2 * 100003] and p.seed == calls[-1]
     with pytest.raises(ValueError):
         fegen.valid_seed(lambda s: fegen.cube_laplace(5, s, jitter=0.9), 1, tries=2)
+
+
+def test_element_quantities_are_those_of_the_mesh():
+    """The exported elements: every tet of the grid once, its 4 distinct nodes, a
+    symmetric element matrix with constants (Laplace) or the 6 rigid-body modes
+    of its own vertices (elasticity) in its null space, and a positive diagonal."""
+    for p in (fegen.cube_laplace(5, 31, elements=True), fegen.shell_laplace(3, 6, 8, 32, elements=True),
+              fegen.cube_elasticity(4, 33, elements=True)):
+        ne = p.elem_nodes.shape[0]
+        assert ne == p.n_elems and p.elem_mats.shape[1:] == (4 * p.dofs_per_node,) * 2
+        assert all(len(set(t)) == 4 for t in p.elem_nodes.tolist())
+        assert p.elem_nodes.min() >= 0 and p.elem_nodes.max() < p.n_nodes
+        K = p.elem_mats
+        assert np.array_equal(K, np.transpose(K, (0, 2, 1)))
+        assert np.all(np.diagonal(K, axis1=1, axis2=2) > 0)
+        scale = np.abs(K).max(axis=(1, 2))[:, None]
+        if p.dofs_per_node == 1:
+            assert np.all(np.abs(K.sum(axis=2)) <= 1e-13 * scale)
+        else:
+            x = p.node_xyz[p.elem_nodes]                     # (ne, 4, 3) vertex coordinates
+            for k in range(6):                               # 3 translations, 3 rotations
+                u = np.zeros((ne, 4, 3))
+                if k < 3:
+                    u[:, :, k] = 1.0
+                else:
+                    a, b = [(1, 2), (2, 0), (0, 1)][k - 3]
+                    u[:, :, a] = -x[:, :, b]
+                    u[:, :, b] = x[:, :, a]
+                r = np.einsum("eij,ej->ei", K, u.reshape(ne, 12))
+                assert np.all(np.abs(r) <= 1e-12 * scale * 4)
+
+
+def test_block_diagonal_helper_of_the_bench():
+    import bench
+    ps = [fegen.cube_laplace(4, 41), fegen.cube_laplace(5, 42)]
+    rp, ci, va, xyz = bench.block_diagonal(ps)
+    n = sum(p.n_rows for p in ps)
+    dense = np.zeros((n, n))
+    for i in range(n):
+        dense[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    off = 0
+    for p in ps:
+        blk = np.zeros((p.n_rows, p.n_rows))
+        for i in range(p.n_rows):
+            blk[i, p.colind[p.rowptr[i]:p.rowptr[i + 1]]] = p.values[p.rowptr[i]:p.rowptr[i + 1]]
+        assert np.array_equal(dense[off:off + p.n_rows, off:off + p.n_rows], blk)
+        off += p.n_rows
+    assert np.count_nonzero(dense) == sum(np.count_nonzero(p.values) for p in ps)
+    assert xyz.shape == (n, 3)
