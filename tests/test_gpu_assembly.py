@@ -145,3 +145,38 @@ def test_assembly_full_size_elasticity_64():
     fs.assembly_matrix(P, Ke)
     torch.cuda.synchronize()
     same_handles(R, Z, (fs.FESPMV_EXPORT_VALUES, fs.FESPMV_EXPORT_DIAG, fs.FESPMV_EXPORT_VALUES_F32))
+
+
+def test_assembly_edge_cases():
+    """No elements at all (every row constrained: the identity), permuted vectors on a
+    CSR handle rejected, and a second map on the same handle giving the same values."""
+    n = 40
+    rowptr = np.arange(n + 1, dtype=np.int64)
+    colind = np.arange(n, dtype=np.int32)
+    A = fs.spmv_create(rowptr, colind, np.full(n, 3.0), sigma=8, precisions=fs.FESPMV_PREC_F32)
+    P = fs.assembly_create(A, rowptr, colind, np.zeros((0, 4), dtype=np.int32), 1, np.ones(n, dtype=np.uint8))
+    assert fs.assembly_get_info(P)["contributions"] == 0
+    fs.assembly_matrix(P, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    info = fs.spmv_get_info(A)
+    vals = fs.spmv_export(A, fs.FESPMV_EXPORT_VALUES)
+    assert np.array_equal(np.sort(vals)[-n:], np.ones(n)) and np.count_nonzero(vals) == n
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_DIAG), np.ones(n))
+    assert info["packed_len"] >= n
+    p = MESHES["elasticity_7"]()
+    C = handle(p, 2.0 * p.values, "csr")
+    Q = fs.assembly_create(C, p.rowptr, p.colind, p.elem_nodes, 3, p.dirichlet)
+    r = torch.zeros(p.n_rows, dtype=torch.float64, device="cuda")
+    re = torch.zeros((p.n_elems, 12), dtype=torch.float64, device="cuda")
+    with pytest.raises(fs.FespmvError) as e:
+        fs.assembly_vector(Q, re, r, fs.FESPMV_IO_PERMUTED)
+    assert e.value.status == fs.FESPMV_ERR_INVALID_ARG
+    Z = handle(p, 2.0 * p.values, "tiled")
+    P1 = fs.assembly_create(Z, p.rowptr, p.colind, p.elem_nodes, 3, p.dirichlet)
+    P2 = fs.assembly_create(Z, p.rowptr, p.colind, p.elem_nodes, 3, p.dirichlet)
+    Ke = torch.from_numpy(p.elem_mats).cuda()
+    fs.assembly_matrix(P1, Ke)
+    v1 = fs.spmv_export(Z, fs.FESPMV_EXPORT_VALUES).copy()
+    fs.assembly_matrix(P2, 3.0 * Ke)
+    fs.assembly_matrix(P2, Ke)
+    assert np.array_equal(v1, fs.spmv_export(Z, fs.FESPMV_EXPORT_VALUES))
