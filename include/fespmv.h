@@ -427,6 +427,9 @@ int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* co
  *   FESPMV_CG_F64: every stop of the recurrence (||r|| <= tol ||b||) is checked
  *   against the FP64 residual b - A x; above tol the column restarts from x
  *   (max_restarts times).  relres and true_relres are both that FP64 residual.
+ *   On a handle created with FESPMV_PREC_DF64 every FP64 product of the solve
+ *   (inner and residual) runs as float pairs on the FP32 pipe (see
+ *   FESPMV_PREC_DF64), with the p.q sums in FP64.
  *   FESPMV_CG_F32_REFINE: the iterative refinement (or, with FESPMV_CG_RELIABLE,
  *   the reliable updates) of cg_solve, per column, with one difference: a column
  *   whose inner residual has fallen by inner_tol keeps iterating until the next

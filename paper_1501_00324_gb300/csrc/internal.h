@@ -171,6 +171,10 @@ int launch_gather_split(const double* x, const int32_t* idx, double* xp, float2*
 // its grid (with part == nullptr it only returns the grid).
 unsigned launch_multi_dot(const fespmv_mat* A, const void* P, void* Q, int kw, bool f64, double* part,
                           cudaStream_t s);
+// The same product and sums on a FESPMV_PREC_DF64 handle as float pairs: P is split
+// into Pdf (n x kw pairs, the caller's scratch) first.
+unsigned launch_multi_dot_pairs(const fespmv_mat* A, const double* P, double* Q, float2* Pdf, int kw, double* part,
+                                cudaStream_t s);
 // Y = A X in FP64 (float pairs on FESPMV_PREC_DF64 handles).
 int launch_multi_f64(fespmv_mat* A, const double* X, double* Y, int kw, cudaStream_t s);
 // dst[i, j] = src[idx[i], j] (idx null: identity) for j < k, 0 for k <= j < ldd.

@@ -252,21 +252,18 @@ __device__ __forceinline__ void ld_v_pairs(const float2* p, float2 (&a)[V]) {
     }
 }
 
+// One warp's unit of a float-pair product: as multi_unit, every product and sum as
+// float pairs; rows whose pair sums meet a marked pair are summed again in FP64.
+// Stores the rows of Y and leaves their values in out.
 template <int V, int KW, int RW>
-__global__ void __launch_bounds__(128, 4) sliced_multi_df(const uint4* __restrict__ meta,
-                                                          const int32_t* __restrict__ col,
-                                                          const float2* __restrict__ vdf,
-                                                          const double* __restrict__ val,
-                                                          const float2* __restrict__ Xdf,
-                                                          const double* __restrict__ X64,
-                                                          double* __restrict__ Y, int64_t n_slices,
-                                                          int64_t n) {
+__device__ __forceinline__ void multi_unit_df(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
+                                              const float2* __restrict__ vdf, const double* __restrict__ val,
+                                              const float2* __restrict__ Xdf, const double* __restrict__ X64,
+                                              double* __restrict__ Y, int64_t gw, int64_t n, int lane,
+                                              double (&out)[RW / (32 / (KW / 4))][4]) {
     constexpr int LPG = KW / 4, G = 32 / LPG, R = RW / G, WPS = 32 / RW;
     static_assert(R >= 1 && RW * WPS == 32, "bad multi-RHS tiling");
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t slice = gw / WPS;
-    if (slice >= n_slices) return;
-    const int lane = threadIdx.x & 31;
     const int g = lane / LPG, q = lane % LPG;
     const uint4 m = meta[slice];
     const int first_row = (int)(gw % WPS) * RW + g * R;
@@ -307,7 +304,7 @@ __global__ void __launch_bounds__(128, 4) sliced_multi_df(const uint4* __restric
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int64_t row = (int64_t)m.z + first_row + i;
-        double yv[4];
+        double* yv = out[i];
         bool bad = false;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -333,6 +330,70 @@ __global__ void __launch_bounds__(128, 4) sliced_multi_df(const uint4* __restric
             reinterpret_cast<double2*>(yp)[1] = make_double2(yv[2], yv[3]);
         }
     }
+}
+
+template <int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi_df(const uint4* __restrict__ meta,
+                                                          const int32_t* __restrict__ col,
+                                                          const float2* __restrict__ vdf,
+                                                          const double* __restrict__ val,
+                                                          const float2* __restrict__ Xdf,
+                                                          const double* __restrict__ X64,
+                                                          double* __restrict__ Y, int64_t n_slices,
+                                                          int64_t n) {
+    constexpr int R = RW / (32 / (KW / 4));
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (gw >= n_slices * (32 / RW)) return;
+    double out[R][4];
+    multi_unit_df<V, KW, RW>(meta, col, vdf, val, Xdf, X64, Y, gw, n, threadIdx.x & 31, out);
+}
+
+// The FP64 product of the lockstep CG on a float-pair handle: Q = A P as
+// sliced_multi_df computes it (P given in double and split into pairs), and the
+// per-column sums of p_ij q_ij as sliced_multi_dot forms them, in FP64.
+template <int V, int KW, int RW>
+__global__ void __launch_bounds__(128, 4) sliced_multi_df_dot(const uint4* __restrict__ meta,
+                                                              const int32_t* __restrict__ col,
+                                                              const float2* __restrict__ vdf,
+                                                              const double* __restrict__ val,
+                                                              const float2* __restrict__ Pdf,
+                                                              const double* __restrict__ P,
+                                                              double* __restrict__ Q, int64_t n_slices,
+                                                              int64_t n, double* __restrict__ part) {
+    constexpr int LPG = KW / 4, G = 32 / LPG, R = RW / G, WPS = 32 / RW;
+    __shared__ double sh[4][KW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int g = lane / LPG, q = lane % LPG;
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t units = n_slices * WPS;
+    for (int64_t gw = (int64_t)blockIdx.x * 4 + wib; gw < units; gw += (int64_t)gridDim.x * 4) {
+        double out[R][4];
+        multi_unit_df<V, KW, RW>(meta, col, vdf, val, Pdf, P, Q, gw, n, lane, out);
+        const int64_t row0 = (int64_t)meta[gw / WPS].z + (int)(gw % WPS) * RW + g * R;
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (row0 + i < n) {
+                double pv[4] = {0.0, 0.0, 0.0, 0.0};
+                ld_x4(P + (row0 + i) * KW + 4 * q, true, pv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t[j] = fma(pv[j], out[i][j], t[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] += t[j];
+    }
+#pragma unroll
+    for (int o = LPG; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
+    if (g == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[wib][4 * q + j] = d[j];
+    __syncthreads();
+    if (threadIdx.x < KW)
+        part[(int64_t)blockIdx.x * KW + threadIdx.x] =
+            ((sh[0][threadIdx.x] + sh[1][threadIdx.x]) + sh[2][threadIdx.x]) + sh[3][threadIdx.x];
 }
 
 // X in pairs (df_split: marked pairs for values outside the fast range).
@@ -445,6 +506,34 @@ static void launch_multi_df_kw(const fespmv_mat* A, const float2* Xdf, const dou
                                                  A->n_slices, A->n);
 }
 
+template <int V, int KW>
+static unsigned multi_df_dot_kw(const fespmv_mat* A, const double* P, double* Q, const float2* Pdf, double* part,
+                                cudaStream_t s) {
+    constexpr int RW = multi_rows_per_warp<double, double, V, KW>();
+    auto kernel = sliced_multi_df_dot<V, KW, RW>;
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    const int64_t units = A->n_slices * (32 / RW);
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (units + 3) / 4));
+    if (part)
+        kernel<<<grid, 128, 0, s>>>(A->d_meta, A->d_col, A->d_vdf, A->d_val, Pdf, P, Q, A->n_slices, A->n, part);
+    return grid;
+}
+
+template <int V>
+static unsigned multi_df_dot_v(const fespmv_mat* A, const double* P, double* Q, const float2* Pdf, int kw,
+                               double* part, cudaStream_t s) {
+    switch (kw) {
+        case 4: return multi_df_dot_kw<V, 4>(A, P, Q, Pdf, part, s);
+        case 8: return multi_df_dot_kw<V, 8>(A, P, Q, Pdf, part, s);
+        case 16: return multi_df_dot_kw<V, 16>(A, P, Q, Pdf, part, s);
+        default: return multi_df_dot_kw<V, 32>(A, P, Q, Pdf, part, s);
+    }
+}
+
 template <int V>
 static void launch_multi_df_v(const fespmv_mat* A, const float2* Xdf, const double* X, double* Y, int kw,
                               cudaStream_t s) {
@@ -524,6 +613,19 @@ unsigned launch_multi_dot(const fespmv_mat* A, const void* P, void* Q, int kw, b
     if (f64)
         return multi_dot<double, double>(A, A->d_val, (const double*)P, (double*)Q, kw, part, s);
     return multi_dot<float, float>(A, A->d_val32, (const float*)P, (float*)Q, kw, part, s);
+}
+
+unsigned launch_multi_dot_pairs(const fespmv_mat* A, const double* P, double* Q, float2* Pdf, int kw, double* part,
+                                cudaStream_t s) {
+    if (part) {
+        const int64_t len = A->n * kw;
+        split_rows<<<grid_for(len, 256), 256, 0, s>>>(P, Pdf, len);
+    }
+    switch (A->vec) {
+        case 1: return multi_df_dot_v<1>(A, P, Q, Pdf, kw, part, s);
+        case 4: return multi_df_dot_v<4>(A, P, Q, Pdf, kw, part, s);
+        default: return multi_df_dot_v<2>(A, P, Q, Pdf, kw, part, s);
+    }
 }
 
 int launch_multi_f64(fespmv_mat* A, const double* X, double* Y, int kw, cudaStream_t s) {

@@ -66,6 +66,7 @@ struct MultiWork {
     int64_t part_len = 0;
     MScal* sc = nullptr;
     MScal* h_sc = nullptr;                       // pinned mirror
+    float2* pdf = nullptr;                       // p as float pairs (FESPMV_PREC_DF64 handles)
     int64_t bytes = 0;                           // device bytes held
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -472,7 +473,13 @@ static void inner_kw(const fespmv_mat* A, MultiWork* w, unsigned dot_grid, unsig
     T* rv = static_cast<T*>(w->r);
     T* pv = static_cast<T*>(w->p);
     T* qv = static_cast<T*>(w->q);
-    launch_multi_dot(A, pv, qv, KW, std::is_same<T, double>::value, w->part, s);
+    if constexpr (std::is_same<T, double>::value) {
+        // FP64 products as float pairs on handles that keep them (the FP32 pipe)
+        if (w->pdf) launch_multi_dot_pairs(A, pv, qv, w->pdf, KW, w->part, s);
+        else launch_multi_dot(A, pv, qv, KW, true, w->part, s);
+    } else {
+        launch_multi_dot(A, pv, qv, KW, false, w->part, s);
+    }
     mc_finalize_pq<<<KW, 256, 0, s>>>(w->part, dot_grid, KW, w->sc);
     mc_update<T, KW, PRE><<<upd_grid, kUpdBlock, 0, s>>>(A->n, wv, rv, pv, qv, w->dinv, w->part, w->sc);
     mc_finalize_rr<<<KW, 256, 0, s>>>(w->part, upd_grid, KW, PRE ? 1 : 0, w->sc);
@@ -559,7 +566,7 @@ static void destroy_multi_work(MultiWork* w) {
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
     if (w->cap) cudaStreamDestroy(w->cap);
-    void* ptrs[] = {w->x, w->b, w->q64, w->dinv, w->w, w->r, w->p, w->q, w->part, w->sc};
+    void* ptrs[] = {w->x, w->b, w->q64, w->dinv, w->w, w->r, w->p, w->q, w->part, w->sc, w->pdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -579,10 +586,16 @@ static int mw_alloc(MultiWork* w, void** p, size_t bytes, const char* what) {
     return FESPMV_OK;
 }
 
+// Grid of the FP64 inner product: float pairs on handles that keep them.
+static unsigned dot_grid_of(const fespmv_mat* A, int kw, bool f64) {
+    if (f64 && A->d_vdf) return launch_multi_dot_pairs(A, nullptr, nullptr, nullptr, kw, nullptr, nullptr);
+    return launch_multi_dot(A, nullptr, nullptr, kw, f64, nullptr, nullptr);
+}
+
 // Partial sums for either precision's grids at width kw.
 static int64_t multi_part_len(const fespmv_mat* A, int kw) {
-    const unsigned g32 = launch_multi_dot(A, nullptr, nullptr, kw, false, nullptr, nullptr);
-    const unsigned g64 = launch_multi_dot(A, nullptr, nullptr, kw, true, nullptr, nullptr);
+    const unsigned g32 = dot_grid_of(A, kw, false);
+    const unsigned g64 = dot_grid_of(A, kw, true);
     return (int64_t)std::max({g32, g64, 4 * update_grid(A->n, kw)}) * kw;
 }
 
@@ -602,7 +615,8 @@ static int create_multi_work(const fespmv_mat* A, int kw, MultiWork** out) {
         (rc = mw_alloc(w, &w->p, bytes, "multi-RHS p")) || (rc = mw_alloc(w, &w->q, bytes, "multi-RHS q")) ||
         (rc = mw_alloc(w, (void**)&w->dinv, sizeof(double) * (size_t)A->n, "multi-RHS dinv")) ||
         (rc = mw_alloc(w, (void**)&w->part, sizeof(double) * (size_t)pl, "multi-RHS partial sums")) ||
-        (rc = mw_alloc(w, (void**)&w->sc, sizeof(MScal) * 32, "multi-RHS scalars"))) {
+        (rc = mw_alloc(w, (void**)&w->sc, sizeof(MScal) * 32, "multi-RHS scalars")) ||
+        (A->d_vdf && (rc = mw_alloc(w, (void**)&w->pdf, sizeof(float2) * (size_t)A->n * kw, "multi-RHS p pairs")))) {
         destroy_multi_work(w);
         return rc;
     }
@@ -779,7 +793,7 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
     const bool f64 = sh.f64;
     const int kw = sh.kw;
     const int64_t n = A->n;
-    const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, f64, nullptr, nullptr);
+    const unsigned dot_grid = dot_grid_of(A, kw, f64);
     const unsigned upd_grid = update_grid(n, kw);
     if ((rc = ensure_handle_work(A, kw))) return rc;
     MultiWork* w = A->mcg;
@@ -981,7 +995,7 @@ int group_width_auto(const fespmv_mat* A) {
 
 int64_t group_bytes(const fespmv_mat* A, int kw) {
     return (int64_t)sizeof(double) * (7 * kw + 2) * A->n + (int64_t)sizeof(double) * multi_part_len(A, kw) +
-           (int64_t)sizeof(MScal) * 32;
+           (int64_t)sizeof(MScal) * 32 + (A->d_vdf ? (int64_t)sizeof(float2) * kw * A->n : 0);
 }
 
 int group_create(fespmv_mat* A, int kw, const cg_options& o, MultiGroup** out) {
@@ -1002,7 +1016,7 @@ int group_create(fespmv_mat* A, int kw, const cg_options& o, MultiGroup** out) {
     g->period = (int64_t)o.check_every * kOuterChunks;
     g->cols.resize((size_t)kw);
     g->upd_grid = update_grid(A->n, kw);
-    const unsigned dot_grid = launch_multi_dot(A, nullptr, nullptr, kw, g->sh.f64, nullptr, nullptr);
+    const unsigned dot_grid = dot_grid_of(A, kw, g->sh.f64);
     cudaError_t e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
