@@ -9,6 +9,13 @@
  * and runs the Jacobi-preconditioned conjugate-gradient solve of K dx = R that
  * the paper's Newton loop performs (Sec. 2.1, Sec. 4), on one GPU.
  *
+ * Entry points, in these groups: handles and products (spmv_create,
+ * spmv_apply, spmv_apply_multi, spmv_apply_scaled, spmv_update_values,
+ * spmv_autotune, spmv_plan / spmv_plan_tiles host-only planning, spmv_export);
+ * solves (cg_solve, cg_solve_csr_static, cg_solve_multi); assembly from element
+ * quantities (assembly_*, Sec. 4); batches of independent problems (batch_*);
+ * the solve server (srv_*).
+ *
  * Conventions for every entry point:
  *   - Return 0 (FESPMV_OK) on success or a negative FESPMV_ERR_* code; nothing
  *     aborts or traps.  fespmv_last_error() gives a message for the calling
