@@ -174,3 +174,13 @@ def test_block_diagonal_helper_of_the_bench():
         off += p.n_rows
     assert np.count_nonzero(dense) == sum(np.count_nonzero(p.values) for p in ps)
     assert xyz.shape == (n, 3)
+
+
+def test_committed_headline_profile_matches_the_kernel_source():
+    """The bench reports the headline kernel's DRAM traffic from the committed ncu
+    summary only while the summary's source hash matches the kernel sources; a
+    kernel edit without a new capture must show up here, not as a silent null."""
+    import bench
+    traffic, source = bench.profile_traffic("tiled_f64")
+    assert traffic is not None, source
+    assert 3.0e8 < traffic < 4.3e8          # the tiled layout's bytes, below the algorithmic 420 MB
