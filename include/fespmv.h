@@ -399,13 +399,15 @@ int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts,
  *                          FESPMV_CG_NO_PRECOND are rejected)
  * Same Jacobi-PCG recurrences and kernels as cg_solve on a FESPMV_FMT_CSR handle.
  * The workspace (about 8.8 MB) is one fixed device array inside this library;
- * every GPU that loads the library holds it until the process exits.  The
- * first call on a device resolves that array's address for the device, so make
- * that first call before any stream capture.  Every call shares the array and
- * leaves its contents behind; each call clears the state it needs, but calls
- * whose work overlaps on the GPU (from several threads or streams) race on
- * the array and must be serialised by the caller.  The call calls no device or
- * host allocator and blocks the host until the solve ends.
+ * every GPU that loads the library holds it until the process exits.  Each
+ * call looks up that array's address on the current device (so a device reset
+ * between calls is harmless).  Every call shares the array and leaves its
+ * contents behind; each call clears the state it needs, but calls whose work
+ * overlaps on the GPU (from several threads or streams) race on the array and
+ * must be serialised by the caller.  The call calls no device or host
+ * allocator.  It reads the solver's scalars back to the host and synchronises
+ * `stream` several times, so it blocks until the solve ends and must not be
+ * called while `stream` is being captured into a CUDA graph.
  */
 int cg_solve_csr_static(int64_t n_rows, const int64_t* rowptr, const int32_t* colind,
                         const double* values, const double* b, double* x, int32_t csr_lanes,

@@ -19,7 +19,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "internal.h"
 #include "spmv_device.cuh"
@@ -1370,26 +1369,15 @@ static_assert(sizeof(CgScalars) <= 512, "the static scratch reserves 512 bytes f
 
 static __device__ __align__(256) unsigned char g_cg_static_scratch[kStaticBytes];
 
-static std::mutex g_static_mutex;
-static void* g_static_ptr[64];  // device address of the array, per device ordinal
-
-// Resolves the array's device address for the current device (first call on
-// that device only).
+// Device address of the array for the current device, looked up on every call.
+// The lookup is cheap once the module is loaded, and a cached address could go
+// stale: a cudaDeviceReset (or any teardown of the primary context) loads the
+// module again, and the array may then sit elsewhere.
 static int static_scratch(void** out) {
-    int dev = 0;
-    FESPMV_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        set_error("device ordinal %d not supported by cg_solve_csr_static", dev);
-        return FESPMV_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_cg_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_cg_static_scratch)");
-        g_static_ptr[dev] = ptr;
-    }
-    *out = g_static_ptr[dev];
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_cg_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_cg_static_scratch)");
+    *out = ptr;
     return FESPMV_OK;
 }
 
