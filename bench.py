@@ -77,12 +77,17 @@ def parse_args():
     ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "assembly"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-seconds", type=float, default=8.0,
-                    help="length of each serving run (server and one-at-a-time); 0 skips")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="the full serving pool: 48 meshes of 5k..3M rows (else 12 of 5k..300k)")
+    ap.add_argument("--cpu-seconds", type=float, default=16.0,
+                    help="host seconds of the CPU baseline (oracle SpMV and CG, 1 core and all cores)")
+    ap.add_argument("--c1", type=int, default=1,
+                    help="1: also measure the 20^3 cube Laplacian (us per product, CG to 1e-10)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="length of each serving run (per arm and arrival rate); 0 skips")
+    ap.add_argument("--serve-small", action="store_true",
+                    help="a small serving pool: 12 meshes of 5k..300k rows (default: 48 of 5k..3M)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-sweep", type=str, default="0.25,0.5,0.75,1.0,1.25",
+                    help="arrival rates as fractions of the grouped server's saturation rate")
     ap.add_argument("--shell", type=int, default=1,
                     help="1: also measure the 24x256x512 shell Laplacian (FP64/BF16 products, refined CG)")
     ap.add_argument("--batch-meshes", type=int, default=256,
@@ -203,35 +208,141 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_oracle_spmv(p, x, seconds):
-    """Time the oracle's FP64 CSR product (one host core) for about `seconds`."""
-    import oracle
-    oracle.csr_spmv(p.rowptr, p.colind, p.values, x)          # warm
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def timed_repeats(fn, seconds, min_reps=1):
+    """Call fn until `seconds` have passed (at least min_reps times); (reps, elapsed)."""
     t0 = time.perf_counter()
     k = 0
     while True:
-        oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        fn()
         k += 1
         el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return k, el
+        if el >= seconds and k >= min_reps:
+            return k, el
+
+
+def cpu_oracle_spmv(p, x, seconds, threads=1):
+    """Time the oracle's FP64 CSR product on `threads` host cores for about `seconds`."""
+    import oracle
+    oracle.set_threads(threads)
+    try:
+        oracle.csr_spmv(p.rowptr, p.colind, p.values, x)          # warm
+        return timed_repeats(lambda: oracle.csr_spmv(p.rowptr, p.colind, p.values, x), seconds)
+    finally:
+        oracle.set_threads(1)
+
+
+def cpu_baseline_leg(p, x, y_gpu, seconds, c1=None, cg_iters=None):
+    """The CPU oracle on the host cores, bounded samples of the benchmark's workloads:
+    the FP64 CSR product of the 64^3 elasticity matrix on 1 core and on all cores,
+    Jacobi-PCG iterations on it (all cores; the per-iteration time times the full
+    solve's iteration count), and the 20^3 cube Laplacian (product warm and after a
+    256 MB host write; full CG solves to 1e-10, 1 core and all cores).  It also
+    checks the GPU's headline product y_gpu (input numbering) against the oracle's
+    product of the same x: |y - y_oracle| <= 1e-12 * (|A| |x|) per row."""
+    import oracle
+    import fegen
+    cores = host_cores()
+    mb = min_bytes(p.n_rows, p.nnz)
+    k1, el1 = cpu_oracle_spmv(p, x, 0.25 * seconds, 1)
+    kn, eln = cpu_oracle_spmv(p, x, 0.15 * seconds, cores)
+    out = {"value": round(mb * kn / eln / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "sample": (f"{kn} FP64 CSR products of the {WORKLOAD} matrix in {eln:.1f} s on {cores} cores "
+                      f"(row-parallel, same sums as 1 core); 1 core: {k1} in {el1:.1f} s"),
+           "spmv_1core_gbs": round(mb * k1 / el1 / 1e9, 3),
+           "spmv_1core_ms": round(el1 / k1 * 1e3, 2), "spmv_allcore_ms": round(eln / kn * 1e3, 2),
+           "l2_note": "the 420 MB matrix exceeds every host cache: each product is cold"}
+    # the headline product's output against the oracle (sampled from the timed kernel)
+    if y_gpu is not None:
+        oracle.set_threads(cores)
+        try:
+            yo = oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+            bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(x))
+        finally:
+            oracle.set_threads(1)
+        err = np.abs(y_gpu - yo)
+        ratio = np.where(bound > 0, err / np.where(bound > 0, bound, 1.0), np.where(err > 0, np.inf, 0.0))
+        out["headline_output_check"] = {"rows": int(p.n_rows), "worst_err_over_abs_bound": float(ratio.max()),
+                                        "bound": 1e-12, "pass": bool(ratio.max() <= 1e-12)}
+    # Jacobi-PCG on the elasticity matrix: a bounded number of iterations on all cores
+    b = fegen.random_vector(p.n_rows, 1505)
+    oracle.set_threads(cores)
+    try:
+        kit = 30
+        t0 = time.perf_counter()
+        _, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-30, max_iter=kit, max_restarts=0)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    per_it = el / max(1, info["iters"])
+    cg = {"cores": cores, "iters_timed": info["iters"], "ms_per_iteration": round(per_it * 1e3, 2)}
+    if cg_iters:
+        cg.update({"iters_full_solve": cg_iters, "est_s_per_solve": round(per_it * cg_iters, 2),
+                   "est_solves_per_s": round(1.0 / (per_it * cg_iters), 4),
+                   "note": "iteration time x the iteration count of the FP64 solve to 1e-10 "
+                           "(the GPU's count, held within 2 % + 2 of the oracle's by the tests)"})
+    out["cg_cube_elasticity_64"] = cg
+    if c1 is not None:
+        q = c1
+        xq = fegen.random_vector(q.n_rows, 1504)
+        flush = np.empty(256 * 1024 * 1024 // 8)
+        c1o = {}
+        for th in (1, cores):
+            oracle.set_threads(th)
+            try:
+                kw, elw = timed_repeats(lambda: oracle.csr_spmv(q.rowptr, q.colind, q.values, xq), 0.05 * seconds, 3)
+                cold = []
+                for _ in range(5):
+                    flush.fill(1.0)
+                    t0 = time.perf_counter()
+                    oracle.csr_spmv(q.rowptr, q.colind, q.values, xq)
+                    cold.append(time.perf_counter() - t0)
+                u = fegen.manufactured_solution(q)
+                bq = oracle.csr_spmv(q.rowptr, q.colind, q.values, u)
+                lat = []
+                t_end = time.perf_counter() + 0.05 * seconds
+                while time.perf_counter() < t_end or len(lat) < 3:
+                    t0 = time.perf_counter()
+                    xs, inf = oracle.pcg(q.rowptr, q.colind, q.values, bq, tol=1e-10)
+                    lat.append(time.perf_counter() - t0)
+            finally:
+                oracle.set_threads(1)
+            lat_ms = sorted(1e3 * t for t in lat)
+            c1o[f"{th}_cores"] = {"spmv_us_warm": round(elw / kw * 1e6, 2),
+                                  "spmv_us_cold": round(float(np.median(cold)) * 1e6, 2),
+                                  "cg_solves_per_s": round(len(lat) / sum(lat), 2),
+                                  "cg_p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                                  "cg_p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                                  "cg_iters": inf["iters"], "cg_status": inf["status"],
+                                  "true_relres": inf["true_relres"]}
+        out["cube_laplace_20"] = c1o
+    return out
 
 
 def run_reference(args, world, rank):
-    """CPU oracle arm: the same matrix and metric, FP64 CSR product on one host core."""
+    """CPU oracle arm: the same matrix and metric, the oracle's FP64 CSR product on the
+    host cores (row-parallel; every row one sequential sum, as on one core)."""
     if rank != 0:
         return
     import fegen
     import oracle
+    cores = host_cores()
     p = fegen.cube_elasticity(64, 1502)
     x = fegen.random_vector(p.n_rows, 1504)
+    oracle.set_threads(cores)
     for _ in range(max(0, args.warmup)):
         oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
     el = time.perf_counter() - t0
+    oracle.set_threads(1)
     mb = min_bytes(p.n_rows, p.nnz)
     gbs = mb * args.steps / el / 1e9
     line = {
@@ -240,8 +351,9 @@ def run_reference(args, world, rank):
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rows": p.n_rows, "nnz": p.nnz,
-                   "kernel": "oracle_csr_spmv (plain C, FP64, sequential rows)"},
-        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "kernel": f"oracle_csr_spmv (plain C, FP64, rows in parallel on {cores} host cores, "
+                             "each row a sequential sum)"},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full products of the {WORKLOAD} matrix"},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -449,9 +561,16 @@ def main():
                 extra["shell_24x256x512"] = bench_shell(fs, torch, args)
             if args.batch_meshes > 0:
                 extra["batched"] = bench_batched(fs, torch, args)
+            if args.c1:
+                extra["cube_laplace_20"] = bench_c1(fs, torch, args)
             if args.serve_seconds > 0 and hasattr(fs, "srv_create"):
                 extra["serving"] = bench_serving(fs, torch, args)
     clk = clocks.summary()
+    # the headline product's output (the last timed step), in the input numbering
+    y_check = torch.empty_like(xd)
+    fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)
+    fs.spmv_permute(A, yp, y_check, 1)
+    y_check = y_check.cpu().numpy()
 
     t_mean = t_step * 1e-3
     t_max = reduce_max(t_mean, world)
@@ -470,10 +589,11 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1 and args.cpu_seconds > 0 and not args.only_spmv:
-            k, el = cpu_oracle_spmv(p, x, args.cpu_seconds)
-            cpu = {"value": round(mb * k / el / 1e9, 3), "unit": "GB/s", "cores": 1,
-                   "kind": "oracle",
-                   "sample": f"{k} full FP64 CSR products of the {WORKLOAD} matrix in {el:.1f} s"}
+            import fegen as _fg
+            cg_it = extra.get("cg", {}).get("iters")
+            cpu = cpu_baseline_leg(p, x, y_check, args.cpu_seconds,
+                                   c1=_fg.cube_laplace(20, 1501) if args.c1 else None,
+                                   cg_iters=cg_it[0] if cg_it else None)
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3, 4),
@@ -515,11 +635,151 @@ def main():
         line.update(extra)
         if cpu:
             line["cpu_baseline"] = cpu
+        # last key: a compact view of every stated workload, so that the end of the
+        # line (what a log tail keeps) carries all of them
+        line["configs_summary"] = configs_summary(line)
         print(json.dumps(line), flush=True)
     fs.spmv_destroy(A)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_c1(fs, torch, args):
+    """The 20^3 cube Laplacian (8,000 rows; ~108k stored entries after the Dirichlet
+    face).  Its FP64 FE product (1.4 MB, L2-resident) is launch-bound, so it is
+    reported in microseconds: per launch back to back on the stream, per product
+    inside a CUDA graph of 100 products (device time without the launch overhead),
+    each alone after a 256 MB write (cold L2), and end to end through spmv_apply with
+    pinned host buffers.  Then Jacobi-PCG to 1e-10 on b = A u* (manufactured u*):
+    FP64, and FP32 values with FP64 reliable updates."""
+    import fegen
+    p = fegen.cube_laplace(20, 1501)
+    n, nnz = p.n_rows, p.nnz
+    mb = min_bytes(n, nnz)
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 1, sigma=1024,
+                       precisions=fs.FESPMV_PREC_F32)
+    x = torch.from_numpy(fegen.random_vector(n, 1504)).cuda()
+    xp = torch.empty_like(x)
+    fs.spmv_permute(A, x, xp, 0)
+    yp = torch.empty_like(x)
+    f = lambda: fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    for _ in range(20):
+        f()
+    torch.cuda.synchronize()
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    K = 2000
+    a, b = events()
+    a.record()
+    for _ in range(K):
+        f()
+    b.record()
+    torch.cuda.synchronize()
+    us_b2b = a.elapsed_time(b) / K * 1e3
+    us_graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(100):
+                f()
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = events()
+        a.record()
+        for _ in range(20):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        us_graph = a.elapsed_time(b) / 2000 * 1e3
+        del g
+    except Exception as e:  # graph capture is an extra view; the other figures stand alone
+        us_graph = f"capture failed: {type(e).__name__}"
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    evs = [events() for _ in range(50)]
+    for (ea, eb) in evs:
+        flush.zero_()
+        ea.record()
+        f()
+        eb.record()
+    torch.cuda.synchronize()
+    us_cold = statistics.median(ea.elapsed_time(eb) for ea, eb in evs) * 1e3
+    del flush
+    xh = torch.from_numpy(fegen.random_vector(n, 1504)).pin_memory().numpy()
+    yh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    fs.spmv_apply(A, xh, yh)
+    ke = 500
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        fs.spmv_apply(A, xh, yh)
+    us_e2e = (time.perf_counter() - t0) / ke * 1e6
+    out = {"rows": n, "nnz": nnz,
+           "spmv_us_back_to_back": round(us_b2b, 2),
+           "spmv_us_in_graph": round(us_graph, 2) if isinstance(us_graph, float) else us_graph,
+           "spmv_us_cold_l2": round(us_cold, 2),
+           "spmv_us_e2e_host_buffers": round(us_e2e, 2),
+           "spmv_gbs_in_graph": round(mb / (us_graph * 1e-6) / 1e9, 1) if isinstance(us_graph, float) else None,
+           "cg_f64": bench_cg(fs, torch, A, p, 50, fs.FESPMV_CG_F64),
+           "cg_f32_reliable": bench_cg(fs, torch, A, p, 50, fs.FESPMV_CG_F32_REFINE,
+                                       flags=fs.FESPMV_CG_RELIABLE)}
+    fs.spmv_destroy(A)
+    return out
+
+
+def _pick(d, *keys):
+    """Nested lookup that tolerates missing pieces (None)."""
+    for k in keys:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def configs_summary(line):
+    """One compact object per stated workload (numbers taken from the line)."""
+    cg = lambda c: None if not isinstance(c, dict) else {  # noqa: E731
+        k: c.get(k) for k in ("solves_per_s", "p50_ms", "p99_ms", "iters", "status", "true_relres_max")
+        if c.get(k) is not None}
+    c1 = line.get("cube_laplace_20") or {}
+    cpu = line.get("cpu_baseline") or {}
+    out = {
+        "C1_cube_laplace_20": {
+            "spmv_us": {k: c1.get(f"spmv_us_{k}") for k in ("back_to_back", "in_graph", "cold_l2",
+                                                              "e2e_host_buffers")},
+            "cg_f64_1e-10": cg(c1.get("cg_f64")), "cg_f32_reliable_1e-10": cg(c1.get("cg_f32_reliable")),
+            "cpu": _pick(cpu, "cube_laplace_20")},
+        "C2_cube_elasticity_64": {
+            "f64_spmv_gbs": line.get("value"), "frac_of_measured": _pick(line, "roofline", "frac"),
+            "e2e_gbs": _pick(line, "e2e", "value"), "fp32_spmv_gbs": line.get("fp32_spmv_gbs"),
+            "bf16_spmv_gbs": line.get("bf16_spmv_gbs"), "csr_vector4_gbs": line.get("csr_vector4_gbs"),
+            "cg_f64_1e-10": cg(line.get("cg")), "cg_f32_reliable_1e-10": cg(line.get("cg_f32_reliable")),
+            "output_check": _pick(cpu, "headline_output_check", "worst_err_over_abs_bound"),
+            "cpu_spmv_gbs": {"1_core": cpu.get("spmv_1core_gbs"), f"{cpu.get('cores')}_cores": cpu.get("value")},
+            "cpu_cg_est_solves_per_s": _pick(cpu, "cg_cube_elasticity_64", "est_solves_per_s")},
+        "C3_shell_24x256x512": {k: _pick(line, "shell_24x256x512", k) for k in (
+            "f64_spmv_gbs", "f32_spmv_gbs", "bf16_spmv_gbs")},
+        "C4_batched": {
+            "meshes": _pick(line, "batched", "meshes"), "solves_per_s": _pick(line, "batched", "solves_per_s"),
+            "batch_s": _pick(line, "batched", "batched_reliable_s"),
+            "rhs32_solves_per_s": _pick(line, "cg_multi32", "f32_reliable", "solves_per_s")},
+    }
+    sh = line.get("shell_24x256x512") or {}
+    for k in ("cg_f64", "cg_f32_reliable", "cg_bf16_reliable"):
+        if k in sh:
+            out["C3_shell_24x256x512"][k] = cg(sh[k])
+    sv = line.get("serving")
+    if isinstance(sv, dict):
+        out["C5_serving"] = {"pool": sv.get("pool"), "saturation_per_s": sv.get("saturation_per_s"),
+                             "by_rate": {str(r.get("rate_per_s")): {
+                                 a: [_pick(r, a, "solves_per_s"), _pick(r, a, "p50_ms_offered"),
+                                     _pick(r, a, "p99_ms_offered")]
+                                 for a in ("server", "server_grouped", "one_at_a_time")}
+                                 for r in sv.get("sweep", [])},
+                             "by_rate_fields": "[solves/s, p50 ms, p99 ms over all offered requests; "
+                                               "null: that percentile was not served in the run]"}
+    return out
 
 
 def serving_pool(n_meshes, lo, hi, seed):
@@ -545,23 +805,31 @@ def serving_pool(n_meshes, lo, hi, seed):
 
 
 def bench_serving(fs, torch, args):
-    """Poisson arrivals of CG solves over a resident mesh pool: the solve server
-    (continuous batching, FP32-refined CG) against one-at-a-time FP64 cg_solve on
-    the same arrival trace.  Each run lasts args.serve_seconds; requests still
-    queued at the end are cancelled and counted as not served."""
-    import threading
+    """Poisson arrivals of CG solves over a resident pool of 48 meshes (cube,
+    elasticity, shell; 5k to 3M rows): the solve server (continuous batching,
+    FP32 values with FP64 reliable updates), the same server with lockstep
+    multi-RHS groups, and one-at-a-time FP64 cg_solve, all on the same arrival
+    trace.  First an overload run (args.serve_rate) finds the grouped server's
+    saturation rate; then a sweep of arrival rates at fractions of it, plus one
+    rate at 0.5, 1 and 1.5 times the one-at-a-time capacity.  Each run lasts args.serve_seconds;
+    requests still queued at the end are cancelled and counted as not served."""
     import fegen
-    if args.serve_full:
-        n_mesh, lo, hi = 48, 5_000, 3_000_000
-    else:
+    if args.serve_small:
         n_mesh, lo, hi = 12, 5_000, 300_000
+    else:
+        n_mesh, lo, hi = 48, 5_000, 3_000_000
     t0 = time.perf_counter()
     pool = serving_pool(n_mesh, lo, hi, 1505)
+    gen_s = time.perf_counter() - t0
     mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=1024,
                            precisions=fs.FESPMV_PREC_F32) for p in pool]
     rhs = [[fegen.random_vector(p.n_rows, 7000 + 10 * i + k) for k in range(2)]
            for i, p in enumerate(pool)]
     setup_s = time.perf_counter() - t0
+    pool_info = {"meshes": n_mesh, "rows_min": min(p.n_rows for p in pool),
+                 "rows_max": max(p.n_rows for p in pool), "rows_total": sum(p.n_rows for p in pool),
+                 "nnz_total": sum(p.nnz for p in pool), "gen_s": round(gen_s, 1), "setup_s": round(setup_s, 1)}
+    sizes = [p.n_rows for p in pool]
     T = args.serve_seconds
 
     def make_trace(rate, seed):
@@ -571,15 +839,19 @@ def bench_serving(fs, torch, args):
         return [(float(a), int(rng.integers(n_mesh)), [1e-8, 1e-10][int(rng.integers(2))],
                  int(rng.integers(2))) for a in arrivals]
 
-    trace = make_trace(args.serve_rate, 1506)
-
     def summarize(trace, lat, served, elapsed):
+        """Latency percentiles over the served requests, and over every offered request
+        with the unserved ones counted as slower than any served one (null when the
+        percentile falls on an unserved request: the run left it unanswered)."""
         lat = np.array(sorted(lat)) * 1e3
-        return {"offered": len(trace), "served": served,
-                "offered_per_s": round(len(trace) / T, 1),
-                "solves_per_s": round(served / elapsed, 2) if elapsed > 0 else 0.0,
-                "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
-                "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None}
+        out = {"offered": len(trace), "served": served,
+               "solves_per_s": round(served / elapsed, 2) if elapsed > 0 else 0.0,
+               "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
+               "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None}
+        for q in (50, 99):
+            k = int(np.ceil(q / 100 * len(trace))) - 1
+            out[f"p{q}_ms_offered"] = round(float(lat[k]), 2) if 0 <= k < len(lat) else None
+        return out
 
     def run_server(trace, group=0):
         S = fs.srv_create(48 << 30, 64)
@@ -605,10 +877,8 @@ def bench_serving(fs, torch, args):
         st = fs.srv_get_stats(S)
         fs.srv_destroy(S)
         out = summarize(trace, lat, served, elapsed)
-        out.update({"precision": "f32_reliable", "peak_active": st["peak_active"],
+        out.update({"peak_active": st["peak_active"],
                     "peak_workspace_gb": round(st["peak_workspace_bytes"] / 2 ** 30, 2)})
-        if group:
-            out["grouping"] = "lockstep multi-RHS groups, width by matrix size (srv_set_grouping -1)"
         return out
 
     def run_single(trace):
@@ -621,30 +891,37 @@ def bench_serving(fs, torch, args):
                 break
             if now < a:
                 time.sleep(a - now)
-            x = np.zeros(pool[m].n_rows)
+            x = np.zeros(sizes[m])
             res = fs.cg_solve(mats[m], rhs[m][k], x, tol=tol)
             if res["status"] == 0:
                 served += 1
                 lat.append(time.perf_counter() - start - a)
         elapsed = time.perf_counter() - start
-        out = summarize(trace, lat, served, elapsed)
-        out["precision"] = "f64"
-        return out
+        return summarize(trace, lat, served, elapsed)
 
-    over = {"server": run_server(trace), "server_grouped": run_server(trace, -1),
-            "one_at_a_time": run_single(trace)}
-    # a second arrival stream at 80 % of the one-at-a-time capacity, where queues stay short
-    rate2 = 0.8 * max(1.0, over["one_at_a_time"]["solves_per_s"])
-    trace2 = make_trace(rate2, 1507)
-    steady = {"rate_per_s": round(rate2, 1), "server": run_server(trace2),
-              "server_grouped": run_server(trace2, -1), "one_at_a_time": run_single(trace2)}
+    def three_arms(rate, seed):
+        tr = make_trace(rate, seed)
+        return {"rate_per_s": round(rate, 1), "offered": len(tr), "server": run_server(tr),
+                "server_grouped": run_server(tr, -1), "one_at_a_time": run_single(tr)}
+
+    # warm: graphs and workspaces of every matrix, one solve each on every path
+    run_server([(0.0, m, 1e-8, 0) for m in range(n_mesh)], -1)
+    for m in range(n_mesh):
+        fs.cg_solve(mats[m], rhs[m][0], np.zeros(sizes[m]), tol=1e-8)
+    over = three_arms(args.serve_rate, 1506)
+    sat = max(1.0, over["server_grouped"]["solves_per_s"])
+    single_cap = max(1.0, over["one_at_a_time"]["solves_per_s"])
+    rates = [f * single_cap for f in (0.5, 1.0, 1.5)] + \
+        [f * sat for f in (float(v) for v in args.serve_sweep.split(",") if v)]
+    sweep = [three_arms(r, 1507 + i) for i, r in enumerate(rates)]
     for A in mats:
         fs.spmv_destroy(A)
-    return {"pool": {"meshes": n_mesh, "rows_min": min(p.n_rows for p in pool),
-                     "rows_max": max(p.n_rows for p in pool),
-                     "rows_total": sum(p.n_rows for p in pool),
-                     "nnz_total": sum(p.nnz for p in pool), "setup_s": round(setup_s, 1)},
-            "seconds": T, "overload": dict(rate_per_s=args.serve_rate, **over), "steady": steady}
+    return {"pool": pool_info, "seconds_per_run": T,
+            "arms": {"server": "continuous batching, FP32 values + FP64 reliable updates",
+                     "server_grouped": "the same with lockstep multi-RHS groups per matrix (srv_set_grouping -1)",
+                     "one_at_a_time": "FP64 cg_solve per request, FIFO"},
+            "saturation_per_s": round(sat, 1), "one_at_a_time_capacity_per_s": round(single_cap, 1),
+            "overload": over, "sweep": sweep}
 
 
 def bench_shell(fs, torch, args):

@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -51,6 +51,10 @@ def _lib():
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
         i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.oracle_set_threads.argtypes = [i32]
+        lib.oracle_set_threads.restype = None
+        lib.oracle_get_threads.argtypes = []
+        lib.oracle_get_threads.restype = i32
         lib.oracle_csr_spmv.argtypes = [i64, P, P, P, P, P]
         lib.oracle_csr_spmv.restype = None
         lib.oracle_pcg.argtypes = [i64, P, P, P, P, P, dbl, i32, i32, i32, P, P, P]
@@ -83,6 +87,17 @@ def _csr(rowptr, colind, values):
     return (np.ascontiguousarray(rowptr, dtype=np.int64),
             np.ascontiguousarray(colind, dtype=np.int32),
             np.ascontiguousarray(values, dtype=np.float64))
+
+
+def set_threads(threads: int) -> None:
+    """Host threads of the product's row loop (default 1).  Every row stays one
+    sequential sum, so results do not depend on it; only the CPU-baseline
+    timing uses more than one."""
+    _lib().oracle_set_threads(int(threads))
+
+
+def get_threads() -> int:
+    return int(_lib().oracle_get_threads())
 
 
 def csr_spmv(rowptr, colind, values, x) -> np.ndarray:

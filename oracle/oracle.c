@@ -43,9 +43,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Host threads for the row loop of oracle_csr_spmv (1 unless the benchmark's
+ * CPU baseline asks for more).  Each row is still one sequential sum in stored
+ * order, so the product -- and every routine built on it -- gives bitwise the
+ * same result for any thread count; the other loops stay sequential. */
+static int g_threads = 1;
+
+void oracle_set_threads(int threads) { g_threads = threads < 1 ? 1 : threads; }
+
+int oracle_get_threads(void) { return g_threads; }
+
 /* y = A x, CSR, FP64, row by row, entries in stored order. */
 void oracle_csr_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind,
                      const double* val, const double* x, double* y) {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = s + val[p] * x[colind[p]];

@@ -179,17 +179,30 @@ def test_edge_cases_empty_ragged_and_nonfinite():
         assert np.array_equal(np.isnan(yn), np.isnan(yo))
 
 
-@pytest.mark.parametrize("fmt,kw", [(fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2)),
+@pytest.mark.parametrize("fmt,kw", [(fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=1, threshold=0, tiles=0)),
+                                    (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2)),
                                     (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2, tiles=-1)),
                                     (fs.FESPMV_FMT_SLICED, dict(sigma=1024, vec=2,
                                                                 precisions=fs.FESPMV_PREC_DF64)),
                                     (fs.FESPMV_FMT_CSR, dict(csr_lanes=4))])
 def test_full_size_elasticity_64(fmt, kw):
-    """The benchmark's matrix (64^3 nodes, 786,432 rows, ~34M nnz), every row checked."""
+    """The benchmark's matrix (64^3 nodes, 786,432 rows, ~34M nnz), every row checked;
+    the first layout is the one the benchmark times (one entry per lane per load, sort
+    windows of 1,024 rows, K1 slices, x staged per tile), also in the permuted
+    numbering the timed product runs in."""
     p = fegen.cube_elasticity(64, 1502)
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, format=fmt, **kw)
     x = fegen.random_vector(p.n_rows, 1504)
     check_parity(p, apply(A, x), x)
+    if fmt == fs.FESPMV_FMT_SLICED and kw.get("vec") == 1:
+        info = fs.spmv_get_info(A)
+        assert info["vec"] == 1 and info["n_tiles"] > 0
+        xd = torch.from_numpy(x).cuda()
+        xp, yp, y = torch.empty_like(xd), torch.empty_like(xd), torch.empty_like(xd)
+        fs.spmv_permute(A, xd, xp, 0)
+        fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)
+        fs.spmv_permute(A, yp, y, 1)
+        check_parity(p, y.cpu().numpy(), x)
 
 
 @pytest.mark.parametrize("tiles", [0, -1])

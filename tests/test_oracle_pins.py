@@ -522,3 +522,21 @@ def test_vector_assembly_of_element_products_is_the_global_product(maker):
     ku[p.dirichlet.astype(bool)] = 0.0
     bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(u))
     assert np.all(np.abs(r - ku) <= 1e-13 * (bound + 1e-300) * 30)
+
+
+def test_threaded_product_is_bitwise_the_sequential_one():
+    # the CPU baseline runs the product's row loop on all host cores; each row is
+    # still one sequential sum, so the result must not change by a single bit
+    p = fegen.cube_elasticity(10, 77)
+    x = fegen.random_vector(p.n_rows, 78)
+    y1 = oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+    try:
+        oracle.set_threads(4)
+        y4 = oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        xo4, info4 = oracle.pcg(p.rowptr, p.colind, p.values, x, tol=1e-8)
+    finally:
+        oracle.set_threads(1)
+    xo1, info1 = oracle.pcg(p.rowptr, p.colind, p.values, x, tol=1e-8)
+    assert np.array_equal(y1.view(np.uint64), y4.view(np.uint64))
+    assert info1["iters"] == info4["iters"]
+    assert np.array_equal(xo1.view(np.uint64), xo4.view(np.uint64))
