@@ -484,6 +484,27 @@ def main():
                 f()
                 tl = back_to_back(f, args.steps)
                 extra[f"{name}_spmv_gbs"] = round((nnz * (vb + 4) + n * 8) / (tl * 1e-3) / 1e9, 1)
+            # the same products on 3x3 node blocks (one int32 column per 9 values)
+            NB = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                                vec=args.extras_vec, node_blocks=3,
+                                precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_BF16)
+            nbi = fs.spmv_get_info(NB)
+            xnb = torch.empty_like(xd)
+            fs.spmv_permute(NB, xd, xnb, 0)
+            xnb32, ynb32 = xnb.float(), torch.empty(n, dtype=torch.float32, device=dev)
+            nbo = {"blocks": nbi["nb_len"], "padding_pct": round(100.0 * (9 * nbi["nb_len"] - nnz) / nnz, 2)}
+            for name, prec, vb in (("fp32", fs.FESPMV_PREC_F32, 4), ("bf16", fs.FESPMV_PREC_BF16, 2)):
+                f = lambda: fs.spmv_apply_scaled(NB, xnb32, ynb32, prec, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+                f()
+                tl = back_to_back(f, args.steps)
+                nbo[f"{name}_gbs"] = round((nnz * (vb + 4) + n * 8) / (tl * 1e-3) / 1e9, 1)
+                nbo[f"{name}_us"] = round(tl * 1e3, 2)
+                nbo[f"{name}_moved_gbs"] = round((nbi["nb_len"] * (9 * vb + 4) + n * 8) / (tl * 1e-3) / 1e9, 1)
+            if hasattr(fs, "cg_solve"):
+                nbo["cg_f32_reliable"] = bench_cg(fs, torch, NB, p, args.cg_solves, fs.FESPMV_CG_F32_REFINE,
+                                                  flags=fs.FESPMV_CG_RELIABLE)
+            fs.spmv_destroy(NB)
+            extra["node_blocks_3x3"] = nbo
             # 32 right-hand sides in one pass over the FP32 matrix (row-major n x 32)
             X32 = torch.rand((n, 32), dtype=torch.float32, device=dev)
             Y32 = torch.empty_like(X32)
@@ -754,6 +775,9 @@ def configs_summary(line):
             "f64_spmv_gbs": line.get("value"), "frac_of_measured": _pick(line, "roofline", "frac"),
             "e2e_gbs": _pick(line, "e2e", "value"), "fp32_spmv_gbs": line.get("fp32_spmv_gbs"),
             "bf16_spmv_gbs": line.get("bf16_spmv_gbs"), "csr_vector4_gbs": line.get("csr_vector4_gbs"),
+            "node_block_fp32_bf16_gbs": [_pick(line, "node_blocks_3x3", "fp32_gbs"),
+                                         _pick(line, "node_blocks_3x3", "bf16_gbs")],
+            "cg_f32_reliable_node_blocks": cg(_pick(line, "node_blocks_3x3", "cg_f32_reliable")),
             "cg_f64_1e-10": cg(line.get("cg")), "cg_f32_reliable_1e-10": cg(line.get("cg_f32_reliable")),
             "output_check": _pick(cpu, "headline_output_check", "worst_err_over_abs_bound"),
             "cpu_spmv_gbs": {"1_core": cpu.get("spmv_1core_gbs"), f"{cpu.get('cores')}_cores": cpu.get("value")},
@@ -1224,7 +1248,7 @@ def bench_assembly(fs, torch, args, back_to_back):
            "assembly_gbs": round((nc * 12 + sl * 16) / ta / 1e9, 1),
            "update_values_us": round(tu * 1e6, 1),
            "bitwise_equal_to_csr_handle": bool(ok),
-           "newton_like_steps": newton,
+           "newton_steps_fe_newton_step": newton,
            "bytes_note": "assembly_gbs counts element-matrix reads and 4-byte indices per contribution, "
                          "offsets and the value write per position"}
     del Ke, vals
@@ -1234,12 +1258,12 @@ def bench_assembly(fs, torch, args, back_to_back):
 
 
 def newton_steps(fs, torch, p, A, P, Ke, steps=4):
-    """A Newton-like sequence on a fixed pattern (the loop of Sec. 2.1): every step
-    assembles new values and a new right-hand side on the GPU from element
-    quantities (here the element matrices scaled by 1 + 0.05 k and the element
-    vectors K_e u_k of a slowly varying field u_k), then solves K dx = R to 1e-10
-    (FP32 values with FP64 reliable updates) warm-started from the previous step's
-    solution, against the same solve started from zero."""
+    """A Newton-like sequence on a fixed pattern (the loop of Sec. 2) through the
+    library's fe_newton_step: every step assembles new values and a new right-hand
+    side on the GPU from element quantities (here the element matrices scaled by
+    1 + 0.05 k and the element vectors K_e u_k of a slowly varying field u_k), then
+    solves K dx = R to 1e-10 (FP32 values with FP64 reliable updates) warm-started
+    from the previous step's dx, against the same solve started from zero."""
     import fegen
     dpn = p.dofs_per_node
     idx = torch.from_numpy((dpn * p.elem_nodes[:, :, None] + np.arange(dpn)[None, None, :])
@@ -1247,8 +1271,8 @@ def newton_steps(fs, torch, p, A, P, Ke, steps=4):
     u0 = torch.from_numpy(fegen.manufactured_solution(p)).cuda()
     du = torch.from_numpy(fegen.random_vector(p.n_rows, 1790)).cuda() * 1e-3
     mask = torch.from_numpy(p.dirichlet.astype(bool)).cuda()
-    b = torch.empty_like(u0)
-    x = torch.zeros_like(u0)
+    R = torch.empty_like(u0)
+    dx = torch.zeros_like(u0)
     rows = []
     for k in range(steps):
         Kk = Ke * (1.0 + 0.05 * k)
@@ -1256,20 +1280,16 @@ def newton_steps(fs, torch, p, A, P, Ke, steps=4):
         Rk = torch.einsum("eij,ej->ei", Kk, uk[idx]).contiguous()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fs.assembly_matrix(P, Kk)
-        fs.assembly_vector(P, Rk, b)
+        rw = fs.fe_newton_step(P, Kk, Rk, R, dx, None, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE,
+                               flags=fs.FESPMV_CG_RELIABLE | (fs.FESPMV_CG_X0 if k > 0 else 0))
         torch.cuda.synchronize()
-        t_asm = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        rw = fs.cg_solve(A, b, x, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE,
-                         flags=fs.FESPMV_CG_RELIABLE | (fs.FESPMV_CG_X0 if k > 0 else 0))
-        torch.cuda.synchronize()
-        t_warm = time.perf_counter() - t0
-        xc = torch.zeros_like(u0)
-        rc = fs.cg_solve(A, b, xc, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
-        rows.append({"step": k, "assemble_ms": round(t_asm * 1e3, 2), "solve_ms": round(t_warm * 1e3, 1),
-                     "iters_warm": rw["iters"], "iters_cold": rc["iters"],
-                     "true_relres": rw["true_relres"], "status": rw["status"]})
+        t_step = time.perf_counter() - t0
+        dc = torch.zeros_like(u0)
+        rc = fs.fe_newton_step(P, Kk, Rk, R, dc, None, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE,
+                               flags=fs.FESPMV_CG_RELIABLE)
+        rows.append({"step": k, "step_ms": round(t_step * 1e3, 2),
+                     "iters_warm": rw["last_cg"]["iters"], "iters_cold": rc["last_cg"]["iters"],
+                     "true_relres": rw["last_cg"]["true_relres"], "status": rw["status"]})
         del Kk, Rk
     return rows
 

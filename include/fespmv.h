@@ -96,6 +96,17 @@ typedef struct {
                             entry keeps a 16-bit index into its tile's columns next to the
                             32-bit column; the FP64 and FP32/BF16 products use them.  Left off
                             when one slice alone has more distinct columns.  -1 = off. */
+    int32_t node_blocks; /* SLICED with dofs_per_node = 3 and FESPMV_PREC_F32 or _BF16: 3 = also
+                            keep those copies of S A S as 3x3 node blocks (rows of node I are
+                            3I..3I+2 in the handle's numbering: the length sort moves whole
+                            nodes; each block one int32 column node and 9 values, zero where
+                            the matrix has no entry).  spmv_apply_scaled and the refined CG's
+                            inner products then read the blocks: runs of up to 8 slices of 32
+                            node rows stage the x values of their column nodes (at most 2048)
+                            in shared memory, and each block keeps a 16-bit index into that
+                            list: 2/9 of a byte of index per value, one lookup per 9 values
+                            (tiles = -1: x gathered from L1/L2 with the int32 block columns).  NaN or Inf in x at a column
+                            a block stores as zero reaches its rows.  0 = off. */
 } fespmv_options;
 
 typedef struct {
@@ -115,7 +126,11 @@ typedef struct {
     int64_t n_tiles;         /* SLICED with tiles: tiles (0 when the products gather x from L1/L2) */
     int64_t tile_dict_len;   /* concatenated tile column lists */
     int32_t tile_max_cols;   /* largest tile column list */
-    int32_t pad;
+    int32_t node_blocks;     /* 3 with node blocks, else 0 */
+    int64_t nb_slices;       /* node-block slices (32 node rows each) */
+    int64_t nb_len;          /* node-block slots including padding */
+    int64_t nb_tiles;        /* tiles of node-block slices (0: x gathered from L1/L2) */
+    int64_t nb_tile_dict_len;/* concatenated column-node lists of those tiles */
 } fespmv_info;
 
 /*
@@ -249,6 +264,14 @@ int spmv_apply_scaled(fespmv_mat_t A, const float* x, float* y, int32_t precisio
 #define FESPMV_EXPORT_TILES    9  /* int32[n_tiles*4]: (first slice, slices, column-list offset, D) */
 #define FESPMV_EXPORT_TILE_COLS 10 /* int32[tile_dict_len]: each tile's distinct columns, first-use order */
 #define FESPMV_EXPORT_TILE_INDEX 11 /* uint16[packed_len]: index into the tile's columns; padding = D */
+#define FESPMV_EXPORT_NB_META  12 /* uint32[nb_slices*4]: (offset/32, width, first node row, 0) */
+#define FESPMV_EXPORT_NB_COLS  13 /* int32[nb_len]: block column (node) per slot, -1 = padding */
+#define FESPMV_EXPORT_NB_VALUES_F32 14 /* float[9*nb_len]: block values, plane by plane per slice */
+#define FESPMV_EXPORT_NB_VALUES_BF16 15 /* uint16[9*nb_len]: the same in bfloat16 bits */
+#define FESPMV_EXPORT_NB_MAP   16 /* int64[9*nb_len]: packed position of each block value, -1 = zero */
+#define FESPMV_EXPORT_NB_TILES 17 /* int32[nb_tiles*4]: (first slice, slices, node-list offset, D) */
+#define FESPMV_EXPORT_NB_TILE_NODES 18 /* int32[nb_tile_dict_len]: each tile's column nodes, first-use order */
+#define FESPMV_EXPORT_NB_TILE_INDEX 19 /* uint16[nb_len]: index of a slot's node in its tile's list; padding = D */
 /* Copy internal array `what` into host buffer `out` of `bytes` bytes (must be at
  * least the array's size).  Synchronises the stream.  Errors: INVALID_ARG,
  * UNSUPPORTED (array not held by this handle), CUDA. */
@@ -513,6 +536,61 @@ int assembly_vector(fespmv_assembly_t P, const double* Re, double* r, int32_t fl
 /* Contributions held and device bytes of the map. */
 int assembly_get_info(fespmv_assembly_t P, int64_t* n_contributions, int64_t* device_bytes);
 void assembly_destroy(fespmv_assembly_t P);
+
+/* ---- Newton updates on a fixed pattern (Sec. 2) ----------------------------------- */
+
+typedef struct {
+    int32_t status;      /* FESPMV_OK, NOT_CONVERGED (update limit), or the failing call's code */
+    int32_t steps;       /* Newton updates applied */
+    int64_t cg_iters;    /* CG iterations over all updates */
+    double res_norm0;    /* ||R||_2 of the first residual assembled */
+    double res_norm;     /* ||R||_2 of the last residual assembled */
+    double dx_norm;      /* ||dx||_2 of the last update */
+    cg_result last_cg;   /* the last update's solve */
+} fe_newton_result;
+
+/*
+ * fe_newton_step -- one global Newton update of Sec. 2 (the algorithm table:
+ * assemble the global residual R and iteration matrix K from the element
+ * quantities, then phi <- phi - K^-1 R) on the pattern of P's matrix:
+ *   R  := the sums of the element residuals (assembly_vector, input numbering)
+ *   K  := the sums of the element tangents into P's handle (assembly_matrix)
+ *   dx := the solution of K dx = R by cg_solve with opts (FESPMV_CG_X0: dx holds
+ *         the initial guess; IO flags are rejected: every vector is device memory
+ *         in the input numbering)
+ *   phi := phi - dx (skipped when phi is NULL)
+ *   Ke, Re   device element tangents / residuals, layouts of assembly_matrix /
+ *            assembly_vector (the caller's physics computes them from phi)
+ *   R, dx    device double[n_rows], written
+ *   out      steps = 1, res_norm = ||R||, dx_norm = ||dx||, last_cg = the solve's result
+ * Blocks until the update is applied.  Errors: INVALID_ARG, OOM, CUDA, and the
+ * solve's BREAKDOWN / NOT_CONVERGED (phi is then left unchanged).
+ */
+int fe_newton_step(fespmv_assembly_t P, const double* Ke, const double* Re, double* R, double* dx,
+                   double* phi, const cg_options* opts, fe_newton_result* out, fespmv_stream_t stream);
+
+/* The caller's element routine: fill Ke and Re (device) for the current phi
+ * (device, input numbering), work ordered on `stream`; return 0, or a non-zero
+ * code that stops the iteration. */
+typedef int (*fe_element_fn)(const double* phi, double* Ke, double* Re, void* user, fespmv_stream_t stream);
+
+/*
+ * fe_newton_solve -- the global Newton loop of Sec. 2 for one time step: call
+ * element_fn on phi, assemble R; stop when ||R|| <= newton_tol * ||R_0|| (R_0 the
+ * first residual; also when R = 0); otherwise apply fe_newton_step's update and
+ * repeat, at most max_steps updates (the residual of the last phi is assembled
+ * and tested too).  With FESPMV_CG_X0 in opts every solve starts from the previous
+ * update's dx (dx's content on entry for the first).
+ *   phi            device double[n_rows], the initial iterate; updated in place
+ *   Ke, Re, R, dx  device buffers of assembly_matrix / assembly_vector sizes and n_rows
+ *   newton_tol     >= 0; max_steps >= 1
+ * Returns FESPMV_OK when the test held, NOT_CONVERGED after max_steps updates, or
+ * the failing call's code (the callback's non-zero code becomes INVALID_ARG's
+ * message).  out (nullable) gets the counts and norms.
+ */
+int fe_newton_solve(fespmv_assembly_t P, double* phi, fe_element_fn element_fn, void* user, double* Ke,
+                    double* Re, double* R, double* dx, double newton_tol, int32_t max_steps,
+                    const cg_options* opts, fe_newton_result* out, fespmv_stream_t stream);
 
 /* ---- batches of independent FE problems ------------------------------------------- */
 typedef struct fespmv_batch* fespmv_batch_t;

@@ -234,3 +234,70 @@ def tiles(meta: np.ndarray, col: np.ndarray, max_slices: int = 8, max_cols: int 
     if count > 0:
         close()
     return (np.array(out_tiles, dtype=np.int32).reshape(-1, 4), np.array(out_dict, dtype=np.int32), index)
+
+
+# ---------------------------------------------------------------------------
+# 3x3 node blocks (this library's layout for three dofs per node; not in the
+# paper, which stores one column per value).  The node locality order is sorted
+# stably, longest first, inside windows of ceil(sigma / 3) nodes, a node's
+# length being the longest of its three rows; its dofs stay at rows 3k + c.
+# Block row I holds rows 3I..3I+2; its blocks are the column nodes J that any
+# of those rows touches, ascending.  Slices: 32 node rows each (K1, one block
+# row per lane), width = the longest block row of the slice, block (lane l, step
+# s) at slot off + 32 s + l; each block's value k = 3a + b (row 3I+a, column
+# 3J+b) at index 9 off + k (32 w) + 32 s + l, zero where the matrix stores no
+# entry.  Metadata per slice: (off // 32, w, first node row, 0).
+
+def node_row_permutation(rowptr: np.ndarray, node_xyz=None, reorder: str = "morton",
+                         sigma: int = 0) -> np.ndarray:
+    """P (P[new_row] = old_row) for 3 dofs per node with whole nodes sorted."""
+    n = len(rowptr) - 1
+    assert n % 3 == 0
+    nn = n // 3
+    nodes = node_order(node_xyz, nn, reorder)
+    if sigma > 0:
+        lens = np.diff(rowptr).reshape(nn, 3).max(axis=1)[nodes]
+        wn = -(-sigma // 3)
+        out = np.empty_like(nodes)
+        for s in range(0, nn, wn):
+            seg = slice(s, min(nn, s + wn))
+            out[seg] = nodes[seg][np.argsort(-lens[seg], kind="stable")]
+        nodes = out
+    return (nodes[:, None] * 3 + np.arange(3)[None, :]).ravel().astype(np.int64)
+
+
+def node_blocks(rowptr2, colind2):
+    """Node-block arrays of a node-ordered permuted CSR: (meta uint32 [S,4],
+    col int32 [L], vidx int64 [9L]) with vidx[value index] = permuted CSR
+    position of that block value, -1 where the block stores a zero."""
+    n = len(rowptr2) - 1
+    assert n % 3 == 0
+    nn = n // 3
+    blocks = []
+    for I in range(nn):
+        a, b = int(rowptr2[3 * I]), int(rowptr2[3 * I + 3])
+        blocks.append(sorted(set(int(c) // 3 for c in colind2[a:b])))
+    S = -(-nn // 32)
+    meta = np.zeros((S, 4), dtype=np.uint32)
+    widths = []
+    off = 0
+    for s in range(S):
+        rows = range(32 * s, min(nn, 32 * s + 32))
+        w = max((len(blocks[I]) for I in rows), default=0)
+        meta[s] = (off // 32, w, 32 * s, 0)
+        widths.append(w)
+        off += 32 * w
+    col = np.full(off, -1, dtype=np.int32)
+    vidx = np.full(9 * off, -1, dtype=np.int64)
+    for s in range(S):
+        o, w = int(meta[s, 0]) * 32, widths[s]
+        for I in range(32 * s, min(nn, 32 * s + 32)):
+            lane = I - 32 * s
+            where = {J: st for st, J in enumerate(blocks[I])}
+            for J, st in where.items():
+                col[o + 32 * st + lane] = J
+            for a in range(3):
+                for p in range(int(rowptr2[3 * I + a]), int(rowptr2[3 * I + a + 1])):
+                    J, b = divmod(int(colind2[p]), 3)
+                    vidx[9 * o + (3 * a + b) * 32 * w + 32 * where[J] + lane] = p
+    return meta, col, vidx

@@ -50,6 +50,14 @@ FESPMV_EXPORT_SCALE = 8
 FESPMV_EXPORT_TILES = 9
 FESPMV_EXPORT_TILE_COLS = 10
 FESPMV_EXPORT_TILE_INDEX = 11
+FESPMV_EXPORT_NB_META = 12
+FESPMV_EXPORT_NB_COLS = 13
+FESPMV_EXPORT_NB_VALUES_F32 = 14
+FESPMV_EXPORT_NB_VALUES_BF16 = 15
+FESPMV_EXPORT_NB_MAP = 16
+FESPMV_EXPORT_NB_TILES = 17
+FESPMV_EXPORT_NB_TILE_NODES = 18
+FESPMV_EXPORT_NB_TILE_INDEX = 19
 FESPMV_CG_F64 = 0
 FESPMV_CG_F32_REFINE = 1
 FESPMV_CG_BF16_REFINE = 2
@@ -68,7 +76,7 @@ class FespmvError(RuntimeError):
 class fespmv_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("format", "reorder", "sigma", "threshold", "vec", "csr_lanes", "precisions",
-                 "block", "tiles")]
+                 "block", "tiles", "node_blocks")]
 
 
 class fespmv_mesh_info(ctypes.Structure):
@@ -80,7 +88,8 @@ class fespmv_info(ctypes.Structure):
                 ("packed_len", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("format", ctypes.c_int32), ("vec", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
                 ("tile_dict_len", ctypes.c_int64), ("tile_max_cols", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("node_blocks", ctypes.c_int32), ("nb_slices", ctypes.c_int64), ("nb_len", ctypes.c_int64),
+                ("nb_tiles", ctypes.c_int64), ("nb_tile_dict_len", ctypes.c_int64)]
 
 
 class cg_options(ctypes.Structure):
@@ -94,6 +103,17 @@ class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("outer", ctypes.c_int32), ("relres", ctypes.c_double),
                 ("true_relres", ctypes.c_double)]
+
+
+class fe_newton_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("cg_iters", ctypes.c_int64),
+                ("res_norm0", ctypes.c_double), ("res_norm", ctypes.c_double), ("dx_norm", ctypes.c_double),
+                ("last_cg", cg_result)]
+
+
+# int (*)(const double* phi, double* Ke, double* Re, void* user, stream)
+FE_ELEMENT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p)
 
 
 class srv_timing(ctypes.Structure):
@@ -157,6 +177,12 @@ _lib.assembly_get_info.argtypes = [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64
 _lib.assembly_get_info.restype = ctypes.c_int
 _lib.assembly_destroy.argtypes = [_P]
 _lib.assembly_destroy.restype = None
+_lib.fe_newton_step.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.POINTER(cg_options),
+                                ctypes.POINTER(fe_newton_result), _P]
+_lib.fe_newton_step.restype = ctypes.c_int
+_lib.fe_newton_solve.argtypes = [_P, _P, FE_ELEMENT_FN, _P, _P, _P, _P, _P, ctypes.c_double, _i32,
+                                 ctypes.POINTER(cg_options), ctypes.POINTER(fe_newton_result), _P]
+_lib.fe_newton_solve.restype = ctypes.c_int
 _lib.srv_create.argtypes = [ctypes.POINTER(_P), _i64, _i32]
 _lib.srv_create.restype = ctypes.c_int
 _lib.srv_set_grouping.argtypes = [_P, _i32]
@@ -248,14 +274,15 @@ class Matrix:
 
 def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=FESPMV_FMT_SLICED,
                 reorder=None, sigma=0, threshold=0, vec=0, csr_lanes=0, precisions=0, block=0,
-                tiles=0, stream=None) -> Matrix:
+                tiles=0, node_blocks=0, stream=None) -> Matrix:
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     values = np.ascontiguousarray(values, dtype=np.float64)
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block, tiles)
+    opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block, tiles,
+                          node_blocks)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     h = _P()
     n = len(rowptr) - 1
@@ -306,14 +333,14 @@ def spmv_update_values(A: Matrix, values, flags=0, stream=None):
 
 
 def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
-              threshold=0, vec=0) -> dict:
+              threshold=0, vec=0, node_blocks=0) -> dict:
     """Host-only planning: returns perm, meta (S x 4), cols and srcmap as numpy arrays."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0, 0)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0, 0, node_blocks)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     info = fespmv_info()
     n = len(rowptr) - 1
@@ -381,6 +408,14 @@ _EXPORT_DTYPES = {FESPMV_EXPORT_PERM: (np.int32, "n_rows"), FESPMV_EXPORT_META: 
                   FESPMV_EXPORT_VALUES_BF16: (np.uint16, "packed_len"),
                   FESPMV_EXPORT_SCALE: (np.float64, "n_rows"),
                   FESPMV_EXPORT_TILES: (np.int32, "tiles"),
+                  FESPMV_EXPORT_NB_META: (np.uint32, "nb_meta"),
+                  FESPMV_EXPORT_NB_COLS: (np.int32, "nb_len"),
+                  FESPMV_EXPORT_NB_VALUES_F32: (np.float32, "nb_values"),
+                  FESPMV_EXPORT_NB_VALUES_BF16: (np.uint16, "nb_values"),
+                  FESPMV_EXPORT_NB_MAP: (np.int64, "nb_values"),
+                  FESPMV_EXPORT_NB_TILES: (np.int32, "nb_tiles4"),
+                  FESPMV_EXPORT_NB_TILE_NODES: (np.int32, "nb_tile_dict_len"),
+                  FESPMV_EXPORT_NB_TILE_INDEX: (np.uint16, "nb_len"),
                   FESPMV_EXPORT_TILE_COLS: (np.int32, "tile_dict_len"),
                   FESPMV_EXPORT_TILE_INDEX: (np.uint16, "packed_len")}
 
@@ -388,11 +423,12 @@ _EXPORT_DTYPES = {FESPMV_EXPORT_PERM: (np.int32, "n_rows"), FESPMV_EXPORT_META: 
 def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
     info = spmv_get_info(A)
     dt, key = _EXPORT_DTYPES[what]
-    count = {"meta": info["n_slices"] * 4, "tiles": info["n_tiles"] * 4}.get(key) or info.get(key, 0)
+    count = {"meta": info["n_slices"] * 4, "tiles": info["n_tiles"] * 4, "nb_meta": info["nb_slices"] * 4,
+             "nb_values": info["nb_len"] * 9, "nb_tiles4": info["nb_tiles"] * 4}.get(key) or info.get(key, 0)
     out = np.zeros(max(count, 1), dtype=dt)
     _check(_lib.spmv_export(A.handle, what, _ptr(out), out.nbytes, _stream(stream)))
     out = out[:count]
-    return out.reshape(-1, 4) if key in ("meta", "tiles") else out
+    return out.reshape(-1, 4) if key in ("meta", "tiles", "nb_meta", "nb_tiles4") else out
 
 
 def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
@@ -472,6 +508,52 @@ def assembly_matrix(P: Assembly, elem_mats, flags=0, stream=None):
 def assembly_vector(P: Assembly, elem_vecs, r, flags=0, stream=None):
     _check(_lib.assembly_vector(P.handle, _ptr(elem_vecs), _ptr(r), flags, _stream(stream)))
     return r
+
+
+def _newton_dict(r):
+    out = {f: getattr(r, f) for f, _ in fe_newton_result._fields_ if f != "last_cg"}
+    out["last_cg"] = {f: getattr(r.last_cg, f) for f, _ in cg_result._fields_}
+    return out
+
+
+def fe_newton_step(P: Assembly, elem_mats, elem_vecs, R, dx, phi=None, tol=1e-10, max_iter=0,
+                   precision=FESPMV_CG_F64, flags=0, max_restarts=0, check_every=0, max_outer=0,
+                   inner_tol=0.0, stream=None) -> dict:
+    """One Newton update (Sec. 2): R and K assembled from the element quantities,
+    K dx = R solved by CG, phi -= dx.  All arrays are torch CUDA tensors (input
+    numbering).  Solve outcomes are in result["status"]; other errors raise."""
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
+    r = fe_newton_result()
+    rc = _lib.fe_newton_step(P.handle, _ptr(elem_mats), _ptr(elem_vecs), _ptr(R), _ptr(dx), _ptr(phi),
+                             ctypes.byref(o), ctypes.byref(r), _stream(stream))
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return _newton_dict(r)
+
+
+def fe_newton_solve(P: Assembly, phi, element_fn, Ke, Re, R, dx, newton_tol=1e-8, max_steps=20,
+                    tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0, max_restarts=0,
+                    check_every=0, max_outer=0, inner_tol=0.0, stream=None) -> dict:
+    """Newton's loop of Sec. 2 for one time step.  element_fn(phi, Ke, Re) fills the
+    element tangents Ke and residuals Re (torch CUDA tensors, written in place) for
+    the current phi; it is called from the library, on the calling thread."""
+    def cb(phi_p, ke_p, re_p, user, stream_p):
+        try:
+            element_fn(phi, Ke, Re)
+            return 0
+        except Exception:   # a failing callback stops the loop with an error
+            import traceback
+            traceback.print_exc()
+            return 1
+    fn = FE_ELEMENT_FN(cb)
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
+    r = fe_newton_result()
+    rc = _lib.fe_newton_solve(P.handle, _ptr(phi), fn, None, _ptr(Ke), _ptr(Re), _ptr(R), _ptr(dx),
+                              float(newton_tol), int(max_steps), ctypes.byref(o), ctypes.byref(r),
+                              _stream(stream))
+    if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):
+        _check(rc)
+    return _newton_dict(r)
 
 
 def assembly_get_info(P: Assembly) -> dict:

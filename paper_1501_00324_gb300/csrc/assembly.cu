@@ -332,6 +332,9 @@ int matrix_impl(fespmv_assembly* P, const double* Ke, int32_t flags, cudaStream_
 }
 
 }  // namespace
+
+fespmv_mat* assembly_handle(fespmv_assembly* P) { return P ? P->A : nullptr; }
+
 }  // namespace fespmv
 
 using namespace fespmv;

@@ -48,7 +48,8 @@ void free_handle(fespmv_mat* A) {
                     A->d_src, A->d_diagpos, A->d_diag, A->d_xp, A->d_yp, A->d_xh, A->d_yh,
                     A->d_vals_in, A->d_val32, A->d_val16, A->d_scale, A->d_flag, A->d_xs,
                     A->d_ys, A->d_xk, A->d_yk, A->d_vdf, A->d_xdf, A->d_tiles, A->d_tdict,
-                    A->d_tlidx, A->d_xkdf};
+                    A->d_tlidx, A->d_xkdf, A->d_nbmeta, A->d_nbcol, A->d_nbmap, A->d_nb32, A->d_nb16,
+                    A->d_nbtiles, A->d_nbtdict, A->d_nbtlidx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;
@@ -130,6 +131,40 @@ int upload_tiles(fespmv_mat* A, const Plan& plan, Tiles& t, cudaStream_t s) {
     return FESPMV_OK;
 }
 
+// Node-block arrays of a SLICED handle (values filled by launch_nb3_refresh).
+static int upload_node_blocks(fespmv_mat* A, const NodeBlocks& nb, bool tiles, cudaStream_t s) {
+    A->nb_slices = nb.n_slices;
+    A->nb_len = nb.len;
+    const size_t len = (size_t)std::max<int64_t>(1, nb.len);
+    int rc;
+    if ((rc = device_alloc(A, (void**)&A->d_nbmeta, sizeof(uint4) * (size_t)std::max<int64_t>(1, nb.n_slices), "node-block slices")) ||
+        (rc = device_alloc(A, (void**)&A->d_nbcol, sizeof(int32_t) * len, "node-block columns")) ||
+        (rc = device_alloc(A, (void**)&A->d_nbmap, sizeof(int64_t) * 9 * len, "node-block map")) ||
+        ((A->precisions & FESPMV_PREC_F32) &&
+         (rc = device_alloc(A, (void**)&A->d_nb32, sizeof(float) * 9 * len, "node-block FP32 values"))) ||
+        ((A->precisions & FESPMV_PREC_BF16) &&
+         (rc = device_alloc(A, (void**)&A->d_nb16, sizeof(uint16_t) * 9 * len, "node-block BF16 values"))) ||
+        (rc = ck(cudaMemcpyAsync(A->d_nbmeta, nb.meta.data(), sizeof(uint32_t) * nb.meta.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_nbcol, nb.col.data(), sizeof(int32_t) * nb.col.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+        (rc = ck(cudaMemcpyAsync(A->d_nbmap, nb.map.data(), sizeof(int64_t) * nb.map.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")))
+        return rc;
+    const Tiles& t = nb.tiles;
+    if (tiles && !t.tiles.empty()) {
+        A->nb_tiles = (int64_t)t.tiles.size() / 4;
+        A->nb_tile_dmax = t.dmax;
+        A->nb_tile_dict_len = (int64_t)t.dict.size();
+        if ((rc = device_alloc(A, (void**)&A->d_nbtiles, sizeof(int4) * (size_t)A->nb_tiles, "node-block tiles")) ||
+            (rc = device_alloc(A, (void**)&A->d_nbtdict, sizeof(int32_t) * std::max<size_t>(1, t.dict.size()), "node-block tile nodes")) ||
+            (rc = device_alloc(A, (void**)&A->d_nbtlidx, sizeof(uint16_t) * len, "node-block tile indices")) ||
+            (rc = ck(cudaMemcpyAsync(A->d_nbtiles, t.tiles.data(), sizeof(int32_t) * t.tiles.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+            (rc = ck(cudaMemcpyAsync(A->d_nbtdict, t.dict.data(), sizeof(int32_t) * t.dict.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+            (rc = ck(cudaMemcpyAsync(A->d_nbtlidx, t.lidx.data(), sizeof(uint16_t) * t.lidx.size(), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")))
+            return rc;
+    }
+    A->nb = 3;
+    return FESPMV_OK;
+}
+
 static bool pow2_upto32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
 
 static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, const int32_t* colind,
@@ -184,6 +219,13 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32 | FESPMV_PREC_BF16 | FESPMV_PREC_DF64)) {
         set_error("unknown precision bits 0x%x", o.precisions); return FESPMV_ERR_INVALID_ARG;
     }
+    if (o.node_blocks != 0 &&
+        (o.node_blocks != 3 || o.format != FESPMV_FMT_SLICED || !mesh || mesh->dofs_per_node != 3 ||
+         !(o.precisions & (FESPMV_PREC_F32 | FESPMV_PREC_BF16)))) {
+        set_error("node_blocks = 3 needs a SLICED handle, dofs_per_node = 3 and FP32 or BF16 values (got %d)",
+                  o.node_blocks);
+        return FESPMV_ERR_INVALID_ARG;
+    }
     int rc = validate_csr(n, rowptr, colind);
     if (rc) return rc;
     const int64_t nnz = rowptr[n];
@@ -231,9 +273,11 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
         TRY(ck(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
     } else {
         Plan plan;
+        NodeBlocks nb;   // host arrays stay alive until the stream synchronisation below
         TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
-                       o.threshold, o.vec, plan));
+                       o.threshold, o.vec, plan, o.node_blocks ? &nb : nullptr));
         TRY(upload_sliced(A, plan, s));
+        if (o.node_blocks) TRY(upload_node_blocks(A, nb, o.tiles >= 0, s));
         Tiles tiles;  // host arrays stay alive until the stream synchronisation below
         if (o.tiles >= 0) TRY(upload_tiles(A, plan, tiles, s));
         if (A->precisions & FESPMV_PREC_DF64) {
@@ -458,9 +502,14 @@ int spmv_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, const fes
     if (n > 0 && rowptr[n] > 0 && !colind) { set_error("colind is NULL"); return FESPMV_ERR_INVALID_ARG; }
     int rc = validate_csr(n, rowptr, colind);
     if (rc) return rc;
+    const int dpn = (mesh && mesh->dofs_per_node > 0) ? mesh->dofs_per_node : 1;
+    if (o.node_blocks != 0 && (o.node_blocks != 3 || dpn != 3)) {
+        set_error("node_blocks = 3 needs dofs_per_node = 3"); return FESPMV_ERR_INVALID_ARG;
+    }
     Plan plan;
-    rc = build_plan(n, rowptr, colind, (mesh && mesh->dofs_per_node > 0) ? mesh->dofs_per_node : 1,
-                    mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma, o.threshold, o.vec, plan);
+    NodeBlocks nb;
+    rc = build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma, o.threshold,
+                    o.vec, plan, o.node_blocks ? &nb : nullptr);
     if (rc) return rc;
     info->n_rows = n;
     info->nnz = rowptr[n];
@@ -618,7 +667,11 @@ int spmv_get_info(fespmv_mat_t A, fespmv_info* info) {
     info->n_tiles = A->tiled ? A->n_tiles : 0;
     info->tile_dict_len = A->tiled ? A->tile_dict_len : 0;
     info->tile_max_cols = A->tiled ? A->tile_dmax : 0;
-    info->pad = 0;
+    info->node_blocks = A->nb;
+    info->nb_slices = A->nb_slices;
+    info->nb_len = A->nb_len;
+    info->nb_tiles = A->nb_tiles;
+    info->nb_tile_dict_len = A->nb_tile_dict_len;
     return FESPMV_OK;
 }
 
@@ -644,6 +697,14 @@ int spmv_export(fespmv_mat_t A, int32_t what, void* out, size_t bytes, fespmv_st
         case FESPMV_EXPORT_TILES: src = A->d_tiles; need = 16 * (size_t)A->n_tiles; break;
         case FESPMV_EXPORT_TILE_COLS: src = A->d_tdict; need = 4 * (size_t)A->tile_dict_len; break;
         case FESPMV_EXPORT_TILE_INDEX: src = A->d_tlidx; need = 2 * (size_t)A->packed_len; break;
+        case FESPMV_EXPORT_NB_META: src = A->d_nbmeta; need = 16 * (size_t)A->nb_slices; break;
+        case FESPMV_EXPORT_NB_COLS: src = A->d_nbcol; need = 4 * (size_t)A->nb_len; break;
+        case FESPMV_EXPORT_NB_VALUES_F32: src = A->d_nb32; need = 36 * (size_t)A->nb_len; break;
+        case FESPMV_EXPORT_NB_VALUES_BF16: src = A->d_nb16; need = 18 * (size_t)A->nb_len; break;
+        case FESPMV_EXPORT_NB_MAP: src = A->d_nbmap; need = 72 * (size_t)A->nb_len; break;
+        case FESPMV_EXPORT_NB_TILES: src = A->d_nbtiles; need = 16 * (size_t)A->nb_tiles; break;
+        case FESPMV_EXPORT_NB_TILE_NODES: src = A->d_nbtdict; need = 4 * (size_t)A->nb_tile_dict_len; break;
+        case FESPMV_EXPORT_NB_TILE_INDEX: src = A->d_nbtlidx; need = 2 * (size_t)A->nb_len; break;
         default: set_error("unknown export %d", what); return FESPMV_ERR_INVALID_ARG;
     }
     if (!src) { set_error("array %d is not held by this handle", what); return FESPMV_ERR_UNSUPPORTED; }

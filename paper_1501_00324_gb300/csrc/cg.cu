@@ -19,10 +19,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "spmv_device.cuh"
 #include "tiled_device.cuh"
+#include "nodeblock_device.cuh"
 #include "cg_run.h"
 
 namespace fespmv {
@@ -562,6 +564,70 @@ __global__ void __launch_bounds__(kTiledBlock) cg32_spmv_dot_tiled(const uint4* 
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
+// The inner product on 3x3 node blocks (handles with node_blocks): persistent
+// warps over the node-block slices, three rows per lane.
+template <typename VT, int U>
+__global__ void __launch_bounds__(256) cg32_spmv_dot_nb(const uint4* __restrict__ meta,
+                                                        const int32_t* __restrict__ col,
+                                                        const VT* __restrict__ val, const float* __restrict__ p,
+                                                        float* __restrict__ q, int64_t n_slices, int64_t n_nodes,
+                                                        double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = warp; sl < n_slices; sl += nw) {
+        const uint4 m = meta[sl];
+        float s[3];
+        nb3_row_sums<VT, U>(m, col, val, p, lane, s);
+        const int64_t node = (int64_t)m.z + lane;
+        if (node < n_nodes) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                q[3 * node + a] = s[a];
+                v[0] = fma((double)p[3 * node + a], (double)s[a], v[0]);
+            }
+        }
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+}
+
+// The same with x staged per tile: persistent blocks over the node-block tiles.
+template <typename VT, int U>
+__global__ void __launch_bounds__(256, 8) cg32_spmv_dot_nb_tiled(const uint4* __restrict__ meta,
+                                                              const uint16_t* __restrict__ lidx,
+                                                              const VT* __restrict__ val,
+                                                              const int4* __restrict__ tiles,
+                                                              const int32_t* __restrict__ dict,
+                                                              const float* __restrict__ p, float* __restrict__ q,
+                                                              int64_t n_tiles, int64_t n_nodes, double* partials,
+                                                              CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    float* xs = reinterpret_cast<float*>(tile_smem);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[1] = {0.0};
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int4 tl = nb3_stage(tiles + t, dict, p, xs);
+        if (wid < tl.y) {
+            const uint4 m = meta[tl.x + wid];
+            float s[3];
+            nb3_row_sums_tiled<VT, U>(m, lidx, val, xs, lane, s);
+            const int64_t node = (int64_t)m.z + lane;
+            if (node < n_nodes) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    q[3 * node + a] = s[a];
+                    v[0] = fma((double)p[3 * node + a], (double)s[a], v[0]);
+                }
+            }
+        }
+        __syncthreads();   // the next tile overwrites xs
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
+}
+
 template <typename VT, int L>
 __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                   const VT* __restrict__ val, const float* __restrict__ p,
@@ -757,7 +823,8 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
-    const int64_t np = grid_sum_doubles(std::max<int64_t>({(int64_t)spmv_grid(A), upd, A->tiled ? A->n_tiles : 0}));
+    const int64_t np = grid_sum_doubles(
+        std::max<int64_t>({(int64_t)spmv_grid(A), upd, A->tiled ? A->n_tiles : 0, A->nb_tiles}));
     int64_t b = 8 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
@@ -787,7 +854,7 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
     // one partial per block of the largest reduction grid: the persistent products, the
     // vector updates, or the tiled products (at most one block per tile)
     const size_t np = (size_t)grid_sum_doubles(
-        std::max<int64_t>({(int64_t)spmv_grid(A), (int64_t)w->upd_grid, A->tiled ? A->n_tiles : 0}));
+        std::max<int64_t>({(int64_t)spmv_grid(A), (int64_t)w->upd_grid, A->tiled ? A->n_tiles : 0, A->nb_tiles}));
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
         (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
         destroy_work(w);
@@ -946,6 +1013,24 @@ static void launch_inner_dot_csr(const fespmv_mat* A, CgWork* w, const VT* val, 
 
 template <typename VT>
 static void launch_inner_dot(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
+    if (A->nb) {
+        const VT* nbv = std::is_same<VT, float>::value ? reinterpret_cast<const VT*>(A->d_nb32)
+                                                       : reinterpret_cast<const VT*>(A->d_nb16);
+        if (A->nb_tiles > 0) {
+            // one block per tile: a tile is a large unit (256 node rows), so blocks striding
+            // over tiles would leave the last round of tiles to a few SMs
+            const size_t smem = sizeof(float) * 3 * (size_t)(A->nb_tile_dmax + 1);
+            const unsigned g = (unsigned)A->nb_tiles;
+            cg32_spmv_dot_nb_tiled<VT, std::is_same<VT, float>::value ? 2 : 4><<<g, 256, smem, s>>>(A->d_nbmeta, A->d_nbtlidx, nbv, A->d_nbtiles,
+                                                               A->d_nbtdict, w->p32, w->q32, A->nb_tiles, A->n / 3,
+                                                               w->partials, w->sc);
+            return;
+        }
+        const unsigned g = std::max(1u, std::min(spmv_grid(A), grid_for(A->nb_slices * 32, 256)));
+        cg32_spmv_dot_nb<VT, 2><<<g, 256, 0, s>>>(A->d_nbmeta, A->d_nbcol, nbv, w->p32, w->q32, A->nb_slices,
+                                                  A->n / 3, w->partials, w->sc);
+        return;
+    }
     if (A->format == FESPMV_FMT_SLICED) {
         switch (A->vec) {
             case 1: launch_inner_dot_sliced<VT, 1>(A, w, val, s); break;

@@ -31,7 +31,9 @@ struct Plan {
     std::vector<int64_t> diagpos;   // new row -> input CSR position of its diagonal, -1 none
     int64_t n_slices = 0;
     int64_t packed_len = 0;
+    std::vector<int64_t> ppos;      // permuted CSR entry -> packed position (when asked for)
 };
+
 
 // Tiles of consecutive slices for the x-staging kernels: each tile's distinct
 // columns form its dictionary (first-use order); every packed entry carries its
@@ -49,6 +51,22 @@ struct Tiles {
 bool build_tiles(const std::vector<uint32_t>& meta, const std::vector<int32_t>& col, int64_t n,
                  int max_slices, int max_cols, Tiles& out);
 
+// 3x3 node blocks of a node-ordered permuted CSR (rows 3I..3I+2 of node I): K1
+// slices of 32 node rows, one block row per lane, blocks column-major in the
+// slice; each block one int32 block column and 9 values stored plane by plane
+// (value k = 3a + b of the block at step s, lane l of a slice at offset off with
+// width w: index 9 off + k (32 w) + 32 s + l).
+struct NodeBlocks {
+    std::vector<uint32_t> meta;     // 4 per slice: offset/32 (block slots), width, first node row, 0
+    std::vector<int32_t> col;       // per block slot: block column (node), -1 = padding
+    std::vector<int64_t> map;       // per value: packed position of the entry, -1 = zero fill
+    int64_t n_slices = 0;
+    int64_t len = 0;                // block slots including padding
+    Tiles tiles;                    // tiles of node-block slices (x of the column nodes staged)
+};
+int pack_node_blocks(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
+                     const std::vector<int64_t>& ppos, NodeBlocks& out);
+
 // Permuted CSR (stage 1 of planning): P, Pinv, rows in new order with columns
 // renumbered and sorted, each entry's input position, each row's diagonal position.
 struct Permuted {
@@ -58,18 +76,22 @@ struct Permuted {
     std::vector<int64_t> s2;      // input CSR position; -2 = constant 1.0 (batch padding)
     std::vector<int64_t> diagpos;
 };
+// node_sort: the windowed length sort moves whole nodes (windows of ceil(sigma /
+// dofs_per_node) nodes, key = the longest row of the node), so that the dofs of
+// every node stay adjacent at rows dofs_per_node * k + c.
 int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
-                      const double* node_xyz, int reorder, int sigma, Permuted& out);
-// Stage 2: the K1/K2 warp slices of a permuted CSR (meta, col, src, sizes of `out`).
+                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort = false);
+// Stage 2: the K1/K2 warp slices of a permuted CSR (meta, col, src, sizes of `out`;
+// with_ppos: also each permuted entry's packed position).
 int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
-                const std::vector<int64_t>& s2, int threshold, int vec, Plan& out);
+                const std::vector<int64_t>& s2, int threshold, int vec, Plan& out, bool with_ppos = false);
 
 // Builds the locality order, windowed length sort, symmetric renumbering with
 // sorted columns and the warp-slice packing.  Returns FESPMV_OK or an error code
 // (message set).
 int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
                const double* node_xyz, int reorder, int sigma, int threshold, int vec,
-               Plan& out);
+               Plan& out, NodeBlocks* nb = nullptr);
 
 // Validates a host CSR (monotone offsets, columns in range); duplicates are
 // detected by build_plan for SLICED and by validate_csr_rows for CSR.
@@ -135,6 +157,21 @@ struct fespmv_mat {
     uint16_t* d_tlidx = nullptr;
     float* d_xs = nullptr;            // float permuted-I/O scratch (n each)
     float* d_ys = nullptr;
+    // 3x3 node blocks (SLICED, options.node_blocks = 3): the FP32 / BF16 copies of S A S
+    int nb = 0;                       // 3 when in use
+    int64_t nb_slices = 0;
+    int64_t nb_len = 0;               // block slots including padding
+    uint4* d_nbmeta = nullptr;
+    int32_t* d_nbcol = nullptr;
+    int64_t* d_nbmap = nullptr;       // 9 per slot: packed position, -1 = zero
+    float* d_nb32 = nullptr;          // 9 per slot
+    uint16_t* d_nb16 = nullptr;       // 9 per slot, bfloat16 bits
+    int64_t nb_tiles = 0;             // tiles of node-block slices (0: x gathered from L1/L2)
+    int nb_tile_dmax = 0;             // largest tile node list
+    int64_t nb_tile_dict_len = 0;
+    int4* d_nbtiles = nullptr;
+    int32_t* d_nbtdict = nullptr;     // the tiles' column nodes
+    uint16_t* d_nbtlidx = nullptr;    // per slot: index of its column node in the tile's list
 
     fespmv::CgWork* cg = nullptr;     // CG workspace, allocated by the first cg_solve
     fespmv::MultiWork* mcg = nullptr; // multi-RHS CG workspace, allocated by the first cg_solve_multi
@@ -156,6 +193,8 @@ int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s);
 unsigned grid_for(int64_t work, int block);
 // Rebuilds S and the FP32/BF16 copies of S A S from the FP64 values (if held).
 int launch_build_scaled(fespmv_mat* A, cudaStream_t s);
+int launch_nb3_refresh(fespmv_mat* A, cudaStream_t s);   // node-block copies from the scalar ones
+int launch_nb3_product(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 // y = B x with the FP32 (precision FESPMV_PREC_F32) or BF16 copy, handle numbering.
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s);
@@ -191,4 +230,9 @@ int upload_sliced(fespmv_mat* A, const Plan& plan, cudaStream_t s);
 void free_cg(fespmv_mat* A);
 void free_multi_cg(fespmv_mat* A);
 
+}  // namespace fespmv
+
+struct fespmv_assembly;
+namespace fespmv {
+fespmv_mat* assembly_handle(fespmv_assembly* P);   // the matrix an assembly map writes
 }  // namespace fespmv

@@ -88,7 +88,7 @@ static void morton_node_order(int64_t n_nodes, const double* xyz, std::vector<in
 }
 
 int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
-                      const double* node_xyz, int reorder, int sigma, Permuted& out) {
+                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort) {
     if (dpn <= 0) dpn = 1;
     if (n % dpn != 0) {
         set_error("n_rows %lld is not a multiple of dofs_per_node %d", (long long)n, dpn);
@@ -104,12 +104,27 @@ int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, i
         nodes.resize((size_t)n_nodes);
         std::iota(nodes.begin(), nodes.end(), (int64_t)0);
     }
+    // 2a. (node_sort) stable longest-first sort of whole nodes inside windows of
+    //     ceil(sigma / dpn) nodes, a node's length being its longest row
+    if (node_sort && sigma > 0) {
+        const int64_t wn = (sigma + dpn - 1) / dpn;
+        auto len = [&](int64_t node) {
+            int64_t m = 0;
+            for (int c = 0; c < dpn; ++c) m = std::max(m, rowptr[node * dpn + c + 1] - rowptr[node * dpn + c]);
+            return m;
+        };
+        for (int64_t s = 0; s < n_nodes; s += wn) {
+            int64_t e = std::min<int64_t>(n_nodes, s + wn);
+            std::stable_sort(nodes.begin() + s, nodes.begin() + e,
+                             [&](int64_t a, int64_t b) { return len(a) > len(b); });
+        }
+    }
     out.perm.resize((size_t)n);
     for (int64_t k = 0; k < n_nodes; ++k)
         for (int c = 0; c < dpn; ++c) out.perm[(size_t)(k * dpn + c)] = (int32_t)(nodes[(size_t)k] * dpn + c);
 
     // 2. stable longest-first sort inside windows of sigma rows
-    if (sigma > 0) {
+    if (sigma > 0 && !node_sort) {
         for (int64_t s = 0; s < n; s += sigma) {
             int64_t e = std::min<int64_t>(n, s + sigma);
             std::stable_sort(out.perm.begin() + s, out.perm.begin() + e, [&](int32_t a, int32_t b) {
@@ -151,7 +166,7 @@ int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, i
 }
 
 int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
-                const std::vector<int64_t>& s2, int threshold, int V, Plan& out) {
+                const std::vector<int64_t>& s2, int threshold, int V, Plan& out, bool with_ppos) {
     const int64_t n = (int64_t)rp2.size() - 1;
     // slice plan: per 32-row group choose T, split into T warps of 32/T rows
     struct Slice { int64_t r0; int nr; int T; int64_t w; };
@@ -186,6 +201,7 @@ int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
     out.col.assign((size_t)total, -1);
     out.src.assign((size_t)total, -1);
     out.meta.assign((size_t)out.n_slices * 4, 0);
+    if (with_ppos) out.ppos.assign(c2.size(), -1);
     int64_t off = 0;
     for (size_t si = 0; si < slices.size(); ++si) {
         const Slice& s = slices[si];
@@ -203,6 +219,7 @@ int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
                 int64_t pos = off + (step / V) * 32 * V + lane * V + step % V;
                 out.col[(size_t)pos] = c2[(size_t)(a + k)];
                 out.src[(size_t)pos] = s2[(size_t)(a + k)];
+                if (with_ppos) out.ppos[(size_t)(a + k)] = pos;
             }
         }
         off += 32 * s.w;
@@ -283,13 +300,87 @@ bool build_tiles(const std::vector<uint32_t>& meta, const std::vector<int32_t>& 
     return true;
 }
 
+// The node blocks of Sec. 5's slices for 3-dof nodes: block row I holds rows
+// 3I..3I+2, its blocks are the column nodes J any of them touches (ascending),
+// one block row per lane, 32 per slice, padded to the slice's longest block row.
+int pack_node_blocks(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
+                     const std::vector<int64_t>& ppos, NodeBlocks& out) {
+    const int64_t n = (int64_t)rp2.size() - 1;
+    if (n % 3 != 0) {
+        set_error("node blocks need n_rows divisible by 3 (got %lld)", (long long)n);
+        return FESPMV_ERR_INVALID_ARG;
+    }
+    const int64_t nn = n / 3;
+    // block columns of every node row
+    std::vector<int64_t> bp((size_t)nn + 1, 0);
+    std::vector<int32_t> bc;
+    std::vector<int32_t> cols;
+    for (int64_t I = 0; I < nn; ++I) {
+        cols.clear();
+        for (int a = 0; a < 3; ++a)
+            for (int64_t p = rp2[(size_t)(3 * I + a)]; p < rp2[(size_t)(3 * I + a + 1)]; ++p)
+                cols.push_back(c2[(size_t)p] / 3);
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        bc.insert(bc.end(), cols.begin(), cols.end());
+        bp[(size_t)I + 1] = (int64_t)bc.size();
+    }
+    out = NodeBlocks();
+    out.n_slices = (nn + 31) / 32;
+    out.meta.assign((size_t)out.n_slices * 4, 0);
+    int64_t total = 0;
+    for (int64_t s = 0; s < out.n_slices; ++s) {
+        int64_t w = 0;
+        for (int64_t I = 32 * s; I < std::min<int64_t>(nn, 32 * s + 32); ++I)
+            w = std::max(w, bp[(size_t)I + 1] - bp[(size_t)I]);
+        out.meta[(size_t)s * 4 + 0] = (uint32_t)(total / 32);
+        out.meta[(size_t)s * 4 + 1] = (uint32_t)w;
+        out.meta[(size_t)s * 4 + 2] = (uint32_t)(32 * s);
+        total += 32 * w;
+    }
+    if (total / 32 > (int64_t)UINT32_MAX) {
+        set_error("node blocks too large for 32-bit slice offsets");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    out.len = total;
+    out.col.assign((size_t)total, -1);
+    out.map.assign((size_t)total * 9, -1);
+    for (int64_t s = 0; s < out.n_slices; ++s) {
+        const int64_t off = 32 * (int64_t)out.meta[(size_t)s * 4], w = out.meta[(size_t)s * 4 + 1];
+        for (int64_t I = 32 * s; I < std::min<int64_t>(nn, 32 * s + 32); ++I) {
+            const int64_t lane = I - 32 * s;
+            for (int64_t k = bp[(size_t)I]; k < bp[(size_t)I + 1]; ++k) {
+                const int64_t step = k - bp[(size_t)I];
+                out.col[(size_t)(off + 32 * step + lane)] = bc[(size_t)k];
+            }
+            // the entries of the three rows, each to its block's value slot
+            for (int a = 0; a < 3; ++a) {
+                int64_t k = bp[(size_t)I];
+                for (int64_t p = rp2[(size_t)(3 * I + a)]; p < rp2[(size_t)(3 * I + a + 1)]; ++p) {
+                    const int32_t J = c2[(size_t)p] / 3, b = c2[(size_t)p] % 3;
+                    while (bc[(size_t)k] != J) ++k;   // columns ascend within the row
+                    const int64_t step = k - bp[(size_t)I];
+                    out.map[(size_t)(9 * off + (3 * a + b) * 32 * w + 32 * step + lane)] = ppos[(size_t)p];
+                }
+            }
+        }
+    }
+    return FESPMV_OK;
+}
+
 int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
-               const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out) {
+               const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out,
+               NodeBlocks* nb) {
     Permuted pm;
-    int rc = order_and_permute(n, rowptr, colind, dpn, node_xyz, reorder, sigma, pm);
+    int rc = order_and_permute(n, rowptr, colind, dpn, node_xyz, reorder, sigma, pm, nb != nullptr);
     if (rc) return rc;
-    rc = pack_slices(pm.rp2, pm.c2, pm.s2, threshold, V, out);
+    rc = pack_slices(pm.rp2, pm.c2, pm.s2, threshold, V, out, nb != nullptr);
     if (rc) return rc;
+    if (nb) {
+        if ((rc = pack_node_blocks(pm.rp2, pm.c2, out.ppos, *nb))) return rc;
+        // tiles of up to 8 node-block slices whose column nodes (at most 2048) are staged
+        build_tiles(nb->meta, nb->col, n / 3, 8, 2048, nb->tiles);
+    }
     out.perm.swap(pm.perm);
     out.pinv.swap(pm.pinv);
     out.diagpos.swap(pm.diagpos);

@@ -288,7 +288,7 @@ int launch_build_scaled(fespmv_mat* A, cudaStream_t s) {
                                                            A->d_val32, A->d_val16, A->n);
     }
     FESPMV_CUDA(cudaGetLastError());
-    return FESPMV_OK;
+    return launch_nb3_refresh(A, s);
 }
 
 int launch_fill_values(fespmv_mat* A, const double* vals_in, cudaStream_t s) {
@@ -359,6 +359,7 @@ static void dispatch_low(const fespmv_mat* A, const VT* val, const float* x, flo
 
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s) {
     if (A->n == 0) return FESPMV_OK;
+    if (A->nb) return launch_nb3_product(A, precision, x, y, s);
     if (A->tiled) return launch_spmv_low_tiled(A, precision, x, y, s);
     if (precision == FESPMV_PREC_F32)
         dispatch_low<float>(A, A->d_val32, x, y, s);

@@ -540,3 +540,59 @@ def test_threaded_product_is_bitwise_the_sequential_one():
     assert np.array_equal(y1.view(np.uint64), y4.view(np.uint64))
     assert info1["iters"] == info4["iters"]
     assert np.array_equal(xo1.view(np.uint64), xo4.view(np.uint64))
+
+
+def test_node_blocks_hand_example():
+    # two nodes, six rows; node 0's rows touch column nodes 0 and 1, so do node 1's
+    rowptr = np.array([0, 3, 4, 6, 7, 9, 11], dtype=np.int64)
+    colind = np.array([0, 1, 4, 1, 2, 5, 3, 0, 4, 2, 5], dtype=np.int32)
+    meta, col, vidx = layout.node_blocks(rowptr, colind)
+    assert meta.tolist() == [[0, 2, 0, 0]]
+    want_col = np.full(64, -1)
+    want_col[[0, 32, 1, 33]] = [0, 1, 0, 1]
+    assert np.array_equal(col, want_col)
+    want = np.full(9 * 64, -1)
+    # (value index) -> CSR position, worked out by hand from index = k*64 + 32*step + lane
+    for idx, p in ((0, 0), (64, 1), (96, 2), (256, 3), (512, 4), (544, 5),
+                   (33, 6), (193, 7), (289, 8), (513, 9), (545, 10)):
+        want[idx] = p
+    assert np.array_equal(vidx, want)
+
+
+@pytest.mark.parametrize("n,sigma", [(5, 96), (6, 0)])
+def test_node_blocks_hold_every_entry_once(n, sigma):
+    p = fegen.cube_elasticity(n, 60 + n)
+    P = layout.node_row_permutation(p.rowptr, p.node_xyz, "morton", sigma)
+    # whole nodes: rows 3k..3k+2 are the three dofs of one node
+    assert np.all(P.reshape(-1, 3) // 3 == (P.reshape(-1, 3) // 3)[:, :1])
+    assert np.array_equal(P.reshape(-1, 3) % 3, np.tile(np.arange(3), (len(P) // 3, 1)))
+    rp2, c2, v2, _ = layout.permute_csr(p.rowptr, p.colind, p.values, P)
+    meta, col, vidx = layout.node_blocks(rp2, c2)
+    live = vidx[vidx >= 0]
+    assert np.array_equal(np.sort(live), np.arange(p.nnz))
+    # the blocks rebuild the permuted matrix
+    nr = p.n_rows
+    D = np.zeros((nr, nr))
+    for s, (o32, w, first, _) in enumerate(meta):
+        o = int(o32) * 32
+        for lane in range(32):
+            I = int(first) + lane
+            if I >= nr // 3:
+                break
+            for st in range(int(w)):
+                J = col[o + 32 * st + lane]
+                if J < 0:
+                    continue
+                for k in range(9):
+                    q = vidx[9 * o + k * 32 * int(w) + 32 * st + lane]
+                    a, b = divmod(k, 3)
+                    D[3 * I + a, 3 * J + b] += v2[q] if q >= 0 else 0.0
+    assert np.array_equal(D, dense_of(rp2, c2, v2, nr))
+    # and the library's host planner orders the rows the same way
+    pl = fs_plan(p, sigma)
+    assert np.array_equal(pl["perm"], P)
+
+
+def fs_plan(p, sigma):
+    fs = pytest.importorskip("paper_1501_00324_gb300")
+    return fs.spmv_plan(p.rowptr, p.colind, p.node_xyz, 3, sigma=sigma, vec=1, node_blocks=3)
