@@ -6,7 +6,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 mixed-precision refinement; ``layout.py`` holds the numpy definitions of the
 row/column permutation and the warp-slice packing.
 
-``oracle.c`` also assembles global values and vectors from element quantities
+``oracle.c`` also holds a flexible CG (Notay 2000) preconditioned by a few
+steps of low-precision CG on S A S, and assembles global values and vectors from element quantities
 (the sum of the element contributions to each entry, Sec. 4).
 
 Pins (tests that tie the oracle to something other than itself) live in
@@ -65,6 +66,8 @@ def _lib():
         lib.oracle_refine.restype = i32
         lib.oracle_refine_reliable.argtypes = [i64, P, P, P, P, P, dbl, dbl, i32, i32, P, P, P]
         lib.oracle_refine_reliable.restype = i32
+        lib.oracle_fcg.argtypes = [i64, P, P, P, P, P, dbl, i32, i32, i32, P, P, P]
+        lib.oracle_fcg.restype = i32
         lib.oracle_scaled_values.argtypes = [i64, P, P, P, i32, P]
         lib.oracle_scaled_values.restype = i32
         lib.oracle_csr_spmv_f32.argtypes = [i64, P, P, P, P, P]
@@ -188,6 +191,24 @@ def refine_reliable(rowptr, colind, values, b, x0=None, tol=1e-10, delta=0.1, ma
                                        {"f32": 0, "bf16": 1}[storage], ctypes.byref(u), ctypes.byref(i),
                                        ctypes.byref(tr))
     return x, dict(status=STATUS[st], updates=u.value, iters=i.value, true_relres=tr.value)
+
+
+def fcg(rowptr, colind, values, b, tol=1e-10, inner_steps=8, max_iter=20000, storage="bf16"):
+    """Flexible CG (one previous direction kept) preconditioned by `inner_steps` steps
+    of CG on S A S in float / bfloat16 ('f32', 'bf16') or exact FP64 ('f64');
+    info: status, iters (outer steps), inner (inner steps), true_relres."""
+    rp, ci, va = _csr(rowptr, colind, values)
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n)
+    it = ctypes.c_int(0)
+    inn = ctypes.c_int(0)
+    tr = ctypes.c_double(0)
+    st = _lib().oracle_fcg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, inner_steps, max_iter,
+                           {"f32": 0, "bf16": 1, "f64": 2}[storage], ctypes.byref(it), ctypes.byref(inn),
+                           ctypes.byref(tr))
+    return x, dict(status={0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_input"}[st],
+                   iters=it.value, inner=inn.value, true_relres=tr.value)
 
 
 def assemble_matrix(rowptr, colind, elem_nodes, elem_mats, dofs_per_node, mask=None) -> np.ndarray:

@@ -574,3 +574,144 @@ void oracle_assemble_vector(int64_t n, int64_t n_elems, int npe, int dpn, const 
                 r[I] += Re[e * m + dpn * a + c];
             }
 }
+
+/*
+ * Flexible CG with a low-precision inner CG as the preconditioner.
+ *
+ * Outer: the flexible conjugate gradient method of Y. Notay, "Flexible conjugate
+ * gradients", SIAM J. Sci. Comput. 22 (2000), keeping one previous direction:
+ *   x = 0;  r = b
+ *   repeat:  z = M_k(r)
+ *            p = z                                   (first step)
+ *            p = z - (z.q / p.q) p                    (later: A-orthogonal to the last p)
+ *            q = A p;  alpha = (p.r) / (p.q)          (p.q <= 0: breakdown)
+ *            x += alpha p;  r -= alpha q               (FP64)
+ *            stop when ||r|| / ||b|| <= tol, then check the true residual and
+ *            restart from x (at most 3 times) as oracle_pcg does
+ * Preconditioner M_k: `inner_steps` steps of plain CG on B w = S r from w = 0,
+ * B = S A S, S = diag(A)^(-1/2) (fewer if the inner residual vanishes), then
+ * z = S w.  storage 0 / 1: B rounded to float / bfloat16 with float vectors
+ * and FP64 dot products, the inner arithmetic of oracle_refine; storage 2: B
+ * and the inner vectors in FP64 (no rounding of B), for the pins.  The inner
+ * CG is a different polynomial in B at every step, so the outer iteration must
+ * be flexible.  Returns 0 converged, 1 not converged (max_iter outer steps),
+ * 2 breakdown, 3 bad input (non-positive diagonal); iters_out counts outer
+ * steps, inner_out inner steps.
+ */
+int oracle_fcg(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+               const double* b, double* x, double tol, int inner_steps, int max_iter, int storage,
+               int* iters_out, int* inner_out, double* true_relres_out) {
+    const int64_t nnz = rowptr[n];
+    const size_t nd = (size_t)(n > 0 ? n : 1);
+    double* s = (double*)malloc(sizeof(double) * nd);
+    double* r = (double*)malloc(sizeof(double) * nd);
+    double* z = (double*)malloc(sizeof(double) * nd);
+    double* p = (double*)malloc(sizeof(double) * nd);
+    double* q = (double*)malloc(sizeof(double) * nd);
+    float* bv = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    double* bd = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    float* wf = (float*)malloc(sizeof(float) * nd);
+    float* rf = (float*)malloc(sizeof(float) * nd);
+    float* pf = (float*)malloc(sizeof(float) * nd);
+    float* qf = (float*)malloc(sizeof(float) * nd);
+    double* wd = (double*)malloc(sizeof(double) * nd);
+    double* rd = (double*)malloc(sizeof(double) * nd);
+    double* pd = (double*)malloc(sizeof(double) * nd);
+    double* qd = (double*)malloc(sizeof(double) * nd);
+    int status = 1, iters = 0, inner = 0;
+    double relres = 0.0, pq_prev = 0.0;
+    diagonal(n, rowptr, colind, val, z);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(z[i] > 0.0)) { status = 3; goto done; }
+        s[i] = 1.0 / sqrt(z[i]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            bd[k] = s[i] * val[k] * s[colind[k]];
+            float f = (float)bd[k];
+            bv[k] = storage == 1 ? round_bf16(f) : f;
+        }
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) { status = 0; goto done; }
+    for (int restart = 0; restart <= 3; ++restart) {
+        oracle_csr_spmv(n, rowptr, colind, val, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = 0; goto done; }
+        int converged = 0;
+        for (int k = 0; iters < max_iter; ++k) {
+            /* z = S w, w = inner_steps CG steps on B w = S r */
+            if (storage == 2) {
+                for (int64_t i = 0; i < n; ++i) { wd[i] = 0.0; rd[i] = s[i] * r[i]; pd[i] = rd[i]; }
+                double rho = dot(n, rd, rd);
+                for (int j = 0; j < inner_steps && rho > 0.0; ++j) {
+                    oracle_csr_spmv(n, rowptr, colind, bd, pd, qd);
+                    double piq = dot(n, pd, qd);
+                    if (!(piq > 0.0)) break;
+                    double a = rho / piq;
+                    for (int64_t i = 0; i < n; ++i) wd[i] = wd[i] + a * pd[i];
+                    for (int64_t i = 0; i < n; ++i) rd[i] = rd[i] - a * qd[i];
+                    ++inner;
+                    double rn = dot(n, rd, rd);
+                    double bt = rn / rho;
+                    rho = rn;
+                    for (int64_t i = 0; i < n; ++i) pd[i] = rd[i] + bt * pd[i];
+                }
+                for (int64_t i = 0; i < n; ++i) z[i] = s[i] * wd[i];
+            } else {
+                for (int64_t i = 0; i < n; ++i) { wf[i] = 0.0f; rf[i] = (float)(s[i] * r[i]); pf[i] = rf[i]; }
+                double rho = dot_f(n, rf, rf);
+                for (int j = 0; j < inner_steps && rho > 0.0; ++j) {
+                    spmv_f32(n, rowptr, colind, bv, pf, qf);
+                    double piq = dot_f(n, pf, qf);
+                    if (!(piq > 0.0)) break;
+                    float a = (float)(rho / piq);
+                    for (int64_t i = 0; i < n; ++i) wf[i] = wf[i] + a * pf[i];
+                    for (int64_t i = 0; i < n; ++i) rf[i] = rf[i] - a * qf[i];
+                    ++inner;
+                    double rn = dot_f(n, rf, rf);
+                    float bt = (float)(rn / rho);
+                    rho = rn;
+                    for (int64_t i = 0; i < n; ++i) pf[i] = rf[i] + bt * pf[i];
+                }
+                for (int64_t i = 0; i < n; ++i) z[i] = s[i] * (double)wf[i];
+            }
+            /* the new direction, A-orthogonal to the previous one */
+            if (k == 0) {
+                for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+            } else {
+                double beta = -dot(n, z, q) / pq_prev;
+                for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+            }
+            oracle_csr_spmv(n, rowptr, colind, val, p, q);
+            double pq = dot(n, p, q);
+            double pr = dot(n, p, r);
+            if (!(pq > 0.0) || !isfinite(pq) || !isfinite(pr)) { status = 2; goto final; }
+            double alpha = pr / pq;
+            pq_prev = pq;
+            for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+            for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+            ++iters;
+            relres = sqrt(dot(n, r, r)) / bnorm;
+            if (!isfinite(relres)) { status = 2; goto final; }
+            if (relres <= tol) { converged = 1; break; }
+        }
+        if (!converged) { status = 1; break; }
+        oracle_csr_spmv(n, rowptr, colind, val, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = 0; goto done; }
+    }
+final:
+    oracle_csr_spmv(n, rowptr, colind, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    relres = bnorm > 0 ? sqrt(dot(n, r, r)) / bnorm : 0.0;
+done:
+    if (iters_out) *iters_out = iters;
+    if (inner_out) *inner_out = inner;
+    if (true_relres_out) *true_relres_out = relres;
+    free(s); free(r); free(z); free(p); free(q); free(bv); free(bd);
+    free(wf); free(rf); free(pf); free(qf); free(wd); free(rd); free(pd); free(qd);
+    return status;
+}

@@ -596,3 +596,57 @@ def test_node_blocks_hold_every_entry_once(n, sigma):
 def fs_plan(p, sigma):
     fs = pytest.importorskip("paper_1501_00324_gb300")
     return fs.spmv_plan(p.rowptr, p.colind, p.node_xyz, 3, sigma=sigma, vec=1, node_blocks=3)
+
+
+# ---- flexible CG with a low-precision inner CG (oracle_fcg) ----------------------
+
+def test_fcg_with_one_exact_inner_step_is_jacobi_pcg():
+    # one FP64 inner step on S A S gives z = c D^-1 r: the flexible directions are
+    # Jacobi-PCG's up to scale, so the iterates are PCG's
+    p = fegen.shell_laplace(5, 16, 24, 52)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    xo, io = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    x, info = oracle.fcg(p.rowptr, p.colind, p.values, b, tol=1e-10, inner_steps=1, storage="f64")
+    assert info["status"] == "converged" and abs(info["iters"] - io["iters"]) <= 1
+    assert info["inner"] == info["iters"]
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-11
+
+
+def test_fcg_finite_termination_and_diagonal():
+    # Jacobi-scaled, the 3-eigenvalue matrix of the PCG pin has eigenvalues {1/2, 1, 3/2}
+    n_blocks, n4 = 5, 4
+    rows, cols, vals = [], [], []
+    for blk in range(n_blocks):
+        i = 2 * blk
+        for (r, c, v) in ((i, i, 2.0), (i, i + 1, 1.0), (i + 1, i, 1.0), (i + 1, i + 1, 2.0)):
+            rows.append(r), cols.append(c), vals.append(v)
+    for k in range(n4):
+        i = 2 * n_blocks + k
+        rows.append(i), cols.append(i), vals.append(4.0)
+    n = 2 * n_blocks + n4
+    order = np.lexsort((cols, rows))
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))])
+    b = fegen.random_vector(n, 3)
+    x, info = oracle.fcg(rowptr, np.array(cols)[order], np.array(vals)[order], b, tol=1e-13,
+                         inner_steps=1, storage="f64")
+    assert info["status"] == "converged" and info["iters"] == 3
+    # a diagonal matrix: S A S = I, the (FP64) inner solve is exact, one outer step
+    d = np.arange(1, 10, dtype=float)
+    bd = fegen.random_vector(9, 4)
+    x, info = oracle.fcg(np.arange(10), np.arange(9), d, bd, tol=1e-14, inner_steps=3, storage="f64")
+    assert info["iters"] == 1 and np.allclose(x, bd / d, rtol=1e-14)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f32"])
+def test_fcg_low_precision_inner_matches_dense_solve(storage):
+    p = fegen.cube_elasticity(4, 24)
+    A = dense_of(p.rowptr, p.colind, p.values, p.n_rows)
+    b = fegen.random_vector(p.n_rows, 25)
+    x, info = oracle.fcg(p.rowptr, p.colind, p.values, b, tol=1e-12, inner_steps=6, storage=storage)
+    assert info["status"] == "converged" and info["true_relres"] <= 1e-12
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 10 * np.linalg.cond(A) * 1e-12
+    # the inner steps pay: fewer outer steps than Jacobi-PCG's iterations
+    _, io = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-12)
+    assert info["iters"] < io["iters"] / 2
