@@ -572,6 +572,8 @@ def main():
                                                   fs.FESPMV_CG_F32_REFINE)
                 extra["cg_f32_reliable"] = bench_cg(fs, torch, A, p, args.cg_solves,
                                                     fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)
+                extra["cg_bf16_flexible"] = bench_cg(fs, torch, A, p, args.cg_solves,
+                                                     fs.FESPMV_CG_BF16_REFINE, flags=fs.FESPMV_CG_FLEXIBLE)
             if hasattr(fs, "cg_solve_multi") and args.multi_cg:
                 extra["cg_multi32"] = bench_cg_multi(fs, torch, p, args)
             if hasattr(fs, "assembly_create") and args.assembly:
@@ -779,6 +781,7 @@ def configs_summary(line):
                                          _pick(line, "node_blocks_3x3", "bf16_gbs")],
             "cg_f32_reliable_node_blocks": cg(_pick(line, "node_blocks_3x3", "cg_f32_reliable")),
             "cg_f64_1e-10": cg(line.get("cg")), "cg_f32_reliable_1e-10": cg(line.get("cg_f32_reliable")),
+            "cg_bf16_flexible_1e-10": cg(line.get("cg_bf16_flexible")),
             "output_check": _pick(cpu, "headline_output_check", "worst_err_over_abs_bound"),
             "cpu_spmv_gbs": {"1_core": cpu.get("spmv_1core_gbs"), f"{cpu.get('cores')}_cores": cpu.get("value")},
             "cpu_cg_est_solves_per_s": _pick(cpu, "cg_cube_elasticity_64", "est_solves_per_s")},
@@ -790,7 +793,7 @@ def configs_summary(line):
             "rhs32_solves_per_s": _pick(line, "cg_multi32", "f32_reliable", "solves_per_s")},
     }
     sh = line.get("shell_24x256x512") or {}
-    for k in ("cg_f64", "cg_f32_reliable", "cg_bf16_reliable"):
+    for k in ("cg_f64", "cg_f32_reliable", "cg_bf16_reliable", "cg_bf16_flexible"):
         if k in sh:
             out["C3_shell_24x256x512"][k] = cg(sh[k])
     sv = line.get("serving")
@@ -986,7 +989,8 @@ def bench_shell(fs, torch, args):
            "bf16_spmv_gbs": round((nnz * 6 + n * 8) / t16 / 1e9, 1)}
     for name, prec, fl in (("cg_f64", fs.FESPMV_CG_F64, 0), ("cg_f32_refine", fs.FESPMV_CG_F32_REFINE, 0),
                            ("cg_f32_reliable", fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE),
-                           ("cg_bf16_reliable", fs.FESPMV_CG_BF16_REFINE, fs.FESPMV_CG_RELIABLE)):
+                           ("cg_bf16_reliable", fs.FESPMV_CG_BF16_REFINE, fs.FESPMV_CG_RELIABLE),
+                           ("cg_bf16_flexible", fs.FESPMV_CG_BF16_REFINE, fs.FESPMV_CG_FLEXIBLE)):
         out[name] = bench_cg(fs, torch, A, p, 2, prec, flags=fl)
     fs.spmv_destroy(A)
     return out
@@ -1144,6 +1148,7 @@ def bench_cg(fs, torch, A, p, n_solves, precision, flags=0):
     return {"precision": name, "tol": 1e-10,
             "variant": ("single_reduction" if flags & fs.FESPMV_CG_SINGLE_REDUCTION else
                         "reliable_updates" if flags & fs.FESPMV_CG_RELIABLE else
+                        "flexible_cg_8_inner_steps" if flags & fs.FESPMV_CG_FLEXIBLE else
                         "restarted_refinement" if precision else "textbook"),
             "solves": n_solves, "outer": outer[0], "true_relres_max": max(rel),
             "solves_per_s": round(n_solves / sum(lat), 3),

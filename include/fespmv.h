@@ -321,6 +321,8 @@ int spmv_plan_tiles(int64_t n_rows, int64_t n_slices, const uint32_t* meta, int6
 #define FESPMV_CG_NO_PRECOND   8  /* flag: plain CG instead of Jacobi-PCG */
 #define FESPMV_CG_SINGLE_REDUCTION 16 /* flag: single-reduction (Chronopoulos-Gear) PCG, below */
 #define FESPMV_CG_RELIABLE     32 /* flag: refined precisions without restarts (reliable updates), below */
+#define FESPMV_CG_FLEXIBLE     64 /* flag: refined precisions as the preconditioner of a flexible
+                                     FP64 CG (Notay 2000), below */
 
 typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2; 0 = 1e-10 */
@@ -332,6 +334,8 @@ typedef struct {
     int32_t check_every;   /* iterations per graph launch between host polls; 0 = 16 */
     int32_t max_outer;     /* refinement: FP64 residual steps; 0 = 60 */
     double inner_tol;      /* refinement: inner CG stops at ||r_in|| <= inner_tol ||S r||; 0 = 1e-2 */
+    int32_t inner_steps;   /* FESPMV_CG_FLEXIBLE: low-precision CG steps per outer step; 0 = 8 */
+    int32_t pad;
 } cg_options;
 
 typedef struct {
@@ -400,6 +404,19 @@ typedef struct {
  * FESPMV_ERR_BREAKDOWN (p.Ap <= 0 -- delta - beta gamma / alpha_old <= 0 in the
  * single-reduction form -- non-finite scalars or a non-positive diagonal with
  * Jacobi), INVALID_ARG, UNSUPPORTED, OOM or CUDA.
+ *
+ * flag FESPMV_CG_FLEXIBLE (refined precisions only, else UNSUPPORTED; not with
+ * FESPMV_CG_RELIABLE): the low-precision CG becomes the preconditioner of an
+ * FP64 flexible CG (Y. Notay, SIAM J. Sci. Comput. 22, 2000, keeping one
+ * previous direction), x0 = 0 (or x with FESPMV_CG_X0):
+ *   r = b - A x;  repeat: w = inner_steps steps of CG on B w = S r from w = 0
+ *   (FP32 vectors, FP32 or BF16 values, FP64 dots);  z = S w;
+ *   p = z (first) or z - (z.q / p.q) p;  q = A p (FP64);  alpha = p.r / p.q;
+ *   x += alpha p;  r -= alpha q;  stop when ||r|| <= tol ||b||, confirmed on the
+ *   true residual (restarts as FP64 CG).
+ * Each step applies a different polynomial in B, which the flexible recurrence
+ * tolerates, so BF16 values converge to FP64 accuracy where refinement stalls
+ * (cond(B) 2^-8 >= 1).  iters counts outer (FP64) steps, outer the inner steps.
  */
 int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts, cg_result* res,
              fespmv_stream_t stream);

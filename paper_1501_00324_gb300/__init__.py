@@ -65,6 +65,7 @@ FESPMV_CG_X0 = 4
 FESPMV_CG_NO_PRECOND = 8
 FESPMV_CG_SINGLE_REDUCTION = 16
 FESPMV_CG_RELIABLE = 32
+FESPMV_CG_FLEXIBLE = 64
 
 
 class FespmvError(RuntimeError):
@@ -96,7 +97,7 @@ class cg_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_outer", ctypes.c_int32),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("inner_steps", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class cg_result(ctypes.Structure):
@@ -432,14 +433,15 @@ def spmv_export(A: Matrix, what: int, stream=None) -> np.ndarray:
 
 
 def cg_solve(A: Matrix, b, x, tol=1e-10, max_iter=0, precision=FESPMV_CG_F64, flags=0,
-             max_restarts=0, check_every=0, max_outer=0, inner_tol=0.0, stream=None) -> dict:
+             max_restarts=0, check_every=0, max_outer=0, inner_tol=0.0, inner_steps=0, stream=None) -> dict:
     """Solve A x = b; returns the cg_result fields as a dict.
 
     CG outcomes (converged, not converged, breakdown) are reported in
     result["status"]; argument and CUDA errors raise FespmvError."""
     if isinstance(b, np.ndarray):
         flags |= FESPMV_IO_HOST
-    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol)
+    o = cg_options(tol, max_iter, precision, flags, max_restarts, check_every, max_outer, inner_tol,
+                   inner_steps)
     r = cg_result()
     rc = _lib.cg_solve(A.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r), _stream(stream))
     if rc not in (FESPMV_OK, FESPMV_ERR_NOT_CONVERGED, FESPMV_ERR_BREAKDOWN):

@@ -547,8 +547,8 @@ static int batch_solve_impl(fespmv_batch* B, const double* b, double* x, const c
     if (o.precision == FESPMV_CG_F64) o.precision = FESPMV_CG_F32_REFINE;
     int rc = normalize_options(o);
     if (rc) return rc;
-    if (o.flags & (FESPMV_IO_PERMUTED | FESPMV_CG_NO_PRECOND)) {
-        set_error("batch_cg_solve: IO_PERMUTED and NO_PRECOND are not supported");
+    if (o.flags & (FESPMV_IO_PERMUTED | FESPMV_CG_NO_PRECOND | FESPMV_CG_FLEXIBLE)) {
+        set_error("batch_cg_solve: IO_PERMUTED, NO_PRECOND and FLEXIBLE are not supported");
         return FESPMV_ERR_INVALID_ARG;
     }
     fespmv_mat* M = B->M;

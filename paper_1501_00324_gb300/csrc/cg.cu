@@ -737,6 +737,101 @@ __global__ void __launch_bounds__(256, 8) refine_update(int64_t n, double* __res
         x[i] = fma(scale[i], (double)w[i], x[i]);
 }
 
+// ------------------------------------------------------------------ flexible CG (FESPMV_CG_FLEXIBLE)
+// Notay's flexible CG with one kept direction, in FP64, preconditioned by a fixed
+// number of low-precision CG steps on B = S A S (the inner kernels above, with a
+// scalar block of their own).  Per outer step: inner start, m inner steps,
+// beta = -z.q / p.q, p = z + beta p with p.r, q = A p with p.q (alpha = p.r / p.q),
+// then x, r and ||r||.  z = S w is formed on the fly and never stored.
+
+// Inner start from the outer residual: r_in = float(S r), w = 0, p_in = r_in.
+__global__ void __launch_bounds__(256) fcg_inner_init(int64_t n, const double* __restrict__ r,
+                                                      const double* __restrict__ scale, float* __restrict__ w,
+                                                      float* __restrict__ rin, float* __restrict__ pin, int m,
+                                                      double* partials, CgScalars* sc_in, const CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float rs = (float)(scale[i] * r[i]);
+        w[i] = 0.0f;
+        rin[i] = rs;
+        pin[i] = rs;
+        v[0] = fma((double)rs, (double)rs, v[0]);
+    }
+    if (grid_sum<1>(v, partials, sc_in->counters) && threadIdx.x == 0) {
+        sc_in->rho = v[0];
+        sc_in->iters_in = 0;
+        sc_in->max_iter = m;
+        sc_in->thresh_in = 0.0;
+        sc_in->status = !isfinite(v[0]) ? CG_BREAKDOWN : (v[0] > 0.0 ? CG_RUNNING : CG_CONVERGED);
+    }
+}
+
+// beta = -(S w).q / p.q with q = A p of the previous direction (0 at the first step).
+__global__ void __launch_bounds__(256) fcg_beta(int64_t n, const float* __restrict__ w,
+                                                const double* __restrict__ scale, const double* __restrict__ q,
+                                                double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING || sc->first) return;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[0] = fma(scale[i] * (double)w[i], q[i], v[0]);
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) {
+        sc->beta = -v[0] / sc->pq;
+        if (!isfinite(sc->beta)) sc->status = CG_BREAKDOWN;
+    }
+}
+
+// p = S w + beta p (p = S w at the first step) and p.r, the numerator of alpha.
+__global__ void __launch_bounds__(256) fcg_direction(int64_t n, const float* __restrict__ w,
+                                                     const double* __restrict__ scale, double* __restrict__ p,
+                                                     const double* __restrict__ r, float2* __restrict__ pdf,
+                                                     double* partials, CgScalars* sc) {
+    if (sc->status != CG_RUNNING) return;
+    const bool first = sc->first;
+    const double beta = sc->beta;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double z = scale[i] * (double)w[i];
+        const double pi = first ? z : fma(beta, p[i], z);
+        p[i] = pi;
+        if (pdf) pdf[i] = df_split(pi);
+        v[0] = fma(pi, r[i], v[0]);
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) {
+        sc->rho = v[0];
+        sc->first = 0;
+        if (!isfinite(v[0])) sc->status = CG_BREAKDOWN;
+    }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2; counts the outer step and copies the inner
+// step count for the host.
+__global__ void __launch_bounds__(256, 4) fcg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                     const double* __restrict__ p, const double* __restrict__ q,
+                                                     double* partials, CgScalars* sc, const CgScalars* sc_in) {
+    if (sc->status != CG_RUNNING) return;
+    const double a = sc->alpha;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(a, p[i], x[i]);
+        const double ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        v[0] = fma(ri, ri, v[0]);
+    }
+    if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->iters_in = sc_in->iters;
+        sc->rr = v[0];
+        if (!isfinite(v[0])) sc->status = CG_BREAKDOWN;
+        else if (v[0] <= sc->thresh2) sc->status = CG_CONVERGED;
+        else if (sc->iters >= sc->max_iter) sc->status = CG_MAXITER;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 //
 // A solve in flight is a CgRun: a small state machine that enqueues work on
@@ -786,10 +881,12 @@ void destroy_work(CgWork* w) {
     if (w->graph_cg1) cudaGraphExecDestroy(w->graph_cg1);
     for (cudaGraphExec_t g : w->graph_low)
         if (g) cudaGraphExecDestroy(g);
+    for (cudaGraphExec_t g : w->graph_flex)
+        if (g) cudaGraphExecDestroy(g);
     for (cudaEvent_t e : w->ev)
         if (e) cudaEventDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
-    void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc,
+    void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc, w->sc_in,
                     w->w32, w->r32, w->p32, w->q32, w->pdf, w->u, w->s};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -825,7 +922,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
     const int64_t upd = std::max(1u, std::min(grid_for(A->n, 256), (unsigned)(sms * 8)));
     const int64_t np = grid_sum_doubles(
         std::max<int64_t>({(int64_t)spmv_grid(A), upd, A->tiled ? A->n_tiles : 0, A->nb_tiles}));
-    int64_t b = 8 * 8 * A->n + 8 * np + (int64_t)sizeof(CgScalars);
+    int64_t b = 8 * 8 * A->n + 8 * np + 2 * (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
     if (refine) b += 4 * 4 * A->n;
     return b;
@@ -856,7 +953,8 @@ int create_work(const fespmv_mat* A, bool host_staging, CgWork** out) {
     const size_t np = (size_t)grid_sum_doubles(
         std::max<int64_t>({(int64_t)spmv_grid(A), (int64_t)w->upd_grid, A->tiled ? A->n_tiles : 0, A->nb_tiles}));
     if ((rc = work_alloc(w, (void**)&w->partials, sizeof(double) * np, "CG partial sums")) ||
-        (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars"))) {
+        (rc = work_alloc(w, (void**)&w->sc, sizeof(CgScalars), "CG scalars")) ||
+        (rc = work_alloc(w, (void**)&w->sc_in, sizeof(CgScalars), "inner CG scalars"))) {
         destroy_work(w);
         return rc;
     }
@@ -917,7 +1015,8 @@ static void launch_spmv_dot_df(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
                                                            w->partials, w->sc);
 }
 
-static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+// q = A p with p.q (alpha = rho / p.q), the FP64 product of the handle.
+static void launch_spmv_dot(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
     if (A->d_vdf) {
         switch (A->vec) {
             case 1: launch_spmv_dot_df<1>(A, w, s); break;
@@ -940,6 +1039,10 @@ static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
             default: launch_spmv_dot_csr<32>(A, w, s); break;
         }
     }
+}
+
+static void launch_iteration(const fespmv_mat* A, CgWork* w, cudaStream_t s) {
+    launch_spmv_dot(A, w, s);
     cg_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->p, w->q, w->dinv, w->partials, w->sc);
     cg_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p, w->r, w->dinv, w->pdf, w->sc);
 }
@@ -1058,12 +1161,33 @@ static void launch_inner_iteration(const fespmv_mat* A, CgWork* w, int bf16, cud
     cg32_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p32, w->r32, w->sc);
 }
 
-// Graph of `chunk` iterations (kind 0: FP64; 1: FP32 inner; 2: BF16 inner) for
-// this workspace; kernel arguments are the workspace's fixed pointers.
-static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
-    cudaGraphExec_t& slot = kind == 0 ? w->graph : (kind == 3 ? w->graph_cg1 : w->graph_low[kind - 1]);
-    int& slot_chunk = kind == 0 ? w->graph_chunk : (kind == 3 ? w->chunk_cg1 : w->chunk_low[kind - 1]);
-    if (slot && slot_chunk == chunk) return FESPMV_OK;
+// One outer step of the flexible CG: inner start, m inner steps on the inner
+// scalars, then the FP64 direction, product and update.
+static void launch_flexible_iteration(const fespmv_mat* A, CgWork* w, int bf16, int m, cudaStream_t s) {
+    fcg_inner_init<<<w->upd_grid, 256, 0, s>>>(A->n, w->r, A->d_scale, w->w32, w->r32, w->p32, m, w->partials,
+                                               w->sc_in, w->sc);
+    CgScalars* outer = w->sc;
+    w->sc = w->sc_in;   // the inner kernels read the workspace's scalar block
+    for (int j = 0; j < m; ++j) launch_inner_iteration(A, w, bf16, s);
+    w->sc = outer;
+    fcg_beta<<<w->upd_grid, 256, 0, s>>>(A->n, w->w32, A->d_scale, w->q, w->partials, w->sc);
+    fcg_direction<<<w->upd_grid, 256, 0, s>>>(A->n, w->w32, A->d_scale, w->p, w->r, w->pdf, w->partials, w->sc);
+    launch_spmv_dot(A, w, s);
+    fcg_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->p, w->q, w->partials, w->sc, w->sc_in);
+}
+
+// Graph of `chunk` iterations (kind 0: FP64; 1: FP32 inner; 2: BF16 inner; 3:
+// single-reduction FP64; 4, 5: flexible CG outer steps with FP32 / BF16 inner
+// steps, `m` of them) for this workspace; kernel arguments are the workspace's
+// fixed pointers.
+static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk, int m = 0) {
+    cudaGraphExec_t& slot = kind == 0 ? w->graph
+                          : kind == 3 ? w->graph_cg1
+                          : kind >= 4 ? w->graph_flex[kind - 4] : w->graph_low[kind - 1];
+    int& slot_chunk = kind == 0 ? w->graph_chunk
+                    : kind == 3 ? w->chunk_cg1
+                    : kind >= 4 ? w->chunk_flex[kind - 4] : w->chunk_low[kind - 1];
+    if (slot && slot_chunk == chunk && (kind < 4 || w->steps_flex[kind - 4] == m)) return FESPMV_OK;
     if (slot) {
         cudaGraphExecDestroy(slot);
         slot = nullptr;
@@ -1073,6 +1197,7 @@ static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
     for (int i = 0; i < chunk; ++i) {
         if (kind == 0) launch_iteration(A, w, w->cap);
         else if (kind == 3) launch_iteration_cg1(A, w, w->cap);
+        else if (kind >= 4) launch_flexible_iteration(A, w, kind - 4, m, w->cap);
         else launch_inner_iteration(A, w, kind - 1, w->cap);
     }
     cudaError_t e = cudaStreamEndCapture(w->cap, &g);
@@ -1081,6 +1206,7 @@ static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     slot_chunk = chunk;
+    if (kind >= 4) w->steps_flex[kind - 4] = m;
     return FESPMV_OK;
 }
 
@@ -1108,11 +1234,13 @@ int normalize_options(cg_options& o) {
     if (o.check_every == 0) o.check_every = 16;
     if (o.max_outer == 0) o.max_outer = 60;
     if (o.inner_tol == 0.0) o.inner_tol = (o.flags & FESPMV_CG_RELIABLE) ? 1e-1 : 1e-2;
+    if (o.inner_steps == 0) o.inner_steps = 8;
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.check_every < 1 || o.check_every > 4096 ||
         o.precision < FESPMV_CG_F64 || o.precision > FESPMV_CG_BF16_REFINE || o.max_outer < 0 ||
         !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
+        o.inner_steps < 1 || o.inner_steps > 1024 ||
         (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND |
-                     FESPMV_CG_SINGLE_REDUCTION | FESPMV_CG_RELIABLE))) {
+                     FESPMV_CG_SINGLE_REDUCTION | FESPMV_CG_RELIABLE | FESPMV_CG_FLEXIBLE))) {
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
     }
@@ -1122,6 +1250,10 @@ int normalize_options(cg_options& o) {
     }
     if ((o.flags & FESPMV_CG_RELIABLE) && o.precision == FESPMV_CG_F64) {
         set_error("FESPMV_CG_RELIABLE applies to the refined precisions only");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    if ((o.flags & FESPMV_CG_FLEXIBLE) && (o.precision == FESPMV_CG_F64 || (o.flags & FESPMV_CG_RELIABLE))) {
+        set_error("FESPMV_CG_FLEXIBLE applies to the refined precisions, without FESPMV_CG_RELIABLE");
         return FESPMV_ERR_UNSUPPORTED;
     }
     return FESPMV_OK;
@@ -1157,9 +1289,11 @@ static int enqueue_graph(CgRun& r) {
 }
 
 static int start_graphs(CgRun& r, int kind, int max_iter) {
-    int rc = ensure_graph(r.A, r.w, kind, r.o.check_every);
+    int rc = ensure_graph(r.A, r.w, kind, r.o.check_every, r.o.inner_steps);
     if (rc) return rc;
-    r.graph = kind == 0 ? r.w->graph : (kind == 3 ? r.w->graph_cg1 : r.w->graph_low[kind - 1]);
+    r.graph = kind == 0 ? r.w->graph
+            : kind == 3 ? r.w->graph_cg1
+            : kind >= 4 ? r.w->graph_flex[kind - 4] : r.w->graph_low[kind - 1];
     r.graphs_left = (int64_t)max_iter / r.o.check_every + 3;
     r.head = 0;
     r.queued = 0;
@@ -1220,7 +1354,12 @@ int run_begin(CgRun& r) {
     // the pinned slot doubles as the upload buffer: it is not read until the first status copy
     w->h_sc[1] = init;
     FESPMV_CUDA(cudaMemcpyAsync(w->sc, &w->h_sc[1], sizeof(CgScalars), cudaMemcpyHostToDevice, r.s));
-    if (r.o.precision == FESPMV_CG_F64) {
+    const bool flexible = r.o.flags & FESPMV_CG_FLEXIBLE;
+    if (flexible) {   // the inner scalars (their reduction counters and step count) start at zero
+        if ((rc = ensure_low_work(w))) return rc;
+        FESPMV_CUDA(cudaMemsetAsync(w->sc_in, 0, sizeof(CgScalars), r.s));
+    }
+    if (r.o.precision == FESPMV_CG_F64 || flexible) {
         cg_dinv<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, r.A->d_diag, w->dinv,
                                               (r.o.flags & FESPMV_CG_NO_PRECOND) ? 0 : 1, w->sc);
         FESPMV_CUDA(cudaGetLastError());
@@ -1281,8 +1420,11 @@ int run_step(CgRun& r, bool block, bool* progress) {
                 r.last.true_rr = 0.0;
                 return finish(r, CG_CONVERGED);
             }
-            if (h.status == CG_RUNNING)
-                return start_graphs(r, (r.o.flags & FESPMV_CG_SINGLE_REDUCTION) ? 3 : 0, r.o.max_iter);
+            if (h.status == CG_RUNNING) {
+                const int kind = (r.o.flags & FESPMV_CG_FLEXIBLE) ? (r.o.precision == FESPMV_CG_BF16_REFINE ? 5 : 4)
+                               : (r.o.flags & FESPMV_CG_SINGLE_REDUCTION) ? 3 : 0;
+                return start_graphs(r, kind, r.o.max_iter);
+            }
             // converged (or failed) before iterating: confirm on the true residual
             if ((rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
             cg_true_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, w->q, w->partials, w->sc);
@@ -1295,7 +1437,7 @@ int run_step(CgRun& r, bool block, bool* progress) {
             r.head ^= 1;
             if (h.status == CG_RUNNING && r.graphs_left > 0) return enqueue_graph(r);
             if (r.queued > 0) return FESPMV_OK;  // let the no-op graphs drain
-            if (r.o.precision == FESPMV_CG_F64) {
+            if (r.o.precision == FESPMV_CG_F64 || (r.o.flags & FESPMV_CG_FLEXIBLE)) {
                 if ((rc = launch_spmv(r.A, w->x, w->q, r.s))) return rc;
                 cg_true_residual<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->b, w->q, w->partials, w->sc);
                 FESPMV_CUDA(cudaGetLastError());
@@ -1360,8 +1502,8 @@ int run_result(const CgRun& r, cg_result* res) {
         res->status = out;
         res->iters = h.iters;
         res->restarts = r.restarts;
-        res->outer = r.outer;
-        if (r.o.precision == FESPMV_CG_F64) {
+        res->outer = (r.o.flags & FESPMV_CG_FLEXIBLE) ? h.iters_in : r.outer;
+        if (r.o.precision == FESPMV_CG_F64 || (r.o.flags & FESPMV_CG_FLEXIBLE)) {
             res->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
             res->true_relres = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
         } else {
@@ -1370,7 +1512,7 @@ int run_result(const CgRun& r, cg_result* res) {
         }
     }
     if (out == FESPMV_ERR_BREAKDOWN) set_error("CG breakdown (p.Ap <= 0 or a non-finite scalar)");
-    if (out == FESPMV_ERR_NOT_CONVERGED && r.o.precision == FESPMV_CG_F64)
+    if (out == FESPMV_ERR_NOT_CONVERGED && (r.o.precision == FESPMV_CG_F64 || (r.o.flags & FESPMV_CG_FLEXIBLE)))
         set_error("CG stopped above the tolerance");
     return out;
 }

@@ -23,6 +23,7 @@ struct CgWork {
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *dinv = nullptr;
     double* partials = nullptr;
     CgScalars* sc = nullptr;
+    CgScalars* sc_in = nullptr;   // flexible CG: the inner (low-precision) CG's scalars
     CgScalars* h_sc = nullptr;  // pinned host mirror, 2 slots
     unsigned upd_grid = 0;
     cudaStream_t cap = nullptr;
@@ -33,6 +34,8 @@ struct CgWork {
     float *w32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
     int chunk_low[2] = {0, 0};
+    cudaGraphExec_t graph_flex[2] = {nullptr, nullptr}; // flexible CG outer steps, FP32 / BF16 inner
+    int chunk_flex[2] = {0, 0}, steps_flex[2] = {0, 0};
     double* h_io = nullptr;     // pinned host staging of n doubles (solve server)
     float2* pdf = nullptr;      // float-pair split of p (handles with FESPMV_PREC_DF64)
     double *u = nullptr, *s = nullptr;  // single-reduction CG: u = D^-1 r, s = A p

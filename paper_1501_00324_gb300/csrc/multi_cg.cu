@@ -784,6 +784,10 @@ static int solve_multi_impl(fespmv_mat* A, const double* B, double* X, int k, co
     if (opts) o = *opts;
     int rc = normalize_options(o);
     if (rc || (rc = check_multi_options(A, o, "cg_solve_multi"))) return rc;
+    if (o.flags & FESPMV_CG_FLEXIBLE) {
+        set_error("cg_solve_multi: FESPMV_CG_FLEXIBLE is not supported");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
     if (A->n == 0) {   // empty system: every column is solved by x = 0
         if (res)
             for (int j = 0; j < k; ++j) std::memset(&res[j], 0, sizeof(cg_result));
