@@ -68,7 +68,7 @@ def parse_args():
                     help="FP64 product: DFMA (f64) or float pairs on the FP32 pipe (df64)")
     ap.add_argument("--only-spmv", action="store_true",
                     help="time the FE product only (for profiling runs)")
-    ap.add_argument("--ablation", type=int, default=0,
+    ap.add_argument("--ablation", type=int, default=1,
                     help="the layout ablation (CSR, slices, sort, Morton order, tiles) on two workloads")
     ap.add_argument("--assembly", type=int, default=1,
                     help="time the assembly of the workload matrix from its element matrices")
@@ -838,8 +838,9 @@ def bench_serving(fs, torch, args):
     multi-RHS groups, and one-at-a-time FP64 cg_solve, all on the same arrival
     trace.  First an overload run (args.serve_rate) finds the grouped server's
     saturation rate; then a sweep of arrival rates at fractions of it, plus one
-    rate at 0.5, 1 and 1.5 times the one-at-a-time capacity.  Each run lasts args.serve_seconds;
-    requests still queued at the end are cancelled and counted as not served."""
+    rate at 0.5, 1 and 1.5 times the one-at-a-time capacity.  Arrivals span args.serve_seconds;
+    either arm may start queued requests for one more second, then what still waits
+    is cancelled and counted as not served."""
     import fegen
     if args.serve_small:
         n_mesh, lo, hi = 12, 5_000, 300_000
@@ -858,6 +859,7 @@ def bench_serving(fs, torch, args):
                  "nnz_total": sum(p.nnz for p in pool), "gen_s": round(gen_s, 1), "setup_s": round(setup_s, 1)}
     sizes = [p.n_rows for p in pool]
     T = args.serve_seconds
+    DRAIN = 1.0   # seconds after the last arrival in which either arm may still start queued requests
 
     def make_trace(rate, seed):
         rng = np.random.default_rng(seed)
@@ -893,6 +895,10 @@ def bench_serving(fs, torch, args):
                 time.sleep(a - now)
             tickets.append(fs.srv_submit(S, ids[m], rhs[m][k], tol=tol,
                                          precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE))
+        # a drain window as long as the one-at-a-time arm's, then what still waits is cancelled
+        t_end = start + T + DRAIN
+        while time.perf_counter() < t_end and fs.srv_get_stats(S)["queued"] > 0:
+            time.sleep(0.005)
         fs.srv_cancel_queued(S)
         lat, served = [], 0
         for t in tickets:
@@ -914,7 +920,7 @@ def bench_serving(fs, torch, args):
         start = time.perf_counter()
         for (a, m, tol, k) in trace:
             now = time.perf_counter() - start
-            if now >= T:
+            if now >= T + DRAIN:
                 break
             if now < a:
                 time.sleep(a - now)
@@ -1324,7 +1330,15 @@ def bench_ablation(fs, torch, args, back_to_back):
             ("slices, generator numbering, global length sort", dict(reorder=NONE, sigma=n, tiles=-1, vec=1)),
             ("slices, Morton order, no sort", dict(reorder=MORTON, sigma=0, tiles=-1, vec=1)),
             ("slices, Morton order, sort windows of 1024", dict(reorder=MORTON, sigma=1024, tiles=-1, vec=1)),
-            ("+ x staged per tile, 16-bit indices", dict(reorder=MORTON, sigma=1024, vec=1)),
+            ("K1: input column numbers (y through P^-1), Morton, windows, x from cache",
+             dict(reorder=MORTON, sigma=1024, tiles=-1, vec=1, col_order=fs.FESPMV_COLS_ORIGINAL)),
+            ("K1r: renumbered, unsorted columns, Morton, windows, x from cache",
+             dict(reorder=MORTON, sigma=1024, tiles=-1, vec=1, col_order=fs.FESPMV_COLS_RENUMBERED)),
+            ("K1rs: renumbered, sorted columns, Morton, windows, x from cache (as two lines up)",
+             dict(reorder=MORTON, sigma=1024, tiles=-1, vec=1)),
+            ("K1r + x staged per tile, 16-bit indices",
+             dict(reorder=MORTON, sigma=1024, vec=1, col_order=fs.FESPMV_COLS_RENUMBERED)),
+            ("+ x staged per tile, 16-bit indices (K1rs: the headline layout)", dict(reorder=MORTON, sigma=1024, vec=1)),
         ]
         rows = []
         for name, kw in variants:
@@ -1332,21 +1346,27 @@ def bench_ablation(fs, torch, args, back_to_back):
             A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, **kw)
             create_s = time.perf_counter() - t0
             sliced = kw.get("format", fs.FESPMV_FMT_SLICED) != CSR
+            k1 = kw.get("col_order", 0) == fs.FESPMV_COLS_ORIGINAL
             xp = torch.empty_like(x)
-            if sliced:
+            if sliced and not k1:
                 fs.spmv_permute(A, x, xp, 0)
             else:
                 xp.copy_(x)
             yp = torch.empty_like(x)
-            flags = fs.FESPMV_IO_PERMUTED if sliced else 0
+            flags = fs.FESPMV_IO_PERMUTED if sliced and not k1 else 0
             fa = lambda: fs.spmv_apply(A, xp, yp, flags)  # noqa: E731
+            fi = lambda: fs.spmv_apply(A, x, yp, 0)  # noqa: E731
             fu = lambda: fs.spmv_update_values(A, vals)  # noqa: E731
             fa()
+            fi()
             fu()
             ta = back_to_back(fa, max(20, args.steps // 4))
+            ti = back_to_back(fi, max(20, args.steps // 4))
             tu = back_to_back(fu, 10)
             info = fs.spmv_get_info(A)
             rows.append({"variant": name, "gbs": round(mb / (ta * 1e-3) / 1e9, 1), "us": round(ta * 1e3, 1),
+                         "gbs_input_numbering": round(mb / (ti * 1e-3) / 1e9, 1),
+                         "gbs_includes_y_remap": k1,
                          "padding": round(info["packed_len"] / nnz - 1.0, 4) if sliced else 0.0,
                          "tiles": info["n_tiles"], "plan_s": round(create_s, 2),
                          "refresh_products": round(tu / ta, 2)})

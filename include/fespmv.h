@@ -63,6 +63,15 @@ typedef struct fespmv_mat* fespmv_mat_t;      /* opaque; owns the device memory 
 #define FESPMV_REORDER_NONE    0  /* keep the input numbering */
 #define FESPMV_REORDER_MORTON  1  /* Z-order curve of node_xyz (requires mesh->node_xyz) */
 
+/* Column numbering of FESPMV_FMT_SLICED (the paper's K1 / K1r / K1rs, Sec. 5.1-5.3). */
+#define FESPMV_COLS_SORTED     0  /* K1rs: renumbered with the rows (c' = P^-1[c]) and sorted per row */
+#define FESPMV_COLS_RENUMBERED 1  /* K1r: renumbered, each row in the input's order */
+#define FESPMV_COLS_ORIGINAL   2  /* K1: the input numbering; the product reads x in the input
+                                     numbering and writes y in the handle's (spmv_apply without
+                                     FESPMV_IO_PERMUTED returns y in the input numbering).  FP64
+                                     products only: no FP32/BF16/float-pair copies, node blocks,
+                                     CG, multi-RHS or assembly on such a handle. */
+
 /* Kernel selection for FESPMV_FMT_CSR (csr_lanes) is by lanes per row:
  * 1 = one thread per row (CSR scalar, Sec. 4), 2..32 (power of two) = that many
  * lanes of a warp per row with a shuffle reduction (CSR vector, Sec. 4). */
@@ -107,6 +116,7 @@ typedef struct {
                             list: 2/9 of a byte of index per value, one lookup per 9 values
                             (tiles = -1: x gathered from L1/L2 with the int32 block columns).  NaN or Inf in x at a column
                             a block stores as zero reaches its rows.  0 = off. */
+    int32_t col_order;   /* SLICED: FESPMV_COLS_*; 0 = sorted (K1rs) */
 } fespmv_options;
 
 typedef struct {

@@ -113,8 +113,11 @@ def inverse(P: np.ndarray) -> np.ndarray:
     return Pinv
 
 
-def permute_csr(rowptr, colind, values, P):
-    """Symmetrically permuted CSR (rows P, columns renumbered by Pinv and sorted).
+def permute_csr(rowptr, colind, values, P, col_order: str = "sorted"):
+    """Row-permuted CSR: rows in the order P.  col_order 'sorted' (K1rs, Sec. 5.3):
+    columns renumbered by Pinv and sorted per row; 'renumbered' (K1r, Sec. 5.2):
+    renumbered, each row in the input's order; 'original' (K1, Sec. 5.1): the
+    input's column numbers and order.
 
     Returns (rowptr2, colind2, values2, vmap) with vmap[old_position] =
     position of the same entry in the permuted CSR."""
@@ -127,8 +130,14 @@ def permute_csr(rowptr, colind, values, P):
     nnz = int(rowptr[-1])
     old_row = np.repeat(np.arange(n), lens)
     new_row = Pinv[old_row]
-    new_col = Pinv[colind.astype(np.int64)]
-    order = np.lexsort((new_col, new_row))           # row-major, columns ascending
+    if col_order == "original":
+        new_col = colind.astype(np.int64)
+    else:
+        new_col = Pinv[colind.astype(np.int64)]
+    if col_order == "sorted":
+        order = np.lexsort((new_col, new_row))       # row-major, columns ascending
+    else:
+        order = np.lexsort((np.arange(nnz), new_row))  # row-major, the input's order in a row
     colind2 = new_col[order].astype(np.int32)
     values2 = np.asarray(values)[order]
     vmap = np.empty(nnz, dtype=np.int64)

@@ -32,6 +32,9 @@ FESPMV_FMT_CSR = 0
 FESPMV_FMT_SLICED = 1
 FESPMV_REORDER_NONE = 0
 FESPMV_REORDER_MORTON = 1
+FESPMV_COLS_SORTED = 0
+FESPMV_COLS_RENUMBERED = 1
+FESPMV_COLS_ORIGINAL = 2
 FESPMV_PREC_F64 = 1
 FESPMV_PREC_F32 = 2
 FESPMV_PREC_BF16 = 4
@@ -77,7 +80,7 @@ class FespmvError(RuntimeError):
 class fespmv_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("format", "reorder", "sigma", "threshold", "vec", "csr_lanes", "precisions",
-                 "block", "tiles", "node_blocks")]
+                 "block", "tiles", "node_blocks", "col_order")]
 
 
 class fespmv_mesh_info(ctypes.Structure):
@@ -275,7 +278,7 @@ class Matrix:
 
 def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=FESPMV_FMT_SLICED,
                 reorder=None, sigma=0, threshold=0, vec=0, csr_lanes=0, precisions=0, block=0,
-                tiles=0, node_blocks=0, stream=None) -> Matrix:
+                tiles=0, node_blocks=0, col_order=0, stream=None) -> Matrix:
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     values = np.ascontiguousarray(values, dtype=np.float64)
@@ -283,7 +286,7 @@ def spmv_create(rowptr, colind, values, node_xyz=None, dofs_per_node=1, format=F
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
     opts = fespmv_options(format, reorder, sigma, threshold, vec, csr_lanes, precisions, block, tiles,
-                          node_blocks)
+                          node_blocks, col_order)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     h = _P()
     n = len(rowptr) - 1
@@ -334,14 +337,14 @@ def spmv_update_values(A: Matrix, values, flags=0, stream=None):
 
 
 def spmv_plan(rowptr, colind, node_xyz=None, dofs_per_node=1, reorder=None, sigma=0,
-              threshold=0, vec=0, node_blocks=0) -> dict:
+              threshold=0, vec=0, node_blocks=0, col_order=0) -> dict:
     """Host-only planning: returns perm, meta (S x 4), cols and srcmap as numpy arrays."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
     if reorder is None:
         reorder = FESPMV_REORDER_MORTON if xyz is not None else FESPMV_REORDER_NONE
-    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0, 0, node_blocks)
+    opts = fespmv_options(FESPMV_FMT_SLICED, reorder, sigma, threshold, vec, 0, 0, 0, 0, node_blocks, col_order)
     mesh = fespmv_mesh_info(dofs_per_node, None if xyz is None else xyz.ctypes.data)
     info = fespmv_info()
     n = len(rowptr) - 1

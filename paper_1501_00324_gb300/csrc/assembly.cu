@@ -349,6 +349,10 @@ int assembly_create(fespmv_assembly_t* out, fespmv_mat_t A, const int64_t* rowpt
             set_error("null argument");
             return FESPMV_ERR_INVALID_ARG;
         }
+        if (A->col_order == FESPMV_COLS_ORIGINAL) {
+            set_error("assembly needs a handle with renumbered columns (not FESPMV_COLS_ORIGINAL)");
+            return FESPMV_ERR_UNSUPPORTED;
+        }
         return create_impl(out, A, rowptr, colind, n_elems, nodes_per_elem, dofs_per_node, elem_nodes, dirichlet,
                            (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {

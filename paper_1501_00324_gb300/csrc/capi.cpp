@@ -219,6 +219,14 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     if (o.precisions & ~(FESPMV_PREC_F64 | FESPMV_PREC_F32 | FESPMV_PREC_BF16 | FESPMV_PREC_DF64)) {
         set_error("unknown precision bits 0x%x", o.precisions); return FESPMV_ERR_INVALID_ARG;
     }
+    if (o.col_order < FESPMV_COLS_SORTED || o.col_order > FESPMV_COLS_ORIGINAL) {
+        set_error("unknown col_order %d", o.col_order); return FESPMV_ERR_INVALID_ARG;
+    }
+    if (o.col_order == FESPMV_COLS_ORIGINAL &&
+        (o.format != FESPMV_FMT_SLICED || o.node_blocks || (o.precisions & ~FESPMV_PREC_F64))) {
+        set_error("FESPMV_COLS_ORIGINAL: SLICED handles with FP64 values only");
+        return FESPMV_ERR_INVALID_ARG;
+    }
     if (o.node_blocks != 0 &&
         (o.node_blocks != 3 || o.format != FESPMV_FMT_SLICED || !mesh || mesh->dofs_per_node != 3 ||
          !(o.precisions & (FESPMV_PREC_F32 | FESPMV_PREC_BF16)))) {
@@ -274,8 +282,9 @@ static int create_impl(fespmv_mat_t* out, int64_t n, const int64_t* rowptr, cons
     } else {
         Plan plan;
         NodeBlocks nb;   // host arrays stay alive until the stream synchronisation below
+        A->col_order = o.col_order;
         TRY(build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma,
-                       o.threshold, o.vec, plan, o.node_blocks ? &nb : nullptr));
+                       o.threshold, o.vec, plan, o.node_blocks ? &nb : nullptr, o.col_order));
         TRY(upload_sliced(A, plan, s));
         if (o.node_blocks) TRY(upload_node_blocks(A, nb, o.tiles >= 0, s));
         Tiles tiles;  // host arrays stay alive until the stream synchronisation below
@@ -369,6 +378,29 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (A->n == 0) return FESPMV_OK;
+    if (A->col_order == FESPMV_COLS_ORIGINAL) {
+        // K1: x in the input numbering feeds the kernel as it is; y leaves through P^-1
+        if (flags & FESPMV_IO_PERMUTED) {
+            set_error("a FESPMV_COLS_ORIGINAL handle reads x in the input numbering only");
+            return FESPMV_ERR_UNSUPPORTED;
+        }
+        const double* xk = x;
+        if (flags & FESPMV_IO_HOST) {
+            int rc = ensure_host_staging(A);
+            if (rc) return rc;
+            FESPMV_CUDA(cudaMemcpyAsync(A->d_xh, x, sizeof(double) * A->n, cudaMemcpyHostToDevice, s));
+            xk = A->d_xh;
+        }
+        double* yk = (flags & FESPMV_IO_HOST) ? A->d_yh : y;
+        int rc;
+        if ((rc = launch_spmv(A, xk, A->d_yp, s)) || (rc = launch_gather(A->d_yp, A->d_pinv, yk, A->n, s)))
+            return rc;
+        if (flags & FESPMV_IO_HOST) {
+            FESPMV_CUDA(cudaMemcpyAsync(y, yk, sizeof(double) * A->n, cudaMemcpyDeviceToHost, s));
+            FESPMV_CUDA(cudaStreamSynchronize(s));
+        }
+        return FESPMV_OK;
+    }
     const double* xd = x;
     double* yd = y;
     if ((flags & FESPMV_IO_HOST) && A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED) &&
@@ -508,8 +540,11 @@ int spmv_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, const fes
     }
     Plan plan;
     NodeBlocks nb;
+    if (o.col_order < FESPMV_COLS_SORTED || o.col_order > FESPMV_COLS_ORIGINAL) {
+        set_error("unknown col_order %d", o.col_order); return FESPMV_ERR_INVALID_ARG;
+    }
     rc = build_plan(n, rowptr, colind, dpn, mesh ? mesh->node_xyz : nullptr, o.reorder, o.sigma, o.threshold,
-                    o.vec, plan, o.node_blocks ? &nb : nullptr);
+                    o.vec, plan, o.node_blocks ? &nb : nullptr, o.col_order);
     if (rc) return rc;
     info->n_rows = n;
     info->nnz = rowptr[n];

@@ -1260,6 +1260,10 @@ int normalize_options(cg_options& o) {
 }
 
 int check_precision(const fespmv_mat* A, int precision) {
+    if (A->col_order == FESPMV_COLS_ORIGINAL) {
+        set_error("CG needs x and A x in one numbering: not on a FESPMV_COLS_ORIGINAL handle");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
     if (precision == FESPMV_CG_F32_REFINE && !A->d_val32) {
         set_error("FESPMV_CG_F32_REFINE needs a handle created with FESPMV_PREC_F32");
         return FESPMV_ERR_UNSUPPORTED;

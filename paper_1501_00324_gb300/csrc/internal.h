@@ -79,8 +79,11 @@ struct Permuted {
 // node_sort: the windowed length sort moves whole nodes (windows of ceil(sigma /
 // dofs_per_node) nodes, key = the longest row of the node), so that the dofs of
 // every node stay adjacent at rows dofs_per_node * k + c.
+// col_order: FESPMV_COLS_SORTED (Sec. 5.3, K1rs), _RENUMBERED (Sec. 5.2, K1r: renumbered,
+// in the input's order) or _ORIGINAL (Sec. 5.1, K1: the input numbering, not renumbered).
 int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
-                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort = false);
+                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort = false,
+                      int col_order = 0);
 // Stage 2: the K1/K2 warp slices of a permuted CSR (meta, col, src, sizes of `out`;
 // with_ppos: also each permuted entry's packed position).
 int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
@@ -91,7 +94,7 @@ int pack_slices(const std::vector<int64_t>& rp2, const std::vector<int32_t>& c2,
 // (message set).
 int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dofs_per_node,
                const double* node_xyz, int reorder, int sigma, int threshold, int vec,
-               Plan& out, NodeBlocks* nb = nullptr);
+               Plan& out, NodeBlocks* nb = nullptr, int col_order = 0);
 
 // Validates a host CSR (monotone offsets, columns in range); duplicates are
 // detected by build_plan for SLICED and by validate_csr_rows for CSR.
@@ -121,6 +124,7 @@ struct fespmv_mat {
 
     // FESPMV_FMT_SLICED
     int vec = 2;
+    int col_order = 0;                // FESPMV_COLS_*; ORIGINAL: x in the input numbering
     int64_t n_slices = 0;
     int64_t packed_len = 0;
     uint4* d_meta = nullptr;

@@ -653,7 +653,7 @@ extern "C" int spmv_apply_multi(fespmv_mat_t A, const void* X, void* Y, int32_t 
             set_error("spmv_apply_multi: bad argument");
             return FESPMV_ERR_INVALID_ARG;
         }
-        if (A->format != FESPMV_FMT_SLICED || A->max_lanes_log2 != 0) {
+        if (A->format != FESPMV_FMT_SLICED || A->max_lanes_log2 != 0 || A->col_order == FESPMV_COLS_ORIGINAL) {
             set_error("spmv_apply_multi needs a SLICED handle with one lane per row (threshold 0)");
             return FESPMV_ERR_UNSUPPORTED;
         }

@@ -88,7 +88,8 @@ static void morton_node_order(int64_t n_nodes, const double* xyz, std::vector<in
 }
 
 int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
-                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort) {
+                      const double* node_xyz, int reorder, int sigma, Permuted& out, bool node_sort,
+                      int col_order) {
     if (dpn <= 0) dpn = 1;
     if (n % dpn != 0) {
         set_error("n_rows %lld is not a multiple of dofs_per_node %d", (long long)n, dpn);
@@ -146,20 +147,30 @@ int order_and_permute(int64_t n, const int64_t* rowptr, const int32_t* colind, i
     out.s2.resize((size_t)nnz);
     out.diagpos.assign((size_t)n, -1);
     std::vector<std::pair<int32_t, int64_t>> row;
+    std::vector<int32_t> seen;
     for (int64_t i = 0; i < n; ++i) {
         int64_t o = out.perm[(size_t)i];
         row.clear();
+        // K1 keeps the input's column numbers; K1r / K1rs renumber them (c' = P^-1[c])
         for (int64_t p = rowptr[o]; p < rowptr[o + 1]; ++p)
-            row.emplace_back(out.pinv[(size_t)colind[p]], p);
-        std::sort(row.begin(), row.end());
-        for (size_t k = 0; k < row.size(); ++k) {
-            if (k > 0 && row[k].first == row[k - 1].first) {
-                set_error("duplicate column %d in row %lld", colind[row[k].second], (long long)o);
+            row.emplace_back(col_order == FESPMV_COLS_ORIGINAL ? colind[p] : out.pinv[(size_t)colind[p]], p);
+        if (col_order == FESPMV_COLS_SORTED) {
+            std::sort(row.begin(), row.end());
+        }
+        seen.clear();
+        for (const auto& e : row) seen.push_back(e.first);
+        std::sort(seen.begin(), seen.end());
+        for (size_t k = 1; k < seen.size(); ++k)
+            if (seen[k] == seen[k - 1]) {
+                set_error("duplicate column in row %lld", (long long)o);
                 return FESPMV_ERR_BAD_CSR;
             }
+        // the diagonal: new column i, or old column o when columns keep the input numbering
+        const int32_t dcol = col_order == FESPMV_COLS_ORIGINAL ? (int32_t)o : (int32_t)i;
+        for (size_t k = 0; k < row.size(); ++k) {
             out.c2[(size_t)out.rp2[(size_t)i] + k] = row[k].first;
             out.s2[(size_t)out.rp2[(size_t)i] + k] = row[k].second;
-            if (row[k].first == (int32_t)i) out.diagpos[(size_t)i] = row[k].second;
+            if (row[k].first == dcol) out.diagpos[(size_t)i] = row[k].second;
         }
     }
     return FESPMV_OK;
@@ -370,9 +381,9 @@ int pack_node_blocks(const std::vector<int64_t>& rp2, const std::vector<int32_t>
 
 int build_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int dpn,
                const double* node_xyz, int reorder, int sigma, int threshold, int V, Plan& out,
-               NodeBlocks* nb) {
+               NodeBlocks* nb, int col_order) {
     Permuted pm;
-    int rc = order_and_permute(n, rowptr, colind, dpn, node_xyz, reorder, sigma, pm, nb != nullptr);
+    int rc = order_and_permute(n, rowptr, colind, dpn, node_xyz, reorder, sigma, pm, nb != nullptr, col_order);
     if (rc) return rc;
     rc = pack_slices(pm.rp2, pm.c2, pm.s2, threshold, V, out, nb != nullptr);
     if (rc) return rc;

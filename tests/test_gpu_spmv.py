@@ -333,3 +333,28 @@ def test_full_size_shell_24x256x512():
     bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(bv).astype(np.float64), np.abs(x32).astype(np.float64))
     L = np.diff(p.rowptr).max()
     assert np.all(np.abs(yd.cpu().numpy().astype(np.float64) - yo) <= 2 * L * 2.0 ** -24 * bound)
+
+
+@pytest.mark.parametrize("tiles", [0, -1])
+@pytest.mark.parametrize("col_order", [fs.FESPMV_COLS_RENUMBERED, fs.FESPMV_COLS_ORIGINAL])
+def test_column_orders_k1_and_k1r(col_order, tiles):
+    """K1 (input column numbers) and K1r (renumbered, unsorted) handles: the FP64
+    product within the componentwise bound, input and host I/O; K1 handles take x
+    in the input numbering only and carry no CG."""
+    p = problem("elasticity_9")
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=128, tiles=tiles,
+                       col_order=col_order)
+    x = fegen.random_vector(p.n_rows, 31)
+    check_parity(p, apply(A, x), x)
+    yh = np.zeros(p.n_rows)
+    fs.spmv_apply(A, x.copy(), yh)
+    check_parity(p, yh, x)
+    xd = torch.from_numpy(x).cuda()
+    if col_order == fs.FESPMV_COLS_ORIGINAL:
+        with pytest.raises(fs.FespmvError):
+            fs.spmv_apply(A, xd, torch.empty_like(xd), fs.FESPMV_IO_PERMUTED)
+        with pytest.raises(fs.FespmvError):
+            fs.cg_solve(A, xd, torch.zeros_like(xd))
+    else:
+        res = fs.cg_solve(A, xd, torch.zeros_like(xd), tol=1e-10)
+        assert res["status"] == 0

@@ -184,3 +184,27 @@ def test_committed_headline_profile_matches_the_kernel_source():
     traffic, source = bench.profile_traffic("tiled_f64")
     assert traffic is not None, source
     assert 3.0e8 < traffic < 4.3e8          # the tiled layout's bytes, below the algorithmic 420 MB
+
+
+@pytest.mark.parametrize("col_order", ["sorted", "renumbered", "original"])
+def test_column_orders_of_the_host_plan(col_order):
+    """The planner's K1rs / K1r / K1 column numbering (Sec. 5.1-5.3) against the
+    oracle's definition, bit for bit, without a GPU."""
+    fs = pytest.importorskip("paper_1501_00324_gb300")
+    from oracle import layout
+    p = fegen.cube_elasticity(5, 111)
+    code = {"sorted": 0, "renumbered": 1, "original": 2}[col_order]
+    pl = fs.spmv_plan(p.rowptr, p.colind, p.node_xyz, 3, sigma=96, vec=2, col_order=code)
+    P = layout.row_permutation(p.rowptr, 3, p.node_xyz, "morton", 96)
+    assert np.array_equal(pl["perm"], P)
+    rp2, c2, v2, vmap = layout.permute_csr(p.rowptr, p.colind, p.values, P, col_order)
+    meta, col, val, pmap = layout.pack(rp2, c2, v2, 0, 2)
+    assert np.array_equal(pl["meta"], meta) and np.array_equal(pl["cols"], col)
+    src = np.full(len(col), -1, dtype=np.int64)
+    inp = np.empty_like(vmap)
+    inp[vmap] = np.arange(len(vmap))
+    src[pmap] = inp
+    assert np.array_equal(pl["srcmap"], src)
+    if col_order != "sorted":   # an FE row in the input's order is not sorted after renumbering
+        a, b = int(rp2[40]), int(rp2[41])
+        assert not np.all(np.diff(c2[a:b]) > 0) or col_order == "original"
