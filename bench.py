@@ -789,6 +789,7 @@ def configs_summary(line):
             "f64_spmv_gbs", "f32_spmv_gbs", "bf16_spmv_gbs")},
         "C4_batched": {
             "meshes": _pick(line, "batched", "meshes"), "solves_per_s": _pick(line, "batched", "solves_per_s"),
+            "frac_of_measured": _pick(line, "batched", "roofline", "frac"),
             "batch_s": _pick(line, "batched", "batched_reliable_s"),
             "rhs32_solves_per_s": _pick(line, "cg_multi32", "f32_reliable", "solves_per_s")},
     }
@@ -1042,6 +1043,15 @@ def bench_batched(fs, torch, args):
 
     batch_rel_s, res_rel = batch_time(fs.FESPMV_CG_RELIABLE)
     batch_s, res = batch_time(0)
+    # the batch's roofline: every problem's inner steps times the algorithmic bytes of one
+    # FP32 product of it (values + int32 indices, float x and y), over the batch's time
+    alg = sum(r["iters"] * (p.nnz * 8 + p.n_rows * 8) for r, p in zip(res_rel, ps))
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roof = {"bound": "hbm", "achieved": round(alg / batch_rel_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(alg / batch_rel_s / 1e9 / peak, 4),
+            "note": "sum over problems of inner steps x (nnz x 8 + n x 8) bytes / batch time; the FP64 "
+                    "residual products of the reliable updates are not counted"}
     info = fs.batch_get_info(B)
     fs.batch_destroy(B)
     seq = {}
@@ -1066,6 +1076,9 @@ def bench_batched(fs, torch, args):
             "autotune": {k: tune[k] for k in ("vec", "threshold", "block", "best_us", "tried")},
             "nnz_total": info["nnz"], "gen_s": round(gen_s, 1), "create_s": round(create_s, 1),
             "batched_reliable_s": round(batch_rel_s, 4),
+            "solver": "reliable updates: one launch of thread-block clusters (8 CTAs), each cluster "
+                      "solving whole problems largest first; restarted refinement: lockstep graphs",
+            "roofline": roof,
             "solves_per_s": round(len(ps) / batch_rel_s, 1),
             "max_updates": max(r["outer"] for r in res_rel), "max_iters": max(r["iters"] for r in res_rel),
             "batched_restarted_s": round(batch_s, 4),

@@ -13,11 +13,13 @@
 // problem, fixed order), problems that have finished are skipped by every
 // kernel, and one CUDA graph holds `check_every` inner iterations of the whole
 // batch (five launches per iteration, whatever the number of problems).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <numeric>
 #include <thread>
 
 #include "cg_run.h"
@@ -52,6 +54,9 @@ struct fespmv_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0, graph_bf16 = -1;
+    // the cluster solver (reliable updates): problems largest first, a work counter
+    int32_t* d_order = nullptr;
+    unsigned* d_next = nullptr;
 };
 
 namespace fespmv {
@@ -261,6 +266,183 @@ __global__ void b_outer_count(int count, BScal* sc) {
     if (j < count && sc[j].status_out == CG_RUNNING) sc[j].outer += 1;
 }
 
+// ------------------------------------------------------------------ cluster solver
+//
+// Reliable-update refinement (the algorithm of cg_solve with FESPMV_CG_RELIABLE,
+// per problem) for the whole batch in one persistent launch: thread-block
+// clusters of kClusterCtas CTAs take problems from a work counter (largest
+// first) and each runs its problem's iteration to the end, synchronising only
+// within the cluster (hardware cluster barriers) and reducing dot products
+// through distributed shared memory: every CTA adds the CTAs' partial sums in
+// rank order, so all CTAs hold the same bits and take the same decisions.  No
+// grid-wide synchronisation and no host polling: finished problems cost nothing,
+// and a small problem's iterations cost a few cluster barriers each.
+namespace cgx = cooperative_groups;
+constexpr int kClusterCtas = 8;      // CTAs per cluster (the portable maximum) and
+constexpr int kClusterThreads = 256; // threads per CTA: two CTAs per SM, 38 clusters at once
+
+struct ClusterRed {
+    double slot[2][4];   // per-CTA partial sums, two slots used in turn
+    int job;
+};
+
+// Sum of K values over the cluster (fixed order: a block tree per CTA, then the
+// CTAs in rank order); every thread of every CTA returns the same sums.
+template <int K>
+__device__ __forceinline__ void cluster_sum(cgx::cluster_group& cl, ClusterRed& red, int& turn, double (&v)[K]) {
+    __shared__ double sh[K][kClusterThreads / 32];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < kClusterThreads / 32; ++w) t += sh[k][w];
+            red.slot[turn][k] = t;
+        }
+    cl.sync();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0.0;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) {
+        const double* rp = cl.map_shared_rank(&red.slot[turn][0], r);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += rp[k];
+    }
+    turn ^= 1;
+}
+
+template <typename VT, int V, int U>
+__global__ void __launch_bounds__(kClusterThreads, 2) b_cluster_reliable(
+    const uint4* __restrict__ meta, const int32_t* __restrict__ col, const VT* __restrict__ val32,
+    const double* __restrict__ val64, const double* __restrict__ scale, const double* __restrict__ b,
+    double* __restrict__ x, double* __restrict__ q64, float* __restrict__ w, float* __restrict__ rin,
+    float* __restrict__ p, float* __restrict__ q32, const int64_t* __restrict__ pslice,
+    const int64_t* __restrict__ pwarp, const int32_t* __restrict__ order, int count, unsigned* next,
+    BScal* sc, double tol2, double in2, int has_x0, int max_iter, int max_outer) {
+    cgx::cluster_group cl = cgx::this_cluster();
+    __shared__ ClusterRed red;
+    const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)rank * (kClusterThreads / 32) + (threadIdx.x >> 5), nwarps = (int64_t)C * (kClusterThreads / 32);
+    const int64_t tid = (int64_t)rank * kClusterThreads + threadIdx.x, nthreads = (int64_t)C * kClusterThreads;
+    int turn = 0;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) red.job = (int)atomicAdd(next, 1u);
+        cl.sync();
+        const int job = *cl.map_shared_rank(&red.job, 0);
+        if (job >= count) break;
+        const int j = order[job];
+        const int64_t s0 = pslice[j], s1 = pslice[j + 1], r0 = 32 * pwarp[j], r1 = 32 * pwarp[j + 1];
+        int iters = 0, outer = 0, status = CG_RUNNING;
+        double rho = 0.0, rr = 0.0, bb = 0.0, thresh2 = 0.0, thresh_in = 0.0, prev = INFINITY;
+        bool first = true;
+        for (;;) {
+            // ---- FP64 residual: r = b - A x, r_in = float(S r), w = 0 (x += S w first after a step)
+            if (!first) {
+                for (int64_t i = r0 + tid; i < r1; i += nthreads) {
+                    x[i] = fma(scale[i], (double)w[i], x[i]);
+                }
+                cl.sync();
+            }
+            if (!first || has_x0) {
+                for (int64_t sl = s0 + gw; sl < s1; sl += nwarps) {
+                    const uint4 m = meta[sl];
+                    const double sum = sliced_row_sum_f64<V, U>(m, col, val64, x, lane);
+                    const int lt = (int)m.w;
+                    if ((lane & ((1 << lt) - 1)) == 0) q64[(int64_t)m.z + (lane >> lt)] = sum;
+                }
+                cl.sync();
+            }
+            double v3[3] = {0.0, 0.0, 0.0};
+            const bool ax = !first || has_x0;
+            for (int64_t i = r0 + tid; i < r1; i += nthreads) {
+                const double bi = b[i];
+                const double ri = ax ? bi - q64[i] : bi;
+                const float rs = (float)(scale[i] * ri);
+                w[i] = 0.0f;
+                rin[i] = rs;
+                if (first) p[i] = rs;
+                v3[0] = fma(ri, ri, v3[0]);
+                v3[1] = fma((double)rs, (double)rs, v3[1]);
+                v3[2] = fma(bi, bi, v3[2]);
+            }
+            cluster_sum<3>(cl, red, turn, v3);
+            rr = v3[0];
+            const double rhs2 = v3[1];
+            if (first) {
+                bb = v3[2];
+                thresh2 = tol2 * bb;
+            }
+            if (!isfinite(rr) || !isfinite(rhs2)) { status = CG_BREAKDOWN; break; }
+            if (rr <= thresh2) { status = CG_CONVERGED; break; }
+            if (outer >= max_outer || iters >= max_iter || !(rr < prev)) { status = CG_MAXITER; break; }
+            prev = rr;
+            // the kept direction takes the replaced residual: p = r_in + beta p (p = r_in first)
+            const double beta0 = first ? 0.0 : rhs2 / rho;
+            rho = rhs2;
+            thresh_in = fmax(in2 * rhs2, rr > 0.0 ? tol2 * bb * rhs2 / rr : 0.0);
+            if (!first) {
+                const float bt = (float)beta0;
+                for (int64_t i = r0 + tid; i < r1; i += nthreads) p[i] = fmaf(bt, p[i], rin[i]);
+            }
+            first = false;
+            cl.sync();
+            // ---- inner CG steps on B until the reliable-update test
+            for (;;) {
+                double v1[1] = {0.0};
+                for (int64_t sl = s0 + gw; sl < s1; sl += nwarps) {
+                    const uint4 m = meta[sl];
+                    const float sum = sliced_row_sum_low<VT, V, U>(m, col, val32, p, lane);
+                    const int lt = (int)m.w;
+                    if ((lane & ((1 << lt) - 1)) == 0) {
+                        const int64_t row = (int64_t)m.z + (lane >> lt);
+                        q32[row] = sum;
+                        v1[0] = fma((double)p[row], (double)sum, v1[0]);
+                    }
+                }
+                cluster_sum<1>(cl, red, turn, v1);
+                const double pq = v1[0];
+                if (!(pq > 0.0) || !isfinite(pq)) { status = CG_BREAKDOWN; break; }
+                const float a = (float)(rho / pq);
+                double v2[1] = {0.0};
+                for (int64_t i = r0 + tid; i < r1; i += nthreads) {
+                    w[i] = fmaf(a, p[i], w[i]);
+                    const float ri = fmaf(-a, q32[i], rin[i]);
+                    rin[i] = ri;
+                    v2[0] = fma((double)ri, (double)ri, v2[0]);
+                }
+                cluster_sum<1>(cl, red, turn, v2);
+                const double rn = v2[0];
+                ++iters;
+                if (!isfinite(rn)) { status = CG_BREAKDOWN; break; }
+                if (rn <= thresh_in || iters >= max_iter) break;   // -> reliable update
+                const float bt = (float)(rn / rho);
+                rho = rn;
+                for (int64_t i = r0 + tid; i < r1; i += nthreads) p[i] = fmaf(bt, p[i], rin[i]);
+                cl.sync();
+            }
+            if (status != CG_RUNNING) break;
+            ++outer;
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            BScal& o = sc[j];
+            o.status_out = status;
+            o.status_in = CG_CONVERGED;
+            o.iters = iters;
+            o.outer = outer;
+            o.rr = rr;
+            o.bb = bb;
+        }
+        cl.sync();   // the job word and the reduction slots are reused by the next problem
+    }
+    cl.sync();       // no CTA leaves while another may still read its shared memory
+}
+
 // ------------------------------------------------------------------ host side
 
 static void destroy_batch(fespmv_batch* B) {
@@ -268,7 +450,7 @@ static void destroy_batch(fespmv_batch* B) {
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->cap) cudaStreamDestroy(B->cap);
     void* ptrs[] = {B->d_slice_prob, B->d_warp_prob, B->d_pslice, B->d_pwarp, B->d_perm_g, B->d_pinv_g,
-                    B->x, B->b, B->q, B->part, B->w32, B->r32, B->p32, B->q32, B->sc};
+                    B->x, B->b, B->q, B->part, B->w32, B->r32, B->p32, B->q32, B->sc, B->d_order, B->d_next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (B->h_sc) cudaFreeHost(B->h_sc);
@@ -533,6 +715,75 @@ static int batch_graph(fespmv_batch* B, int bf16, int chunk) {
     return FESPMV_OK;
 }
 
+// The cluster solver's launch: as many clusters of kClusterCtas CTAs as are resident
+// at once (at most one per problem), a work counter set to zero first.
+template <typename VT, int V>
+static int launch_cluster_t(fespmv_batch* B, const VT* val32, double tol2, double in2, int has_x0,
+                            int max_iter, int max_outer, cudaStream_t s) {
+    constexpr int U = (V == 4) ? 2 : (V == 2 ? 4 : 8);
+    fespmv_mat* M = B->M;
+    auto kernel = b_cluster_reliable<VT, V, U>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0, csize = kClusterCtas;
+    for (; csize >= 1; csize /= 2) {   // the largest cluster size the device places
+        attr[0].val.clusterDim.x = csize;
+        cfg.gridDim = dim3(csize);
+        if (cudaOccupancyMaxActiveClusters(&clusters, (void*)kernel, &cfg) == cudaSuccess && clusters > 0) break;
+        cudaGetLastError();
+    }
+    if (csize < 1 || clusters < 1) {
+        set_error("batch_cg_solve: no thread-block cluster fits the device");
+        return FESPMV_ERR_UNSUPPORTED;
+    }
+    clusters = std::min(clusters, (int)B->count);
+    cfg.gridDim = dim3((unsigned)(clusters * csize));
+    FESPMV_CUDA(cudaMemsetAsync(B->d_next, 0, sizeof(unsigned), s));
+    FESPMV_CUDA(cudaLaunchKernelEx(&cfg, kernel, (const uint4*)M->d_meta, (const int32_t*)M->d_col, val32,
+                                   (const double*)M->d_val, (const double*)M->d_scale, (const double*)B->b, B->x,
+                                   B->q, B->w32, B->r32, B->p32, B->q32, (const int64_t*)B->d_pslice,
+                                   (const int64_t*)B->d_pwarp, (const int32_t*)B->d_order, (int)B->count,
+                                   B->d_next, B->sc, tol2, in2, has_x0, max_iter, max_outer));
+    return FESPMV_OK;
+}
+
+template <typename VT>
+static int launch_cluster_v(fespmv_batch* B, const VT* val32, double tol2, double in2, int has_x0, int max_iter,
+                            int max_outer, cudaStream_t s) {
+    switch (B->M->vec) {
+        case 1: return launch_cluster_t<VT, 1>(B, val32, tol2, in2, has_x0, max_iter, max_outer, s);
+        case 4: return launch_cluster_t<VT, 4>(B, val32, tol2, in2, has_x0, max_iter, max_outer, s);
+        default: return launch_cluster_t<VT, 2>(B, val32, tol2, in2, has_x0, max_iter, max_outer, s);
+    }
+}
+
+// Problems in decreasing order of their rows (the largest start first) and the
+// work counter, on the first cluster solve.
+static int ensure_cluster_work(fespmv_batch* B, cudaStream_t s) {
+    if (B->d_order) return FESPMV_OK;
+    std::vector<int32_t> order((size_t)B->count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+        return B->pwarp[(size_t)a + 1] - B->pwarp[(size_t)a] > B->pwarp[(size_t)c + 1] - B->pwarp[(size_t)c];
+    });
+    int rc;
+    if ((rc = device_alloc(B->M, (void**)&B->d_order, sizeof(int32_t) * (size_t)B->count, "batch order")) ||
+        (rc = device_alloc(B->M, (void**)&B->d_next, sizeof(unsigned), "batch work counter")))
+        return rc;
+    FESPMV_CUDA(cudaMemcpyAsync(B->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, s));
+    FESPMV_CUDA(cudaStreamSynchronize(s));
+    return FESPMV_OK;
+}
+
 static int read_bsc(fespmv_batch* B, cudaStream_t s) {
     FESPMV_CUDA(cudaMemcpyAsync(B->h_sc, B->sc, sizeof(BScal) * B->count, cudaMemcpyDeviceToHost, s));
     FESPMV_CUDA(cudaStreamSynchronize(s));
@@ -593,7 +844,15 @@ static int batch_solve_impl(fespmv_batch* B, const double* b, double* x, const c
     const double tol2 = o.tol * o.tol, in2 = o.inner_tol * o.inner_tol;
     const int reliable = (o.flags & FESPMV_CG_RELIABLE) ? 1 : 0;
     const int64_t max_graphs = (int64_t)o.max_iter / o.check_every + 3;
-    for (int step = 0;; ++step) {
+    if (reliable) {   // every problem to the end in one launch of thread-block clusters
+        if ((rc = ensure_cluster_work(B, s))) return rc;
+        rc = bf16 ? launch_cluster_v<__nv_bfloat16>(B, reinterpret_cast<const __nv_bfloat16*>(M->d_val16), tol2, in2,
+                                                      x0 ? 1 : 0, o.max_iter, o.max_outer, s)
+                  : launch_cluster_v<float>(B, M->d_val32, tol2, in2, x0 ? 1 : 0, o.max_iter, o.max_outer, s);
+        if (rc) return rc;
+        if ((rc = read_bsc(B, s))) return rc;
+    }
+    for (int step = 0; !reliable; ++step) {
         const bool ax = x0 || step > 0;
         if (ax && (rc = launch_spmv(M, B->x, B->q, s))) return rc;
         b_residual<<<grid_for(np, 256), 256, 0, s>>>(np, B->b, ax ? B->q : nullptr, M->d_scale, B->w32,
