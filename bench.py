@@ -514,6 +514,16 @@ def main():
             extra["multi32_fp32"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
                                      "us_per_apply": round(tmean * 1e6, 1),
                                      "us_per_rhs": round(tmean * 1e6 / 32, 2)}
+            # the same on 3x3 node blocks (one X row gathered per column node serves 3 rows)
+            NBm = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
+                                 vec=args.extras_vec, node_blocks=3, precisions=fs.FESPMV_PREC_F32)
+            fm = lambda: fs.spmv_apply_multi(NBm, X32, Y32, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+            fm()
+            tmean = back_to_back(fm, max(10, args.steps // 8)) * 1e-3
+            extra["multi32_fp32_node_blocks"] = {"gbs": round((nnz * 8 + n * 32 * 8) / tmean / 1e9, 1),
+                                                 "us_per_apply": round(tmean * 1e6, 1),
+                                                 "us_per_rhs": round(tmean * 1e6 / 32, 2)}
+            fs.spmv_destroy(NBm)
             del X32, Y32
             # the same with the FP64 matrix and FP64 right-hand sides
             X64 = torch.rand((n, 32), dtype=torch.float64, device=dev)
@@ -791,7 +801,8 @@ def configs_summary(line):
             "meshes": _pick(line, "batched", "meshes"), "solves_per_s": _pick(line, "batched", "solves_per_s"),
             "frac_of_measured": _pick(line, "batched", "roofline", "frac"),
             "batch_s": _pick(line, "batched", "batched_reliable_s"),
-            "rhs32_solves_per_s": _pick(line, "cg_multi32", "f32_reliable", "solves_per_s")},
+            "rhs32_solves_per_s": _pick(line, "cg_multi32", "f32_reliable", "solves_per_s"),
+            "rhs32_product_gbs": [_pick(line, "multi32_fp32", "gbs"), _pick(line, "multi32_fp32_node_blocks", "gbs")]},
     }
     sh = line.get("shell_24x256x512") or {}
     for k in ("cg_f64", "cg_f32_reliable", "cg_bf16_reliable", "cg_bf16_flexible"):
@@ -1193,13 +1204,13 @@ def block_diagonal(ps):
 
 def bench_cg_multi(fs, torch, p, args):
     """32 right-hand sides of the same matrix solved to 1e-10 in lockstep
-    (cg_solve_multi): FP32 values with FP64 reliable updates (timed over a few
-    solves after a warm-up that builds the graphs), and FP64 (one solve) -- on a
-    handle that keeps float pairs, so that every FP64 product of both solves runs
-    on the FP32 pipe (within the FP64 bound)."""
+    (cg_solve_multi): FP32 values with FP64 reliable updates, their products on 3x3
+    node blocks (timed over a few solves after a warm-up that builds the graphs),
+    and FP64 (one solve) -- on a handle that keeps float pairs, so that every FP64
+    product of both solves runs on the FP32 pipe (within the FP64 bound)."""
     import fegen
     E = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma, vec=args.extras_vec,
-                       precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_DF64)
+                       node_blocks=3, precisions=fs.FESPMV_PREC_F32 | fs.FESPMV_PREC_DF64)
     k = 32
     B = np.stack([fegen.random_vector(p.n_rows, 1700 + j) for j in range(k)], axis=1)
     B[:, 0] = manufactured_rhs(fs, torch, E, p)

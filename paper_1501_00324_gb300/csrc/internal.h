@@ -199,6 +199,10 @@ unsigned grid_for(int64_t work, int block);
 int launch_build_scaled(fespmv_mat* A, cudaStream_t s);
 int launch_nb3_refresh(fespmv_mat* A, cudaStream_t s);   // node-block copies from the scalar ones
 int launch_nb3_product(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
+int launch_nb3_multi(const fespmv_mat* A, const float* X, float* Y, int kw, cudaStream_t s);  // FP32, KW = kw
+// The lockstep CG's FP32 product with per-block column sums of p.q (part == nullptr:
+// only the grid, i.e. the number of partial rows, is returned).
+unsigned launch_nb3_multi_dot(const fespmv_mat* A, const float* P, float* Q, int kw, double* part, cudaStream_t s);
 // y = B x with the FP32 (precision FESPMV_PREC_F32) or BF16 copy, handle numbering.
 int launch_spmv_low(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_gather_f32(const float* in, const int32_t* idx, float* out, int64_t n, cudaStream_t s);

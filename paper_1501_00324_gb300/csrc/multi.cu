@@ -598,6 +598,9 @@ static int apply_multi_t(fespmv_mat* A, const XT* X, XT* Y, int k, int flags, cu
         } else {
             launch_multi<double, double>(A, A->d_val, xs, ys, kw, s);  // FP64 values and sums
         }
+    } else if (A->nb && A->d_nb32) {
+        int rc = launch_nb3_multi(A, xs, ys, kw, s);                 // FP32 node blocks
+        if (rc) return rc;
     } else {
         launch_multi<float, float>(A, A->d_val32, xs, ys, kw, s);   // FP32 copy of S A S
     }
@@ -612,6 +615,7 @@ unsigned launch_multi_dot(const fespmv_mat* A, const void* P, void* Q, int kw, b
                           cudaStream_t s) {
     if (f64)
         return multi_dot<double, double>(A, A->d_val, (const double*)P, (double*)Q, kw, part, s);
+    if (A->nb && A->d_nb32) return launch_nb3_multi_dot(A, (const float*)P, (float*)Q, kw, part, s);
     return multi_dot<float, float>(A, A->d_val32, (const float*)P, (float*)Q, kw, part, s);
 }
 

@@ -13,6 +13,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "spmv_device.cuh"
 #include "nodeblock_device.cuh"
@@ -59,6 +61,215 @@ __global__ void __launch_bounds__(256, 8) nb3_product_tiled(const uint4* __restr
         y[3 * node] = s[0];
         y[3 * node + 1] = s[1];
         y[3 * node + 2] = s[2];
+    }
+}
+
+// Y = B X for X, Y row-major n x KW (KW = 4..32 right-hand sides, FP32): KW / 4
+// lanes per node row, each lane 4 consecutive right-hand sides of the node's 3
+// rows; per block the 9 values (the same words for the row's lanes) and one
+// 16-byte load of each of the 3 X rows the block's column node names, so one X
+// row serves the 3 rows of the node.  The matrix streams once for all columns.
+template <int KW, int NV, int U>
+__global__ void __launch_bounds__(256) nb3_multi(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
+                                                 const float* __restrict__ val, const float* __restrict__ X,
+                                                 float* __restrict__ Y, int64_t n_nodes, int64_t n_slices) {
+    constexpr int LPR = KW / (4 * NV), RPW = 32 / LPR;   // lanes per node row, node rows per warp
+    const int lane = threadIdx.x & 31, g = lane / LPR, c = lane % LPR;
+    const int64_t nr = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * RPW + g;   // node row slot
+    if (nr >= n_slices * 32) return;   // RPW divides 32: a warp never straddles two slices
+    const uint4 m = meta[nr >> 5];
+    const int ls = (int)(nr & 31);
+    const int64_t off = (int64_t)m.x * 32, plane = 32 * (int64_t)m.y;
+    const int w = (int)m.y;
+    const int32_t* cp = col + off + ls;
+    const float* vp = val + 9 * off + ls;
+    float acc[3][4 * NV];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 4 * NV; ++j) acc[a][j] = 0.0f;
+    int st = 0;
+    auto block = [&](int32_t J, const float (&v)[9]) {
+        if (J < 0) return;
+        const float* xp = X + 3 * (int64_t)J * KW + 4 * NV * c;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int h = 0; h < NV; ++h) {
+                const float4 xb = __ldg(reinterpret_cast<const float4*>(xp + b * KW + 4 * h));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[a][4 * h + 0] = fmaf(v[3 * a + b], xb.x, acc[a][4 * h + 0]);
+                    acc[a][4 * h + 1] = fmaf(v[3 * a + b], xb.y, acc[a][4 * h + 1]);
+                    acc[a][4 * h + 2] = fmaf(v[3 * a + b], xb.z, acc[a][4 * h + 2]);
+                    acc[a][4 * h + 3] = fmaf(v[3 * a + b], xb.w, acc[a][4 * h + 3]);
+                }
+            }
+    };
+    for (; st + U <= w; st += U) {
+        int32_t J[U];
+        float v[U][9];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            J[u] = ld_stream(cp + 32 * (st + u));
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[u][k] = ld_stream(vp + k * plane + 32 * (st + u));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) block(J[u], v[u]);
+    }
+    for (; st < w; ++st) {
+        float v[9];
+        const int32_t J = ld_stream(cp + 32 * st);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + k * plane + 32 * st);
+        block(J, v);
+    }
+    const int64_t node = (int64_t)m.z + ls;
+    if (node < n_nodes)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int h = 0; h < NV; ++h)
+                *reinterpret_cast<float4*>(Y + (3 * node + a) * KW + 4 * NV * c + 4 * h) =
+                    make_float4(acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]);
+}
+
+template <int KW, int NV, int U>
+static void nb3_multi_launch(const fespmv_mat* A, const float* X, float* Y, cudaStream_t s) {
+    const int64_t warps = A->nb_slices * 32 / (32 / (KW / (4 * NV)));
+    nb3_multi<KW, NV, U><<<grid_for(warps * 32, 256), 256, 0, s>>>(A->d_nbmeta, A->d_nbcol, A->d_nb32, X, Y,
+                                                                   A->n / 3, A->nb_slices);
+}
+
+int launch_nb3_multi(const fespmv_mat* A, const float* X, float* Y, int kw, cudaStream_t s) {
+    if (A->n == 0) return FESPMV_OK;
+    switch (kw) {
+        case 4: nb3_multi_launch<4, 1, 2>(A, X, Y, s); break;
+        case 8: nb3_multi_launch<8, 1, 2>(A, X, Y, s); break;
+        case 16: nb3_multi_launch<16, 1, 2>(A, X, Y, s); break;
+        default: nb3_multi_launch<32, 1, 2>(A, X, Y, s); break;
+    }
+    FESPMV_CUDA(cudaGetLastError());
+    return FESPMV_OK;
+}
+
+// The lockstep multi-RHS CG's product on node blocks: Q = B P as nb3_multi, and
+// for every column j the sum of p_ij q_ij over the rows this block covered at
+// part[blockIdx.x * KW + j] (per lane in float over its node's 3 rows, then in
+// FP64 over its units, then over the groups of a warp and the warps in order).
+// Persistent: warps stride over units of 32 / (KW / 4) node rows.
+template <int KW, int U>
+__global__ void __launch_bounds__(128, 6) nb3_multi_dot(const uint4* __restrict__ meta,
+                                                        const int32_t* __restrict__ col,
+                                                        const float* __restrict__ val, const float* __restrict__ P,
+                                                        float* __restrict__ Q, int64_t n_nodes, int64_t n_slices,
+                                                        double* __restrict__ part) {
+    constexpr int LPR = KW / 4, RPW = 32 / LPR;
+    __shared__ double sh[4][KW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, g = lane / LPR, c = lane % LPR;
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t units = n_slices * 32 / RPW;
+    for (int64_t u = (int64_t)blockIdx.x * 4 + wib; u < units; u += (int64_t)gridDim.x * 4) {
+        const int64_t nr = u * RPW + g;
+        const uint4 m = meta[nr >> 5];
+        const int ls = (int)(nr & 31);
+        const int64_t off = (int64_t)m.x * 32, plane = 32 * (int64_t)m.y;
+        const int w = (int)m.y;
+        const int32_t* cp = col + off + ls;
+        const float* vp = val + 9 * off + ls;
+        float acc[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[a][j] = 0.0f;
+        auto block = [&](int32_t J, const float (&v)[9]) {
+            if (J < 0) return;
+            const float* xp = P + 3 * (int64_t)J * KW + 4 * c;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float4 xb = __ldg(reinterpret_cast<const float4*>(xp + b * KW));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[a][0] = fmaf(v[3 * a + b], xb.x, acc[a][0]);
+                    acc[a][1] = fmaf(v[3 * a + b], xb.y, acc[a][1]);
+                    acc[a][2] = fmaf(v[3 * a + b], xb.z, acc[a][2]);
+                    acc[a][3] = fmaf(v[3 * a + b], xb.w, acc[a][3]);
+                }
+            }
+        };
+        int st = 0;
+        for (; st + U <= w; st += U) {
+            int32_t J[U];
+            float v[U][9];
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) {
+                J[uu] = ld_stream(cp + 32 * (st + uu));
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[uu][k] = ld_stream(vp + k * plane + 32 * (st + uu));
+            }
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) block(J[uu], v[uu]);
+        }
+        for (; st < w; ++st) {
+            float v[9];
+            const int32_t J = ld_stream(cp + 32 * st);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + k * plane + 32 * st);
+            block(J, v);
+        }
+        const int64_t node = (int64_t)m.z + ls;
+        if (node < n_nodes) {
+            float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int64_t row = 3 * node + a;
+                *reinterpret_cast<float4*>(Q + row * KW + 4 * c) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                const float4 pv = __ldg(reinterpret_cast<const float4*>(P + row * KW + 4 * c));
+                t[0] = fmaf(pv.x, acc[a][0], t[0]);
+                t[1] = fmaf(pv.y, acc[a][1], t[1]);
+                t[2] = fmaf(pv.z, acc[a][2], t[2]);
+                t[3] = fmaf(pv.w, acc[a][3], t[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) d[j] += (double)t[j];
+        }
+    }
+    // lanes with the same c hold the same columns: sum over the warp's groups
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
+    if (g == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[wib][4 * c + j] = d[j];
+    __syncthreads();
+    if (threadIdx.x < KW)
+        part[(int64_t)blockIdx.x * KW + threadIdx.x] =
+            ((sh[0][threadIdx.x] + sh[1][threadIdx.x]) + sh[2][threadIdx.x]) + sh[3][threadIdx.x];
+}
+
+template <int KW>
+static unsigned nb3_multi_dot_kw(const fespmv_mat* A, const float* P, float* Q, double* part, cudaStream_t s) {
+    auto kernel = nb3_multi_dot<KW, 2>;
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    const int64_t units = A->nb_slices * 32 / (32 / (KW / 4));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (units + 3) / 4));
+    if (part) kernel<<<grid, 128, 0, s>>>(A->d_nbmeta, A->d_nbcol, A->d_nb32, P, Q, A->n / 3, A->nb_slices, part);
+    return grid;
+}
+
+unsigned launch_nb3_multi_dot(const fespmv_mat* A, const float* P, float* Q, int kw, double* part, cudaStream_t s) {
+    switch (kw) {
+        case 4: return nb3_multi_dot_kw<4>(A, P, Q, part, s);
+        case 8: return nb3_multi_dot_kw<8>(A, P, Q, part, s);
+        case 16: return nb3_multi_dot_kw<16>(A, P, Q, part, s);
+        default: return nb3_multi_dot_kw<32>(A, P, Q, part, s);
     }
 }
 

@@ -290,3 +290,34 @@ def test_multi_cg_full_size_elasticity_64_32_rhs():
     assert all(r["status"] == 0 and r["true_relres"] <= 1e-10 for r in res)
     for j in (0, 17, 31):
         assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+
+
+@pytest.mark.parametrize("reliable", [True, False])
+def test_multi_cg_on_node_blocks(reliable):
+    """The lockstep FP32 solves with their products on 3x3 node blocks: every column
+    meets the FP64 tolerance, agrees with the oracle's PCG, stays within the
+    reliable-update step bound, and is bitwise independent of the other columns."""
+    p = fegen.cube_elasticity(8, 340)
+    k = 13
+    B = rhs(p, k, 341)
+    A = make(p, node_blocks=3)
+    assert fs.spmv_get_info(A)["node_blocks"] == 3
+    flags = fs.FESPMV_CG_RELIABLE if reliable else 0
+    kw = dict(tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=flags)
+    rc, X, res = solve(A, B, **kw)
+    assert rc == fs.FESPMV_OK
+    cond = cond_of(p)
+    for j in range(k):
+        assert res[j]["status"] == 0, (j, res[j])
+        assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+        xo, _ = oracle.pcg(p.rowptr, p.colind, p.values, B[:, j], tol=1e-10)
+        assert np.linalg.norm(X[:, j] - xo) / np.linalg.norm(xo) <= cond * 2e-10
+        if reliable:
+            _, info = oracle.refine_reliable(p.rowptr, p.colind, p.values, B[:, j], tol=1e-10)
+            assert res[j]["iters"] <= 1.3 * info["iters"] + 5, (j, res[j], info)
+    order = np.arange(k)[::-1]
+    _, X2, r2 = solve(A, B[:, order], **kw)
+    for j in range(k):
+        jj = int(np.where(order == j)[0][0])
+        assert np.array_equal(X[:, j].view(np.uint64), X2[:, jj].view(np.uint64)), j
+        assert res[j]["iters"] == r2[jj]["iters"]

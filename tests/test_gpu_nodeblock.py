@@ -150,3 +150,24 @@ def test_node_blocks_rejected_without_three_dofs():
     q = fegen.cube_elasticity(4, 98)
     with pytest.raises(fs.FespmvError):     # nothing to store in blocks without FP32 / BF16 values
         fs.spmv_create(q.rowptr, q.colind, q.values, q.node_xyz, 3, node_blocks=3)
+
+
+@pytest.mark.parametrize("k", [1, 4, 7, 16, 32])
+def test_multi_rhs_product_on_node_blocks(k):
+    """Y = B X with FP32 node blocks, every column against the oracle's float product
+    (bound of the single products), host-side padding of k to 4/8/16/32 included."""
+    p = fegen.cube_elasticity(9, 99)
+    A = make(p, 96, precisions=fs.FESPMV_PREC_F32)
+    bv = oracle.scaled_values(p.rowptr, p.colind, p.values, "f32")
+    X = np.stack([fegen.random_vector(p.n_rows, 200 + j) for j in range(k)], axis=1).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Yd = torch.full_like(Xd, float("nan"))
+    fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F32)
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy()
+    L = np.diff(p.rowptr).max()
+    for j in range(k):
+        x = np.ascontiguousarray(X[:, j])
+        yo = oracle.csr_spmv_f32(p.rowptr, p.colind, bv, x)
+        bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(bv).astype(np.float64), np.abs(x).astype(np.float64))
+        assert np.all(np.abs(Y[:, j].astype(np.float64) - yo) <= 2 * L * 2.0 ** -24 * bound), j
