@@ -74,7 +74,8 @@ def parse_args():
                     help="time the assembly of the workload matrix from its element matrices")
     ap.add_argument("--multi-cg", type=int, default=1,
                     help="time cg_solve_multi with 32 right-hand sides on the workload matrix")
-    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "assembly"], default=None,
+    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "assembly",
+                                                 "nb_fp32", "nb_multi", "batch"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=16.0,
@@ -861,8 +862,10 @@ def bench_serving(fs, torch, args):
     t0 = time.perf_counter()
     pool = serving_pool(n_mesh, lo, hi, 1505)
     gen_s = time.perf_counter() - t0
+    # elasticity meshes keep their FP32 values as 3x3 node blocks (the refined solves' products)
     mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=1024,
-                           precisions=fs.FESPMV_PREC_F32) for p in pool]
+                           node_blocks=3 if p.dofs_per_node == 3 else 0, precisions=fs.FESPMV_PREC_F32)
+            for p in pool]
     rhs = [[fegen.random_vector(p.n_rows, 7000 + 10 * i + k) for k in range(2)]
            for i, p in enumerate(pool)]
     setup_s = time.perf_counter() - t0
@@ -1106,11 +1109,32 @@ def profile_piece(fs, torch, A, p, xp, args):
     --extras-vec), the CG pieces on the headline handle, as in the timed run."""
     n = p.n_rows
     t = args.profile_target
-    if t in ("multi", "multi64", "fp32", "cg_multi"):
+    if t in ("multi", "multi64", "fp32", "cg_multi", "nb_fp32", "nb_multi"):
         A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
-                           vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32)
+                           vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32,
+                           node_blocks=3 if t.startswith("nb_") else 0)
         xp = torch.rand_like(xp)          # any x in this handle's numbering
-    if t == "multi":
+    if t == "batch":
+        # the 256-cube batch of the bench, one reliable-update solve per run
+        import fegen
+        rng = np.random.default_rng(2000)
+        sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=args.batch_meshes))
+        ps = [fegen.valid_seed(lambda sd: fegen.cube_laplace(max(3, round(N ** (1 / 3))), sd), 2000 + i)
+              for i, N in enumerate(sizes)]
+        Bt = fs.batch_create([(q.rowptr, q.colind, q.values, q.node_xyz, 1) for q in ps], sigma=1024)
+        bd = torch.from_numpy(np.concatenate([fegen.random_vector(q.n_rows, 5000 + j)
+                                              for j, q in enumerate(ps)])).cuda()
+        xb = torch.zeros_like(bd)
+        f = lambda: fs.batch_cg_solve(Bt, bd, xb, tol=1e-10, flags=fs.FESPMV_CG_RELIABLE)  # noqa: E731
+    elif t == "nb_fp32":
+        xs = xp.float()
+        ys = torch.empty_like(xs)
+        f = lambda: fs.spmv_apply_scaled(A, xs, ys, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "nb_multi":
+        X = torch.rand((n, 32), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
+    elif t == "multi":
         X = torch.rand((n, 32), dtype=torch.float32, device="cuda")
         Y = torch.empty_like(X)
         f = lambda: fs.spmv_apply_multi(A, X, Y, fs.FESPMV_PREC_F32, fs.FESPMV_IO_PERMUTED)  # noqa: E731
