@@ -333,6 +333,8 @@ int spmv_plan_tiles(int64_t n_rows, int64_t n_slices, const uint32_t* meta, int6
 #define FESPMV_CG_RELIABLE     32 /* flag: refined precisions without restarts (reliable updates), below */
 #define FESPMV_CG_FLEXIBLE     64 /* flag: refined precisions as the preconditioner of a flexible
                                      FP64 CG (Notay 2000), below */
+#define FESPMV_CG_NO_CLUSTER  128 /* flag: keep the CUDA-graph iterations of reliable updates
+                                     on a small handle (see "Small handles" below) */
 
 typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2; 0 = 1e-10 */
@@ -427,6 +429,15 @@ typedef struct {
  * Each step applies a different polynomial in B, which the flexible recurrence
  * tolerates, so BF16 values converge to FP64 accuracy where refinement stalls
  * (cond(B) 2^-8 >= 1).  iters counts outer (FP64) steps, outer the inner steps.
+ *
+ * Small handles: on a SLICED handle of at most 16,384 rows without float pairs,
+ * reliable-update refinement (FESPMV_CG_RELIABLE) runs as one launch of one
+ * thread-block cluster (8 CTAs that synchronise with cluster barriers and reduce
+ * through distributed shared memory) instead of CUDA graphs of kernel launches:
+ * the same recurrences and tests; the reductions run in another fixed order, so
+ * the iterates differ from the graphs' in rounding only.  FESPMV_CG_NO_CLUSTER
+ * keeps the graphs.  The solve server takes the same path, so a result is bitwise
+ * the same alone and served.
  */
 int cg_solve(fespmv_mat_t A, const double* b, double* x, const cg_options* opts, cg_result* res,
              fespmv_stream_t stream);

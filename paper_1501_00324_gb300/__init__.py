@@ -69,6 +69,7 @@ FESPMV_CG_NO_PRECOND = 8
 FESPMV_CG_SINGLE_REDUCTION = 16
 FESPMV_CG_RELIABLE = 32
 FESPMV_CG_FLEXIBLE = 64
+FESPMV_CG_NO_CLUSTER = 128
 
 
 class FespmvError(RuntimeError):

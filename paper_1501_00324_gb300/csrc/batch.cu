@@ -13,7 +13,6 @@
 // problem, fixed order), problems that have finished are skipped by every
 // kernel, and one CUDA graph holds `check_every` inner iterations of the whole
 // batch (five launches per iteration, whatever the number of problems).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +22,7 @@
 #include <thread>
 
 #include "cg_run.h"
+#include "cluster_device.cuh"
 #include "internal.h"
 #include "spmv_device.cuh"
 
@@ -268,54 +268,12 @@ __global__ void b_outer_count(int count, BScal* sc) {
 
 // ------------------------------------------------------------------ cluster solver
 //
-// Reliable-update refinement (the algorithm of cg_solve with FESPMV_CG_RELIABLE,
-// per problem) for the whole batch in one persistent launch: thread-block
-// clusters of kClusterCtas CTAs take problems from a work counter (largest
-// first) and each runs its problem's iteration to the end, synchronising only
-// within the cluster (hardware cluster barriers) and reducing dot products
-// through distributed shared memory: every CTA adds the CTAs' partial sums in
-// rank order, so all CTAs hold the same bits and take the same decisions.  No
-// grid-wide synchronisation and no host polling: finished problems cost nothing,
-// and a small problem's iterations cost a few cluster barriers each.
-namespace cgx = cooperative_groups;
-constexpr int kClusterCtas = 8;      // CTAs per cluster (the portable maximum) and
-constexpr int kClusterThreads = 256; // threads per CTA: two CTAs per SM, 38 clusters at once
-
-struct ClusterRed {
-    double slot[2][4];   // per-CTA partial sums, two slots used in turn
-    int job;
-};
-
-// Sum of K values over the cluster (fixed order: a block tree per CTA, then the
-// CTAs in rank order); every thread of every CTA returns the same sums.
-template <int K>
-__device__ __forceinline__ void cluster_sum(cgx::cluster_group& cl, ClusterRed& red, int& turn, double (&v)[K]) {
-    __shared__ double sh[K][kClusterThreads / 32];
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (int w = 0; w < kClusterThreads / 32; ++w) t += sh[k][w];
-            red.slot[turn][k] = t;
-        }
-    cl.sync();
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = 0.0;
-    for (unsigned r = 0; r < cl.num_blocks(); ++r) {
-        const double* rp = cl.map_shared_rank(&red.slot[turn][0], r);
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] += rp[k];
-    }
-    turn ^= 1;
-}
-
+// Reliable-update refinement for the whole batch in one persistent launch:
+// thread-block clusters take problems from a work counter (largest first) and
+// each runs its problem's solve to the end (cluster_reliable in
+// cluster_device.cuh), synchronising only within the cluster.  No grid-wide
+// synchronisation and no host polling: finished problems cost nothing, and a
+// small problem's iterations cost a few cluster barriers each.
 template <typename VT, int V, int U>
 __global__ void __launch_bounds__(kClusterThreads, 2) b_cluster_reliable(
     const uint4* __restrict__ meta, const int32_t* __restrict__ col, const VT* __restrict__ val32,
@@ -326,10 +284,7 @@ __global__ void __launch_bounds__(kClusterThreads, 2) b_cluster_reliable(
     BScal* sc, double tol2, double in2, int has_x0, int max_iter, int max_outer) {
     cgx::cluster_group cl = cgx::this_cluster();
     __shared__ ClusterRed red;
-    const unsigned rank = cl.block_rank(), C = cl.num_blocks();
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)rank * (kClusterThreads / 32) + (threadIdx.x >> 5), nwarps = (int64_t)C * (kClusterThreads / 32);
-    const int64_t tid = (int64_t)rank * kClusterThreads + threadIdx.x, nthreads = (int64_t)C * kClusterThreads;
+    const unsigned rank = cl.block_rank();
     int turn = 0;
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) red.job = (int)atomicAdd(next, 1u);
@@ -337,106 +292,17 @@ __global__ void __launch_bounds__(kClusterThreads, 2) b_cluster_reliable(
         const int job = *cl.map_shared_rank(&red.job, 0);
         if (job >= count) break;
         const int j = order[job];
-        const int64_t s0 = pslice[j], s1 = pslice[j + 1], r0 = 32 * pwarp[j], r1 = 32 * pwarp[j + 1];
-        int iters = 0, outer = 0, status = CG_RUNNING;
-        double rho = 0.0, rr = 0.0, bb = 0.0, thresh2 = 0.0, thresh_in = 0.0, prev = INFINITY;
-        bool first = true;
-        for (;;) {
-            // ---- FP64 residual: r = b - A x, r_in = float(S r), w = 0 (x += S w first after a step)
-            if (!first) {
-                for (int64_t i = r0 + tid; i < r1; i += nthreads) {
-                    x[i] = fma(scale[i], (double)w[i], x[i]);
-                }
-                cl.sync();
-            }
-            if (!first || has_x0) {
-                for (int64_t sl = s0 + gw; sl < s1; sl += nwarps) {
-                    const uint4 m = meta[sl];
-                    const double sum = sliced_row_sum_f64<V, U>(m, col, val64, x, lane);
-                    const int lt = (int)m.w;
-                    if ((lane & ((1 << lt) - 1)) == 0) q64[(int64_t)m.z + (lane >> lt)] = sum;
-                }
-                cl.sync();
-            }
-            double v3[3] = {0.0, 0.0, 0.0};
-            const bool ax = !first || has_x0;
-            for (int64_t i = r0 + tid; i < r1; i += nthreads) {
-                const double bi = b[i];
-                const double ri = ax ? bi - q64[i] : bi;
-                const float rs = (float)(scale[i] * ri);
-                w[i] = 0.0f;
-                rin[i] = rs;
-                if (first) p[i] = rs;
-                v3[0] = fma(ri, ri, v3[0]);
-                v3[1] = fma((double)rs, (double)rs, v3[1]);
-                v3[2] = fma(bi, bi, v3[2]);
-            }
-            cluster_sum<3>(cl, red, turn, v3);
-            rr = v3[0];
-            const double rhs2 = v3[1];
-            if (first) {
-                bb = v3[2];
-                thresh2 = tol2 * bb;
-            }
-            if (!isfinite(rr) || !isfinite(rhs2)) { status = CG_BREAKDOWN; break; }
-            if (rr <= thresh2) { status = CG_CONVERGED; break; }
-            if (outer >= max_outer || iters >= max_iter || !(rr < prev)) { status = CG_MAXITER; break; }
-            prev = rr;
-            // the kept direction takes the replaced residual: p = r_in + beta p (p = r_in first)
-            const double beta0 = first ? 0.0 : rhs2 / rho;
-            rho = rhs2;
-            thresh_in = fmax(in2 * rhs2, rr > 0.0 ? tol2 * bb * rhs2 / rr : 0.0);
-            if (!first) {
-                const float bt = (float)beta0;
-                for (int64_t i = r0 + tid; i < r1; i += nthreads) p[i] = fmaf(bt, p[i], rin[i]);
-            }
-            first = false;
-            cl.sync();
-            // ---- inner CG steps on B until the reliable-update test
-            for (;;) {
-                double v1[1] = {0.0};
-                for (int64_t sl = s0 + gw; sl < s1; sl += nwarps) {
-                    const uint4 m = meta[sl];
-                    const float sum = sliced_row_sum_low<VT, V, U>(m, col, val32, p, lane);
-                    const int lt = (int)m.w;
-                    if ((lane & ((1 << lt) - 1)) == 0) {
-                        const int64_t row = (int64_t)m.z + (lane >> lt);
-                        q32[row] = sum;
-                        v1[0] = fma((double)p[row], (double)sum, v1[0]);
-                    }
-                }
-                cluster_sum<1>(cl, red, turn, v1);
-                const double pq = v1[0];
-                if (!(pq > 0.0) || !isfinite(pq)) { status = CG_BREAKDOWN; break; }
-                const float a = (float)(rho / pq);
-                double v2[1] = {0.0};
-                for (int64_t i = r0 + tid; i < r1; i += nthreads) {
-                    w[i] = fmaf(a, p[i], w[i]);
-                    const float ri = fmaf(-a, q32[i], rin[i]);
-                    rin[i] = ri;
-                    v2[0] = fma((double)ri, (double)ri, v2[0]);
-                }
-                cluster_sum<1>(cl, red, turn, v2);
-                const double rn = v2[0];
-                ++iters;
-                if (!isfinite(rn)) { status = CG_BREAKDOWN; break; }
-                if (rn <= thresh_in || iters >= max_iter) break;   // -> reliable update
-                const float bt = (float)(rn / rho);
-                rho = rn;
-                for (int64_t i = r0 + tid; i < r1; i += nthreads) p[i] = fmaf(bt, p[i], rin[i]);
-                cl.sync();
-            }
-            if (status != CG_RUNNING) break;
-            ++outer;
-        }
+        const ClusterOut o = cluster_reliable<VT, V, U>(cl, red, turn, meta, col, val32, val64, scale, b, x, q64, w,
+                                                        rin, p, q32, pslice[j], pslice[j + 1], 32 * pwarp[j],
+                                                        32 * pwarp[j + 1], tol2, in2, has_x0, max_iter, max_outer);
         if (rank == 0 && threadIdx.x == 0) {
-            BScal& o = sc[j];
-            o.status_out = status;
-            o.status_in = CG_CONVERGED;
-            o.iters = iters;
-            o.outer = outer;
-            o.rr = rr;
-            o.bb = bb;
+            BScal& s = sc[j];
+            s.status_out = o.status;
+            s.status_in = CG_CONVERGED;
+            s.iters = o.iters;
+            s.outer = o.outer;
+            s.rr = o.rr;
+            s.bb = o.bb;
         }
         cl.sync();   // the job word and the reduction slots are reused by the next problem
     }

@@ -1240,7 +1240,8 @@ int normalize_options(cg_options& o) {
         !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
         o.inner_steps < 1 || o.inner_steps > 1024 ||
         (o.flags & ~(FESPMV_IO_PERMUTED | FESPMV_IO_HOST | FESPMV_CG_X0 | FESPMV_CG_NO_PRECOND |
-                     FESPMV_CG_SINGLE_REDUCTION | FESPMV_CG_RELIABLE | FESPMV_CG_FLEXIBLE))) {
+                     FESPMV_CG_SINGLE_REDUCTION | FESPMV_CG_RELIABLE | FESPMV_CG_FLEXIBLE |
+                     FESPMV_CG_NO_CLUSTER))) {
         set_error("bad cg_options");
         return FESPMV_ERR_INVALID_ARG;
     }
@@ -1358,6 +1359,20 @@ int run_begin(CgRun& r) {
     // the pinned slot doubles as the upload buffer: it is not read until the first status copy
     w->h_sc[1] = init;
     FESPMV_CUDA(cudaMemcpyAsync(w->sc, &w->h_sc[1], sizeof(CgScalars), cudaMemcpyHostToDevice, r.s));
+    // small handles: reliable-update refinement in one cluster launch
+    const bool reliable_only = (r.o.flags & FESPMV_CG_RELIABLE) && !(r.o.flags & FESPMV_CG_FLEXIBLE);
+    if (r.A->format == FESPMV_FMT_SLICED && r.A->n <= kClusterSolveMaxRows && !r.A->d_vdf &&
+        !(r.o.flags & FESPMV_CG_NO_CLUSTER) && reliable_only) {
+        if ((rc = ensure_low_work(w))) return rc;
+        cg_copy_flag<<<1, 32, 0, r.s>>>(w->sc, r.A->d_flag);
+        FESPMV_CUDA(cudaGetLastError());
+        rc = launch_cluster_cg_reliable(r.A, w, r.o.precision == FESPMV_CG_BF16_REFINE ? 1 : 0, r.o.tol * r.o.tol,
+                                        r.o.inner_tol * r.o.inner_tol, r.has_x0 ? 1 : 0, r.o.max_iter,
+                                        r.o.max_outer, r.s);
+        if (rc) return rc;
+        r.phase = PH_CLUSTER_WAIT;
+        return enqueue_status(r, 0);
+    }
     const bool flexible = r.o.flags & FESPMV_CG_FLEXIBLE;
     if (flexible) {   // the inner scalars (their reduction counters and step count) start at zero
         if ((rc = ensure_low_work(w))) return rc;
@@ -1486,6 +1501,17 @@ int run_step(CgRun& r, bool block, bool* progress) {
             }
             r.prev = h.true_rr;
             return start_graphs(r, r.o.precision == FESPMV_CG_BF16_REFINE ? 2 : 1, r.o.max_iter);
+        case PH_CLUSTER_WAIT: {   // the one-launch solve has finished
+            r.last = h;
+            if (h.pad) {
+                set_error("refinement needs a positive, finite diagonal (S = diag(A)^-1/2)");
+                r.error = FESPMV_ERR_BREAKDOWN;
+                r.phase = PH_DONE;
+                return FESPMV_OK;
+            }
+            r.outer = h.iters_in;
+            return finish(r, h.status == CG_RUNNING ? CG_MAXITER : h.status);
+        }
         case PH_OUT_WAIT:
             r.phase = PH_DONE;
             return FESPMV_OK;

@@ -62,7 +62,13 @@ struct CgRun {
     CgScalars last{};
 };
 
-enum Phase { PH_INIT_WAIT, PH_ITER, PH_TRUE_WAIT, PH_RES_WAIT, PH_OUT_WAIT, PH_DONE };
+enum Phase { PH_INIT_WAIT, PH_ITER, PH_TRUE_WAIT, PH_RES_WAIT, PH_OUT_WAIT, PH_DONE, PH_CLUSTER_WAIT };
+
+// Handles with at most this many rows run reliable-update refinement in one
+// cluster launch (cluster_cg.cu).
+constexpr int64_t kClusterSolveMaxRows = 16384;
+int launch_cluster_cg_reliable(const fespmv_mat* A, CgWork* w, int bf16, double tol2, double in2, int has_x0,
+                               int max_iter, int max_outer, cudaStream_t s);
 
 // Workspace for one solve of A (vectors, partial sums, scalars, graphs, stream
 // for capture, events; pinned staging of n doubles when host_staging).

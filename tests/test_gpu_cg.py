@@ -199,3 +199,45 @@ def test_single_reduction_cg_full_size_elasticity_64():
     assert res["status"] == 0, res
     assert true_relres(p, x, b) <= 1.01e-10
     assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-5
+
+
+@pytest.mark.parametrize("flags", [0, fs.FESPMV_CG_NO_CLUSTER])
+@pytest.mark.parametrize("name", ["cube_laplace_20", "elasticity_8"])
+def test_small_handles_cluster_and_graph_paths(name, flags):
+    """Small handles run reliable-update refinement in one cluster launch unless
+    FESPMV_CG_NO_CLUSTER keeps the graphs: both meet the oracle's bar (true residual,
+    step and update counts), reproducibly, with a warm start and a step limit; FP64
+    PCG (graphs either way) alongside."""
+    p = {"cube_laplace_20": lambda: fegen.cube_laplace(20, 1501),
+         "elasticity_8": lambda: fegen.cube_elasticity(8, 51)}[name]()
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    A = make(p, sigma=256, precisions=fs.FESPMV_PREC_F32)
+    x, res = solve(A, b, tol=1e-10, flags=flags)
+    assert res["status"] == 0 and true_relres(p, x, b) <= 1.01e-10
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    assert abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-6
+    # repeated solves are bitwise equal
+    x2, res2 = solve(A, b, tol=1e-10, flags=flags)
+    assert res2["iters"] == res["iters"] and np.array_equal(x.view(np.uint64), x2.view(np.uint64))
+    # warm start from the solution: no iteration
+    bd, xd = dev(b), dev(x)
+    r3 = fs.cg_solve(A, bd, xd, tol=1e-10, flags=flags | fs.FESPMV_CG_X0)
+    assert r3["status"] == 0 and r3["iters"] == 0
+    # an iteration limit
+    _, r4 = solve(A, b, tol=1e-10, max_iter=5, max_restarts=-1, flags=flags)
+    assert r4["status"] == fs.FESPMV_ERR_NOT_CONVERGED and r4["iters"] == 5
+    # reliable-update refinement
+    kw = dict(tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=flags | fs.FESPMV_CG_RELIABLE)
+    xr, rr = solve(A, b, **kw)
+    assert rr["status"] == 0 and true_relres(p, xr, b) <= 1.01e-10
+    _, ir = oracle.refine_reliable(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    assert abs(rr["iters"] - ir["iters"]) <= 0.1 * ir["iters"] + 5
+    assert abs(rr["outer"] - ir["updates"]) <= 2
+    xr2, rr2 = solve(A, b, **kw)
+    assert rr2["iters"] == rr["iters"] and np.array_equal(xr.view(np.uint64), xr2.view(np.uint64))
+    r5 = fs.cg_solve(A, bd, dev(xr), **dict(kw, flags=kw["flags"] | fs.FESPMV_CG_X0))
+    assert r5["status"] == 0 and r5["iters"] == 0
+    _, r6 = solve(A, b, **dict(kw, max_iter=7))
+    assert r6["status"] == fs.FESPMV_ERR_NOT_CONVERGED and r6["iters"] <= 7
