@@ -276,7 +276,7 @@ int spmv_apply_scaled(fespmv_mat_t A, const float* x, float* y, int32_t precisio
 #define FESPMV_EXPORT_TILE_INDEX 11 /* uint16[packed_len]: index into the tile's columns; padding = D */
 #define FESPMV_EXPORT_NB_META  12 /* uint32[nb_slices*4]: (offset/32, width, first node row, 0) */
 #define FESPMV_EXPORT_NB_COLS  13 /* int32[nb_len]: block column (node) per slot, -1 = padding */
-#define FESPMV_EXPORT_NB_VALUES_F32 14 /* float[9*nb_len]: block values, plane by plane per slice */
+#define FESPMV_EXPORT_NB_VALUES_F32 14 /* float[9*nb_len]: block values, 9 words of 32 lanes per slot step */
 #define FESPMV_EXPORT_NB_VALUES_BF16 15 /* uint16[9*nb_len]: the same in bfloat16 bits */
 #define FESPMV_EXPORT_NB_MAP   16 /* int64[9*nb_len]: packed position of each block value, -1 = zero */
 #define FESPMV_EXPORT_NB_TILES 17 /* int32[nb_tiles*4]: (first slice, slices, node-list offset, D) */

@@ -308,5 +308,5 @@ def node_blocks(rowptr2, colind2):
             for a in range(3):
                 for p in range(int(rowptr2[3 * I + a]), int(rowptr2[3 * I + a + 1])):
                     J, b = divmod(int(colind2[p]), 3)
-                    vidx[9 * o + (3 * a + b) * 32 * w + 32 * where[J] + lane] = p
+                    vidx[9 * (o + 32 * where[J]) + 32 * (3 * a + b) + lane] = p
     return meta, col, vidx

@@ -645,6 +645,11 @@ __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int3
     if (grid_sum<1, 1024>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
+// Inner step of the refinement: w += a p, r_in -= a q, r_in.r_in.  Rows four at a
+// time (float4; the vectors are 16-byte aligned) and the rows past the last group
+// one by one.  Each thread sums its rows' squares as a float pair (Dot2) on the
+// FP32 pipe; where its |r_in| leave [2^-60, 2^60] (the squares would leave the
+// float range, or NaN/Inf) it sums them again in FP64.
 __global__ void __launch_bounds__(256, 4) cg32_update(int64_t n, float* __restrict__ w,
                                                    float* __restrict__ r,
                                                    const float* __restrict__ p,
@@ -652,13 +657,52 @@ __global__ void __launch_bounds__(256, 4) cg32_update(int64_t n, float* __restri
                                                    CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     const float a = (float)sc->alpha;
-    double v[1] = {0.0};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    float4* W4 = reinterpret_cast<float4*>(w);
+    float4* R4 = reinterpret_cast<float4*>(r);
+    const float4* P4 = reinterpret_cast<const float4*>(p);
+    const float4* Q4 = reinterpret_cast<const float4*>(q);
+    Dot2 acc;
+    float amax = 0.0f;
+    for (int64_t g = tid; g < n4; g += nth) {
+        const float4 pv = P4[g], qv = Q4[g];
+        float4 rv = R4[g], wv = W4[g];
+        wv.x = fmaf(a, pv.x, wv.x);
+        wv.y = fmaf(a, pv.y, wv.y);
+        wv.z = fmaf(a, pv.z, wv.z);
+        wv.w = fmaf(a, pv.w, wv.w);
+        rv.x = fmaf(-a, qv.x, rv.x);
+        rv.y = fmaf(-a, qv.y, rv.y);
+        rv.z = fmaf(-a, qv.z, rv.z);
+        rv.w = fmaf(-a, qv.w, rv.w);
+        W4[g] = wv;
+        R4[g] = rv;
+        acc.add(rv.x, rv.x);
+        acc.add(rv.y, rv.y);
+        acc.add(rv.z, rv.z);
+        acc.add(rv.w, rv.w);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(rv.x), fabsf(rv.y)), fmaxf(fabsf(rv.z), fabsf(rv.w))));
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += nth) {
         w[i] = fmaf(a, p[i], w[i]);
         const float ri = fmaf(-a, q[i], r[i]);
         r[i] = ri;
-        v[0] = fma((double)ri, (double)ri, v[0]);
+        acc.add(ri, ri);
+        amax = fmaxf(amax, fabsf(ri));
+    }
+    double v[1] = {acc.value()};
+    if (!(amax <= 0x1p60f) || (amax > 0.0f && amax < 0x1p-60f) || !isfinite(v[0])) {
+        double t = 0.0;
+        for (int64_t g = tid; g < n4; g += nth) {
+            const float4 rv = R4[g];
+            t = fma((double)rv.x, (double)rv.x, t);
+            t = fma((double)rv.y, (double)rv.y, t);
+            t = fma((double)rv.z, (double)rv.z, t);
+            t = fma((double)rv.w, (double)rv.w, t);
+        }
+        for (int64_t i = 4 * n4 + tid; i < n; i += nth) t = fma((double)r[i], (double)r[i], t);
+        v[0] = t;
     }
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->iters += 1;
@@ -674,13 +718,21 @@ __global__ void __launch_bounds__(256, 4) cg32_update(int64_t n, float* __restri
     }
 }
 
+// p = r_in + beta p, four rows at a time.
 __global__ void __launch_bounds__(256, 4) cg32_pupdate(int64_t n, float* __restrict__ p,
                                                     const float* __restrict__ r, const CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     const float beta = (float)sc->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fmaf(beta, p[i], r[i]);
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    float4* P4 = reinterpret_cast<float4*>(p);
+    const float4* R4 = reinterpret_cast<const float4*>(r);
+    for (int64_t g = tid; g < n4; g += nth) {
+        const float4 pv = P4[g], rv = R4[g];
+        P4[g] = make_float4(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y), fmaf(beta, pv.z, rv.z),
+                            fmaf(beta, pv.w, rv.w));
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += nth) p[i] = fmaf(beta, p[i], r[i]);
 }
 
 // Outer step: r = b - Ax (FP64; Ax = q or 0), rhs = float(S r); inner state

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) nb3_multi(const uint4* __restrict__ meta,
     if (nr >= n_slices * 32) return;   // RPW divides 32: a warp never straddles two slices
     const uint4 m = meta[nr >> 5];
     const int ls = (int)(nr & 31);
-    const int64_t off = (int64_t)m.x * 32, plane = 32 * (int64_t)m.y;
+    const int64_t off = (int64_t)m.x * 32;
     const int w = (int)m.y;
     const int32_t* cp = col + off + ls;
     const float* vp = val + 9 * off + ls;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) nb3_multi(const uint4* __restrict__ meta,
         for (int u = 0; u < U; ++u) {
             J[u] = ld_stream(cp + 32 * (st + u));
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[u][k] = ld_stream(vp + k * plane + 32 * (st + u));
+            for (int k = 0; k < 9; ++k) v[u][k] = ld_stream(vp + 288 * (st + u) + 32 * k);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) block(J[u], v[u]);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) nb3_multi(const uint4* __restrict__ meta,
         float v[9];
         const int32_t J = ld_stream(cp + 32 * st);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + k * plane + 32 * st);
+        for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + 288 * st + 32 * k);
         block(J, v);
     }
     const int64_t node = (int64_t)m.z + ls;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(128, 6) nb3_multi_dot(const uint4* __restrict_
         const int64_t nr = u * RPW + g;
         const uint4 m = meta[nr >> 5];
         const int ls = (int)(nr & 31);
-        const int64_t off = (int64_t)m.x * 32, plane = 32 * (int64_t)m.y;
+        const int64_t off = (int64_t)m.x * 32;
         const int w = (int)m.y;
         const int32_t* cp = col + off + ls;
         const float* vp = val + 9 * off + ls;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(128, 6) nb3_multi_dot(const uint4* __restrict_
             for (int uu = 0; uu < U; ++uu) {
                 J[uu] = ld_stream(cp + 32 * (st + uu));
 #pragma unroll
-                for (int k = 0; k < 9; ++k) v[uu][k] = ld_stream(vp + k * plane + 32 * (st + uu));
+                for (int k = 0; k < 9; ++k) v[uu][k] = ld_stream(vp + 288 * (st + uu) + 32 * k);
             }
 #pragma unroll
             for (int uu = 0; uu < U; ++uu) block(J[uu], v[uu]);
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128, 6) nb3_multi_dot(const uint4* __restrict_
             float v[9];
             const int32_t J = ld_stream(cp + 32 * st);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + k * plane + 32 * st);
+            for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + 288 * st + 32 * k);
             block(J, v);
         }
         const int64_t node = (int64_t)m.z + ls;

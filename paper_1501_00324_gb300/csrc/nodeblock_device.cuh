@@ -24,7 +24,6 @@ __device__ __forceinline__ void nb3_row_sums(const uint4 m, const int32_t* __res
                                              float (&s)[3]) {
     const int64_t off = (int64_t)m.x * 32;
     const int w = (int)m.y;
-    const int64_t plane = 32 * (int64_t)w;
     const int32_t* cp = col + off + lane;
     const VT* vp = val + 9 * off + lane;
     s[0] = s[1] = s[2] = 0.0f;
@@ -36,7 +35,7 @@ __device__ __forceinline__ void nb3_row_sums(const uint4 m, const int32_t* __res
         for (int u = 0; u < U; ++u) {
             J[u] = ld_stream(cp + 32 * (st + u));
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[u][k] = nb3_value(vp + k * plane + 32 * (st + u));
+            for (int k = 0; k < 9; ++k) v[u][k] = nb3_value(vp + 288 * (st + u) + 32 * k);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -55,7 +54,7 @@ __device__ __forceinline__ void nb3_row_sums(const uint4 m, const int32_t* __res
         const int32_t J = ld_stream(cp + 32 * st);
         float v[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = nb3_value(vp + k * plane + 32 * st);
+        for (int k = 0; k < 9; ++k) v[k] = nb3_value(vp + 288 * st + 32 * k);
         if (J < 0) continue;
         const float* xp = x + 3 * (int64_t)J;
         const float x0 = __ldg(xp), x1 = __ldg(xp + 1), x2 = __ldg(xp + 2);
@@ -89,7 +88,6 @@ __device__ __forceinline__ void nb3_row_sums_tiled(const uint4 m, const uint16_t
                                                    float (&s)[3]) {
     const int64_t off = (int64_t)m.x * 32;
     const int w = (int)m.y;
-    const int64_t plane = 32 * (int64_t)w;
     const unsigned short* cp = reinterpret_cast<const unsigned short*>(lidx) + off + lane;
     const VT* vp = val + 9 * off + lane;
     s[0] = s[1] = s[2] = 0.0f;
@@ -101,7 +99,7 @@ __device__ __forceinline__ void nb3_row_sums_tiled(const uint4 m, const uint16_t
         for (int u = 0; u < U; ++u) {
             li[u] = ld_stream(cp + 32 * (st + u));
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[u][k] = nb3_value(vp + k * plane + 32 * (st + u));
+            for (int k = 0; k < 9; ++k) v[u][k] = nb3_value(vp + 288 * (st + u) + 32 * k);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -118,7 +116,7 @@ __device__ __forceinline__ void nb3_row_sums_tiled(const uint4 m, const uint16_t
         const int li = ld_stream(cp + 32 * st);
         float v[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = nb3_value(vp + k * plane + 32 * st);
+        for (int k = 0; k < 9; ++k) v[k] = nb3_value(vp + 288 * st + 32 * k);
         const float x0 = xs[3 * li], x1 = xs[3 * li + 1], x2 = xs[3 * li + 2];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {

@@ -371,7 +371,7 @@ int pack_node_blocks(const std::vector<int64_t>& rp2, const std::vector<int32_t>
                     const int32_t J = c2[(size_t)p] / 3, b = c2[(size_t)p] % 3;
                     while (bc[(size_t)k] != J) ++k;   // columns ascend within the row
                     const int64_t step = k - bp[(size_t)I];
-                    out.map[(size_t)(9 * off + (3 * a + b) * 32 * w + 32 * step + lane)] = ppos[(size_t)p];
+                    out.map[(size_t)(9 * (off + 32 * step) + 32 * (3 * a + b) + lane)] = ppos[(size_t)p];
                 }
             }
         }

@@ -552,9 +552,10 @@ def test_node_blocks_hand_example():
     want_col[[0, 32, 1, 33]] = [0, 1, 0, 1]
     assert np.array_equal(col, want_col)
     want = np.full(9 * 64, -1)
-    # (value index) -> CSR position, worked out by hand from index = k*64 + 32*step + lane
-    for idx, p in ((0, 0), (64, 1), (96, 2), (256, 3), (512, 4), (544, 5),
-                   (33, 6), (193, 7), (289, 8), (513, 9), (545, 10)):
+    # (value index) -> CSR position, worked out by hand from index = 288*step + 32*k + lane
+    # (k = 3a + b: row a of the node, column b of the block's column node)
+    for idx, p in ((0, 0), (32, 1), (320, 2), (128, 3), (256, 4), (544, 5),
+                   (289, 6), (97, 7), (417, 8), (257, 9), (545, 10)):
         want[idx] = p
     assert np.array_equal(vidx, want)
 
@@ -584,7 +585,7 @@ def test_node_blocks_hold_every_entry_once(n, sigma):
                 if J < 0:
                     continue
                 for k in range(9):
-                    q = vidx[9 * o + k * 32 * int(w) + 32 * st + lane]
+                    q = vidx[9 * (o + 32 * st) + 32 * k + lane]
                     a, b = divmod(k, 3)
                     D[3 * I + a, 3 * J + b] += v2[q] if q >= 0 else 0.0
     assert np.array_equal(D, dense_of(rp2, c2, v2, nr))
