@@ -21,6 +21,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "dot2.cuh"
 #include "internal.h"
 #include "spmv_device.cuh"
 #include "tiled_device.cuh"

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "cg_run.h"
+#include "dot2.cuh"
 #include "spmv_device.cuh"
 
 namespace fespmv {
