@@ -100,6 +100,14 @@ def min_bytes(n, nnz, val_bytes=8, vec_bytes=8):
     return nnz * (val_bytes + 4) + n * 2 * vec_bytes
 
 
+def fp64_peak_tflops(torch, dev, peaks):
+    """FP64 FMA peak of the device: 2 lanes per SM per clock (GB300's nominal 1.25
+    TFLOP/s over 152 SMs at 2.07 GHz), 2 FLOP per FMA, at the maximum SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+    return 2 * 2 * sms * mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -655,7 +663,17 @@ def main():
                          "bytes_per_launch": mb,
                          "layout_bytes_per_launch": layout_bytes,
                          "note": "achieved = algorithmic bytes (FP64 values, int32 indices, x, y) / time; "
-                                 "the tiled layout moves layout_bytes_per_launch"},
+                                 "the tiled layout moves layout_bytes_per_launch; the kernel is FP64-pipe "
+                                 "bound (roofline_fp64)"},
+            # the same kernel against the FP64 pipe, the roof it actually sits on (one DFMA
+            # per stored entry; GB300's nominal 1.25 TFLOP/s FP64 is 2 FMA lanes per SM per
+            # clock: peak = 2 FLOP x 2 lanes x SMs x the maximum SM clock)
+            "roofline_fp64": None if args.kernel != "f64" else {
+                "bound": "alu", "unit": "TFLOP/s",
+                "achieved": round(2 * nnz / t_mean / 1e12, 4),
+                "peak": round(fp64_peak_tflops(torch, dev, peaks), 4),
+                "frac": round(2 * nnz / t_mean / 1e12 / fp64_peak_tflops(torch, dev, peaks), 4),
+                "peak_source": "derived: 2 FP64 FMA lanes per SM per clock x SMs x max SM clock"},
             "gpu_launches": args.steps * (2 if args.kernel == "df64" else 1),
             "step_with_l2_flush": {"ms": round(statistics.mean(times_flushed), 4),
                                    "gbs": round(mb / (statistics.mean(times_flushed) * 1e-3) / 1e9, 1),

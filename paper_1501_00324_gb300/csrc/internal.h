@@ -53,9 +53,9 @@ bool build_tiles(const std::vector<uint32_t>& meta, const std::vector<int32_t>& 
 
 // 3x3 node blocks of a node-ordered permuted CSR (rows 3I..3I+2 of node I): K1
 // slices of 32 node rows, one block row per lane, blocks column-major in the
-// slice; each block one int32 block column and 9 values stored plane by plane
-// (value k = 3a + b of the block at step s, lane l of a slice at offset off with
-// width w: index 9 off + k (32 w) + 32 s + l).
+// slice; each block one int32 block column and 9 values stored step-major
+// (value k = 3a + b of the block at step s, lane l of a slice at offset off:
+// index 9 (off + 32 s) + 32 k + l, so that a warp reads one contiguous run per step).
 struct NodeBlocks {
     std::vector<uint32_t> meta;     // 4 per slice: offset/32 (block slots), width, first node row, 0
     std::vector<int32_t> col;       // per block slot: block column (node), -1 = padding
