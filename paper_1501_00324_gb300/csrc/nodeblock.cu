@@ -64,91 +64,97 @@ __global__ void __launch_bounds__(256, 8) nb3_product_tiled(const uint4* __restr
     }
 }
 
+// One node row's products with its 3 x 4 accumulators (rows 3I+a, the lane's four
+// right-hand sides): per block (ascending column node J) rows a = 0..2 add
+// v[3a+b] * X[3J+b] for b = 0..2.  The block columns of the next U steps are
+// loaded one iteration ahead, so that a step's X gathers (three 16-byte loads, one
+// per X row of the column node) are issued together with its value loads instead
+// of after a dependent column load.
+template <int KW, int U>
+__device__ __forceinline__ void nb3_multi_rows(const int32_t* cp, const float* vp,
+                                               const float* xc, int w, float (&acc)[3][4]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[a][j] = 0.0f;
+    int32_t Jn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) Jn[u] = u < w ? ld_stream(cp + 32 * u) : -1;
+    for (int st = 0; st < w; st += U) {
+        int32_t J[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            J[u] = Jn[u];
+            Jn[u] = st + U + u < w ? ld_stream(cp + 32 * (st + U + u)) : -1;
+        }
+        float4 xb[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                xb[u][b] = J[u] >= 0 ? __ldg(reinterpret_cast<const float4*>(xc + (3 * (int64_t)J[u] + b) * KW))
+                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float v[U][9];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[u][k] = st + u < w ? ld_stream(vp + 288 * (st + u) + 32 * k) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (J[u] < 0) continue;   // a padding slot
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[a][0] = fmaf(v[u][3 * a + b], xb[u][b].x, acc[a][0]);
+                    acc[a][1] = fmaf(v[u][3 * a + b], xb[u][b].y, acc[a][1]);
+                    acc[a][2] = fmaf(v[u][3 * a + b], xb[u][b].z, acc[a][2]);
+                    acc[a][3] = fmaf(v[u][3 * a + b], xb[u][b].w, acc[a][3]);
+                }
+        }
+    }
+}
+
 // Y = B X for X, Y row-major n x KW (KW = 4..32 right-hand sides, FP32): KW / 4
 // lanes per node row, each lane 4 consecutive right-hand sides of the node's 3
 // rows; per block the 9 values (the same words for the row's lanes) and one
 // 16-byte load of each of the 3 X rows the block's column node names, so one X
 // row serves the 3 rows of the node.  The matrix streams once for all columns.
-template <int KW, int NV, int U>
-__global__ void __launch_bounds__(256) nb3_multi(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
+template <int KW, int U>
+__global__ void __launch_bounds__(256, 1) nb3_multi(const uint4* __restrict__ meta, const int32_t* __restrict__ col,
                                                  const float* __restrict__ val, const float* __restrict__ X,
                                                  float* __restrict__ Y, int64_t n_nodes, int64_t n_slices) {
-    constexpr int LPR = KW / (4 * NV), RPW = 32 / LPR;   // lanes per node row, node rows per warp
+    constexpr int LPR = KW / 4, RPW = 32 / LPR;   // lanes per node row, node rows per warp
     const int lane = threadIdx.x & 31, g = lane / LPR, c = lane % LPR;
     const int64_t nr = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * RPW + g;   // node row slot
     if (nr >= n_slices * 32) return;   // RPW divides 32: a warp never straddles two slices
     const uint4 m = meta[nr >> 5];
     const int ls = (int)(nr & 31);
     const int64_t off = (int64_t)m.x * 32;
-    const int w = (int)m.y;
-    const int32_t* cp = col + off + ls;
-    const float* vp = val + 9 * off + ls;
-    float acc[3][4 * NV];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int j = 0; j < 4 * NV; ++j) acc[a][j] = 0.0f;
-    int st = 0;
-    auto block = [&](int32_t J, const float (&v)[9]) {
-        if (J < 0) return;
-        const float* xp = X + 3 * (int64_t)J * KW + 4 * NV * c;
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int h = 0; h < NV; ++h) {
-                const float4 xb = __ldg(reinterpret_cast<const float4*>(xp + b * KW + 4 * h));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    acc[a][4 * h + 0] = fmaf(v[3 * a + b], xb.x, acc[a][4 * h + 0]);
-                    acc[a][4 * h + 1] = fmaf(v[3 * a + b], xb.y, acc[a][4 * h + 1]);
-                    acc[a][4 * h + 2] = fmaf(v[3 * a + b], xb.z, acc[a][4 * h + 2]);
-                    acc[a][4 * h + 3] = fmaf(v[3 * a + b], xb.w, acc[a][4 * h + 3]);
-                }
-            }
-    };
-    for (; st + U <= w; st += U) {
-        int32_t J[U];
-        float v[U][9];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            J[u] = ld_stream(cp + 32 * (st + u));
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v[u][k] = ld_stream(vp + 288 * (st + u) + 32 * k);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) block(J[u], v[u]);
-    }
-    for (; st < w; ++st) {
-        float v[9];
-        const int32_t J = ld_stream(cp + 32 * st);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + 288 * st + 32 * k);
-        block(J, v);
-    }
+    float acc[3][4];
+    nb3_multi_rows<KW, U>(col + off + ls, val + 9 * off + ls, X + 4 * c, (int)m.y, acc);
     const int64_t node = (int64_t)m.z + ls;
     if (node < n_nodes)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int h = 0; h < NV; ++h)
-                *reinterpret_cast<float4*>(Y + (3 * node + a) * KW + 4 * NV * c + 4 * h) =
-                    make_float4(acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]);
+            *reinterpret_cast<float4*>(Y + (3 * node + a) * KW + 4 * c) =
+                make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
 }
 
-template <int KW, int NV, int U>
+template <int KW, int U>
 static void nb3_multi_launch(const fespmv_mat* A, const float* X, float* Y, cudaStream_t s) {
-    const int64_t warps = A->nb_slices * 32 / (32 / (KW / (4 * NV)));
-    nb3_multi<KW, NV, U><<<grid_for(warps * 32, 256), 256, 0, s>>>(A->d_nbmeta, A->d_nbcol, A->d_nb32, X, Y,
-                                                                   A->n / 3, A->nb_slices);
+    const int64_t warps = A->nb_slices * 32 / (32 / (KW / 4));
+    nb3_multi<KW, U><<<grid_for(warps * 32, 256), 256, 0, s>>>(A->d_nbmeta, A->d_nbcol, A->d_nb32, X, Y,
+                                                               A->n / 3, A->nb_slices);
 }
 
 int launch_nb3_multi(const fespmv_mat* A, const float* X, float* Y, int kw, cudaStream_t s) {
     if (A->n == 0) return FESPMV_OK;
     switch (kw) {
-        case 4: nb3_multi_launch<4, 1, 2>(A, X, Y, s); break;
-        case 8: nb3_multi_launch<8, 1, 2>(A, X, Y, s); break;
-        case 16: nb3_multi_launch<16, 1, 2>(A, X, Y, s); break;
-        default: nb3_multi_launch<32, 1, 2>(A, X, Y, s); break;
+        case 4: nb3_multi_launch<4, 2>(A, X, Y, s); break;
+        case 8: nb3_multi_launch<8, 2>(A, X, Y, s); break;
+        case 16: nb3_multi_launch<16, 2>(A, X, Y, s); break;
+        default: nb3_multi_launch<32, 2>(A, X, Y, s); break;
     }
     FESPMV_CUDA(cudaGetLastError());
     return FESPMV_OK;
@@ -175,49 +181,8 @@ __global__ void __launch_bounds__(128, 6) nb3_multi_dot(const uint4* __restrict_
         const uint4 m = meta[nr >> 5];
         const int ls = (int)(nr & 31);
         const int64_t off = (int64_t)m.x * 32;
-        const int w = (int)m.y;
-        const int32_t* cp = col + off + ls;
-        const float* vp = val + 9 * off + ls;
         float acc[3][4];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[a][j] = 0.0f;
-        auto block = [&](int32_t J, const float (&v)[9]) {
-            if (J < 0) return;
-            const float* xp = P + 3 * (int64_t)J * KW + 4 * c;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const float4 xb = __ldg(reinterpret_cast<const float4*>(xp + b * KW));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    acc[a][0] = fmaf(v[3 * a + b], xb.x, acc[a][0]);
-                    acc[a][1] = fmaf(v[3 * a + b], xb.y, acc[a][1]);
-                    acc[a][2] = fmaf(v[3 * a + b], xb.z, acc[a][2]);
-                    acc[a][3] = fmaf(v[3 * a + b], xb.w, acc[a][3]);
-                }
-            }
-        };
-        int st = 0;
-        for (; st + U <= w; st += U) {
-            int32_t J[U];
-            float v[U][9];
-#pragma unroll
-            for (int uu = 0; uu < U; ++uu) {
-                J[uu] = ld_stream(cp + 32 * (st + uu));
-#pragma unroll
-                for (int k = 0; k < 9; ++k) v[uu][k] = ld_stream(vp + 288 * (st + uu) + 32 * k);
-            }
-#pragma unroll
-            for (int uu = 0; uu < U; ++uu) block(J[uu], v[uu]);
-        }
-        for (; st < w; ++st) {
-            float v[9];
-            const int32_t J = ld_stream(cp + 32 * st);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = ld_stream(vp + 288 * st + 32 * k);
-            block(J, v);
-        }
+        nb3_multi_rows<KW, U>(col + off + ls, val + 9 * off + ls, P + 4 * c, (int)m.y, acc);
         const int64_t node = (int64_t)m.z + ls;
         if (node < n_nodes) {
             float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
