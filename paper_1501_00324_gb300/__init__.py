@@ -236,6 +236,11 @@ def _check(rc: int):
         raise FespmvError(rc, msg)
 
 
+def last_error() -> str:
+    """The calling thread's last error message of the library (fespmv_last_error)."""
+    return _lib.fespmv_last_error().decode()
+
+
 def _stream(stream):
     if stream is None:
         import torch

@@ -180,3 +180,30 @@ def test_assembly_edge_cases():
     fs.assembly_matrix(P2, 3.0 * Ke)
     fs.assembly_matrix(P2, Ke)
     assert np.array_equal(v1, fs.spmv_export(Z, fs.FESPMV_EXPORT_VALUES))
+
+
+@pytest.mark.parametrize("fmt", ["tiled", "csr"])
+def test_assembly_partial_node_masks_and_uncontributed_entries(fmt):
+    """Three dofs per node with single dofs marked (nodes partly constrained) on a
+    pattern that keeps every entry, plus one stored entry no element touches: the
+    assembled handle equals the handle of the oracle's assembly, bit for bit
+    (marked rows: unit diagonal and zeros; entries with a marked column: zero; the
+    untouched entry: zero)."""
+    p = MESHES["elasticity_6_neumann"]()
+    rng = np.random.default_rng(508)
+    mask = (rng.random(p.n_rows) < 0.1).astype(np.uint8)
+    # one more stored entry in row 0, at a column no element couples to it
+    row0 = set(p.colind[p.rowptr[0]:p.rowptr[1]].tolist())
+    extra = next(c for c in range(p.n_rows - 1, 0, -1) if c not in row0)
+    cols0 = np.sort(np.array(sorted(row0) + [extra], dtype=np.int32))
+    colind = np.concatenate([cols0, p.colind[p.rowptr[1]:]]).astype(np.int32)
+    rowptr = p.rowptr.copy()
+    rowptr[1:] += 1
+    vals = oracle.assemble_matrix(rowptr, colind, p.elem_nodes, p.elem_mats, 3, mask)
+    kw = dict(FORMATS[fmt])
+    R = fs.spmv_create(rowptr, colind, vals, p.node_xyz, 3, precisions=fs.FESPMV_PREC_F32, **kw)
+    Z = fs.spmv_create(rowptr, colind, 2.0 * vals + 1.0, p.node_xyz, 3, precisions=fs.FESPMV_PREC_F32, **kw)
+    P = fs.assembly_create(Z, rowptr, colind, p.elem_nodes, 3, mask)
+    fs.assembly_matrix(P, torch.from_numpy(p.elem_mats).cuda())
+    torch.cuda.synchronize()
+    same_handles(R, Z, (fs.FESPMV_EXPORT_VALUES, fs.FESPMV_EXPORT_DIAG, fs.FESPMV_EXPORT_VALUES_F32))

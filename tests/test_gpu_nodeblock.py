@@ -122,7 +122,7 @@ def test_refined_cg_on_node_blocks(storage, tiles):
         xd = torch.zeros_like(bd)
         res = fs.cg_solve(A, bd, xd, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=flags)
         torch.cuda.synchronize()
-        assert res["status"] == 0, res
+        assert res["status"] == 0, (res, fs.last_error())
         x = xd.cpu().numpy()
         r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
         assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
