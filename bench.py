@@ -74,7 +74,7 @@ def parse_args():
                     help="time the assembly of the workload matrix from its element matrices")
     ap.add_argument("--multi-cg", type=int, default=1,
                     help="time cg_solve_multi with 32 right-hand sides on the workload matrix")
-    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "assembly",
+    ap.add_argument("--profile-target", choices=["multi", "multi64", "fp32", "cg", "cg_f32", "cg_multi", "nb_cg_multi", "assembly",
                                                  "nb_fp32", "nb_multi", "batch"], default=None,
                     help="run only this piece a few times (for ncu), no JSON line")
     ap.add_argument("--cg-solves", type=int, default=5)
@@ -1127,7 +1127,7 @@ def profile_piece(fs, torch, A, p, xp, args):
     --extras-vec), the CG pieces on the headline handle, as in the timed run."""
     n = p.n_rows
     t = args.profile_target
-    if t in ("multi", "multi64", "fp32", "cg_multi", "nb_fp32", "nb_multi"):
+    if t in ("multi", "multi64", "fp32", "cg_multi", "nb_fp32", "nb_multi", "nb_cg_multi"):
         A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, sigma=args.sigma,
                            vec=args.extras_vec, precisions=fs.FESPMV_PREC_F32,
                            node_blocks=3 if t.startswith("nb_") else 0)
@@ -1167,7 +1167,7 @@ def profile_piece(fs, torch, A, p, xp, args):
         P = fs.assembly_create(A, q.rowptr, q.colind, q.elem_nodes, 3, q.dirichlet)
         Ke = torch.from_numpy(q.elem_mats).cuda()
         f = lambda: fs.assembly_matrix(P, Ke)  # noqa: E731
-    elif t == "cg_multi":
+    elif t in ("cg_multi", "nb_cg_multi"):
         B = torch.rand((n, 32), dtype=torch.float64, device="cuda")
         X = torch.zeros_like(B)
         # 48 inner iterations (three graphs of 16) of the 32-RHS FP32 CG with reliable updates
