@@ -173,11 +173,15 @@ void spmv_destroy(fespmv_mat_t A);
  * spmv_apply -- y = A x in FP64.
  *   x, y  n_rows doubles each, device memory unless FESPMV_IO_HOST; x and y must
  *         not overlap.  Without FESPMV_IO_PERMUTED they are in the numbering of
- *         the CSR given to spmv_create; a SLICED handle then permutes x on the way
- *         in and y on the way out (two gathers of n_rows entries).  With
- *         FESPMV_IO_HOST and page-locked (pinned, mapped) host buffers in the input
- *         numbering, those permutations read x and write y in place over the host
- *         link (no staging copies); pageable buffers are copied through staging.
+ *         the CSR given to spmv_create.  For device vectors a SLICED handle with
+ *         tiles (the default) folds the permutations into the product: each tile
+ *         stages x[P[c']] for its columns c' and each row i' stores y[P[i']].
+ *         Otherwise a SLICED handle permutes x on the way in and y on the way out
+ *         (two gathers of n_rows entries); with FESPMV_IO_HOST and page-locked
+ *         (pinned, mapped) host buffers those permutations read x and write y in
+ *         place over the host link (no staging copies; measured faster than one
+ *         contiguous copy each way around the folded product); pageable buffers
+ *         are copied through staging.
  * Result per entry: the exact sum over the stored entries of the row, rounded
  * with a different association than a left-to-right sum (componentwise error
  * well under 1e-12 * sum_j |A_ij x_j|).  Errors: INVALID_ARG, CUDA.

@@ -403,6 +403,10 @@ int spmv_apply(fespmv_mat_t A, const double* x, double* y, int32_t flags, fespmv
     }
     const double* xd = x;
     double* yd = y;
+    if (A->format == FESPMV_FMT_SLICED && A->tiled && !A->d_vdf && !(flags & (FESPMV_IO_PERMUTED | FESPMV_IO_HOST)))
+        // device x and y in the input numbering on a tiled handle: the permutations fold
+        // into the product (x[P[c']] staged per tile, y[P[i']] stored per row)
+        return launch_spmv_tiled_io(A, x, y, s);
     if ((flags & FESPMV_IO_HOST) && A->format == FESPMV_FMT_SLICED && !(flags & FESPMV_IO_PERMUTED) &&
         !A->d_vdf) {
         // pinned host buffers: the permutations read x and write y in place over the host link

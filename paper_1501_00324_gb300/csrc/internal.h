@@ -189,6 +189,9 @@ int device_alloc(fespmv_mat* A, void** p, size_t bytes, const char* what);
 // FESPMV_ERR_CUDA.
 int launch_spmv(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
 int launch_spmv_tiled(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
+// The same FP64 product with x and y in the input numbering (the permutations folded
+// into the tile staging and the row store).
+int launch_spmv_tiled_io(const fespmv_mat* A, const double* x, double* y, cudaStream_t s);
 int launch_spmv_low_tiled(const fespmv_mat* A, int precision, const float* x, float* y, cudaStream_t s);
 int launch_spmv_df_tiled(const fespmv_mat* A, const float2* xdf, const double* x, double* y, cudaStream_t s);
 int launch_gather(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);

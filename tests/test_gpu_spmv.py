@@ -294,7 +294,8 @@ def test_slice_wider_than_a_tile_gathers_from_cache():
 @pytest.mark.parametrize("k", [1, 5, 10, 13])
 def test_pinned_host_buffers_are_read_and_written_in_place(k):
     """Page-locked host x and y (the in-place permutation path) give the same bits as
-    device vectors; pageable host buffers (staging copies) too."""
+    device vectors (on tiled handles: the product with the permutations folded in);
+    pageable host buffers (staging copies) too."""
     p = problem("elasticity_9")
     A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, **KERNELS[k])
     x = fegen.random_vector(p.n_rows, 31)
@@ -358,3 +359,22 @@ def test_column_orders_k1_and_k1r(col_order, tiles):
     else:
         res = fs.cg_solve(A, xd, torch.zeros_like(xd), tol=1e-10)
         assert res["status"] == 0
+
+
+@pytest.mark.parametrize("k", [4, 5, 6, 7, 8])
+def test_input_numbering_folds_the_permutations(k):
+    """On tiled handles the input-numbering product stages x[P[c']] per tile and stores
+    y[P[i']]: bitwise the permuted-numbering product between two gathers."""
+    p = problem("elasticity_9")
+    A = fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, 3, **KERNELS[k])
+    assert fs.spmv_get_info(A)["n_tiles"] > 0
+    x = fegen.random_vector(p.n_rows, 32)
+    xd = dev(x)
+    xp, yp, y = torch.empty_like(xd), torch.full_like(xd, float("nan")), torch.empty_like(xd)
+    fs.spmv_permute(A, xd, xp, 0)
+    fs.spmv_apply(A, xp, yp, fs.FESPMV_IO_PERMUTED)
+    fs.spmv_permute(A, yp, y, 1)
+    torch.cuda.synchronize()
+    yi = apply(A, x)
+    assert np.array_equal(yi.view(np.uint64), y.cpu().numpy().view(np.uint64))
+    check_parity(p, yi, x)
