@@ -533,46 +533,13 @@ __global__ void __launch_bounds__(256, 8) cg32_spmv_dot_sliced(const uint4* __re
     if (grid_sum<1>(v, partials, sc->counters) && threadIdx.x == 0) finish_pq_inner(v[0], sc);
 }
 
-// The inner direction update fused into the tiled products (the `Dir` of a tiled
-// inner step): the direction of step i is p_i = r + beta p_{i-1} (p_i = r where
-// beta = 0: the step after a restart), formed wherever it is read -- for every
-// staged column and for every row's own entry -- with the FMA cg32_pupdate uses,
-// so each p_i value is the same as a separate direction update would store.  The
-// directions alternate between two buffers by the parity of the step count:
-// step i reads p_{i-1} from buf[i & 1], and the lane that owns row j stores p_i(j)
-// in buf[(i + 1) & 1] for the w update that follows.  With p1 == nullptr the
-// direction is read from p0 as stored (cg32_pupdate runs separately).
-struct Dir {
-    const float* pold;
-    float* pnew;
-    const float* r;
-    float beta;
-    __device__ __forceinline__ float at(int64_t j) const {
-        return beta == 0.0f ? r[j] : fmaf(beta, pold[j], r[j]);
-    }
-};
-__device__ __forceinline__ Dir inner_dir(const float* p0, float* p1, const float* r, const CgScalars* sc) {
-    Dir d;
-    if (!p1) {
-        d.pold = p0; d.pnew = nullptr; d.r = nullptr; d.beta = 0.0f;
-        return d;
-    }
-    const int par = sc->iters & 1;
-    d.pold = par ? p1 : p0;
-    d.pnew = par ? const_cast<float*>(p0) : p1;
-    d.r = r;
-    d.beta = (float)sc->beta;
-    return d;
-}
-
 template <typename VT, int V, int U>
 __global__ void __launch_bounds__(kTiledBlock) cg32_spmv_dot_tiled(const uint4* __restrict__ meta,
                                                                    const uint16_t* __restrict__ lidx,
                                                                    const VT* __restrict__ val,
                                                                    const int4* __restrict__ tiles,
                                                                    const int32_t* __restrict__ dict,
-                                                                   const float* p0, float* p1,
-                                                                   const float* __restrict__ r,
+                                                                   const float* __restrict__ p,
                                                                    float* __restrict__ q, int64_t n,
                                                                    int64_t n_tiles, double* partials,
                                                                    CgScalars* sc) {
@@ -580,18 +547,9 @@ __global__ void __launch_bounds__(kTiledBlock) cg32_spmv_dot_tiled(const uint4* 
     extern __shared__ __align__(16) unsigned char tile_smem[];
     float* xs = reinterpret_cast<float*>(tile_smem);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Dir dir = inner_dir(p0, p1, r, sc);
     double v[1] = {0.0};
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        int4 tl;
-        if (dir.pnew) {
-            tl = tiles[t];
-            for (int e = threadIdx.x; e <= tl.w; e += blockDim.x)
-                xs[e] = e < tl.w ? dir.at(__ldg(dict + tl.z + e)) : 0.0f;
-            __syncthreads();
-        } else {
-            tl = stage_tile<float>(tiles + t, dict, p0, xs);
-        }
+        const int4 tl = stage_tile<float>(tiles + t, dict, p, xs);
         if (wid < tl.y) {
             const uint4 m = meta[tl.x + wid];
             const float sum = tiled_row_sum<VT, V, U>(m, lidx, val, xs, lane);
@@ -599,14 +557,7 @@ __global__ void __launch_bounds__(kTiledBlock) cg32_spmv_dot_tiled(const uint4* 
             const int64_t row = (int64_t)m.z + (lane >> lt);
             if ((lane & ((1 << lt) - 1)) == 0 && row < n) {
                 q[row] = sum;
-                float pr;
-                if (dir.pnew) {
-                    pr = dir.at(row);
-                    dir.pnew[row] = pr;
-                } else {
-                    pr = p0[row];
-                }
-                v[0] = fma((double)pr, (double)sum, v[0]);
+                v[0] = fma((double)p[row], (double)sum, v[0]);
             }
         }
         __syncthreads();
@@ -650,28 +601,16 @@ __global__ void __launch_bounds__(256, 8) cg32_spmv_dot_nb_tiled(const uint4* __
                                                               const VT* __restrict__ val,
                                                               const int4* __restrict__ tiles,
                                                               const int32_t* __restrict__ dict,
-                                                              const float* p0, float* p1,
-                                                              const float* __restrict__ r, float* __restrict__ q,
+                                                              const float* __restrict__ p, float* __restrict__ q,
                                                               int64_t n_tiles, int64_t n_nodes, double* partials,
                                                               CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     float* xs = reinterpret_cast<float*>(tile_smem);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Dir dir = inner_dir(p0, p1, r, sc);   // the direction formed where it is read
     double v[1] = {0.0};
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        int4 tl;
-        if (dir.pnew) {
-            tl = tiles[t];
-            for (int e = threadIdx.x; e < 3 * (tl.w + 1); e += blockDim.x) {
-                const int node = e / 3, c = e - 3 * node;
-                xs[e] = node < tl.w ? dir.at(3 * (int64_t)__ldg(dict + tl.z + node) + c) : 0.0f;
-            }
-            __syncthreads();
-        } else {
-            tl = nb3_stage(tiles + t, dict, p0, xs);
-        }
+        const int4 tl = nb3_stage(tiles + t, dict, p, xs);
         if (wid < tl.y) {
             const uint4 m = meta[tl.x + wid];
             float s[3];
@@ -681,14 +620,7 @@ __global__ void __launch_bounds__(256, 8) cg32_spmv_dot_nb_tiled(const uint4* __
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     q[3 * node + a] = s[a];
-                    float pr;
-                    if (dir.pnew) {
-                        pr = dir.at(3 * node + a);
-                        dir.pnew[3 * node + a] = pr;
-                    } else {
-                        pr = p0[3 * node + a];
-                    }
-                    v[0] = fma((double)pr, (double)s[a], v[0]);
+                    v[0] = fma((double)p[3 * node + a], (double)s[a], v[0]);
                 }
             }
         }
@@ -721,12 +653,10 @@ __global__ void cg32_spmv_dot_csr(const int64_t* __restrict__ rowptr, const int3
 // float range, or NaN/Inf) it sums them again in FP64.
 __global__ void __launch_bounds__(256, 4) cg32_update(int64_t n, float* __restrict__ w,
                                                    float* __restrict__ r,
-                                                   const float* p0, const float* p1,
+                                                   const float* __restrict__ p,
                                                    const float* __restrict__ q, double* partials,
                                                    CgScalars* sc) {
     if (sc->status != CG_RUNNING) return;
-    // with the tiled products' fused direction this step's p is in buf[(step + 1) & 1]
-    const float* __restrict__ p = (p1 && !(sc->iters & 1)) ? p1 : p0;
     const float a = (float)sc->alpha;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
     const int64_t n4 = n >> 2;
@@ -835,7 +765,7 @@ __global__ void __launch_bounds__(256) refine_residual(int64_t n, const double* 
     }
     if (grid_sum<3>(v, partials, sc->counters) && threadIdx.x == 0) {
         sc->true_rr = v[0];
-        sc->beta = keep_p ? v[1] / sc->rho : 0.0;   // 0: the next direction is r_in itself
+        if (keep_p) sc->beta = v[1] / sc->rho;
         sc->rho = v[1];
         sc->bb = v[2];
         sc->thresh2 = tol2 * v[2];
@@ -884,7 +814,6 @@ __global__ void __launch_bounds__(256) fcg_inner_init(int64_t n, const double* _
     }
     if (grid_sum<1>(v, partials, sc_in->counters) && threadIdx.x == 0) {
         sc_in->rho = v[0];
-        sc_in->beta = 0.0;   // the first inner direction is r_in itself
         sc_in->iters_in = 0;
         sc_in->max_iter = m;
         sc_in->thresh_in = 0.0;
@@ -1011,7 +940,7 @@ void destroy_work(CgWork* w) {
         if (e) cudaEventDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
     void* ptrs[] = {w->x, w->r, w->p, w->q, w->b, w->dinv, w->partials, w->sc, w->sc_in,
-                    w->w32, w->r32, w->p32, w->q32, w->p32b, w->pdf, w->u, w->s};
+                    w->w32, w->r32, w->p32, w->q32, w->pdf, w->u, w->s};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -1048,7 +977,7 @@ int64_t work_bytes(const fespmv_mat* A, bool refine) {
         std::max<int64_t>({(int64_t)spmv_grid(A), upd, A->tiled ? A->n_tiles : 0, A->nb_tiles}));
     int64_t b = 8 * 8 * A->n + 8 * np + 2 * (int64_t)sizeof(CgScalars);
     if (A->d_vdf) b += 8 * A->n;
-    if (refine) b += 5 * 4 * A->n;
+    if (refine) b += 4 * 4 * A->n;
     return b;
 }
 
@@ -1215,12 +1144,6 @@ static void launch_iteration_cg1(const fespmv_mat* A, CgWork* w, cudaStream_t s)
     cg1_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->x, w->r, w->u, w->p, w->s, w->q, w->dinv, w->sc);
 }
 
-// Whether the inner products stage x per tile, and so form the direction themselves
-// (Dir): then an inner step is two launches, else three (cg32_pupdate).
-static bool inner_fused(const fespmv_mat* A) {
-    return A->nb ? A->nb_tiles > 0 : (A->format == FESPMV_FMT_SLICED && A->tiled);
-}
-
 template <typename VT, int V>
 static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* val, cudaStream_t s) {
     constexpr int U = (V == 4) ? 4 : 8;
@@ -1229,9 +1152,8 @@ static void launch_inner_dot_sliced(const fespmv_mat* A, CgWork* w, const VT* va
         const size_t smem = sizeof(float) * (A->tile_dmax + 1);
         const unsigned g = tiled_grid(A, cg32_spmv_dot_tiled<VT, V, UT>, smem);
         cg32_spmv_dot_tiled<VT, V, UT><<<g, kTiledBlock, smem, s>>>(A->d_meta, A->d_tlidx, val, A->d_tiles,
-                                                                    A->d_tdict, w->p32, inner_fused(A) ? w->p32b : nullptr,
-                                                                    w->r32, w->q32, A->n, A->n_tiles, w->partials,
-                                                                    w->sc);
+                                                                    A->d_tdict, w->p32, w->q32, A->n,
+                                                                    A->n_tiles, w->partials, w->sc);
         return;
     }
     cg32_spmv_dot_sliced<VT, V, U><<<spmv_grid(A), A->block, 0, s>>>(A->d_meta, A->d_col, val, w->p32,
@@ -1255,10 +1177,9 @@ static void launch_inner_dot(const fespmv_mat* A, CgWork* w, const VT* val, cuda
             // over tiles would leave the last round of tiles to a few SMs
             const size_t smem = sizeof(float) * 3 * (size_t)(A->nb_tile_dmax + 1);
             const unsigned g = (unsigned)A->nb_tiles;
-            cg32_spmv_dot_nb_tiled<VT, std::is_same<VT, float>::value ? 2 : 4><<<g, 256, smem, s>>>(
-                A->d_nbmeta, A->d_nbtlidx, nbv, A->d_nbtiles, A->d_nbtdict, w->p32, inner_fused(A) ? w->p32b : nullptr,
-                w->r32, w->q32,
-                A->nb_tiles, A->n / 3, w->partials, w->sc);
+            cg32_spmv_dot_nb_tiled<VT, std::is_same<VT, float>::value ? 2 : 4><<<g, 256, smem, s>>>(A->d_nbmeta, A->d_nbtlidx, nbv, A->d_nbtiles,
+                                                               A->d_nbtdict, w->p32, w->q32, A->nb_tiles, A->n / 3,
+                                                               w->partials, w->sc);
             return;
         }
         const unsigned g = std::max(1u, std::min(spmv_grid(A), grid_for(A->nb_slices * 32, 256)));
@@ -1289,10 +1210,8 @@ static void launch_inner_iteration(const fespmv_mat* A, CgWork* w, int bf16, cud
         launch_inner_dot<__nv_bfloat16>(A, w, reinterpret_cast<const __nv_bfloat16*>(A->d_val16), s);
     else
         launch_inner_dot<float>(A, w, A->d_val32, s);
-    const bool fused = inner_fused(A);
-    cg32_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->w32, w->r32, w->p32, fused ? w->p32b : nullptr, w->q32,
-                                            w->partials, w->sc);
-    if (!fused) cg32_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p32, w->r32, w->sc);
+    cg32_update<<<w->upd_grid, 256, 0, s>>>(A->n, w->w32, w->r32, w->p32, w->q32, w->partials, w->sc);
+    cg32_pupdate<<<w->upd_grid, 256, 0, s>>>(A->n, w->p32, w->r32, w->sc);
 }
 
 // One outer step of the flexible CG: inner start, m inner steps on the inner
@@ -1347,7 +1266,7 @@ static int ensure_graph(const fespmv_mat* A, CgWork* w, int kind, int chunk, int
 int ensure_low_work(CgWork* w) {
     if (w->w32) return FESPMV_OK;
     const size_t nb = sizeof(float) * (size_t)w->n;
-    float** vecs[] = {&w->w32, &w->r32, &w->p32, &w->q32, &w->p32b};
+    float** vecs[] = {&w->w32, &w->r32, &w->p32, &w->q32};
     for (float** v : vecs) {
         int rc = work_alloc(w, (void**)v, nb, "refinement vector");
         if (rc) return rc;
@@ -1470,8 +1389,7 @@ static int enqueue_residual(CgRun& r, bool ax) {
                                                   r.o.inner_tol * r.o.inner_tol, reliable, keep_p,
                                                   w->partials, w->sc);
     // reliable update: the kept direction takes the replaced residual, p = r_in + beta p
-    // (the tiled inner products form that direction themselves, from beta)
-    if (keep_p && !inner_fused(r.A)) cg32_pupdate<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->p32, w->r32, w->sc);
+    if (keep_p) cg32_pupdate<<<w->upd_grid, 256, 0, r.s>>>(r.A->n, w->p32, w->r32, w->sc);
     FESPMV_CUDA(cudaGetLastError());
     r.phase = PH_RES_WAIT;
     return enqueue_status(r, 0);

@@ -32,7 +32,6 @@ struct CgWork {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // refinement (float inner CG): w, r_in, p, q
     float *w32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-    float* p32b = nullptr;      // tiled inner steps: the direction alternates between p32 and p32b
     cudaGraphExec_t graph_low[2] = {nullptr, nullptr};  // FP32, BF16 inner iterations
     int chunk_low[2] = {0, 0};
     cudaGraphExec_t graph_flex[2] = {nullptr, nullptr}; // flexible CG outer steps, FP32 / BF16 inner
