@@ -472,7 +472,7 @@ def main():
         # product steps and the end-to-end calls run, so the GPUs are held no longer than
         # the measurement needs
         if not args.only_spmv and world == 1:
-            # product in the input numbering (permute x in, y out)
+            # product in the input numbering (the permutations folded into the tiled product)
             # (every extra product below is timed back to back, like the headline: each
             # matrix is larger than L2, so it streams from HBM on every launch)
             y_user = torch.empty_like(xd)
