@@ -12,7 +12,7 @@ enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_BREAKDOWN = 2, CG_MAXITER = 3,
 struct CgScalars {
     double rho, pq, alpha, beta, rr, bb, thresh2, true_rr;
     int iters, max_iter, status, pad;
-    unsigned int counters[65];   // grid_sum arrival counters: top + 64 groups (zero between kernels)
+    unsigned int counters[1];    // grid_sum's arrival counter (zero between kernels)
     unsigned int pad2;
     double thresh_in;   // refinement: inner stop threshold on r_in.r_in
     int iters_in, first; // refinement: inner steps of the current outer step; single-reduction: first step
