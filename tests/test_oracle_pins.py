@@ -351,6 +351,24 @@ def test_scaled_values_match_dense_scaling(storage):
     assert np.all(np.abs(y - yd) <= (L + 1) * 2.0 ** -24 * (np.abs(B) @ np.abs(x)))
 
 
+def test_float_spmv_integer_matrix_exact():
+    # Small integers: every product and partial sum is exact in float, so the
+    # float product must equal the integer product exactly (an empty row gives 0).
+    rng = np.random.default_rng(31)
+    n = 40
+    counts = rng.integers(0, 9, size=n)
+    counts[7] = 0
+    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    colind = np.concatenate([np.sort(rng.choice(n, size=c, replace=False)) for c in counts]).astype(np.int32)
+    values = rng.integers(-20, 21, size=rowptr[-1]).astype(np.float32)
+    x = rng.integers(-15, 16, size=n).astype(np.float32)
+    y = oracle.csr_spmv_f32(rowptr, colind, values, x)
+    A = dense_of(rowptr, colind, values.astype(np.float64), n).astype(np.int64)
+    assert y.dtype == np.float32
+    assert np.array_equal(y.astype(np.int64), A @ x.astype(np.int64))
+    assert y[7] == 0.0
+
+
 def _one_step_slices(cols_per_slice):
     """meta/col for slices of one step (w = 1) each: slice s holds 32 entries."""
     meta, col = [], []
