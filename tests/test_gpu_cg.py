@@ -241,3 +241,47 @@ def test_small_handles_cluster_and_graph_paths(name, flags):
     assert r5["status"] == 0 and r5["iters"] == 0
     _, r6 = solve(A, b, **dict(kw, max_iter=7))
     assert r6["status"] == fs.FESPMV_ERR_NOT_CONVERGED and r6["iters"] <= 7
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33])
+def test_tiny_systems_through_every_path(n):
+    """1, 2, 31 and 33 rows (one row, a few, one short of a warp's 32-row slice and
+    one past it) through every product format and the FP64, single-reduction and
+    reliable-update solves: products within the componentwise bound, solves at the
+    oracle's bar.  The matrix is SPD tridiagonal, diagonal 4 + i/n, off-diagonal -1."""
+    cols, vals, ends = [], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                cols.append(j)
+                vals.append(4.0 + i / n if j == i else -1.0)
+        ends.append(len(cols))
+
+    class Q:  # minimal problem record
+        pass
+    p = Q()
+    p.rowptr = np.array([0] + ends, dtype=np.int64)
+    p.colind = np.array(cols, dtype=np.int32)
+    p.values = np.array(vals)
+    p.n_rows, p.node_xyz, p.dofs_per_node = n, None, 1
+    u = fegen.random_vector(n, 60 + n)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)
+    assert info["status"] == "converged" and info["iters"] <= n
+    bound = 1e-12 * oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(u))
+    for kw in FORMATS + [dict(format=fs.FESPMV_FMT_SLICED, sigma=512, precisions=fs.FESPMV_PREC_F32)]:
+        A = make(p, **kw)
+        yd = torch.empty(n, dtype=torch.float64, device="cuda")
+        fs.spmv_apply(A, dev(u), yd)
+        assert np.all(np.abs(yd.cpu().numpy() - b) <= bound), kw
+        for flags in (0, fs.FESPMV_CG_SINGLE_REDUCTION):
+            x, res = solve(A, b, tol=1e-10, flags=flags)
+            assert res["status"] == 0, (kw, flags, res)
+            assert true_relres(p, x, b) <= 1.01e-10
+            assert abs(res["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
+            assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+        if kw.get("precisions") == fs.FESPMV_PREC_F32:
+            for flags in (fs.FESPMV_CG_RELIABLE, fs.FESPMV_CG_RELIABLE | fs.FESPMV_CG_NO_CLUSTER):
+                x, res = solve(A, b, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=flags)
+                assert res["status"] == 0, (flags, res)
+                assert true_relres(p, x, b) <= 1.01e-10
