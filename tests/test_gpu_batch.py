@@ -138,3 +138,35 @@ def test_batch_reliable_updates_match_single_solves():
         assert io["status"] == "converged"
         assert abs(res[j]["iters"] - io["iters"]) <= 0.1 * io["iters"] + 5
     assert sum(r["iters"] for r in res) < sum(r["iters"] for r in res2)
+
+
+def test_batch_of_tiny_systems():
+    """A batch holding 1-, 2- and 33-row problems beside a mesh: products within the
+    bound and every problem solved (FP32 refinement, reliable updates, and FP64).
+    Morton ordering needs coordinates for every problem, so none is given here."""
+    from test_gpu_cg import tridiagonal_problem
+    ps = [tridiagonal_problem(1), fegen.cube_laplace(4, 98), tridiagonal_problem(2), tridiagonal_problem(33)]
+    B = fs.batch_create([(p.rowptr, p.colind, p.values, None, 1) for p in ps], sigma=256,
+                        precisions=fs.FESPMV_PREC_F32)
+    xs = [fegen.random_vector(p.n_rows, 110 + j) for j, p in enumerate(ps)]
+    xd = torch.from_numpy(np.concatenate(xs)).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    fs.batch_spmv(B, xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    bs = []
+    for j, p in enumerate(ps):
+        yo = oracle.csr_spmv(p.rowptr, p.colind, p.values, xs[j])
+        bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(xs[j]))
+        assert np.all(np.abs(y[B.offsets[j]:B.offsets[j + 1]] - yo) <= 1e-12 * bound)
+        bs.append(yo)
+    b = np.concatenate(bs)
+    for prec, flags in ((fs.FESPMV_CG_F32_REFINE, 0), (fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE),
+                        (fs.FESPMV_CG_F64, 0)):
+        x = np.zeros_like(b)
+        rc, res = fs.batch_cg_solve(B, b, x, tol=1e-10, precision=prec, flags=flags)
+        assert rc == 0, (prec, flags, res)
+        for j, p in enumerate(ps):
+            xj = x[B.offsets[j]:B.offsets[j + 1]]
+            r = bs[j] - oracle.csr_spmv(p.rowptr, p.colind, p.values, xj)
+            assert res[j]["status"] == 0 and np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bs[j]), (prec, flags, j)

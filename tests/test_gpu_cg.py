@@ -243,12 +243,12 @@ def test_small_handles_cluster_and_graph_paths(name, flags):
     assert r6["status"] == fs.FESPMV_ERR_NOT_CONVERGED and r6["iters"] <= 7
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 33])
-def test_tiny_systems_through_every_path(n):
-    """1, 2, 31 and 33 rows (one row, a few, one short of a warp's 32-row slice and
-    one past it) through every product format and the FP64, single-reduction and
-    reliable-update solves: products within the componentwise bound, solves at the
-    oracle's bar.  The matrix is SPD tridiagonal, diagonal 4 + i/n, off-diagonal -1."""
+class TinyProblem:
+    """A problem record (the fields the tests read) for matrices that are not meshes."""
+
+
+def tridiagonal_problem(n):
+    """SPD tridiagonal n x n: diagonal 4 + i/n, off-diagonal -1 (eigenvalues in [2, 7])."""
     cols, vals, ends = [], [], []
     for i in range(n):
         for j in (i - 1, i, i + 1):
@@ -256,14 +256,21 @@ def test_tiny_systems_through_every_path(n):
                 cols.append(j)
                 vals.append(4.0 + i / n if j == i else -1.0)
         ends.append(len(cols))
-
-    class Q:  # minimal problem record
-        pass
-    p = Q()
+    p = TinyProblem()
     p.rowptr = np.array([0] + ends, dtype=np.int64)
     p.colind = np.array(cols, dtype=np.int32)
     p.values = np.array(vals)
     p.n_rows, p.node_xyz, p.dofs_per_node = n, None, 1
+    return p
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33])
+def test_tiny_systems_through_every_path(n):
+    """1, 2, 31 and 33 rows (one row, a few, one short of a warp's 32-row slice and
+    one past it) through every product format and the FP64, single-reduction and
+    reliable-update solves: products within the componentwise bound, solves at the
+    oracle's bar.  The matrix is SPD tridiagonal, diagonal 4 + i/n, off-diagonal -1."""
+    p = tridiagonal_problem(n)
     u = fegen.random_vector(n, 60 + n)
     b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
     xo, info = oracle.pcg(p.rowptr, p.colind, p.values, b, tol=1e-10)

@@ -321,3 +321,22 @@ def test_multi_cg_on_node_blocks(reliable):
         jj = int(np.where(order == j)[0][0])
         assert np.array_equal(X[:, j].view(np.uint64), X2[:, jj].view(np.uint64)), j
         assert res[j]["iters"] == r2[jj]["iters"]
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (1, 32), (2, 3), (33, 32)])
+def test_tiny_systems_many_right_hand_sides(n, k):
+    """1, 2 and 33 rows with 1, 3 or 32 columns: every column at the oracle's bar in
+    FP64 and with FP32 reliable updates (the products of one handle on all columns)."""
+    from test_gpu_cg import tridiagonal_problem
+    p = tridiagonal_problem(n)
+    A = make(p)
+    B = np.stack([fegen.random_vector(n, 70 + j) for j in range(k)], axis=1)
+    for kw in (dict(tol=1e-10), dict(tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=fs.FESPMV_CG_RELIABLE)):
+        rc, X, res = solve(A, B, **kw)
+        assert rc == 0, (kw, res)
+        for j in range(k):
+            assert res[j]["status"] == 0, (kw, j, res[j])
+            assert true_relres(p, X[:, j], B[:, j]) <= 1.01e-10
+            if "precision" not in kw:
+                _, info = oracle.pcg(p.rowptr, p.colind, p.values, B[:, j], tol=1e-10)
+                assert abs(res[j]["iters"] - info["iters"]) <= 0.02 * info["iters"] + 2
