@@ -197,3 +197,28 @@ def test_multi_float_pairs_out_of_range_and_nan():
         ok = ~np.isnan(yo)
         bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(vals), np.abs(X[:, j]))
         assert np.all(np.abs(Y[ok, j] - yo[ok]) <= 1e-12 * bound[ok])
+
+
+@pytest.mark.parametrize("n", [1, 33])
+def test_multi_tiny_systems(n):
+    """1 row and 33 rows (one past a 32-row slice) with 1, 5 and 32 columns: FP64
+    within the FP64 bound, FP32 within the float bound of the oracle's product."""
+    from test_gpu_cg import tridiagonal_problem
+    p = tridiagonal_problem(n)
+    A = handle(p, sigma=256)
+    for k in (1, 5, 32):
+        X = np.stack([fegen.random_vector(n, 120 + j) for j in range(k)], axis=1)
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        Yd = torch.full_like(Xd, float("nan"))
+        fs.spmv_apply_multi(A, Xd, Yd, fs.FESPMV_PREC_F64)
+        X32 = np.ascontiguousarray(X.astype(np.float32))
+        X32d = torch.from_numpy(X32).cuda()
+        Y32d = torch.full_like(X32d, float("nan"))
+        fs.spmv_apply_multi(A, X32d, Y32d, fs.FESPMV_PREC_F32)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()
+        for j in range(k):
+            yo = oracle.csr_spmv(p.rowptr, p.colind, p.values, X[:, j])
+            bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(p.values), np.abs(X[:, j]))
+            assert np.all(np.abs(Y[:, j] - yo) <= 1e-12 * bound), (k, j)
+        check_f32(p, X32, Y32d.cpu().numpy())

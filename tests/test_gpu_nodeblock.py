@@ -171,3 +171,34 @@ def test_multi_rhs_product_on_node_blocks(k):
         yo = oracle.csr_spmv_f32(p.rowptr, p.colind, bv, x)
         bound = oracle.csr_spmv(p.rowptr, p.colind, np.abs(bv).astype(np.float64), np.abs(x).astype(np.float64))
         assert np.all(np.abs(Y[:, j].astype(np.float64) - yo) <= 2 * L * 2.0 ** -24 * bound), j
+
+
+@pytest.mark.parametrize("tiles", [0, -1])
+def test_smallest_mesh_on_node_blocks(tiles):
+    """2^3 nodes: one slice holding 8 node rows of its 32, half of them the clamped
+    face's identity blocks.  The layout is bit-exact.  Both storages' products are
+    checked in both numberings.  The refined CG on the blocks reaches the tolerance,
+    through the cluster path and through the graphs."""
+    p = fegen.cube_elasticity(2, 97)
+    A = make(p, 96, precisions=BOTH, tiles=tiles)
+    P = layout.node_row_permutation(p.rowptr, p.node_xyz, "morton", 96)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_PERM), P)
+    rp2, c2, _, _ = layout.permute_csr(p.rowptr, p.colind, p.values, P)
+    meta, col, _ = layout.node_blocks(rp2, c2)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_NB_META), meta)
+    assert np.array_equal(fs.spmv_export(A, fs.FESPMV_EXPORT_NB_COLS), col)
+    x = fegen.random_vector(p.n_rows, 98).astype(np.float32)
+    for storage in ("f32", "bf16"):
+        for permuted in (False, True):
+            check_product(p, A, storage, x, permuted)
+    u = fegen.manufactured_solution(p)
+    b = oracle.csr_spmv(p.rowptr, p.colind, p.values, u)
+    assert np.linalg.norm(b) > 0
+    bd = torch.from_numpy(b).cuda()
+    for flags in (fs.FESPMV_CG_RELIABLE, fs.FESPMV_CG_RELIABLE | fs.FESPMV_CG_NO_CLUSTER, 0):
+        xd = torch.zeros_like(bd)
+        res = fs.cg_solve(A, bd, xd, tol=1e-10, precision=fs.FESPMV_CG_F32_REFINE, flags=flags)
+        torch.cuda.synchronize()
+        assert res["status"] == 0, (flags, res, fs.last_error())
+        r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, xd.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
