@@ -207,3 +207,25 @@ def test_assembly_partial_node_masks_and_uncontributed_entries(fmt):
     fs.assembly_matrix(P, torch.from_numpy(p.elem_mats).cuda())
     torch.cuda.synchronize()
     same_handles(R, Z, (fs.FESPMV_EXPORT_VALUES, fs.FESPMV_EXPORT_DIAG, fs.FESPMV_EXPORT_VALUES_F32))
+
+
+@pytest.mark.parametrize("fmt", list(FORMATS))
+def test_assembly_on_the_smallest_mesh(fmt):
+    """2^3 nodes, 6 tets, half the nodes clamped: the assembled handle equals a handle
+    of the generator's CSR bit for bit, products included."""
+    p = fegen.cube_elasticity(2, 506, elements=True)
+    assert np.array_equal(oracle.assemble_matrix(p.rowptr, p.colind, p.elem_nodes, p.elem_mats,
+                                                 p.dofs_per_node, dirichlet_of(p)), p.values)
+    R = handle(p, p.values, fmt)
+    Z = handle(p, 2.0 * p.values, fmt)
+    P = fs.assembly_create(Z, p.rowptr, p.colind, p.elem_nodes, p.dofs_per_node, dirichlet_of(p))
+    assert fs.assembly_get_info(P)["contributions"] > 0
+    fs.assembly_matrix(P, torch.from_numpy(p.elem_mats).cuda())
+    torch.cuda.synchronize()
+    same_handles(R, Z)
+    x = torch.from_numpy(fegen.random_vector(p.n_rows, 507)).cuda()
+    yr, yz = torch.empty_like(x), torch.empty_like(x)
+    fs.spmv_apply(R, x, yr)
+    fs.spmv_apply(Z, x, yz)
+    torch.cuda.synchronize()
+    assert torch.equal(yr, yz)

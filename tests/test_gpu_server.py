@@ -265,3 +265,39 @@ def test_grouped_cancel_and_errors_are_per_request():
     t = fs.srv_submit(S, ia, fegen.random_vector(p.n_rows, 6200))
     assert fs.srv_poll(S, t, p.n_rows)[0] == 0
     fs.srv_destroy(S)
+
+
+@pytest.mark.parametrize("width", [0, -1])
+def test_tiny_problems_in_the_mix(width):
+    """Matrices of 1, 2 and 33 rows and the smallest elasticity mesh served together
+    (without and with lockstep groups): every result meets its tolerance on the true
+    residual and equals the solve alone bit for bit (cg_solve, or cg_solve_multi of
+    the right-hand side alone at the group's width when it was grouped)."""
+    from test_gpu_cg import tridiagonal_problem
+    ps = [tridiagonal_problem(1), tridiagonal_problem(2), tridiagonal_problem(33), fegen.cube_elasticity(2, 88)]
+    mats = [fs.spmv_create(p.rowptr, p.colind, p.values, p.node_xyz, p.dofs_per_node, sigma=256,
+                           precisions=fs.FESPMV_PREC_F32) for p in ps]
+    S = fs.srv_create(1 << 28, 4)
+    if width:
+        fs.srv_set_grouping(S, width)
+    ids = [fs.srv_register(S, A) for A in mats]
+    reqs = []
+    for k in range(12):
+        m = k % len(ps)
+        prec, fl = [(fs.FESPMV_CG_F64, 0), (fs.FESPMV_CG_F32_REFINE, fs.FESPMV_CG_RELIABLE)][(k // 4) % 2]
+        reqs.append((m, fegen.random_vector(ps[m].n_rows, 1100 + k), [1e-8, 1e-10][k % 2], prec, fl))
+    tickets = [fs.srv_submit(S, ids[m], b, tol=tol, precision=prec, flags=fl) for (m, b, tol, prec, fl) in reqs]
+    results = [fs.srv_poll(S, t, ps[m].n_rows) for t, (m, *_rest) in zip(tickets, reqs)]
+    assert fs.srv_get_stats(S)["completed"] == 12
+    for (m, b, tol, prec, fl), (rc, x, res, tm) in zip(reqs, results):
+        assert rc == 0, res
+        p = ps[m]
+        r = b - oracle.csr_spmv(p.rowptr, p.colind, p.values, x)
+        assert np.linalg.norm(r) <= tol * 1.01 * np.linalg.norm(b)
+        xa, ra = alone(mats[m], b, tol=tol, precision=prec, flags=fl)
+        if width:                                 # these matrices are small: groups of 32
+            xm, rm = multi_alone(mats[m], b, 32, tol=tol, precision=prec, flags=fl)
+            assert same(x, res, xm, rm) or same(x, res, xa, ra), (m, res)
+        else:
+            assert same(x, res, xa, ra), (m, res, ra)
+    fs.srv_destroy(S)
