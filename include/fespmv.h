@@ -34,6 +34,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/* The library is compiled with hidden visibility: the functions declared here are
+ * its only exported symbols. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -792,5 +798,9 @@ const char* fespmv_last_error(void);
 
 #ifdef __cplusplus
 }
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
 #endif
 #endif /* FESPMV_H */

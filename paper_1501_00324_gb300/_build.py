@@ -4,7 +4,9 @@ Every translation unit goes through nvcc for sm_103a only
 (-gencode arch=compute_103a,code=sm_103a), compiled in parallel, then linked
 into one shared library with the static CUDA runtime.  Host code is compiled
 with -ffp-contract=off so that the planner's floating-point decisions round the
-same way on every host.
+same way on every host, and with hidden visibility; the link's version script
+(csrc/fespmv.map) keeps the functions that include/fespmv.h declares as the only
+exported symbols.
 """
 from __future__ import annotations
 
@@ -36,7 +38,7 @@ def sources():
 
 def _inputs():
     return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-            glob.glob(os.path.join(INCLUDE, "*.h")))
+            glob.glob(os.path.join(CSRC, "*.map")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def is_stale() -> bool:
@@ -52,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
-                     "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
+                     "-Xcompiler", "-fPIC,-ffp-contract=off,-fvisibility=hidden", "--expt-relaxed-constexpr"]
     jobs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -74,7 +76,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for (src, _, _), log in zip(jobs, logs):
             print(f"== {os.path.basename(src)}\n{log}")
     tmp = SO + f".tmp{os.getpid()}"
-    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for (_, o, _) in jobs] + ["-lcudart_static"]
+    link = ([nvcc] + ARCH + ["-shared", "-o", tmp] + [o for (_, o, _) in jobs] + ["-lcudart_static"] +
+            ["-Xlinker", "--version-script=" + os.path.join(CSRC, "fespmv.map")])
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libfespmv.so failed:\n{r.stderr}")

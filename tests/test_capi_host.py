@@ -5,6 +5,8 @@ import ctypes
 import glob
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -34,6 +36,18 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(fs.LIB_PATH)
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_library_exports_only_the_declared_symbols():
+    """Hidden visibility and the link's version script leave the header's C functions
+    as the library's whole dynamic interface: no internal or template symbol leaks."""
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm is not installed")
+    out = subprocess.run([nm, "-D", "--defined-only", fs.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert exported == set(declared_functions())
 
 
 def test_status_strings():
